@@ -1,0 +1,370 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints (tests/golden/paper_values.json), closed forms (critical point,
+Poiseuille flow, steady conduction), conservation laws, symmetry and the
+continuum limit of the interaction force.  None needs a GPU.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle
+from paper_2009_05264_gb300 import inputs as I
+from paper_2009_05264_gb300 import params as PP
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+
+
+def prm(nx=64, **kw):
+    return PP.resolve(PP.default_params(**kw), nx)
+
+
+def test_paper_constants_are_the_defaults():
+    p = PP.default_params()
+    for key in ("beta", "c0", "a", "b"):
+        assert p[key] == pytest.approx(GOLD[key]["value"], rel=1e-15)
+    assert p["omega"] == GOLD["omega_R134a"]["value"]
+    assert p["T0_R"] == GOLD["T0_R"]["value"]
+    # Eq. 10: g1 = 4 g2 with g1 = 2G, g2 = G/2 -> the wetting strength 18 G reproduces it with w_i
+    assert (2.0 * p["G"]) / (0.5 * p["G"]) == GOLD["g1_over_g2"]["value"]
+
+
+def test_critical_point_of_eq12():
+    """At T = Tc the PR isotherm has (to the rounding of 0.0778 and 0.45724) a
+    horizontal inflection at p_c = 0.0778 R Tc / b; a loop just below, none above."""
+    p = prm()
+    Tc = oracle.Tc(p)
+    rho = np.linspace(0.05, 0.9 / p["b"], 20001)
+
+    def slope(T):
+        pr = np.array([oracle.pressure(p, r, T) for r in rho])
+        return np.gradient(pr, rho), pr
+
+    s, pr = slope(Tc)
+    k = int(np.argmin(s))
+    assert abs(s[k]) < 2e-3 * pr[k] / rho[k]          # dp/drho ~ 0 at the inflection
+    pc = 0.0778 * p["R"] * Tc / p["b"]
+    assert pr[k] == pytest.approx(pc, rel=2e-3)
+    assert pr[k] / (rho[k] * p["R"] * Tc) == pytest.approx(0.3074, abs=3e-3)  # PR critical compressibility
+    assert slope(0.98 * Tc)[0].min() < 0
+    assert slope(1.02 * Tc)[0].min() > 0
+
+
+def test_dpdT_matches_temperature_derivative():
+    p = prm()
+    Tc = oracle.Tc(p)
+    for rho in (0.3, 0.59, 2.0, 5.9, 7.5):
+        for TR in (0.7, 0.9, 1.2):
+            T = TR * Tc
+            h = 1e-6 * T
+            num = (oracle.pressure(p, rho, T + h) - oracle.pressure(p, rho, T - h)) / (2 * h)
+            assert oracle.dpdT(p, rho, T) == pytest.approx(num, rel=1e-7)
+
+
+def test_psi_inverts_to_eos_pressure():
+    """Eq. 11: the pseudopotential pressure c_s^2 rho + c0 g psi^2 / 2 is the EOS pressure."""
+    p = prm()
+    T = 0.9 * oracle.Tc(p)
+    for rho in (0.2, 0.59, 3.0, 5.95, 8.0):
+        psi = oracle.psi(p, rho, T)
+        assert rho / 3 + p["c0"] * p["G"] * psi ** 2 / 2 == pytest.approx(oracle.pressure(p, rho, T), rel=1e-12)
+
+
+@pytest.mark.parametrize("TR", [0.7, 0.8, 0.86, 0.9, 0.95])
+def test_maxwell_equal_area(TR):
+    """Coexistence: equal pressure and zero area of (p - p_sat) over specific volume,
+    checked with an independent adaptive quadrature."""
+    p = prm()
+    T = TR * oracle.Tc(p)
+    rv, rl, ps = oracle.maxwell(p, T)
+    assert oracle.pressure(p, rv, T) == pytest.approx(ps, rel=1e-9)
+    assert oracle.pressure(p, rl, T) == pytest.approx(ps, rel=1e-9)
+    area, _ = integrate.quad(lambda v: oracle.pressure(p, 1.0 / v, T) - ps, 1.0 / rl, 1.0 / rv,
+                             limit=400, epsabs=1e-14)
+    scale = ps * (1.0 / rv - 1.0 / rl)
+    assert abs(area) < 1e-6 * scale
+    assert rv < rl
+
+
+def test_maxwell_densities_match_paper_at_09Tc():
+    p = prm()
+    rv, rl, _ = oracle.maxwell(p, 0.9 * oracle.Tc(p))
+    assert rl == pytest.approx(GOLD["rho_liquid_at_0.9Tc"]["value"], rel=0.02)
+    assert rv == pytest.approx(GOLD["rho_vapour_at_0.9Tc"]["value"], rel=0.02)
+
+
+def test_shan_chen_force_continuum_limit():
+    """Eqs. 8-11: for a smooth density field the discrete force tends to
+    -grad(p_EOS - c_s^2 rho) (the leading order is independent of beta)."""
+    nx, ny = 256, 3
+    p = prm(nx, geometry="periodic", thermal=0, g_a=0.0)
+    T = 0.9 * oracle.Tc(p)
+    x = np.arange(nx)
+    k = 2 * np.pi / nx
+    rho_x = 3.0 * (1.0 + 0.05 * np.sin(k * x))
+    rho = np.tile(rho_x, (ny, 1))
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(rho, np.zeros_like(rho), np.zeros_like(rho), np.full_like(rho, T))
+    F = O.fields()
+    h = 1e-6
+    dp_drho = np.array([(oracle.pressure(p, r + h, T) - oracle.pressure(p, r - h, T)) / (2 * h) for r in rho_x])
+    expect = -(dp_drho - 1.0 / 3.0) * 3.0 * 0.05 * k * np.cos(k * x)
+    err = np.abs(F["Fx"][1] - expect).max() / np.abs(expect).max()
+    assert err < 5e-3
+    assert np.abs(F["Fy"]).max() < 1e-15
+
+
+def test_wetting_force_neutral_wall():
+    """Eq. 15 with G_wet = 18 G and psi_w = psi(rho_w): with beta = 1 a wall whose
+    false density equals the fluid's exerts exactly the force a fluid row would,
+    so a uniform fluid feels no net force at the wall rows."""
+    nx, ny = 8, 6
+    rho0 = 2.5
+    p = prm(nx, geometry="walls", thermal=0, g_a=0.0, beta=1.0, rho_w=rho0)
+    T = p["T0_R"] * oracle.Tc(p)
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(*I.uniform(nx, ny, rho0, T))
+    F = O.fields()
+    assert np.abs(F["Fx"]).max() < 1e-14 and np.abs(F["Fy"]).max() < 1e-14
+    # a denser false wall attracts the fluid (G < 0): force toward the bottom wall at row 0
+    p2 = prm(nx, geometry="walls", thermal=0, g_a=0.0, beta=1.0, rho_w=4.0)
+    O.set_params(p2)
+    F2 = O.fields()
+    assert (F2["Fy"][0] < 0).all() and (F2["Fy"][-1] > 0).all()
+
+
+def test_uniform_rest_state_is_steady():
+    nx, ny = 12, 10
+    p = prm(nx, geometry="periodic", thermal=1)
+    T = p["T0_R"] * oracle.Tc(p)
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(*I.uniform(nx, ny, 5.9, T))
+    f0, g0 = O.populations()
+    assert O.step(50) == 0
+    f1, g1 = O.populations()
+    assert np.abs(f1 - f0).max() < 1e-14 and np.abs(g1 - g0).max() < 1e-15
+
+
+def _total_momentum(f):
+    return (f * CX[:, None, None]).sum(), (f * CY[:, None, None]).sum()
+
+
+def test_mass_and_momentum_conservation_periodic():
+    """Streaming and BGK conserve mass; the exact-difference term adds F to the
+    momentum and the total Shan-Chen, buoyancy (with the lagged mean) force of a
+    periodic domain sums to zero, so total momentum is conserved too."""
+    nx, ny = 48, 40
+    p = prm(nx, geometry="periodic", thermal=0, g_a=1e-4)
+    T = 0.9 * oracle.Tc(p)
+    rv, rl, _ = oracle.maxwell(p, T)
+    O = oracle.Oracle(nx, ny, p)
+    rho, ux, uy, TT = I.disk(nx, ny, 12, rl, rv, T, seed=3, amp=1e-3)
+    ux = 0.01 * I.unit_noise(nx, ny, 5)
+    O.init_fields(rho, ux, uy, TT)
+    f0, _ = O.populations()
+    m0 = f0.sum()
+    px0, py0 = _total_momentum(f0)
+    assert O.step(400) == 0
+    f1, _ = O.populations()
+    assert abs(f1.sum() - m0) / m0 < 1e-13
+    px1, py1 = _total_momentum(f1)
+    assert abs(px1 - px0) < 1e-11 * m0 and abs(py1 - py0) < 1e-11 * m0
+    d = O.last_diag()
+    assert d["mass"] == pytest.approx(m0, rel=1e-13)
+
+
+def test_energy_budget_equals_source():
+    """Eq. 16 conserves sum g except for the source: in a periodic domain
+    sum T^{n+1} - sum T^n = sum phi^n (second Eq. 19)."""
+    nx, ny = 32, 24
+    p = prm(nx, geometry="periodic", thermal=1, g_a=0.0)
+    T = 0.9 * oracle.Tc(p)
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(*I.smooth_random(nx, ny, 5.5, T, seed=7, drho=0.02, du=0.02, dT=0.01))
+    assert O.step(1) == 0
+    for _ in range(20):
+        e0 = O.last_diag()
+        assert O.step(1) == 0
+        e1 = O.last_diag()
+        assert abs(e1["energy"] - e0["energy"] - e0["source"]) < 1e-13 * e0["energy"]
+    assert abs(e0["source"]) > 1e-9  # the budget test is not vacuous
+
+
+def test_poiseuille_profile():
+    """Sec. 2.D, Fig. 4(a): single-phase duct flow at Re_in = 0.96 is parabolic with
+    peak 1.5 times the mean at x = 8H; halfway bounce-back puts the walls at y = -1/2, H - 1/2."""
+    H, nx = 10, 100
+    tau = 1.0
+    Re = GOLD["poiseuille_Re_in"]["value"]
+    u_in = Re * ((tau - 0.5) / 3.0) / H
+    p = prm(nx, geometry="channel", thermal=0, multiphase=0, g_a=0.0, u_in=u_in, rho_out=1.0, tau_f=tau)
+    O = oracle.Oracle(nx, H, p)
+    O.init_fields(*I.uniform(nx, H, 1.0, 0.0))
+    assert O.step(4000) == 0
+    F = O.fields()
+    u = F["ux"][:, 8 * H]
+    y = np.arange(H) + 0.5                      # node centres; walls at y = 0 and y = H
+    shape = y * (H - y)                         # parabola vanishing at both halfway walls
+    # the continuum peak-to-mean ratio 1.5, seen through sampling at H node centres
+    sampled_ratio = GOLD["poiseuille_peak_to_mean"]["value"] * (shape.max() / (H * H / 4)) / (shape.mean() / (H * H / 6))
+    assert u.max() / u.mean() == pytest.approx(sampled_ratio, rel=0.005)
+    A = u.sum() / shape.sum()
+    assert np.abs(u - A * shape).max() < 0.01 * u.max()
+    # steady mass flux through the section equals the inflow
+    flux_in = (F["rho"][:, 0] * F["ux"][:, 0]).sum()
+    assert (F["rho"][:, 8 * H] * u).sum() == pytest.approx(flux_in, rel=1e-3)
+    # developed-flow pressure gradient of plane Poiseuille flow: dp/dx = -12 mu u_mean / H^2
+    pr = F["rho"][H // 2] / 3.0
+    x0, x1 = 4 * H, 9 * H
+    grad = (pr[x1] - pr[x0]) / (x1 - x0)
+    mu = F["rho"][H // 2, (x0 + x1) // 2] * (tau - 0.5) / 3.0
+    assert grad == pytest.approx(-12 * mu * u.mean() / H ** 2, rel=0.03)
+
+
+def test_open_boundary_moments():
+    """Zou-He (Sec. 2.C): after every step the inlet nodes carry velocity (u_in, 0)
+    and the outlet nodes density rho_out with no transverse momentum, corners included."""
+    nx, ny = 20, 9
+    p = prm(nx, geometry="channel", thermal=1, u_in=0.03, rho_out=5.9)
+    T = p["T0_R"] * oracle.Tc(p)
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(*I.smooth_random(nx, ny, 5.9, T, seed=11, drho=0.01, du=0.01, dT=0.01))
+    for _ in range(3):
+        assert O.step(1) == 0
+        f, _ = O.populations()
+        rho = f.sum(axis=0)
+        jx = (f * CX[:, None, None]).sum(axis=0)
+        jy = (f * CY[:, None, None]).sum(axis=0)
+        np.testing.assert_allclose(jx[:, 0] / rho[:, 0], 0.03, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(jy[:, 0], 0.0, atol=1e-13)
+        np.testing.assert_allclose(rho[:, -1], 5.9, rtol=1e-14)
+        np.testing.assert_allclose(jy[:, -1], 0.0, atol=1e-13)
+
+
+def test_steady_conduction_between_walls():
+    """With u = 0 anti-bounce-back (Sec. 2.C) and g^eq (Eq. 18) reduce to pure
+    diffusion: the steady profile between a heated bottom wall at y = -1/2 and the
+    top wall at y = ny - 1/2 is linear."""
+    nx, ny = 4, 16
+    p = prm(nx, geometry="walls", thermal=1, multiphase=0, g_a=0.0, heater_x0=0, heater_len=nx,
+            heat_on_step=0, dTheat_R=0.1, tau_g=0.8)
+    Tc = oracle.Tc(p)
+    Tin, Th = p["Tin_R"] * Tc, (p["Tin_R"] + p["dTheat_R"]) * Tc
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(*I.uniform(nx, ny, 1.0, Tin))
+    assert O.step(12000) == 0
+    T = O.fields()["T"][:, 0]
+    y = np.arange(ny) + 0.5
+    expect = Th + (Tin - Th) * y / ny
+    assert np.abs(T - expect).max() < 1e-9 * (Th - Tin)
+
+
+def test_heater_switch_on_timing():
+    """The heater superheat enters the boundary condition of step heat_on_step,
+    so the row above it warms first in the state after that step."""
+    nx, ny = 6, 5
+    p = prm(nx, geometry="walls", thermal=1, multiphase=0, g_a=0.0, heater_x0=0, heater_len=nx,
+            heat_on_step=5, dTheat_R=0.1)
+    Tin = p["Tin_R"] * oracle.Tc(p)
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(*I.uniform(nx, ny, 1.0, Tin))
+    O.step(5)
+    assert np.abs(O.fields()["T"] - Tin).max() < 1e-15
+    O.step(1)
+    T = O.fields()["T"]
+    assert (T[0] > Tin + 1e-6).all() and np.abs(T[1:] - Tin).max() < 1e-15
+
+
+def test_flat_interface_coexistence():
+    """Sec. 2.D, Fig. 4(b): flat-interface densities follow the Maxwell
+    construction for T_R >= 0.7 (within a few per cent for this force scheme)."""
+    nx, ny = 4, 96
+    p = prm(nx, geometry="periodic", thermal=0, g_a=0.0)
+    T = 0.9 * oracle.Tc(p)
+    rv, rl, _ = oracle.maxwell(p, T)
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(*I.slab(nx, ny, 24, rl, rv, T))
+    assert O.step(12000) == 0
+    rho = O.fields()["rho"][:, 0]
+    assert rho.max() == pytest.approx(rl, rel=0.04)
+    assert rho.min() == pytest.approx(rv, rel=0.04)
+    assert rho.max() == pytest.approx(GOLD["rho_liquid_at_0.9Tc"]["value"], rel=0.04)
+    assert rho.min() == pytest.approx(GOLD["rho_vapour_at_0.9Tc"]["value"], rel=0.04)
+
+
+@pytest.mark.slow
+def test_laplace_law():
+    """Static droplets: the pressure jump is linear in 1/R with vanishing intercept."""
+    nx = ny = 64
+    p = prm(nx, geometry="periodic", thermal=0, g_a=0.0)
+    T = 0.9 * oracle.Tc(p)
+    rv, rl, _ = oracle.maxwell(p, T)
+    inv_r, dps = [], []
+    for R in (10.0, 13.0, 16.0, 20.0):
+        O = oracle.Oracle(nx, ny, p)
+        O.init_fields(*I.disk(nx, ny, R, rl, rv, T))
+        assert O.step(3000) == 0
+        rho = O.fields()["rho"]
+        p_in = oracle.pressure(p, rho[ny // 2, nx // 2], T)
+        p_out = oracle.pressure(p, rho[0, 0], T)
+        # effective radius from the liquid area
+        area = ((rho - rho.min()) / (rho.max() - rho.min())).sum()
+        inv_r.append(1.0 / math.sqrt(area / math.pi))
+        dps.append(p_in - p_out)
+    slope, icpt = np.polyfit(inv_r, dps, 1)
+    fit = np.polyval([slope, icpt], inv_r)
+    assert slope > 0
+    assert np.abs(fit - dps).max() < 0.03 * max(dps)
+    assert abs(icpt) < 0.1 * max(dps)
+
+
+@pytest.mark.slow
+def test_bubble_rises_under_buoyancy():
+    """Eq. 14: with gravity along -y the lighter vapour bubble moves up
+    (a bubble well above the critical size of a closed box, so it neither condenses nor drifts)."""
+    nx, ny = 48, 80
+    p = prm(nx, geometry="periodic", thermal=0, g_a=2e-4)
+    T = 0.9 * oracle.Tc(p)
+    rv, rl, _ = oracle.maxwell(p, T)
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(*I.disk(nx, ny, 14, rv, rl, T))
+
+    def centroid():
+        rho = O.fields()["rho"]
+        vap = rho < 0.5 * (rl + rv)
+        return (np.arange(ny)[:, None] * np.ones((1, nx)))[vap].mean(), vap.sum()
+
+    assert O.step(400) == 0
+    y0, n0 = centroid()
+    assert O.step(1200) == 0
+    y1, n1 = centroid()
+    assert n1 > 0.8 * n0
+    assert y1 > y0 + 1.5
+
+
+@pytest.mark.slow
+def test_contact_angle_decreases_with_wall_density():
+    """Sec. 3.E, Fig. 15: a false wall density nearer the liquid value wets more
+    (smaller contact angle); nearer the vapour value wets less."""
+    nx, ny = 72, 36
+    thetas = []
+    for rho_w in (1.5, 3.0, 4.5):
+        p = prm(nx, geometry="walls", thermal=0, g_a=0.0, rho_w=rho_w)
+        T = 0.9 * oracle.Tc(p)
+        rv, rl, _ = oracle.maxwell(p, T)
+        O = oracle.Oracle(nx, ny, p)
+        O.init_fields(*I.sessile(nx, ny, 14, rl, rv, T))
+        assert O.step(3000) == 0
+        liquid = O.fields()["rho"] > 0.5 * (rl + rv)
+        base = liquid[0].sum()
+        height = liquid.any(axis=1).sum()
+        thetas.append(PP.contact_angle_from_cap(height, base))
+    assert thetas[0] > thetas[1] > thetas[2]
