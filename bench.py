@@ -1,0 +1,309 @@
+"""Benchmark of the fused pseudopotential thermal LB step (MLUPS, fraction of HBM roofline).
+
+Default workload: one flow-boiling channel of 8000 x 800 nodes (6.4 M), FP32
+populations stored as deviations from the rest weights, thermal field on, the
+microheater switched on, all Sec. 2.C boundary conditions.  One "step" is one
+fused kernel launch updating every node's f and g.  Inputs are synthetic
+(seeded smooth perturbation of saturated liquid at T_R = 0.9).
+
+Under torchrun each rank advances its own independent channel (replicas; no
+data-path collective), so `value` is the total node updates of all ranks per
+second ("weak" scaling).
+
+--impl reference times the FP64 CPU oracle (the plain restatement of the
+paper used by the tests) on the host cores, on a bounded sample of the same
+channel: a 1000 x 800 band of it per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NX, NY = 8000, 800  # the 6.4 M-node roofline channel; --nx/--ny shrink it for profiling captures
+SEED = 2009052642
+WORKLOAD = "single flow-boiling channel 8000x800 D2Q9 + thermal g, FP32 SoA populations"
+
+
+def workload_params(precision: str):
+    from paper_2009_05264_gb300 import params as PP
+
+    return PP.resolve(PP.default_params(geometry="channel", u_in=0.03, dTheat_R=0.08, heater_x0=NX // 5,
+                                        heater_len=40, heat_on_step=0, rho_out=5.95), NX)
+
+
+def bytes_per_node(precision: str, thermal: bool = True) -> int:
+    """Algorithmic HBM bytes per node update: every stored population read once and written once."""
+    elt = 8 if precision == "fp64" else 4
+    return (18 if thermal else 9) * 2 * elt
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if key in d:
+                    v = d[key]
+                    return float(v if not isinstance(v, dict) else v.get("value")), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(steps: int = 2, nx: int = 1000):
+    """The oracle as it stands on one host core: `steps` steps of a nx x 800 band of the channel."""
+    import oracle
+    from paper_2009_05264_gb300 import inputs as I
+
+    p = workload_params("fp64")
+    Tc = oracle.Tc(p)
+    fields = I.smooth_random(nx, NY, 5.95, 0.9 * Tc, seed=SEED, drho=0.002, du=0.005, dT=0.002)
+    orc = oracle.Oracle(nx, NY, p)
+    orc.init_fields(*fields)
+    t0 = time.perf_counter()
+    st = orc.step(steps)
+    dt = time.perf_counter() - t0
+    if st != 0:
+        raise RuntimeError("oracle unstable on the baseline sample")
+    return {"value": nx * NY * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} steps of a {nx}x{NY} band of the channel (same physics), FP64, single thread",
+            "seconds": dt}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle  # noqa: F401
+
+    for _ in range(args.warmup):
+        cpu_baseline(steps=1, nx=200)
+    t0 = time.perf_counter()
+    per = []
+    for _ in range(args.steps):
+        r = cpu_baseline(steps=1, nx=1000)
+        per.append(r["seconds"])
+    total = time.perf_counter() - t0
+    value = 1000 * NY * args.steps / sum(per) / 1e6
+    line = {"impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": NX, "ny": NY,
+                       "sample": f"each step: one oracle step on a 1000x{NY} band"},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"one step of a 1000x{NY} band per timed step"},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2009_05264_gb300 import inputs as I
+    from paper_2009_05264_gb300 import lbm
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = args.precision
+    p = workload_params(prec)
+    Tc = lbm.critical_temperature(p)
+    fields = I.smooth_random(NX, NY, 5.95, 0.9 * Tc, seed=SEED, drho=0.002, du=0.005, dT=0.002, instance=rank)
+
+    lat = lbm.Lattice(NX, NY, prec, device=local)
+    lat.set_params(p)
+    if args.tiling:
+        c, r = (int(x) for x in args.tiling.split("x"))
+        lat.set_tiling(c, r)
+    lat.init_fields(*fields)
+    stream = lat.stream
+    nodes = NX * NY
+
+    # warm-up
+    lat.step(args.warmup)
+
+    # ---- device-timed region: inputs resident in HBM (state 2 x 0.92 GB > L2) ----
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    sampler = ClockSampler(local) if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    launches0 = lat.launches
+    events[0].record(stream)
+    for k in range(args.steps):
+        lat.step_async(1)
+        events[k + 1].record(stream)
+    torch.cuda.synchronize()
+    lat.sync()
+    gpu_launches = lat.launches - launches0
+    total_ms = events[0].elapsed_time(events[-1])
+    per_launch = [events[k].elapsed_time(events[k + 1]) for k in range(args.steps)]
+    clocks = sampler.stop() if sampler else None
+    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = nodes * args.steps * world / (total_ms * 1e-3) / 1e6
+
+    # ---- end to end through the public API with host buffers ----
+    pinned = [torch.empty((NY, NX), dtype=torch.float64).pin_memory() for _ in range(4)]
+    for a, src in zip(pinned, fields):
+        a.numpy()[...] = src
+    outs = [torch.empty((NY, NX), dtype=torch.float64).pin_memory() for _ in range(4)]
+    e2e_steps = args.steps
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat.init_fields(*[a.numpy() for a in pinned])
+    lat.step(e2e_steps)
+    got = lat.fields()
+    for o, k in zip(outs, ("rho", "ux", "uy", "T")):
+        o.numpy()[...] = got[k]
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = nodes * e2e_steps * world / float(te.item()) / 1e6
+    if not np.isfinite(got["rho"]).all():
+        raise RuntimeError("non-finite density after the e2e run")
+
+    if rank == 0:
+        peak, peak_kind = read_peaks()
+        bpn = bytes_per_node(prec)
+        avg_launch_ms = statistics.mean(per_launch)
+        achieved = bpn * nodes / (avg_launch_ms * 1e-3) / 1e9
+        line = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD if prec == "fp32" else WORKLOAD.replace("FP32", "FP64"),
+                       "nx": NX, "ny": NY, "nodes_per_gpu": nodes, "precision": prec,
+                       "tiling": args.tiling or "default (128 columns, rows by heuristic)",
+                       "l2": "inputs larger than L2: 2 x 0.92 GB population buffers vs 129 MB L2",
+                       "parallelism": f"{world} independent channel replicas"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_source": f"{peak_kind} HBM copy bandwidth",
+                         "algorithmic_bytes_per_node": bpn, "kernel": "lbm_fused_kernel (MODE_STEP)"},
+            "e2e": {"value": e2e_value, "unit": "MLUPS",
+                    "h2d_bytes_per_step": 4 * nodes * 8 / e2e_steps, "d2h_bytes_per_step": 4 * nodes * 8 / e2e_steps,
+                    "note": f"init_fields from pinned host arrays + {e2e_steps} steps + read_fields to host"},
+            "gpu_launches": gpu_launches,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--tiling", default=None, help="COLSxROWS, e.g. 128x32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nx", type=int, default=None, help="profiling only: smaller channel length")
+    ap.add_argument("--ny", type=int, default=None, help="profiling only: smaller channel height")
+    args = ap.parse_args()
+    global NX, NY
+    if args.nx:
+        NX = args.nx
+    if args.ny:
+        NY = args.ny
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

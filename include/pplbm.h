@@ -1,0 +1,205 @@
+/*
+ * pplbm -- GB300 (sm_103a) pseudopotential thermal lattice Boltzmann step for
+ * flow boiling in a narrow channel, after Mukherjee, Basu & Mondal, "Mesoscopic
+ * Characterization of Bubble Dynamics in Flow Boiling following A
+ * Pseudopotential-based Approach" (arXiv 2009.05264).
+ *
+ * C ABI.  Plain pointers and sizes only; no exceptions cross it.  Every call
+ * returns an lbm_status; lbm_last_error() gives the text of the last failure
+ * of a context.  All quantities are lattice units (dx = dt = 1, c_s^2 = 1/3).
+ *
+ * Lattice (Sec. 2.A, Fig. 1): D2Q9 with velocities
+ *   0 (0,0) 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1) 5 (1,1) 6 (-1,1) 7 (-1,-1) 8 (1,-1)
+ * and weights 4/9, 1/9 (i = 1..4), 1/36 (i = 5..8).
+ * Grid: fluid nodes x = 0..nx-1 (inlet x = 0, outlet x = nx-1), y = 0..ny-1.
+ * Walls lie halfway between rows: solid rows y = -1 (bottom, carries the
+ * microheater) and y = ny (top).
+ *
+ * Host arrays crossing this interface are row-major, index y*nx + x; population
+ * arrays are 9 such planes, index (i*ny + y)*nx + x.  They are owned by the
+ * caller and only read or written during the call.
+ *
+ * Threading: a context is used by one host thread at a time.  Work is ordered
+ * on the context's CUDA stream.
+ */
+#ifndef PPLBM_H
+#define PPLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ABI_VERSION 1
+
+typedef struct lbm_ctx lbm_ctx;
+typedef struct lbm_batch lbm_batch;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,    /* bad argument: NULL pointer, size mismatch, parameter out of range */
+  LBM_ENOMEM = 2,    /* device or host allocation failed, or caller buffer too small */
+  LBM_EUNSTABLE = 3, /* the lattice left the EOS domain: rho <= 0, rho >= 1/b, NaN, or a
+                        negative psi radicand (Eq. 11).  State is kept for inspection. */
+  LBM_ETIMEOUT = 4,  /* a bounded device wait gave up */
+  LBM_ECUDA = 5,     /* a CUDA runtime call failed (text in lbm_last_error) */
+  LBM_EBUDGET = 6,   /* admission refused: device memory budget exceeded */
+  LBM_ESTATE = 7     /* call out of order (e.g. lbm_step before lbm_set_params) */
+} lbm_status;
+
+typedef enum { LBM_FP32 = 0, LBM_FP64 = 1 } lbm_precision;
+
+enum {
+  LBM_GEOM_PERIODIC = 0, /* periodic in x and y (static droplet / bubble tests) */
+  LBM_GEOM_CHANNEL = 1,  /* Sec. 2.C: velocity inlet x = 0, pressure outlet x = nx-1, walls */
+  LBM_GEOM_WALLS = 2     /* walls at y = -1 and y = ny, periodic in x */
+};
+
+enum { LBM_INIT_UNIFORM = 0, LBM_INIT_DISK = 1 };
+
+/* Diagnostics record of one step, computed in FP64 from that step's moments. */
+enum {
+  LBM_D_STEP = 0,    /* step index n */
+  LBM_D_MASS,        /* sum of rho over fluid nodes (Eq. 4) */
+  LBM_D_ENERGY,      /* sum of T over fluid nodes (Eq. 17) */
+  LBM_D_RHO_AVG,     /* mass / (nx*ny): the rho_avg the buoyancy of step n+1 uses (Eq. 14) */
+  LBM_D_DP,          /* centreline pressure drop p(1, ny/2) - p(nx-2, ny/2) (Sec. 3.B, Fig. 12b) */
+  LBM_D_DTSTAR,      /* (T_wall - T_next_to_heater)/(T_wall - T_bulk) (Sec. 3.B, Fig. 12c); 0 if heater off */
+  LBM_D_FLUX_IN,     /* sum over y of rho * u_act,x at x = 0 */
+  LBM_D_FLUX_OUT,    /* sum over y of rho * u_act,x at x = nx-1 */
+  LBM_D_COUNT
+};
+
+/* Problem parameters (lattice units).  `size` must be sizeof(lbm_params).
+ * lbm_default_params() fills the paper's values; see each field. */
+typedef struct lbm_params {
+  uint32_t size;
+  int32_t geometry;   /* LBM_GEOM_* */
+  int32_t thermal;    /* 1: evolve the temperature distribution g (Eq. 16); 0: T fixed at T0 */
+  int32_t multiphase; /* 1: Shan-Chen (Eq. 9) + wetting (Eq. 15) forces with the PR EOS;
+                         0: single-phase lattice gas p = rho/3 (duct-flow validation, Sec. 2.D) */
+  double tau_f;       /* relaxation time of f (Eq. 2); nu = (tau_f - 1/2)/3.  Default 1 */
+  double tau_g;       /* relaxation time of g (Eq. 16); alpha_T = (tau_g - 1/2)/3.  Default 0.6 (with
+                         tau_g >= 1 thermal runs between walls grow a wall mode and diverge) */
+  double a, b, R;     /* Peng-Robinson constants of Eq. 12: 2/49, 2/21, 1 */
+  double omega;       /* acentric factor (Eq. 12): 0.32 (R134a) */
+  double beta;        /* force mixing weight of Eq. 8: 1.16 */
+  double c0;          /* Eq. 11: 6 */
+  double G;           /* interaction strength g of Eqs. 10-11 (g1 = 2G, g2 = G/2): -1 */
+  double T0_R;        /* initial temperature / Tc (Eq. 13): 0.9 */
+  double Tin_R;       /* inlet and wall temperature / Tc: 0.9 */
+  double dTheat_R;    /* heater superheat / Tc: 0.3 (Sec. 3.A) */
+  double u_in;        /* inlet velocity (x) */
+  double rho_out;     /* outlet density */
+  double rho_w;       /* false wall density of Eq. 15 (sets the contact angle): 5.95 */
+  double G_wet;       /* wetting strength of Eq. 15: 9 (1 + beta) G, so that a wall whose false density
+                         equals the fluid's exerts no net force on uniform fluid under the beta-mixed
+                         Eq. 9 (18 G at beta = 1, where G_wet w_i is the Eq. 10 stencil) */
+  double g_a;         /* gravitational acceleration magnitude, acting along -y (Eq. 14): 5e-5 */
+  double c_v;         /* specific heat at constant volume in the source of Eq. 19: 6 */
+  int32_t heater_x0;  /* first heated bottom-wall site; -1 = nx/5 */
+  int32_t heater_len; /* number of heated sites: 5 */
+  int64_t heat_on_step; /* first step whose boundary condition heats: 10000 */
+  int32_t init_kind;  /* LBM_INIT_UNIFORM: rho = init_rho_out everywhere;
+                         LBM_INIT_DISK: init_rho_in inside a centred disk of init_radius,
+                         tanh interface of init_width, times (1 + perturb_amp * xi) with
+                         xi = splitmix64 hash of (seed, node) in [-1, 1).  u = 0, T = T0. */
+  int32_t reserved0;
+  double init_rho_in, init_rho_out, init_radius, init_width, perturb_amp;
+  uint64_t seed;
+} lbm_params;
+
+/* Fill *p with the defaults listed above (and p->size). */
+void lbm_default_params(lbm_params* p);
+
+/* Device bytes a context of this size needs (state double buffers, reductions). */
+size_t lbm_required_bytes(int32_t nx, int32_t ny, lbm_precision prec);
+
+/* Create a context for an nx x ny lattice on CUDA device `device`.
+ * prec: LBM_FP64 stores and computes populations in FP64; LBM_FP32 stores them in
+ * FP32 as deviations from the rest-state weights (w_i rho_out, w_i T0) and
+ * computes in FP32, with FP64 global reductions.
+ * cuda_stream: a cudaStream_t to order all work on, or NULL for a stream the
+ * context creates and owns.  The context allocates its device memory.
+ * Errors: LBM_EINVAL (nx, ny < 1 or too large), LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_create(lbm_ctx** out, int32_t nx, int32_t ny, lbm_precision prec, int32_t device,
+                      void* cuda_stream);
+
+/* As lbm_create, but the state lives in caller-owned device memory dev_buf of
+ * dev_bytes >= lbm_required_bytes(); it must outlive the context.  dev_buf
+ * must be 256-byte aligned.  Errors as lbm_create, LBM_ENOMEM if dev_bytes is short. */
+lbm_status lbm_create_ex(lbm_ctx** out, int32_t nx, int32_t ny, lbm_precision prec, int32_t device,
+                         void* cuda_stream, void* dev_buf, size_t dev_bytes);
+
+/* Validate and store parameters, then initialise the lattice from p->init_kind
+ * (f = f^eq(rho, 0), Eq. 3; g = g^eq(T0, 0), Eq. 18) at step 0.
+ * Errors: LBM_EINVAL (p NULL, p->size wrong, geometry too small: channel needs
+ * nx >= 3, ny >= 2; walls need ny >= 2; tau <= 1/2; non-positive c_v ...). */
+lbm_status lbm_set_params(lbm_ctx* ctx, const lbm_params* p);
+
+/* Start from host fields (n = nx*ny each, row-major): f = f^eq(rho, u) (Eq. 3),
+ * g = g^eq(T, u) (Eq. 18); T is the absolute lattice temperature (T_R * Tc) and
+ * may be NULL (T0 everywhere).  Sets step 0; the buoyancy mean of the previous
+ * step (Eq. 14) is the row-major FP64 mean of rho.  Requires lbm_set_params. */
+lbm_status lbm_init_fields(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy,
+                           const double* T, size_t n);
+
+/* Advance nsteps time steps (Eqs. 1-19 and the Sec. 2.C boundary conditions),
+ * fused into one kernel per step, then wait and return the stability status.
+ * Errors: LBM_ESTATE (no params), LBM_EUNSTABLE, LBM_ECUDA. */
+lbm_status lbm_step(lbm_ctx* ctx, int64_t nsteps);
+
+/* Enqueue nsteps steps without waiting; lbm_sync() waits and reports status. */
+lbm_status lbm_step_async(lbm_ctx* ctx, int64_t nsteps);
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+/* Macroscopic fields of the current state, FP64, into caller host arrays of n =
+ * nx*ny: rho (Eq. 4), the actual velocity u_act (Eq. 7) and T (Eq. 17).  Any
+ * pointer may be NULL.  Errors: LBM_EINVAL (n != nx*ny), LBM_ESTATE, LBM_ECUDA. */
+lbm_status lbm_read_fields(lbm_ctx* ctx, double* rho, double* ux, double* uy, double* T, size_t n);
+
+/* Post-stream populations f^n, g^n of the current state in FP64 (n = 9*nx*ny
+ * per array; g may be NULL).  In FP32 mode the stored deviations are widened
+ * and the rest-state weights added back. */
+lbm_status lbm_get_populations(lbm_ctx* ctx, double* f, double* g, size_t n);
+
+/* Replace the state by post-stream populations f^n, g^n (n = 9*nx*ny; g NULL
+ * keeps g^eq(T0, 0)), at time step `step`, with the previous step's mean density
+ * rho_avg_prev (Eq. 14); pass NaN to use the mean of the given populations. */
+lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f, const double* g, size_t n, int64_t step,
+                               double rho_avg_prev);
+
+/* Diagnostics record of the most recent step: out[LBM_D_COUNT]. */
+lbm_status lbm_read_diagnostics(lbm_ctx* ctx, double* out, size_t n);
+
+/* Checkpoint / resume: raw state (populations in storage precision, step,
+ * buoyancy mean, parameters).  lbm_state_bytes() gives the buffer size; resume
+ * is bitwise. */
+size_t lbm_state_bytes(const lbm_ctx* ctx);
+lbm_status lbm_save_state(lbm_ctx* ctx, void* host_buf, size_t bytes);
+lbm_status lbm_load_state(lbm_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Tile shape of the fused kernel: columns per CTA (64, 128 or 256) and rows per
+ * CTA (>= 1).  Any shape gives identical results; only speed differs.  0 = default. */
+lbm_status lbm_set_tiling(lbm_ctx* ctx, int32_t cols, int32_t rows);
+
+int64_t lbm_get_step(const lbm_ctx* ctx);
+/* Kernel launches enqueued by this context since creation (all kinds). */
+int64_t lbm_launch_count(const lbm_ctx* ctx);
+/* The CUDA stream the context orders its work on (a cudaStream_t). */
+void* lbm_get_stream(const lbm_ctx* ctx);
+/* Critical temperature of the parameters' Eq. 12: Tc = 0.0778 a / (0.45724 b R). */
+double lbm_critical_temperature(const lbm_params* p);
+
+/* Free the context and its device memory (not caller-provided memory).  NULL-safe. */
+lbm_status lbm_destroy(lbm_ctx* ctx);
+
+const char* lbm_status_string(lbm_status s);
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PPLBM_H */

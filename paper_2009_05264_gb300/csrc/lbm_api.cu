@@ -1,0 +1,736 @@
+// Host side of the pplbm C ABI: contexts, parameter validation, device memory
+// layout, launches and readback.  Every exported function returns a status and
+// never throws.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+#include "pplbm.h"
+
+namespace pplbm {
+cudaError_t launch_lbm_f32(int, int, int, const Inst*, const Tile*, int, cudaStream_t);
+cudaError_t launch_lbm_f64(int, int, int, const Inst*, const Tile*, int, cudaStream_t);
+cudaError_t launch_init_from_fields_f32(const Inst*, int, int, const double*, int, cudaStream_t);
+cudaError_t launch_init_from_fields_f64(const Inst*, int, int, const double*, int, cudaStream_t);
+cudaError_t launch_init_builtin_f32(const Inst*, int, int, InitSpec, cudaStream_t);
+cudaError_t launch_init_builtin_f64(const Inst*, int, int, InitSpec, cudaStream_t);
+
+cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, const Inst* d_inst, const Tile* d_tiles,
+                       int ntiles, cudaStream_t s) {
+  return fp64 ? launch_lbm_f64(thermal, cols, mode, d_inst, d_tiles, ntiles, s)
+              : launch_lbm_f32(thermal, cols, mode, d_inst, d_tiles, ntiles, s);
+}
+cudaError_t launch_init_from_fields(int fp64, const Inst* d_inst, int nx, int ny, const double* d_fields,
+                                    int has_T, cudaStream_t s) {
+  return fp64 ? launch_init_from_fields_f64(d_inst, nx, ny, d_fields, has_T, s)
+              : launch_init_from_fields_f32(d_inst, nx, ny, d_fields, has_T, s);
+}
+cudaError_t launch_init_builtin(int fp64, const Inst* d_inst, int nx, int ny, InitSpec spec, cudaStream_t s) {
+  return fp64 ? launch_init_builtin_f64(d_inst, nx, ny, spec, s) : launch_init_builtin_f32(d_inst, nx, ny, spec, s);
+}
+bool cols_supported(int cols) { return cols == 64 || cols == 128 || cols == 256; }
+}  // namespace pplbm
+
+using namespace pplbm;
+
+namespace {
+
+constexpr int kAuxCols = 128;       // tile width of the field/population readback passes
+constexpr int kAuxRows = 32;
+constexpr int kMinRows = 4;          // smallest band a step tiling may use
+constexpr size_t kAlign = 256;
+constexpr int kMaxDim = 1 << 20;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  int pitch;
+  long long plane;
+  size_t pop_bytes;  // one 9-plane buffer
+  int max_tiles;
+  size_t off_f[2], off_g[2], off_inst, off_state, off_part, off_ring, off_tiles_step, off_tiles_aux, total;
+};
+
+Layout make_layout(int nx, int ny, lbm_precision prec) {
+  Layout L{};
+  const size_t elt = prec == LBM_FP64 ? 8 : 4;
+  L.pitch = (nx + 31) / 32 * 32;
+  L.plane = (long long)L.pitch * ny;
+  L.pop_bytes = align_up(9 * (size_t)L.plane * elt);
+  const long long strips = (nx + 63) / 64;
+  const long long bands = (ny + kMinRows - 1) / kMinRows;
+  L.max_tiles = (int)std::min<long long>(strips * bands, 1ll << 30);
+  size_t off = 0;
+  for (int b = 0; b < 2; ++b) { L.off_f[b] = off; off += L.pop_bytes; }
+  for (int b = 0; b < 2; ++b) { L.off_g[b] = off; off += L.pop_bytes; }
+  L.off_inst = off; off += align_up(sizeof(Inst));
+  L.off_state = off; off += align_up(sizeof(InstState));
+  L.off_part = off; off += align_up((size_t)L.max_tiles * NPART * sizeof(double));
+  L.off_ring = off; off += align_up((size_t)RING * NDIAG * sizeof(double));
+  L.off_tiles_step = off; off += align_up((size_t)L.max_tiles * sizeof(Tile));
+  L.off_tiles_aux = off; off += align_up((size_t)L.max_tiles * sizeof(Tile));
+  L.total = off;
+  return L;
+}
+
+// Peng-Robinson pressure (Eq. 12) in double on the host, for psi(rho_w, T0).
+double host_pressure(const lbm_params& p, double rho, double T) {
+  const double Tc = 0.0778 * p.a / (0.45724 * p.b * p.R);
+  const double kappa = 0.37464 + 1.54226 * p.omega - 0.26992 * p.omega * p.omega;
+  const double s = 1.0 + kappa * (1.0 - std::sqrt(T / Tc));
+  return rho * p.R * T / (1.0 - p.b * rho) - p.a * s * s * rho * rho / (1.0 + 2.0 * p.b * rho - p.b * p.b * rho * rho);
+}
+
+void build_tiles(int nx, int ny, int cols, int rows, std::vector<Tile>& out) {
+  out.clear();
+  const int strips = (nx + cols - 1) / cols;
+  const int bands = (ny + rows - 1) / rows;
+  const int n = strips * bands;
+  int local = 0;
+  for (int b = 0; b < bands; ++b)
+    for (int sidx = 0; sidx < strips; ++sidx) {
+      Tile t{};
+      t.inst = 0;
+      t.x0 = sidx * cols;
+      t.y0 = b * rows;
+      t.y1 = std::min(ny, (b + 1) * rows);
+      t.local = local++;
+      t.ntiles = n;
+      out.push_back(t);
+    }
+}
+
+// Rows per band for a tile width: enough CTAs to fill 152 SMs a few times over
+// while keeping the 4-row band overhead small.
+int default_rows(int nx, int ny, int cols) {
+  const int strips = (nx + cols - 1) / cols;
+  const long long target = 152LL * 8;
+  long long rows = ((long long)ny * strips + target - 1) / target;
+  rows = std::max<long long>(rows, 16);
+  rows = std::min<long long>(rows, 128);
+  rows = std::min<long long>(rows, ny);
+  return (int)std::max<long long>(rows, kMinRows < ny ? kMinRows : ny);
+}
+
+}  // namespace
+
+struct lbm_ctx {
+  int nx = 0, ny = 0;
+  lbm_precision prec = LBM_FP32;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  char* base = nullptr;
+  bool own_mem = false;
+  Layout L{};
+  Inst hinst{};
+  Inst* d_inst = nullptr;
+  InstState* d_state = nullptr;
+  InstState* h_state = nullptr;  // pinned mirror
+  int cols = 128, rows = 16;
+  int ntiles_step = 0, ntiles_aux = 0;
+  Tile* d_tiles_step = nullptr;
+  Tile* d_tiles_aux = nullptr;
+  lbm_params params{};
+  bool have_params = false;
+  int thermal = 0;
+  long long launches = 0;
+  long long step_host = 0;  // step count as last synchronised
+  std::string err;
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx* c, lbm_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, LBM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(ctx, call)                                   \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+size_t elt_size(const lbm_ctx* c) { return c->prec == LBM_FP64 ? 8 : 4; }
+
+lbm_status upload_state(lbm_ctx* c) {
+  LBM_CUDA(c, cudaMemcpyAsync(c->d_state, c->h_state, sizeof(InstState), cudaMemcpyHostToDevice, c->stream));
+  return LBM_OK;
+}
+
+lbm_status fetch_state(lbm_ctx* c) {
+  LBM_CUDA(c, cudaMemcpyAsync(c->h_state, c->d_state, sizeof(InstState), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->step_host = c->h_state->step;
+  return LBM_OK;
+}
+
+lbm_status set_tiling(lbm_ctx* c, int cols, int rows) {
+  std::vector<Tile> t;
+  build_tiles(c->nx, c->ny, cols, rows, t);
+  if ((int)t.size() > c->L.max_tiles) return fail(c, LBM_EINVAL, "tiling needs more tiles than reserved");
+  LBM_CUDA(c, cudaMemcpyAsync(c->d_tiles_step, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->cols = cols;
+  c->rows = rows;
+  c->ntiles_step = (int)t.size();
+  return LBM_OK;
+}
+
+lbm_status launch(lbm_ctx* c, int mode) {
+  const bool step_tiles = mode == MODE_STEP;
+  cudaError_t e = launch_lbm(c->prec == LBM_FP64, c->thermal, step_tiles ? c->cols : kAuxCols, mode, c->d_inst,
+                             step_tiles ? c->d_tiles_step : c->d_tiles_aux,
+                             step_tiles ? c->ntiles_step : c->ntiles_aux, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+  ++c->launches;
+  return LBM_OK;
+}
+
+lbm_status validate_params(const lbm_ctx* c, const lbm_params* p, std::string& why) {
+  if (!p) { why = "params is NULL"; return LBM_EINVAL; }
+  if (p->size != sizeof(lbm_params)) { why = "params.size != sizeof(lbm_params)"; return LBM_EINVAL; }
+  if (p->geometry < 0 || p->geometry > 2) { why = "geometry must be 0, 1 or 2"; return LBM_EINVAL; }
+  if (p->geometry == LBM_GEOM_CHANNEL && (c->nx < 3 || c->ny < 2)) { why = "channel needs nx >= 3 and ny >= 2"; return LBM_EINVAL; }
+  if (p->geometry == LBM_GEOM_WALLS && c->ny < 2) { why = "walls geometry needs ny >= 2"; return LBM_EINVAL; }
+  if (p->thermal != 0 && p->thermal != 1) { why = "thermal must be 0 or 1"; return LBM_EINVAL; }
+  if (p->multiphase != 0 && p->multiphase != 1) { why = "multiphase must be 0 or 1"; return LBM_EINVAL; }
+  if (!(p->tau_f > 0.5) || !(p->tau_g > 0.5)) { why = "tau_f and tau_g must exceed 1/2"; return LBM_EINVAL; }
+  if (!(p->a > 0) || !(p->b > 0) || !(p->R > 0)) { why = "a, b, R must be positive"; return LBM_EINVAL; }
+  if (!(p->T0_R > 0) || !(p->Tin_R > 0) || !(p->Tin_R + p->dTheat_R > 0)) { why = "temperatures must be positive"; return LBM_EINVAL; }
+  if (p->multiphase && (!(p->c0 > 0) || p->G == 0.0 || !std::isfinite(p->G))) { why = "c0 > 0 and G != 0 required"; return LBM_EINVAL; }
+  if (p->thermal && !(p->c_v > 0)) { why = "c_v must be positive"; return LBM_EINVAL; }
+  if (p->geometry == LBM_GEOM_CHANNEL && (!(p->rho_out > 0) || !(std::fabs(p->u_in) < 0.5))) { why = "rho_out > 0 and |u_in| < 0.5 required"; return LBM_EINVAL; }
+  if (p->heater_len < 0) { why = "heater_len must be >= 0"; return LBM_EINVAL; }
+  if (p->init_kind != LBM_INIT_UNIFORM && p->init_kind != LBM_INIT_DISK) { why = "init_kind must be 0 or 1"; return LBM_EINVAL; }
+  if (!(p->init_rho_out > 0) || (p->init_kind == LBM_INIT_DISK && (!(p->init_rho_in > 0) || !(p->init_width > 0)))) {
+    why = "initial densities and width must be positive"; return LBM_EINVAL;
+  }
+  if (!std::isfinite(p->u_in) || !std::isfinite(p->g_a) || !std::isfinite(p->G_wet) || !std::isfinite(p->beta)) {
+    why = "non-finite parameter"; return LBM_EINVAL;
+  }
+  return LBM_OK;
+}
+
+// Fill the device instance descriptor from validated parameters.
+lbm_status apply_params(lbm_ctx* c, const lbm_params* p) {
+  std::string why;
+  lbm_status s = validate_params(c, p, why);
+  if (s != LBM_OK) return fail(c, s, why);
+  Inst& I = c->hinst;
+  I = Inst{};
+  I.nx = c->nx;
+  I.ny = c->ny;
+  I.pitch = c->L.pitch;
+  I.geometry = p->geometry;
+  I.plane = c->L.plane;
+  for (int b = 0; b < 2; ++b) {
+    I.f[b] = c->base + c->L.off_f[b];
+    I.g[b] = c->base + c->L.off_g[b];
+  }
+  I.multiphase = p->multiphase;
+  I.omega_f = 1.0 / p->tau_f;
+  I.omega_g = 1.0 / p->tau_g;
+  const double Tc = 0.0778 * p->a / (0.45724 * p->b * p->R);
+  I.a = p->a;
+  I.b = p->b;
+  I.R = p->R;
+  I.kappa = 0.37464 + 1.54226 * p->omega - 0.26992 * p->omega * p->omega;
+  I.sqrtTc = std::sqrt(Tc);
+  I.inv_sqrtTc = 1.0 / I.sqrtTc;
+  I.T0 = p->T0_R * Tc;
+  I.T_in = p->Tin_R * Tc;
+  I.T_heat = (p->Tin_R + p->dTheat_R) * Tc;
+  {
+    const double sa = 1.0 + I.kappa * (1.0 - std::sqrt(I.T0 / Tc));
+    I.alpha0 = sa * sa;
+  }
+  if (p->multiphase) {
+    I.psi_scale = 2.0 / (p->c0 * p->G);
+    const double rad = (host_pressure(*p, p->rho_w, I.T0) - p->rho_w / 3.0) * I.psi_scale;
+    if (!(rad >= 0.0)) return fail(c, LBM_EINVAL, "psi(rho_w, T0) undefined: negative radicand (Eq. 11)");
+    I.Gwet_psiw = p->G_wet * std::sqrt(rad);
+    if (!(p->b * std::max(p->rho_w, p->init_rho_out) < 1.0)) return fail(c, LBM_EINVAL, "density beyond 1/b");
+  }
+  I.beta = p->beta;
+  I.G2 = 2.0 * p->G;
+  I.Ghalf = 0.5 * p->G;
+  I.g_a = p->g_a;
+  I.inv_cv = p->thermal ? 1.0 / p->c_v : 0.0;
+  I.u_in = p->u_in;
+  I.rho_out = p->rho_out;
+  if (c->prec == LBM_FP32) {
+    I.rho_ref = p->geometry == LBM_GEOM_CHANNEL ? p->rho_out : p->init_rho_out;
+    I.T_ref = I.T0;
+  } else {
+    I.rho_ref = 0.0;
+    I.T_ref = 0.0;
+  }
+  I.heater_x0 = p->heater_x0 < 0 ? c->nx / 5 : p->heater_x0;
+  I.heater_len = p->heater_len;
+  I.heat_on_step = p->heat_on_step;
+  I.st = c->d_state;
+  I.partials = reinterpret_cast<double*>(c->base + c->L.off_part);
+  I.ring = reinterpret_cast<double*>(c->base + c->L.off_ring);
+  LBM_CUDA(c, cudaMemcpyAsync(c->d_inst, &c->hinst, sizeof(Inst), cudaMemcpyHostToDevice, c->stream));
+  c->params = *p;
+  c->thermal = p->thermal;
+  c->have_params = true;
+  return LBM_OK;
+}
+
+void reset_state_mirror(lbm_ctx* c, long long step, int local, double rho_avg_prev) {
+  InstState& S = *c->h_state;
+  std::memset(&S, 0, sizeof(S));
+  S.step = step;
+  S.local_read = local;
+  S.rho_avg[(step - 1) & 1] = rho_avg_prev;
+  S.rho_avg[step & 1] = rho_avg_prev;
+}
+
+lbm_status create_impl(lbm_ctx** out, int32_t nx, int32_t ny, lbm_precision prec, int32_t device, void* stream,
+                       void* dev_buf, size_t dev_bytes) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nx > kMaxDim || ny > kMaxDim) return LBM_EINVAL;
+  if (prec != LBM_FP32 && prec != LBM_FP64) return LBM_EINVAL;
+  if (dev_buf && (reinterpret_cast<uintptr_t>(dev_buf) % kAlign) != 0) return LBM_EINVAL;
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return LBM_ENOMEM;
+  c->nx = nx;
+  c->ny = ny;
+  c->prec = prec;
+  c->device = device;
+  c->L = make_layout(nx, ny, prec);
+  DeviceGuard g(device);
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) { delete c; return LBM_ECUDA; }
+  if (stream) {
+    c->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return LBM_ECUDA; }
+    c->own_stream = true;
+  }
+  if (dev_buf) {
+    if (dev_bytes < c->L.total) { lbm_destroy(c); return LBM_ENOMEM; }
+    c->base = static_cast<char*>(dev_buf);
+  } else {
+    void* p = nullptr;
+    if (cudaMalloc(&p, c->L.total) != cudaSuccess) { cudaGetLastError(); lbm_destroy(c); return LBM_ENOMEM; }
+    c->base = static_cast<char*>(p);
+    c->own_mem = true;
+  }
+  if (cudaMallocHost(&c->h_state, sizeof(InstState)) != cudaSuccess) { lbm_destroy(c); return LBM_ENOMEM; }
+  std::memset(c->h_state, 0, sizeof(InstState));
+  c->d_inst = reinterpret_cast<Inst*>(c->base + c->L.off_inst);
+  c->d_state = reinterpret_cast<InstState*>(c->base + c->L.off_state);
+  c->d_tiles_step = reinterpret_cast<Tile*>(c->base + c->L.off_tiles_step);
+  c->d_tiles_aux = reinterpret_cast<Tile*>(c->base + c->L.off_tiles_aux);
+  std::vector<Tile> t;
+  build_tiles(nx, ny, kAuxCols, std::min(kAuxRows, ny), t);
+  c->ntiles_aux = (int)t.size();
+  if (cudaMemcpyAsync(c->d_tiles_aux, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream) !=
+          cudaSuccess ||
+      cudaMemsetAsync(c->base + c->L.off_state, 0, sizeof(InstState), c->stream) != cudaSuccess) {
+    lbm_destroy(c);
+    return LBM_ECUDA;
+  }
+  const int rows = default_rows(nx, ny, 128);
+  if (set_tiling(c, 128, rows) != LBM_OK) { lbm_destroy(c); return LBM_ECUDA; }
+  *out = c;
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_params(lbm_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->size = sizeof(lbm_params);
+  p->geometry = LBM_GEOM_CHANNEL;
+  p->thermal = 1;
+  p->multiphase = 1;
+  p->tau_f = 1.0;
+  p->tau_g = 0.6;
+  p->a = 2.0 / 49.0;
+  p->b = 2.0 / 21.0;
+  p->R = 1.0;
+  p->omega = 0.32;
+  p->beta = 1.16;
+  p->c0 = 6.0;
+  p->G = -1.0;
+  p->T0_R = 0.9;
+  p->Tin_R = 0.9;
+  p->dTheat_R = 0.3;
+  p->u_in = 0.01;
+  p->rho_out = 5.95;
+  p->rho_w = 5.95;
+  p->G_wet = 9.0 * (1.0 + p->beta) * p->G;
+  p->g_a = 5e-5;
+  p->c_v = 6.0;
+  p->heater_x0 = -1;
+  p->heater_len = 5;
+  p->heat_on_step = 10000;
+  p->init_kind = LBM_INIT_UNIFORM;
+  p->init_rho_in = 5.95;
+  p->init_rho_out = 5.95;
+  p->init_radius = 0.0;
+  p->init_width = 2.0;
+  p->perturb_amp = 0.0;
+  p->seed = 0;
+}
+
+size_t lbm_required_bytes(int32_t nx, int32_t ny, lbm_precision prec) {
+  if (nx < 1 || ny < 1 || nx > kMaxDim || ny > kMaxDim) return 0;
+  return make_layout(nx, ny, prec).total;
+}
+
+lbm_status lbm_create(lbm_ctx** out, int32_t nx, int32_t ny, lbm_precision prec, int32_t device, void* stream) {
+  return create_impl(out, nx, ny, prec, device, stream, nullptr, 0);
+}
+
+lbm_status lbm_create_ex(lbm_ctx** out, int32_t nx, int32_t ny, lbm_precision prec, int32_t device, void* stream,
+                         void* dev_buf, size_t dev_bytes) {
+  if (!dev_buf) return LBM_EINVAL;
+  return create_impl(out, nx, ny, prec, device, stream, dev_buf, dev_bytes);
+}
+
+lbm_status lbm_set_params(lbm_ctx* c, const lbm_params* p) {
+  if (!c) return LBM_EINVAL;
+  DeviceGuard g(c->device);
+  lbm_status s = apply_params(c, p);
+  if (s != LBM_OK) return s;
+  InitSpec spec{};
+  spec.kind = p->init_kind;
+  spec.rho_in = p->init_rho_in;
+  spec.rho_out = p->init_rho_out;
+  spec.radius = p->init_radius;
+  spec.width = p->init_width;
+  spec.amp = p->perturb_amp;
+  spec.T0 = c->hinst.T0;
+  spec.seed = p->seed;
+  spec.instance = 0;
+  reset_state_mirror(c, 0, 1, 0.0);
+  if ((s = upload_state(c)) != LBM_OK) return s;
+  cudaError_t e = launch_init_builtin(c->prec == LBM_FP64, c->d_inst, c->nx, c->ny, spec, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+  ++c->launches;
+  if ((s = launch(c, MODE_MOMENTS)) != LBM_OK) return s;
+  return fetch_state(c);
+}
+
+lbm_status lbm_init_fields(lbm_ctx* c, const double* rho, const double* ux, const double* uy, const double* T,
+                           size_t n) {
+  if (!c || !rho || !ux || !uy) return fail(c, LBM_EINVAL, "NULL field");
+  if (n != (size_t)c->nx * c->ny) return fail(c, LBM_EINVAL, "n != nx*ny");
+  if (!c->have_params) return fail(c, LBM_ESTATE, "lbm_set_params first");
+  DeviceGuard g(c->device);
+  // host fields staged in the spare population buffer (buffer 1 is free at step 0)
+  double* d_fields = reinterpret_cast<double*>(c->base + c->L.off_f[1]);
+  LBM_CUDA(c, cudaMemcpyAsync(d_fields, rho, n * 8, cudaMemcpyHostToDevice, c->stream));
+  LBM_CUDA(c, cudaMemcpyAsync(d_fields + n, ux, n * 8, cudaMemcpyHostToDevice, c->stream));
+  LBM_CUDA(c, cudaMemcpyAsync(d_fields + 2 * n, uy, n * 8, cudaMemcpyHostToDevice, c->stream));
+  if (T) LBM_CUDA(c, cudaMemcpyAsync(d_fields + 3 * n, T, n * 8, cudaMemcpyHostToDevice, c->stream));
+  double mass = 0.0;  // row-major FP64 mean: the buoyancy reference of step 0
+  for (size_t k = 0; k < n; ++k) mass += rho[k];
+  reset_state_mirror(c, 0, 1, mass / (double)n);
+  lbm_status s = upload_state(c);
+  if (s != LBM_OK) return s;
+  cudaError_t e = launch_init_from_fields(c->prec == LBM_FP64, c->d_inst, c->nx, c->ny, d_fields, T ? 1 : 0, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+  ++c->launches;
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->step_host = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_step_async(lbm_ctx* c, int64_t nsteps) {
+  if (!c) return LBM_EINVAL;
+  if (nsteps < 0) return fail(c, LBM_EINVAL, "nsteps < 0");
+  if (!c->have_params) return fail(c, LBM_ESTATE, "lbm_set_params first");
+  DeviceGuard g(c->device);
+  for (int64_t k = 0; k < nsteps; ++k) {
+    lbm_status s = launch(c, MODE_STEP);
+    if (s != LBM_OK) return s;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx* c) {
+  if (!c) return LBM_EINVAL;
+  DeviceGuard g(c->device);
+  lbm_status s = fetch_state(c);
+  if (s != LBM_OK) return s;
+  if (c->h_state->status & STATUS_UNSTABLE)
+    return fail(c, LBM_EUNSTABLE, "lattice left the EOS domain (rho <= 0, rho >= 1/b, NaN or psi radicand < 0)");
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
+  lbm_status s = lbm_step_async(c, nsteps);
+  if (s != LBM_OK) return s;
+  return lbm_sync(c);
+}
+
+lbm_status lbm_read_fields(lbm_ctx* c, double* rho, double* ux, double* uy, double* T, size_t n) {
+  if (!c) return LBM_EINVAL;
+  if (n != (size_t)c->nx * c->ny) return fail(c, LBM_EINVAL, "n != nx*ny");
+  if (!c->have_params) return fail(c, LBM_ESTATE, "lbm_set_params first");
+  DeviceGuard g(c->device);
+  lbm_status s = fetch_state(c);
+  if (s != LBM_OK) return s;
+  if ((s = launch(c, MODE_FIELDS)) != LBM_OK) return s;
+  const double* d_out = reinterpret_cast<const double*>(c->base + c->L.off_f[(c->step_host + 1) & 1]);
+  double* dst[4] = {rho, ux, uy, T};
+  for (int k = 0; k < 4; ++k)
+    if (dst[k]) LBM_CUDA(c, cudaMemcpyAsync(dst[k], d_out + k * n, n * 8, cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx* c, double* f, double* gout, size_t n) {
+  if (!c || !f) return fail(c, LBM_EINVAL, "NULL f");
+  if (n != 9 * (size_t)c->nx * c->ny) return fail(c, LBM_EINVAL, "n != 9*nx*ny");
+  if (!c->have_params) return fail(c, LBM_ESTATE, "lbm_set_params first");
+  DeviceGuard g(c->device);
+  lbm_status s = fetch_state(c);
+  if (s != LBM_OK) return s;
+  if ((s = launch(c, MODE_POPS)) != LBM_OK) return s;
+  const int spare = (int)((c->step_host + 1) & 1);
+  const size_t elt = elt_size(c);
+  std::vector<char> tmp(n * elt);
+  const double rref[2] = {c->hinst.rho_ref, c->hinst.T_ref};
+  double* outs[2] = {f, gout};
+  const size_t offs[2] = {c->L.off_f[spare], c->L.off_g[spare]};
+  for (int a = 0; a < 2; ++a) {
+    if (!outs[a]) continue;
+    if (a == 1 && !c->thermal) {
+      for (int i = 0; i < 9; ++i) {
+        const double w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+        for (size_t k = 0; k < (size_t)c->nx * c->ny; ++k) outs[a][i * (size_t)c->nx * c->ny + k] = w * c->hinst.T0;
+      }
+      continue;
+    }
+    LBM_CUDA(c, cudaMemcpy2DAsync(tmp.data(), c->nx * elt, c->base + offs[a], c->L.pitch * elt, c->nx * elt,
+                                  9 * (size_t)c->ny, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    const size_t np = (size_t)c->nx * c->ny;
+    for (int i = 0; i < 9; ++i) {
+      const double w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+      for (size_t k = 0; k < np; ++k) {
+        const size_t idx = i * np + k;
+        const double v = elt == 8 ? reinterpret_cast<const double*>(tmp.data())[idx]
+                                  : (double)reinterpret_cast<const float*>(tmp.data())[idx];
+        outs[a][idx] = v + w * rref[a];
+      }
+    }
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_ctx* c, const double* f, const double* gin, size_t n, int64_t step,
+                               double rho_avg_prev) {
+  if (!c || !f) return fail(c, LBM_EINVAL, "NULL f");
+  if (n != 9 * (size_t)c->nx * c->ny) return fail(c, LBM_EINVAL, "n != 9*nx*ny");
+  if (step < 0) return fail(c, LBM_EINVAL, "step < 0");
+  if (!c->have_params) return fail(c, LBM_ESTATE, "lbm_set_params first");
+  DeviceGuard g(c->device);
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  const int buf = (int)(step & 1);
+  const size_t elt = elt_size(c);
+  const size_t np = (size_t)c->nx * c->ny;
+  std::vector<char> tmp(n * elt);
+  const double rref[2] = {c->hinst.rho_ref, c->hinst.T_ref};
+  const double* ins[2] = {f, gin};
+  const size_t offs[2] = {c->L.off_f[buf], c->L.off_g[buf]};
+  for (int a = 0; a < 2; ++a) {
+    for (int i = 0; i < 9; ++i) {
+      const double w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+      for (size_t k = 0; k < np; ++k) {
+        const size_t idx = i * np + k;
+        const double full = ins[a] ? ins[a][idx] : w * c->hinst.T0;
+        const double v = full - w * rref[a];
+        if (elt == 8)
+          reinterpret_cast<double*>(tmp.data())[idx] = v;
+        else
+          reinterpret_cast<float*>(tmp.data())[idx] = (float)v;
+      }
+    }
+    LBM_CUDA(c, cudaMemcpy2DAsync(c->base + offs[a], c->L.pitch * elt, tmp.data(), c->nx * elt, c->nx * elt,
+                                  9 * (size_t)c->ny, cudaMemcpyHostToDevice, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  const bool need_mean = std::isnan(rho_avg_prev);
+  reset_state_mirror(c, step, 1, need_mean ? 0.0 : rho_avg_prev);
+  lbm_status s = upload_state(c);
+  if (s != LBM_OK) return s;
+  if (need_mean && (s = launch(c, MODE_MOMENTS)) != LBM_OK) return s;
+  return fetch_state(c);
+}
+
+lbm_status lbm_read_diagnostics(lbm_ctx* c, double* out, size_t n) {
+  if (!c || !out) return fail(c, LBM_EINVAL, "NULL out");
+  if (n < (size_t)LBM_D_COUNT) return fail(c, LBM_EINVAL, "n < LBM_D_COUNT");
+  DeviceGuard g(c->device);
+  lbm_status s = fetch_state(c);
+  if (s != LBM_OK) return s;
+  if (c->step_host <= 0) return fail(c, LBM_ESTATE, "no step taken yet");
+  const long long last = c->step_host - 1;
+  const double* rec = reinterpret_cast<const double*>(c->base + c->L.off_ring) + (last % RING) * NDIAG;
+  LBM_CUDA(c, cudaMemcpyAsync(out, rec, NDIAG * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+namespace {
+struct StateHeader {
+  char magic[8];
+  int32_t nx, ny, prec, abi;
+  lbm_params params;
+  InstState state;
+};
+}  // namespace
+
+size_t lbm_state_bytes(const lbm_ctx* c) {
+  if (!c) return 0;
+  return sizeof(StateHeader) + 2 * 9 * (size_t)c->nx * c->ny * elt_size(c);
+}
+
+lbm_status lbm_save_state(lbm_ctx* c, void* host_buf, size_t bytes) {
+  if (!c || !host_buf) return fail(c, LBM_EINVAL, "NULL buffer");
+  if (bytes < lbm_state_bytes(c)) return fail(c, LBM_ENOMEM, "buffer smaller than lbm_state_bytes");
+  if (!c->have_params) return fail(c, LBM_ESTATE, "lbm_set_params first");
+  DeviceGuard g(c->device);
+  lbm_status s = fetch_state(c);
+  if (s != LBM_OK) return s;
+  StateHeader h{};
+  std::memcpy(h.magic, "PPLBMST", 8);
+  h.nx = c->nx;
+  h.ny = c->ny;
+  h.prec = c->prec;
+  h.abi = LBM_ABI_VERSION;
+  h.params = c->params;
+  h.state = *c->h_state;
+  h.state.counter = 0;
+  char* dst = static_cast<char*>(host_buf);
+  std::memcpy(dst, &h, sizeof(h));
+  dst += sizeof(h);
+  const size_t elt = elt_size(c);
+  const int buf = (int)(c->step_host & 1);
+  const size_t offs[2] = {c->L.off_f[buf], c->L.off_g[buf]};
+  for (int a = 0; a < 2; ++a) {
+    LBM_CUDA(c, cudaMemcpy2DAsync(dst, c->nx * elt, c->base + offs[a], c->L.pitch * elt, c->nx * elt,
+                                  9 * (size_t)c->ny, cudaMemcpyDeviceToHost, c->stream));
+    dst += 9 * (size_t)c->nx * c->ny * elt;
+  }
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t bytes) {
+  if (!c || !host_buf) return fail(c, LBM_EINVAL, "NULL buffer");
+  if (bytes < lbm_state_bytes(c)) return fail(c, LBM_EINVAL, "buffer smaller than lbm_state_bytes");
+  StateHeader h;
+  std::memcpy(&h, host_buf, sizeof(h));
+  if (std::memcmp(h.magic, "PPLBMST", 8) != 0 || h.nx != c->nx || h.ny != c->ny || h.prec != c->prec ||
+      h.abi != LBM_ABI_VERSION)
+    return fail(c, LBM_EINVAL, "state does not match this context");
+  DeviceGuard g(c->device);
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  lbm_status s = apply_params(c, &h.params);
+  if (s != LBM_OK) return s;
+  *c->h_state = h.state;
+  c->h_state->counter = 0;
+  if ((s = upload_state(c)) != LBM_OK) return s;
+  const char* src = static_cast<const char*>(host_buf) + sizeof(h);
+  const size_t elt = elt_size(c);
+  const int buf = (int)(h.state.step & 1);
+  const size_t offs[2] = {c->L.off_f[buf], c->L.off_g[buf]};
+  for (int a = 0; a < 2; ++a) {
+    LBM_CUDA(c, cudaMemcpy2DAsync(c->base + offs[a], c->L.pitch * elt, src, c->nx * elt, c->nx * elt,
+                                  9 * (size_t)c->ny, cudaMemcpyHostToDevice, c->stream));
+    src += 9 * (size_t)c->nx * c->ny * elt;
+  }
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->step_host = h.state.step;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_tiling(lbm_ctx* c, int32_t cols, int32_t rows) {
+  if (!c) return LBM_EINVAL;
+  if (cols == 0) cols = 128;
+  if (!cols_supported(cols)) return fail(c, LBM_EINVAL, "cols must be 64, 128 or 256");
+  if (cols == 256 && c->prec == LBM_FP64) return fail(c, LBM_EINVAL, "FP64 supports 64 or 128 columns");
+  if (rows == 0) rows = default_rows(c->nx, c->ny, cols);
+  if (rows < 1) return fail(c, LBM_EINVAL, "rows must be >= 1");
+  rows = std::min(rows, c->ny);
+  if (rows < kMinRows && rows < c->ny) return fail(c, LBM_EINVAL, "rows must be >= 4 (or the full height)");
+  DeviceGuard g(c->device);
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return set_tiling(c, cols, rows);
+}
+
+int64_t lbm_get_step(const lbm_ctx* c) { return c ? c->step_host : -1; }
+int64_t lbm_launch_count(const lbm_ctx* c) { return c ? c->launches : -1; }
+void* lbm_get_stream(const lbm_ctx* c) { return c ? static_cast<void*>(c->stream) : nullptr; }
+
+double lbm_critical_temperature(const lbm_params* p) {
+  if (!p) return NAN;
+  return 0.0778 * p->a / (0.45724 * p->b * p->R);
+}
+
+lbm_status lbm_destroy(lbm_ctx* c) {
+  if (!c) return LBM_OK;
+  {
+    DeviceGuard g(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->own_mem && c->base) cudaFree(c->base);
+    if (c->h_state) cudaFreeHost(c->h_state);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  }
+  delete c;
+  return LBM_OK;
+}
+
+const char* lbm_status_string(lbm_status s) {
+  switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "out of memory";
+    case LBM_EUNSTABLE: return "lattice unstable";
+    case LBM_ETIMEOUT: return "device wait timed out";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_EBUDGET: return "memory budget exceeded";
+    case LBM_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+
+}  // extern "C"

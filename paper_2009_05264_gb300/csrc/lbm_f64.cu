@@ -1,0 +1,20 @@
+// Kernel instantiations for double storage and arithmetic.
+#include "lbm_kernels.cuh"
+
+namespace pplbm {
+
+cudaError_t launch_lbm_f64(int thermal, int cols, int mode, const Inst* d_inst, const Tile* d_tiles, int ntiles,
+                          cudaStream_t s) {
+  return launch_precision<double>(thermal, cols, mode, d_inst, d_tiles, ntiles, s);
+}
+
+cudaError_t launch_init_from_fields_f64(const Inst* d_inst, int nx, int ny, const double* d_fields, int has_T,
+                                       cudaStream_t s) {
+  return launch_init_fields_t<double>(d_inst, nx, ny, d_fields, has_T, s);
+}
+
+cudaError_t launch_init_builtin_f64(const Inst* d_inst, int nx, int ny, InitSpec spec, cudaStream_t s) {
+  return launch_init_builtin_t<double>(d_inst, nx, ny, spec, s);
+}
+
+}  // namespace pplbm

@@ -1,0 +1,78 @@
+// Internal host/device descriptors of the pplbm library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pplbm {
+
+// Per-tile partial sums folded by the last CTA of an instance:
+// mass, energy, T summed over the heater-adjacent row, inlet flux, outlet flux.
+constexpr int NPART = 5;
+constexpr int NDIAG = 8;  // LBM_D_COUNT
+constexpr int RING = 1024;  // diagnostics records kept per instance
+
+enum : int { GEOM_PERIODIC = 0, GEOM_CHANNEL = 1, GEOM_WALLS = 2 };
+enum : int { MODE_STEP = 0, MODE_FIELDS = 1, MODE_POPS = 2, MODE_MOMENTS = 3 };
+enum : unsigned { STATUS_UNSTABLE = 1u };
+
+// Device-resident mutable state of one lattice instance.
+struct InstState {
+  long long step;       // steps completed
+  int local_read;       // 1: buffer (step & 1) holds post-stream populations (after init/load)
+  unsigned int counter; // tiles of the current launch that have finished
+  unsigned int status;  // sticky STATUS_* bits, cleared by the host
+  int pad0;
+  double rho_avg[2];    // domain-mean rho of step n in slot n & 1 (buoyancy of step n+1, Eq. 14)
+  double p_probe[2];    // EOS pressure at (1, ny/2) and (nx-2, ny/2) of the current step
+};
+
+// Read-only description of one lattice instance (host-filled, device-resident).
+struct Inst {
+  int nx, ny, pitch, geometry;
+  long long plane;      // elements per population plane (pitch * ny)
+  void* f[2];           // population double buffer: 9 planes each (storage precision)
+  void* g[2];
+  int multiphase, pad1;
+  double omega_f, omega_g;          // 1/tau_f, 1/tau_g
+  double a, b, R, kappa, sqrtTc, inv_sqrtTc;
+  double psi_scale;                 // 2/(c0 G) of Eq. 11
+  double beta, G2, Ghalf;           // Eq. 8 beta; Eq. 10 g1 = 2G, g2 = G/2
+  double Gwet_psiw;                 // G_wet * psi(rho_w, T0) of Eq. 15
+  double g_a, inv_cv;
+  double T0, T_in, T_heat, u_in, rho_out;
+  double rho_ref, T_ref;            // storage offsets: f stored as f - w_i rho_ref, g as g - w_i T_ref
+  double alpha0;                    // alpha(T0) of Eq. 12 for isothermal runs
+  int heater_x0, heater_len;
+  long long heat_on_step;
+  InstState* st;
+  double* partials;                 // NPART per tile of this instance
+  double* ring;                     // RING records of NDIAG doubles
+};
+
+// One CTA's work: output columns [x0, x0 + W) of instance `inst`, rows [y0, y1).
+struct Tile {
+  int inst, x0, y0, y1;
+  int local;   // index of this tile among its instance's tiles (partials slot)
+  int ntiles;  // tiles of this instance in the launch
+  int pad0, pad1;
+};
+
+// Launchers (defined per precision).  Tiles must have been built for `cols`.
+cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, const Inst* d_inst, const Tile* d_tiles,
+                       int ntiles, cudaStream_t s);
+// f = f^eq(rho,u), g = g^eq(T,u) into buffer 0 from 4 planes of nx*ny doubles (rho, ux, uy, T).
+cudaError_t launch_init_from_fields(int fp64, const Inst* d_inst, int nx, int ny, const double* d_fields,
+                                    int has_T, cudaStream_t s);
+// Built-in initial state (uniform or seeded disk) into buffer 0.
+struct InitSpec {
+  int kind;
+  double rho_in, rho_out, radius, width, amp, T0;
+  unsigned long long seed;
+  int instance;
+};
+cudaError_t launch_init_builtin(int fp64, const Inst* d_inst, int nx, int ny, InitSpec spec, cudaStream_t s);
+
+bool cols_supported(int cols);
+
+}  // namespace pplbm

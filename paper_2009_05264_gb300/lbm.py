@@ -1,0 +1,263 @@
+"""Python binding of the pplbm C ABI (``include/pplbm.h``): argument marshalling only.
+
+Every step of the lattice update runs in the CUDA library ``_lib/libpplbm.so``;
+this module converts numpy arrays and parameter mappings to pointers and
+sizes.  Device memory comes from PyTorch (one uint8 tensor per lattice, passed
+to ``lbm_create_ex``) and work is ordered on PyTorch's current CUDA stream
+unless another stream is given.  There is no CPU fallback: if the library
+is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+from .params import GEOMETRY, resolve
+
+_lib = None
+
+STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_EUNSTABLE", 4: "LBM_ETIMEOUT",
+          5: "LBM_ECUDA", 6: "LBM_EBUDGET", 7: "LBM_ESTATE"}
+FP32, FP64 = 0, 1
+DIAG_NAMES = ("step", "mass", "energy", "rho_avg", "dp", "dtstar", "flux_in", "flux_out")
+
+# Every function the header declares (checked against the shared library's exports).
+EXPORTS = (
+    "lbm_default_params", "lbm_required_bytes", "lbm_create", "lbm_create_ex", "lbm_set_params",
+    "lbm_init_fields", "lbm_step", "lbm_step_async", "lbm_sync", "lbm_read_fields", "lbm_get_populations",
+    "lbm_set_populations", "lbm_read_diagnostics", "lbm_state_bytes", "lbm_save_state", "lbm_load_state",
+    "lbm_set_tiling", "lbm_get_step", "lbm_launch_count", "lbm_get_stream", "lbm_critical_temperature",
+    "lbm_destroy", "lbm_status_string", "lbm_last_error",
+)
+
+
+class LbmParams(ctypes.Structure):
+    _fields_ = [
+        ("size", ctypes.c_uint32), ("geometry", ctypes.c_int32), ("thermal", ctypes.c_int32),
+        ("multiphase", ctypes.c_int32), ("tau_f", ctypes.c_double), ("tau_g", ctypes.c_double),
+        ("a", ctypes.c_double), ("b", ctypes.c_double), ("R", ctypes.c_double), ("omega", ctypes.c_double),
+        ("beta", ctypes.c_double), ("c0", ctypes.c_double), ("G", ctypes.c_double), ("T0_R", ctypes.c_double),
+        ("Tin_R", ctypes.c_double), ("dTheat_R", ctypes.c_double), ("u_in", ctypes.c_double),
+        ("rho_out", ctypes.c_double), ("rho_w", ctypes.c_double), ("G_wet", ctypes.c_double),
+        ("g_a", ctypes.c_double), ("c_v", ctypes.c_double), ("heater_x0", ctypes.c_int32),
+        ("heater_len", ctypes.c_int32), ("heat_on_step", ctypes.c_int64), ("init_kind", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32), ("init_rho_in", ctypes.c_double), ("init_rho_out", ctypes.c_double),
+        ("init_radius", ctypes.c_double), ("init_width", ctypes.c_double), ("perturb_amp", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libpplbm.so (building it with nvcc first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library not built: {_build.LIB}")
+    L = ctypes.CDLL(_build.LIB)
+    vp, i32, i64, sz, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)
+    P = ctypes.POINTER(LbmParams)
+    sig = {
+        "lbm_default_params": (None, [P]),
+        "lbm_required_bytes": (sz, [i32, i32, ctypes.c_int]),
+        "lbm_create": (ctypes.c_int, [ctypes.POINTER(vp), i32, i32, ctypes.c_int, i32, vp]),
+        "lbm_create_ex": (ctypes.c_int, [ctypes.POINTER(vp), i32, i32, ctypes.c_int, i32, vp, vp, sz]),
+        "lbm_set_params": (ctypes.c_int, [vp, P]),
+        "lbm_init_fields": (ctypes.c_int, [vp, dp, dp, dp, dp, sz]),
+        "lbm_step": (ctypes.c_int, [vp, i64]),
+        "lbm_step_async": (ctypes.c_int, [vp, i64]),
+        "lbm_sync": (ctypes.c_int, [vp]),
+        "lbm_read_fields": (ctypes.c_int, [vp, dp, dp, dp, dp, sz]),
+        "lbm_get_populations": (ctypes.c_int, [vp, dp, dp, sz]),
+        "lbm_set_populations": (ctypes.c_int, [vp, dp, dp, sz, i64, ctypes.c_double]),
+        "lbm_read_diagnostics": (ctypes.c_int, [vp, dp, sz]),
+        "lbm_state_bytes": (sz, [vp]),
+        "lbm_save_state": (ctypes.c_int, [vp, vp, sz]),
+        "lbm_load_state": (ctypes.c_int, [vp, vp, sz]),
+        "lbm_set_tiling": (ctypes.c_int, [vp, i32, i32]),
+        "lbm_get_step": (i64, [vp]),
+        "lbm_launch_count": (i64, [vp]),
+        "lbm_get_stream": (vp, [vp]),
+        "lbm_critical_temperature": (ctypes.c_double, [P]),
+        "lbm_destroy": (ctypes.c_int, [vp]),
+        "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "lbm_last_error": (ctypes.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def make_params(p: dict, nx: int) -> LbmParams:
+    """C parameter struct from a parameter mapping (see params.default_params)."""
+    q = resolve(p, nx)
+    s = LbmParams()
+    load().lbm_default_params(ctypes.byref(s))
+    for name, _ in LbmParams._fields_:
+        if name in ("size", "reserved0"):
+            continue
+        if name in q:
+            v = q[name]
+            if name == "geometry" and isinstance(v, str):
+                v = GEOMETRY[v]
+            setattr(s, name, v)
+    return s
+
+
+def critical_temperature(p: dict) -> float:
+    return float(load().lbm_critical_temperature(ctypes.byref(make_params(p, 8))))
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a, shape):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(shape)
+
+
+class Lattice:
+    """One nx x ny lattice resident on a CUDA device."""
+
+    def __init__(self, nx: int, ny: int, precision: str = "fp32", device: int = 0, stream=None,
+                 torch_memory: bool = True):
+        import torch  # device memory and streams
+
+        self.nx, self.ny = int(nx), int(ny)
+        self.precision = FP64 if precision in ("fp64", "f64", FP64) else FP32
+        self.device = int(device)
+        self._L = load()
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self._stream = stream
+        sptr = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        h = ctypes.c_void_p()
+        if torch_memory:
+            nbytes = int(self._L.lbm_required_bytes(self.nx, self.ny, self.precision))
+            if nbytes == 0:
+                raise LbmError(1, "invalid lattice size")
+            self._mem = torch.empty(nbytes + 256, dtype=torch.uint8, device=f"cuda:{self.device}")
+            base = self._mem.data_ptr()
+            aligned = (base + 255) // 256 * 256
+            st = self._L.lbm_create_ex(ctypes.byref(h), self.nx, self.ny, self.precision, self.device, sptr,
+                                       ctypes.c_void_p(aligned), nbytes)
+        else:
+            self._mem = None
+            st = self._L.lbm_create(ctypes.byref(h), self.nx, self.ny, self.precision, self.device, sptr)
+        if st != 0:
+            raise LbmError(st, "lbm_create failed")
+        self._h = h
+        self.params = None
+
+    # --- lifetime ---------------------------------------------------------
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._L.lbm_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != 0:
+            raise LbmError(st, self._L.lbm_last_error(self._h).decode())
+
+    # --- setup ------------------------------------------------------------
+    def set_params(self, p: dict):
+        self.params = dict(p)
+        self._cparams = make_params(p, self.nx)
+        self._check(self._L.lbm_set_params(self._h, ctypes.byref(self._cparams)))
+
+    def init_fields(self, rho, ux, uy, T=None):
+        shp = (self.ny, self.nx)
+        a = [_f64(x, shp) for x in (rho, ux, uy, T)]
+        self._check(self._L.lbm_init_fields(self._h, *[_dptr(x) for x in a], self.nx * self.ny))
+
+    def set_tiling(self, cols: int, rows: int):
+        self._check(self._L.lbm_set_tiling(self._h, int(cols), int(rows)))
+
+    # --- stepping ---------------------------------------------------------
+    def step(self, n: int = 1):
+        self._check(self._L.lbm_step(self._h, int(n)))
+
+    def step_async(self, n: int = 1):
+        self._check(self._L.lbm_step_async(self._h, int(n)))
+
+    def sync(self):
+        self._check(self._L.lbm_sync(self._h))
+
+    @property
+    def step_count(self) -> int:
+        return int(self._L.lbm_get_step(self._h))
+
+    @property
+    def launches(self) -> int:
+        return int(self._L.lbm_launch_count(self._h))
+
+    @property
+    def stream_handle(self) -> int:
+        return int(self._L.lbm_get_stream(self._h) or 0)
+
+    @property
+    def stream(self):
+        """The CUDA stream the lattice's kernels run on, as a torch stream (for events)."""
+        import torch
+
+        return torch.cuda.ExternalStream(self.stream_handle, device=torch.device("cuda", self.device))
+
+    # --- readback ---------------------------------------------------------
+    def fields(self) -> dict:
+        out = {k: np.empty((self.ny, self.nx)) for k in ("rho", "ux", "uy", "T")}
+        self._check(self._L.lbm_read_fields(self._h, *[_dptr(out[k]) for k in ("rho", "ux", "uy", "T")],
+                                            self.nx * self.ny))
+        return out
+
+    def populations(self):
+        f = np.empty((9, self.ny, self.nx))
+        g = np.empty((9, self.ny, self.nx))
+        self._check(self._L.lbm_get_populations(self._h, _dptr(f), _dptr(g), f.size))
+        return f, g
+
+    def set_populations(self, f, g=None, step: int = 0, rho_avg_prev: float | None = None):
+        shp = (9, self.ny, self.nx)
+        f, g = _f64(f, shp), _f64(g, shp)
+        r = float("nan") if rho_avg_prev is None else float(rho_avg_prev)
+        self._check(self._L.lbm_set_populations(self._h, _dptr(f), _dptr(g), f.size, int(step), r))
+
+    def diagnostics(self) -> dict:
+        d = np.empty(len(DIAG_NAMES))
+        self._check(self._L.lbm_read_diagnostics(self._h, _dptr(d), d.size))
+        return dict(zip(DIAG_NAMES, d.tolist()))
+
+    # --- checkpoint -------------------------------------------------------
+    def save_state(self) -> bytes:
+        n = int(self._L.lbm_state_bytes(self._h))
+        buf = ctypes.create_string_buffer(n)
+        self._check(self._L.lbm_save_state(self._h, buf, n))
+        return buf.raw
+
+    def load_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        self._check(self._L.lbm_load_state(self._h, buf, len(blob)))

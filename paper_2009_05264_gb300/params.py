@@ -18,7 +18,7 @@ def default_params(**overrides) -> dict:
         thermal=1,           # evolve g (Eq. 16)
         multiphase=1,        # Shan-Chen + wetting forces (Eqs. 9, 15)
         tau_f=1.0,           # not stated in the paper (library default)
-        tau_g=1.0,           # not stated in the paper (library default)
+        tau_g=0.6,           # not stated in the paper; 0.6 keeps the anti-bounce-back walls stable
         a=2.0 / 49.0,        # Eq. 12, Sec. 2.A
         b=2.0 / 21.0,        # Eq. 12
         R=1.0,               # Eq. 12
@@ -31,8 +31,9 @@ def default_params(**overrides) -> dict:
         dTheat_R=0.3,        # heater superheat 0.3 Tc (Sec. 3)
         u_in=0.01,           # inlet velocity (library default)
         rho_out=5.95,        # outlet density: liquid density at 0.9 Tc printed in Sec. 3.D
-        rho_w=3.0,           # false wall density of Eq. 15 (sets the contact angle; library default)
-        G_wet=None,          # Eq. 15 strength; None -> 18 G so that G_wet w_i equals the Eq. 10 stencil
+        rho_w=5.95,          # false wall density of Eq. 15 (sets the contact angle; library default)
+        G_wet=None,          # Eq. 15 strength; None -> 9 (1 + beta) G: a wall whose false density equals
+                             # the fluid's then exerts no net force on uniform fluid under the beta-mixed Eq. 9
         g_a=5e-5,            # lattice gravity printed for the pool-boiling check (Sec. 2.D)
         c_v=6.0,             # specific heat of Eq. 19 (not stated in the paper; library default)
         heater_x0=-1,        # -1 -> nx/5 (microheater at one fifth of the length, Sec. 2.C)
@@ -48,7 +49,7 @@ def default_params(**overrides) -> dict:
     )
     p.update(overrides)
     if p["G_wet"] is None:
-        p["G_wet"] = 18.0 * p["G"]
+        p["G_wet"] = 9.0 * (1.0 + p["beta"]) * p["G"]
     return p
 
 
@@ -60,7 +61,7 @@ def resolve(p: dict, nx: int) -> dict:
     if q["heater_x0"] is None or q["heater_x0"] < 0:
         q["heater_x0"] = nx // 5
     if q["G_wet"] is None:
-        q["G_wet"] = 18.0 * q["G"]
+        q["G_wet"] = 9.0 * (1.0 + q["beta"]) * q["G"]
     return q
 
 

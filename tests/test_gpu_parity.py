@@ -1,0 +1,292 @@
+"""GPU parity: the fused CUDA step against the FP64 CPU oracle, element by element.
+
+Tolerances: FP64 storage and arithmetic agree with the oracle to 1e-12
+relative over 1000 steps (only rounding order and FMA contraction differ);
+FP32 storage (deviations from the rest weights) and arithmetic agree to 1e-5
+relative on rho and T and 1e-5 of the velocity scale on u.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_05264_gb300 import inputs as I
+from paper_2009_05264_gb300 import params as PP
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-5
+
+
+def lbm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_05264_gb300 import lbm as L
+
+    return L
+
+
+def prm(nx, **kw):
+    return PP.resolve(PP.default_params(**kw), nx)
+
+
+def rel_err(got, ref, key):
+    if key in ("ux", "uy"):
+        scale = max(np.abs(ref["ux"]).max(), np.abs(ref["uy"]).max(), 1e-12)
+    else:
+        scale = np.abs(ref[key]).max()
+    return np.abs(got[key] - ref[key]).max() / scale
+
+
+def run_pair(nx, ny, p, fields, steps, precision="fp64", tiling=None, chunks=1):
+    L = lbm()
+    lat = L.Lattice(nx, ny, precision)
+    lat.set_params(p)
+    if tiling:
+        lat.set_tiling(*tiling)
+    lat.init_fields(*fields)
+    orc = oracle.Oracle(nx, ny, p)
+    orc.init_fields(*fields)
+    per = steps // chunks
+    for _ in range(chunks):
+        lat.step(per)
+        assert orc.step(per) == 0
+    return lat, orc
+
+
+def channel_case(nx, ny, **kw):
+    base = dict(geometry="channel", u_in=0.01, dTheat_R=0.08, heat_on_step=40, heater_x0=nx // 5,
+                heater_len=max(3, nx // 10), g_a=2e-4)
+    base.update(kw)
+    p = prm(nx, **base)
+    Tc = oracle.Tc(p)
+    fields = I.smooth_random(nx, ny, 5.95, 0.9 * Tc, seed=nx * 131 + ny, drho=0.002, du=0.005, dT=0.002)
+    return p, fields
+
+
+@pytest.mark.parametrize("nx,ny,tiling", [(150, 37, (64, 5)), (150, 37, (128, 16)), (33, 17, (64, 4)),
+                                          (6, 5, (64, 5))])
+def test_fp64_channel_thermal_matches_oracle(nx, ny, tiling):
+    p, fields = channel_case(nx, ny)
+    lat, orc = run_pair(nx, ny, p, fields, 300, "fp64", tiling, chunks=3)
+    got, ref = lat.fields(), orc.fields()
+    for k in ("rho", "ux", "uy", "T"):
+        assert rel_err(got, ref, k) < FP64_TOL, k
+    fg, gg = lat.populations()
+    fo, go = orc.populations()
+    assert np.abs(fg - fo).max() < FP64_TOL * np.abs(fo).max()
+    assert np.abs(gg - go).max() < FP64_TOL * np.abs(go).max()
+    dg, do = lat.diagnostics(), orc.last_diag()
+    for k in ("mass", "energy", "rho_avg", "flux_in", "flux_out"):
+        assert dg[k] == pytest.approx(do[k], rel=1e-12, abs=1e-14), k
+    assert dg["dp"] == pytest.approx(do["dp"], rel=1e-9, abs=1e-14)
+    assert dg["dtstar"] == pytest.approx(do["dtstar"], rel=1e-9, abs=1e-12)
+    assert dg["step"] == do["step"] == 299
+
+
+def test_fp64_channel_1000_steps():
+    nx, ny = 130, 24
+    p, fields = channel_case(nx, ny, heat_on_step=300)
+    lat, orc = run_pair(nx, ny, p, fields, 1000, "fp64", chunks=4)
+    got, ref = lat.fields(), orc.fields()
+    for k in ("rho", "ux", "uy", "T"):
+        assert rel_err(got, ref, k) < FP64_TOL, k
+
+
+def test_fp64_periodic_droplet_1000_steps():
+    nx, ny = 70, 48
+    p = prm(nx, geometry="periodic", thermal=0, g_a=0.0)
+    T = 0.9 * oracle.Tc(p)
+    rv, rl, _ = oracle.maxwell(p, T)
+    fields = I.disk(nx, ny, 14, rl, rv, T, seed=2009052640, amp=1e-3)
+    lat, orc = run_pair(nx, ny, p, fields, 1000, "fp64", (64, 8))
+    got, ref = lat.fields(), orc.fields()
+    for k in ("rho", "ux", "uy"):
+        assert rel_err(got, ref, k) < FP64_TOL, k
+    assert lat.diagnostics()["mass"] == pytest.approx(orc.last_diag()["mass"], rel=1e-13)
+
+
+def test_fp64_walls_thermal_periodic_x():
+    nx, ny = 90, 21
+    p = prm(nx, geometry="walls", thermal=1, heat_on_step=10, heater_x0=80, heater_len=20, g_a=1e-4, rho_w=5.0,
+            dTheat_R=0.1)
+    Tc = oracle.Tc(p)
+    fields = I.smooth_random(nx, ny, 5.95, 0.9 * Tc, seed=5, drho=0.002, du=0.005, dT=0.002)
+    lat, orc = run_pair(nx, ny, p, fields, 200, "fp64", (64, 6))
+    got, ref = lat.fields(), orc.fields()
+    for k in ("rho", "ux", "uy", "T"):
+        assert rel_err(got, ref, k) < FP64_TOL, k
+
+
+def test_fp64_periodic_thermal_two_phase():
+    nx, ny = 40, 40
+    p = prm(nx, geometry="periodic", thermal=1, g_a=1e-4)
+    T = 0.9 * oracle.Tc(p)
+    rv, rl, _ = oracle.maxwell(p, T)
+    fields = I.disk(nx, ny, 10, rl, rv, T, seed=9, amp=1e-3)
+    lat, orc = run_pair(nx, ny, p, fields, 300, "fp64", (64, 7))
+    got, ref = lat.fields(), orc.fields()
+    for k in ("rho", "ux", "uy", "T"):
+        assert rel_err(got, ref, k) < FP64_TOL, k
+
+
+def test_fp64_single_phase_poiseuille():
+    nx, ny = 100, 10
+    p = prm(nx, geometry="channel", thermal=0, multiphase=0, g_a=0.0, u_in=0.016, rho_out=1.0)
+    fields = I.uniform(nx, ny, 1.0, 0.0)
+    lat, orc = run_pair(nx, ny, p, fields, 1000, "fp64")
+    got, ref = lat.fields(), orc.fields()
+    for k in ("rho", "ux", "uy"):
+        assert rel_err(got, ref, k) < FP64_TOL, k
+
+
+@pytest.mark.parametrize("tiling", [(128, 16), (64, 4), (256, 37)])
+def test_fp32_channel_thermal_1000_steps(tiling):
+    nx, ny = 300, 37
+    p, fields = channel_case(nx, ny, heat_on_step=200)
+    lat, orc = run_pair(nx, ny, p, fields, 1000, "fp32", tiling)
+    got, ref = lat.fields(), orc.fields()
+    for k in ("rho", "ux", "uy", "T"):
+        assert rel_err(got, ref, k) < FP32_TOL, k
+
+
+def test_fp32_periodic_droplet_1000_steps():
+    nx, ny = 64, 64
+    p = prm(nx, geometry="periodic", thermal=0, g_a=0.0)
+    T = 0.86 * oracle.Tc(p)
+    p["T0_R"] = 0.86
+    rv, rl, _ = oracle.maxwell(p, T)
+    fields = I.disk(nx, ny, 25 * 64 / 128, rl, rv, T, seed=2009052640, amp=1e-3)
+    p["init_rho_out"] = rv
+    lat, orc = run_pair(nx, ny, p, fields, 1000, "fp32")
+    got, ref = lat.fields(), orc.fields()
+    for k in ("rho", "ux", "uy"):
+        assert rel_err(got, ref, k) < FP32_TOL, k
+
+
+def test_tiling_does_not_change_results():
+    """Per-node arithmetic is tile-independent: without buoyancy (no global sum in the
+    update) every tiling gives bit-identical populations."""
+    L = lbm()
+    nx, ny = 200, 45
+    p, fields = channel_case(nx, ny, g_a=0.0)
+    outs = []
+    for tiling in [(64, 4), (128, 16), (256, 45), (128, 7)]:
+        lat = L.Lattice(nx, ny, "fp32")
+        lat.set_params(p)
+        lat.set_tiling(*tiling)
+        lat.init_fields(*fields)
+        lat.step(100)
+        outs.append(lat.populations())
+    for f, g in outs[1:]:
+        assert np.array_equal(f, outs[0][0]) and np.array_equal(g, outs[0][1])
+
+
+def test_checkpoint_resume_is_bitwise():
+    L = lbm()
+    nx, ny = 90, 20
+    for prec in ("fp32", "fp64"):
+        p, fields = channel_case(nx, ny, heat_on_step=30)
+        a = L.Lattice(nx, ny, prec)
+        a.set_params(p)
+        a.init_fields(*fields)
+        a.step(60)
+        blob = a.save_state()
+        a.step(40)
+        b = L.Lattice(nx, ny, prec)
+        b.set_params(p)
+        b.load_state(blob)
+        assert b.step_count == 60
+        b.step(40)
+        fa, ga = a.populations()
+        fb, gb = b.populations()
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
+def test_set_populations_roundtrip_and_oracle_state_injection():
+    """A state taken from the oracle mid-run, injected with its step and buoyancy mean,
+    continues exactly like the oracle."""
+    L = lbm()
+    nx, ny = 64, 19
+    p, fields = channel_case(nx, ny, heat_on_step=25)
+    orc = oracle.Oracle(nx, ny, p)
+    orc.init_fields(*fields)
+    orc.step(20)
+    f, g = orc.populations()
+    lat = L.Lattice(nx, ny, "fp64")
+    lat.set_params(p)
+    lat.set_populations(f, g, step=orc.step_count, rho_avg_prev=orc.rho_avg_prev)
+    f2, g2 = lat.populations()
+    assert np.array_equal(f2, f) and np.array_equal(g2, g)
+    lat.step(30)
+    orc.step(30)
+    got, ref = lat.fields(), orc.fields()
+    for k in ("rho", "ux", "uy", "T"):
+        assert rel_err(got, ref, k) < FP64_TOL, k
+
+
+def test_builtin_disk_init_matches_input_generator():
+    L = lbm()
+    nx, ny = 100, 64
+    p = prm(nx, geometry="periodic", thermal=0, g_a=0.0, init_kind=1, init_rho_in=5.88, init_rho_out=0.59,
+            init_radius=20.0, init_width=2.0, perturb_amp=1e-3, seed=2009052640)
+    lat = L.Lattice(nx, ny, "fp64")
+    lat.set_params(p)
+    rho = lat.fields()["rho"]
+    T0 = p["T0_R"] * oracle.Tc(p)
+    ref = I.disk(nx, ny, 20.0, 5.88, 0.59, T0, width=2.0, seed=2009052640, amp=1e-3)[0]
+    assert np.abs(rho - ref).max() < 1e-13 * ref.max()
+
+
+def test_unstable_state_is_reported_not_trapped():
+    L = lbm()
+    nx, ny = 40, 10
+    p, fields = channel_case(nx, ny)
+    rho = fields[0].copy()
+    rho[5, 20] = 11.0  # beyond 1/b = 10.5: outside the Peng-Robinson domain
+    lat = L.Lattice(nx, ny, "fp64")
+    lat.set_params(p)
+    lat.init_fields(rho, fields[1], fields[2], fields[3])
+    with pytest.raises(L.LbmError) as e:
+        lat.step(1)
+    assert e.value.status == 3
+    # the context stays usable
+    lat.init_fields(*fields)
+    lat.step(2)
+
+
+def test_bad_arguments_are_rejected():
+    L = lbm()
+    lat = L.Lattice(20, 10, "fp32")
+    with pytest.raises(L.LbmError):
+        lat.step(1)  # no parameters yet
+    p = prm(20, geometry="channel", tau_f=0.4)
+    with pytest.raises(L.LbmError):
+        lat.set_params(p)
+    with pytest.raises(L.LbmError):
+        lat.set_tiling(96, 8)
+    small = L.Lattice(2, 10, "fp32")
+    with pytest.raises(L.LbmError):
+        small.set_params(prm(2, geometry="channel"))
+
+
+def test_full_size_channel_against_oracle():
+    """8000 x 800 thermal channel in the benchmark's FP32 launch configuration:
+    two fused steps compared with the oracle over every node."""
+    L = lbm()
+    nx, ny = 8000, 800
+    p = prm(nx, geometry="channel", u_in=0.03, dTheat_R=0.08, heater_x0=1600, heater_len=40, heat_on_step=1,
+            rho_out=5.95)
+    Tc = oracle.Tc(p)
+    fields = I.smooth_random(nx, ny, 5.95, 0.9 * Tc, seed=2009052643, drho=0.002, du=0.005, dT=0.002)
+    lat = L.Lattice(nx, ny, "fp32")
+    lat.set_params(p)
+    lat.init_fields(*fields)
+    lat.step(2)
+    orc = oracle.Oracle(nx, ny, p)
+    orc.init_fields(*fields)
+    assert orc.step(2) == 0
+    got, ref = lat.fields(), orc.fields()
+    for k in ("rho", "ux", "uy", "T"):
+        assert rel_err(got, ref, k) < FP32_TOL, k
