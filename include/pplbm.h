@@ -123,7 +123,8 @@ size_t lbm_required_bytes(int32_t nx, int32_t ny, lbm_precision prec);
  * computes in FP32, with FP64 global reductions.
  * cuda_stream: a cudaStream_t to order all work on, or NULL for a stream the
  * context creates and owns.  The context allocates its device memory.
- * Errors: LBM_EINVAL (nx, ny < 1 or too large), LBM_ENOMEM, LBM_ECUDA. */
+ * Errors: LBM_EINVAL (nx, ny < 1, or 9 * ny * pitch >= 2^31 elements, pitch = nx rounded
+ * up to 32: about 238 M nodes), LBM_ENOMEM, LBM_ECUDA. */
 lbm_status lbm_create(lbm_ctx** out, int32_t nx, int32_t ny, lbm_precision prec, int32_t device,
                       void* cuda_stream);
 
@@ -181,8 +182,10 @@ size_t lbm_state_bytes(const lbm_ctx* ctx);
 lbm_status lbm_save_state(lbm_ctx* ctx, void* host_buf, size_t bytes);
 lbm_status lbm_load_state(lbm_ctx* ctx, const void* host_buf, size_t bytes);
 
-/* Tile shape of the fused kernel: columns per CTA (64, 128 or 256) and rows per
- * CTA (>= 1).  Any shape gives identical results; only speed differs.  0 = default. */
+/* Tile shape of the fused kernel: threads per CTA (64, 128 or 256; a CTA writes
+ * cols - 8 columns, the other 8 lanes cover halo columns) and rows per CTA (>= 4, or
+ * the full height).  Results do not depend on the shape except through
+ * the summation order of the domain-mean density (Eq. 14); only speed differs.  0 = default. */
 lbm_status lbm_set_tiling(lbm_ctx* ctx, int32_t cols, int32_t rows);
 
 int64_t lbm_get_step(const lbm_ctx* ctx);

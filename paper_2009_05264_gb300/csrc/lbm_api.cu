@@ -64,7 +64,7 @@ Layout make_layout(int nx, int ny, lbm_precision prec) {
   L.pitch = (nx + 31) / 32 * 32;
   L.plane = (long long)L.pitch * ny;
   L.pop_bytes = align_up(9 * (size_t)L.plane * elt);
-  const long long strips = (nx + 63) / 64;
+  const long long strips = (nx + 55) / 56;  // narrowest tiling: 64 threads, 56 output columns
   const long long bands = (ny + kMinRows - 1) / kMinRows;
   L.max_tiles = (int)std::min<long long>(strips * bands, 1ll << 30);
   size_t off = 0;
@@ -88,9 +88,11 @@ double host_pressure(const lbm_params& p, double rho, double T) {
   return rho * p.R * T / (1.0 - p.b * rho) - p.a * s * s * rho * rho / (1.0 + 2.0 * p.b * rho - p.b * p.b * rho * rho);
 }
 
+// Tiles of a kernel with `cols` threads per CTA, each writing cols - 8 columns.
 void build_tiles(int nx, int ny, int cols, int rows, std::vector<Tile>& out) {
   out.clear();
-  const int strips = (nx + cols - 1) / cols;
+  const int w = cols - 8;
+  const int strips = (nx + w - 1) / w;
   const int bands = (ny + rows - 1) / rows;
   const int n = strips * bands;
   int local = 0;
@@ -98,7 +100,7 @@ void build_tiles(int nx, int ny, int cols, int rows, std::vector<Tile>& out) {
     for (int sidx = 0; sidx < strips; ++sidx) {
       Tile t{};
       t.inst = 0;
-      t.x0 = sidx * cols;
+      t.x0 = sidx * w;
       t.y0 = b * rows;
       t.y1 = std::min(ny, (b + 1) * rows);
       t.local = local++;
@@ -110,7 +112,7 @@ void build_tiles(int nx, int ny, int cols, int rows, std::vector<Tile>& out) {
 // Rows per band for a tile width: enough CTAs to fill 152 SMs a few times over
 // while keeping the 4-row band overhead small.
 int default_rows(int nx, int ny, int cols) {
-  const int strips = (nx + cols - 1) / cols;
+  const int strips = (nx + cols - 9) / (cols - 8);
   const long long target = 152LL * 8;
   long long rows = ((long long)ny * strips + target - 1) / target;
   rows = std::max<long long>(rows, 16);
@@ -289,6 +291,20 @@ lbm_status apply_params(lbm_ctx* c, const lbm_params* p) {
     I.rho_ref = 0.0;
     I.T_ref = 0.0;
   }
+  if (c->prec == LBM_FP32 && p->multiphase) {
+    const double rr = I.rho_ref, Tr = I.T_ref;
+    const double u1r = 1.0 - p->b * rr, Dr = 1.0 + 2.0 * p->b * rr - p->b * p->b * rr * rr;
+    if (!(u1r > 0.0) || !(Dr > 0.0)) return fail(c, LBM_EINVAL, "reference density beyond 1/b");
+    I.sa_r = 1.0 + I.kappa * (1.0 - std::sqrt(Tr / Tc));
+    I.p_ref = rr * p->R * Tr / u1r - p->a * I.sa_r * I.sa_r * rr * rr / Dr;
+    I.rad_ref = (I.p_ref - rr / 3.0) * I.psi_scale;
+    if (!(I.rad_ref >= 0.0)) return fail(c, LBM_EINVAL, "psi undefined at the reference state (Eq. 11)");
+    I.psi_ref = std::sqrt(I.rad_ref);
+    I.inv_u1r = 1.0 / u1r;
+    I.inv_Dr = 1.0 / Dr;
+    I.sqrtT_r = std::sqrt(Tr);
+    I.rr2_Dr = rr * rr / Dr;
+  }
   I.heater_x0 = p->heater_x0 < 0 ? c->nx / 5 : p->heater_x0;
   I.heater_len = p->heater_len;
   I.heat_on_step = p->heat_on_step;
@@ -318,6 +334,8 @@ lbm_status create_impl(lbm_ctx** out, int32_t nx, int32_t ny, lbm_precision prec
   if (nx < 1 || ny < 1 || nx > kMaxDim || ny > kMaxDim) return LBM_EINVAL;
   if (prec != LBM_FP32 && prec != LBM_FP64) return LBM_EINVAL;
   if (dev_buf && (reinterpret_cast<uintptr_t>(dev_buf) % kAlign) != 0) return LBM_EINVAL;
+  // kernels index one 9-plane population buffer with 32-bit element offsets
+  if (9ll * make_layout(nx, ny, prec).plane >= (1ll << 31)) return LBM_EINVAL;
   lbm_ctx* c = new (std::nothrow) lbm_ctx();
   if (!c) return LBM_ENOMEM;
   c->nx = nx;
@@ -685,7 +703,6 @@ lbm_status lbm_set_tiling(lbm_ctx* c, int32_t cols, int32_t rows) {
   if (!c) return LBM_EINVAL;
   if (cols == 0) cols = 128;
   if (!cols_supported(cols)) return fail(c, LBM_EINVAL, "cols must be 64, 128 or 256");
-  if (cols == 256 && c->prec == LBM_FP64) return fail(c, LBM_EINVAL, "FP64 supports 64 or 128 columns");
   if (rows == 0) rows = default_rows(c->nx, c->ny, cols);
   if (rows < 1) return fail(c, LBM_EINVAL, "rows must be >= 1");
   rows = std::min(rows, c->ny);

@@ -43,6 +43,9 @@ struct Inst {
   double T0, T_in, T_heat, u_in, rho_out;
   double rho_ref, T_ref;            // storage offsets: f stored as f - w_i rho_ref, g as g - w_i T_ref
   double alpha0;                    // alpha(T0) of Eq. 12 for isothermal runs
+  // FP32 reference state of the pseudopotential: psi is carried as psi - psi_ref,
+  // evaluated from exact difference forms of Eq. 12 in rho - rho_ref and T - T_ref
+  double psi_ref, rad_ref, p_ref, inv_u1r, inv_Dr, sa_r, sqrtT_r, rr2_Dr;
   int heater_x0, heater_len;
   long long heat_on_step;
   InstState* st;

@@ -46,9 +46,24 @@ __host__ __device__ constexpr int lat_cy(int i) {
 __host__ __device__ constexpr int lat_opp(int i) {
   return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
 }
+// D2Q9 weights.  In FP32 the rounded 4/9, 1/9, 1/36 sum to 1 + 7.6e-9, which would
+// create mass (and energy) in every collision in proportion to the stored deviation;
+// the FP32 set below (1/36 lowered by one ulp) sums to exactly 1.
+template <typename Real>
+struct LatWeights {
+  __host__ __device__ static constexpr Real w0() { return Real(4.0 / 9.0); }
+  __host__ __device__ static constexpr Real w1() { return Real(1.0 / 9.0); }
+  __host__ __device__ static constexpr Real w5() { return Real(1.0 / 36.0); }
+};
+template <>
+struct LatWeights<float> {
+  __host__ __device__ static constexpr float w0() { return 0x1.c71c72p-2f; }
+  __host__ __device__ static constexpr float w1() { return 0x1.c71c72p-4f; }
+  __host__ __device__ static constexpr float w5() { return 0x1.c71c70p-6f; }
+};
 template <typename Real>
 __host__ __device__ constexpr Real lat_w(int i) {
-  return i == 0 ? Real(4.0 / 9.0) : (i <= 4 ? Real(1.0 / 9.0) : Real(1.0 / 36.0));
+  return i == 0 ? LatWeights<Real>::w0() : (i <= 4 ? LatWeights<Real>::w1() : LatWeights<Real>::w5());
 }
 
 __device__ __forceinline__ int wrap_index(int v, int n) {
@@ -80,23 +95,121 @@ __device__ __forceinline__ void block_sum(double (&v)[NPART], double (*red)[NPAR
   }
 }
 
+// Reciprocal and reciprocal square root: MUFU approximations (about 2 ulp) in
+// FP32, IEEE operations in FP64 (the FP64 path matches the oracle to round-off).
+__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double fast_rsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float fast_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+__device__ __forceinline__ double fast_sqrt(double x) { return sqrt(x); }
+
+// Asynchronous global -> shared copies of one element (cp.async, Ampere and later).
+__device__ __forceinline__ void cp_async_elem(float* smem, const float* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double* smem, const double* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Ring depths of the staged populations: f of rows r+1 (in flight), r (pulled
+// now) and r-1 (collided now); g additionally keeps row r-2 (collided now).
+constexpr int F_SLOTS = 3;
+constexpr int G_SLOTS = 4;
+
+// A CTA of B threads owns B - 8 output columns: its threads map to the columns
+// [x0 - 2, x0 + B - 6), i.e. the output columns plus two halo columns per side, and
+// the last 4 lanes idle, so that every CTA's output starts on a 32-byte sector.
+template <int B>
+__host__ __device__ constexpr int out_cols() { return B - 8; }
+
+template <typename Real, bool THERMAL, int B>
+constexpr size_t fused_smem_bytes() {
+  return sizeof(Real) * (size_t)(B - 4) * (9 * F_SLOTS + (THERMAL ? 9 * G_SLOTS : 0) + 9);
+}
+
+// ---------------------------------------------------------------------------
+// Per-instance constants of the update, converted once per CTA to the compute
+// precision (the instance descriptor holds them in FP64).
+// ---------------------------------------------------------------------------
+template <typename Real>
+struct KConst {
+  Real omega_f, omega_g, a, b, R, kappa, inv_sqrtTc, psi_scale, beta, G2, Gh, mix, g_a, inv_cv;
+  Real T0, rho_ref, T_ref, alpha0, u_in, drho_out, dT_in, dT_heat;
+  // FP32 pseudopotential reference state (zero in FP64)
+  Real inv_u1r, inv_Dr, sqrtT_r, sa_r, rr2_Dr, rad_ref, psi_ref, p_ref;
+  // force on a row next to the bottom wall: wall0 + d * wall1 (the top wall: minus that)
+  Real wall0, wall1;
+  Real rho_ref_minus_avg;  // rho_ref - rho_avg of the previous step (buoyancy, Eq. 14)
+};
+
+template <typename Real>
+__device__ __forceinline__ void fill_consts(KConst<Real>& c, const Inst& I, double rho_avg_prev) {
+  c.omega_f = Real(I.omega_f);
+  c.omega_g = Real(I.omega_g);
+  c.a = Real(I.a);
+  c.b = Real(I.b);
+  c.R = Real(I.R);
+  c.kappa = Real(I.kappa);
+  c.inv_sqrtTc = Real(I.inv_sqrtTc);
+  c.psi_scale = Real(I.psi_scale);
+  c.beta = Real(I.beta);
+  c.G2 = Real(I.G2);
+  c.Gh = Real(I.Ghalf);
+  c.mix = Real(0.5 * (1.0 - I.beta));
+  c.g_a = Real(I.g_a);
+  c.inv_cv = Real(I.inv_cv);
+  c.T0 = Real(I.T0);
+  c.rho_ref = Real(I.rho_ref);
+  c.T_ref = Real(I.T_ref);
+  c.alpha0 = Real(I.alpha0);
+  c.u_in = Real(I.u_in);
+  c.drho_out = Real(I.rho_out - I.rho_ref);
+  c.dT_in = Real(I.T_in - I.T_ref);
+  c.dT_heat = Real(I.T_heat - I.T_ref);
+  c.inv_u1r = Real(I.inv_u1r);
+  c.inv_Dr = Real(I.inv_Dr);
+  c.sqrtT_r = Real(I.sqrtT_r);
+  c.sa_r = Real(I.sa_r);
+  c.rr2_Dr = Real(I.rr2_Dr);
+  c.rad_ref = Real(I.rad_ref);
+  c.psi_ref = Real(I.psi_ref);
+  c.p_ref = Real(I.p_ref);
+  // Wall rows: the fluid neighbours of a row above the bottom wall have sum G_i c_iy = 3G
+  // and its solid neighbours sum w_i c_iy = -1/6, so with psi = psi_ref + d the reference
+  // parts of Eqs. 9 and 15 combine to wall0 + d wall1 (FP64 here: they cancel exactly for a
+  // balanced wall, which keeps the FP32 force free of the cancellation).
+  const double G3 = 1.5 * I.G2, pr = I.psi_ref, mixd = 0.5 * (1.0 - I.beta);
+  c.wall0 = Real(-G3 * (I.beta + mixd) * pr * pr + I.Gwet_psiw * pr / 6.0);
+  c.wall1 = Real(-G3 * I.beta * pr + I.Gwet_psiw / 6.0);
+  c.rho_ref_minus_avg = Real(I.rho_ref - rho_avg_prev);
+}
+
 // ---------------------------------------------------------------------------
 // The fused kernel.  MODE_STEP advances one step; MODE_FIELDS writes rho, u_act
 // and T (FP64) of the current state to the spare f buffer; MODE_POPS writes
 // the post-stream populations to the spare buffers; MODE_MOMENTS only folds
 // the mean density into the buoyancy slot of the previous step.
 // ---------------------------------------------------------------------------
-template <typename Real, bool THERMAL, int W, int MODE>
-__global__ void __launch_bounds__(W + 32, (sizeof(Real) == 4 ? (W <= 64 ? 6 : (W <= 128 ? 3 : 2))
-                                                              : (W <= 64 ? 4 : (W <= 128 ? 2 : 1))))
+template <typename Real, bool THERMAL, int B, int MODE>
+__global__ void __launch_bounds__(B, (sizeof(Real) == 4 ? (B <= 64 ? 10 : (B <= 128 ? 5 : 2))
+                                                        : (B <= 64 ? 4 : (B <= 128 ? 2 : 1))))
 lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) {
-  constexpr int BLOCK = W + 32;
-  constexpr int NS = W + 4;
+  constexpr int BLOCK = B;
+  constexpr int W = out_cols<B>();
+  constexpr int NS = B - 4;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  Real* const sF = reinterpret_cast<Real*>(dyn_smem);               // [F_SLOTS][9][NS]
+  Real* const sG = sF + F_SLOTS * 9 * NS;                           // [G_SLOTS][9][NS]
+  Real* const sPsi = sG + (THERMAL ? G_SLOTS * 9 * NS : 0);         // [3][NS]
+  Real* const sUx = sPsi + 3 * NS;                                  // [3][NS]
+  Real* const sUy = sUx + 3 * NS;                                   // [3][NS]
   __shared__ Inst sI;
-  __shared__ Real sPsi[3][NS];
-  __shared__ Real sUx[3][NS];
-  __shared__ Real sUy[3][NS];
-  __shared__ Real sG[THERMAL ? 3 : 1][9][THERMAL ? W : 1];
+  __shared__ KConst<Real> sC;
   __shared__ double sRed[BLOCK / 32][NPART];
   __shared__ int sLast;
 
@@ -108,11 +221,13 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
     for (int k = tid; k < (int)(sizeof(Inst) / 4); k += BLOCK) dst[k] = src[k];
   }
   __syncthreads();
-
-  const int nx = sI.nx, ny = sI.ny, pitch = sI.pitch;
-  const long long plane = sI.plane;
   InstState* st = sI.st;
   const long long step = st->step;
+  if (tid == 0) fill_consts<Real>(sC, sI, st->rho_avg[(step - 1) & 1]);
+  __syncthreads();
+
+  const int nx = sI.nx, ny = sI.ny, pitch = sI.pitch;
+  const int plane = (int)sI.plane;  // the host guarantees 9 * plane < 2^31
   const bool local = st->local_read != 0;
   const bool perx = sI.geometry != GEOM_CHANNEL;
   const bool pery = sI.geometry == GEOM_PERIODIC;
@@ -123,44 +238,20 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
   const Real* __restrict__ Gin = static_cast<const Real*>(sI.g[step & 1]);
   Real* __restrict__ Fout = static_cast<Real*>(sI.f[(step + 1) & 1]);
   Real* __restrict__ Gout = static_cast<Real*>(sI.g[(step + 1) & 1]);
+  const Real rho_ref = sC.rho_ref, T_ref = sC.T_ref, T0 = sC.T0;
 
-  // constants in the compute precision
-  const Real omega_f = Real(sI.omega_f), omega_g = Real(sI.omega_g);
-  const Real pa = Real(sI.a), pb = Real(sI.b), pR = Real(sI.R), kappa = Real(sI.kappa);
-  const Real sqrtTc = Real(sI.sqrtTc), inv_sqrtTc = Real(sI.inv_sqrtTc);
-  const Real psi_scale = Real(sI.psi_scale), beta = Real(sI.beta);
-  const Real G2 = Real(sI.G2), Gh = Real(sI.Ghalf), Gwet_psiw = Real(sI.Gwet_psiw);
-  const Real g_a = Real(sI.g_a), inv_cv = Real(sI.inv_cv);
-  const Real T0 = Real(sI.T0), rho_ref = Real(sI.rho_ref), T_ref = Real(sI.T_ref);
-  const Real alpha0 = Real(sI.alpha0), u_in = Real(sI.u_in), rho_out = Real(sI.rho_out);
-  const Real drho_out = Real(sI.rho_out - sI.rho_ref);
-  const Real dT_in = Real(sI.T_in - sI.T_ref), dT_heat = Real(sI.T_heat - sI.T_ref);
-  const Real rho_avg_prev = Real(st->rho_avg[(step - 1) & 1]);
-  // heater state of the boundary condition that produced the pulled populations (step n-1)
-  const bool heat_bc = THERMAL && sI.heater_len > 0 && (step - 1) >= sI.heat_on_step;
-  const int hx0 = sI.heater_x0, hx1 = sI.heater_x0 + sI.heater_len;
-
-  // column owned by this thread
-  int s, xc;
-  if (tid < W) {
-    s = tid + 2;
-    xc = tile.x0 + tid;
-  } else if (tid < W + 4) {
-    const int h = tid - W;
-    s = (h < 2) ? h : W + h;
-    xc = tile.x0 - 2 + s;
-  } else {
-    s = -1;
-    xc = 0;
-  }
+  // column owned by this thread: x0 - 2 + tid (two halo columns on each side of the W outputs)
+  const int s = tid < NS ? tid : 0;
+  const int xc = tile.x0 - 2 + s;
+  const bool lane_used = tid < NS;
   int xn = xc;
-  bool col_ok = s >= 0;
+  bool col_ok = lane_used;
   if (perx) {
     xn = wrap_index(xc, nx);
   } else {
     col_ok = col_ok && xc >= 0 && xc < nx;
   }
-  const bool out_col = tid < W && xc < nx;
+  const bool out_col = tid >= 2 && tid < W + 2 && xc < nx;
   const bool f_col = col_ok && s >= 1 && s <= W + 2;
   // shared-memory neighbours; at the open ends the ghost column repeats the end column
   const int sm = (!perx && xc == 0) ? s : s - 1;
@@ -172,79 +263,134 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
   }
   const bool inl = channel && xn == 0;
   const bool outl = channel && xn == nx - 1;
-
-  // per-thread diagnostics accumulators
-  double acc[NPART] = {0.0, 0.0, 0.0, 0.0, 0.0};
-
-  // registers carried between iterations: row r-1 (f collision) and r-2 (g collision)
-  Real fp[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) fp[i] = Real(0);
-  Real rho_p = Real(1), drho_p = Real(0), ux_p = Real(0), uy_p = Real(0), T_p = T0, dT_p = Real(0),
-       coef_p = Real(0);
-  Real T_p2 = T0, dT_p2 = Real(0), coef_p2 = Real(0);
+  const bool inner_col = xn >= 1 && xn <= nx - 2;  // no wrap and no open end on either side
 
   const int nrow = tile.y1 - tile.y0;
   const int kbeg = (MODE == MODE_STEP) ? 0 : (MODE == MODE_FIELDS ? 1 : 2);
   const int kend = (MODE == MODE_STEP) ? nrow + 4 : (MODE == MODE_FIELDS ? nrow + 3 : nrow + 2);
-  int k3 = kbeg % 3;
 
+  // Issue the asynchronous pull of row index k (row y0 - 2 + k) into ring slots
+  // (fslot, gslot).  Interior links copy f*_i(x - c_i); links from a wall row copy
+  // f*_opp(x) (halfway bounce-back; the g sign flip and wall temperature are
+  // applied when the row is read); links from outside an open end are filled at
+  // read time.
+  auto issue_row = [&](int k, int fslot, int gslot) {
+    if (col_ok && k < kend) {
+      const int r = tile.y0 - 2 + k;
+      if (pery || (r >= 0 && r < ny)) {
+        const int rn = pery ? wrap_index(r, ny) : r;
+        Real* f_dst = sF + fslot * 9 * NS + s;
+        Real* g_dst = sG + gslot * 9 * NS + s;
+        const int node = rn * pitch + xn;
+        const Real* fn = Fin + node;
+        const Real* gn = Gin + node;
+        if (local) {
+#pragma unroll
+          for (int i = 0; i < 9; ++i) {
+            cp_async_elem(f_dst + i * NS, fn + i * plane);
+            if (THERMAL) cp_async_elem(g_dst + i * NS, gn + i * plane);
+          }
+        } else if (inner_col && rn >= 1 && rn <= ny - 2) {
+          // interior: the source of link i is node - c_iy * pitch - c_ix in plane i
+#pragma unroll
+          for (int i = 0; i < 9; ++i) {
+            const int off = i * plane - lat_cy(i) * pitch - lat_cx(i);
+            cp_async_elem(f_dst + i * NS, fn + off);
+            if (THERMAL) cp_async_elem(g_dst + i * NS, gn + off);
+          }
+        } else {
+          int rm = rn - 1, rp = rn + 1;
+          if (pery) {
+            if (rm < 0) rm += ny;
+            if (rp >= ny) rp -= ny;
+          }
+          const bool wlo = !pery && rn == 0;
+          const bool whi = !pery && rn == ny - 1;
+#pragma unroll
+          for (int i = 0; i < 9; ++i) {
+            const int cxi = lat_cx(i), cyi = lat_cy(i);
+            const bool wall = (cyi == 1 && wlo) || (cyi == -1 && whi);
+            const bool unknown = (cxi == 1 && inl) || (cxi == -1 && outl);
+            int src;
+            int pl = i;
+            if (wall) {
+              src = node;
+              pl = lat_opp(i);
+            } else if (!unknown) {
+              src = (cyi == 1 ? rm : (cyi == -1 ? rp : rn)) * pitch + (cxi == 1 ? xm : (cxi == -1 ? xp : xn));
+            } else {
+              continue;
+            }
+            cp_async_elem(f_dst + i * NS, Fin + pl * plane + src);
+            if (THERMAL) cp_async_elem(g_dst + i * NS, Gin + pl * plane + src);
+          }
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
+  // per-thread diagnostics partials over this band (in the compute precision)
+  Real acc_m = Real(0), acc_e = Real(0), acc_h = Real(0), acc_fi = Real(0), acc_fo = Real(0);
+
+  // scalars carried between iterations: row r-1 (f collision), row r-2 (g collision)
+  Real rho_p = Real(1), drho_p = Real(0), ux_p = Real(0), uy_p = Real(0), T_p = T0, dT_p = Real(0),
+       coef_p = Real(0);
+  Real T_p2 = T0, dT_p2 = Real(0), coef_p2 = Real(0);
+
+  // ring slots: f and psi/u rings have 3 slots (row index mod 3), g has 4 (mod 4)
+  int f_cur = kbeg % F_SLOTS, g_cur = kbeg % G_SLOTS;
+  issue_row(kbeg, f_cur, g_cur);
   for (int k = kbeg; k < kend; ++k) {
     const int r = tile.y0 - 2 + k;
-    // ===================== Phase A: pull row r, moments, EOS =====================
+    const int f_next = (f_cur == F_SLOTS - 1) ? 0 : f_cur + 1;
+    const int f_prev = (f_cur == 0) ? F_SLOTS - 1 : f_cur - 1;  // row r-1
+    const int f_prev2 = (f_prev == 0) ? F_SLOTS - 1 : f_prev - 1;  // row r-2 (= r+1)
+    const int g_next = (g_cur + 1) & (G_SLOTS - 1);
+    const int g_prev2 = (g_cur + 2) & (G_SLOTS - 1);  // row r-2
+    issue_row(k + 1, f_next, g_next);
+    cp_async_wait_1();  // this thread's copies of row k have landed
+
+    // ===================== Phase A: row r: boundary fill, moments, EOS =====================
     const bool row_ok = pery || (r >= 0 && r < ny);
     const int rn = pery ? wrap_index(r, ny) : r;
-    Real fc[9], gc[9];
     Real rho_c = Real(1), drho_c = Real(0), ux_c = Real(0), uy_c = Real(0), T_c = T0, dT_c = Real(0),
          coef_c = Real(0);
     if (col_ok && row_ok) {
-      const long long node = (long long)rn * pitch + xn;
-      if (local) {
+      Real* fs = sF + f_cur * 9 * NS + s;
+      Real* gs = sG + g_cur * 9 * NS + s;
+      Real fc[9], gc[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          fc[i] = ld_ro(Fin + i * plane + node);
-          gc[i] = THERMAL ? ld_ro(Gin + i * plane + node) : Real(0);
-        }
-      } else {
-        int rm = rn - 1, rp = rn + 1;
-        if (pery) {
-          if (rm < 0) rm += ny;
-          if (rp >= ny) rp -= ny;
-        }
-        const bool wlo = !pery && rn == 0;       // links with c_y = +1 come from the bottom wall
-        const bool whi = !pery && rn == ny - 1;  // links with c_y = -1 come from the top wall
+      for (int i = 0; i < 9; ++i) {
+        fc[i] = fs[i * NS];
+        gc[i] = THERMAL ? gs[i * NS] : Real(0);
+      }
+      const bool wlo = !pery && rn == 0;
+      const bool whi = !pery && rn == ny - 1;
+      if (!local && (wlo || whi || inl || outl)) {
+        const long long node = (long long)rn * pitch + xn;
+        const Real dT_in = sC.dT_in;
+        if (THERMAL && (wlo || whi)) {
+          // anti-bounce-back at the wall temperature (the heater heats the bottom wall
+          // once the boundary condition of step heat_on_step has been applied)
+          const bool heat_bc = sI.heater_len > 0 && (step - 1) >= sI.heat_on_step;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          const int cxi = lat_cx(i), cyi = lat_cy(i);
-          const bool wall = (cyi == 1 && wlo) || (cyi == -1 && whi);
-          const bool unknown = (cxi == 1 && inl) || (cxi == -1 && outl);
-          if (wall) {
-            // halfway bounce-back (f), anti-bounce-back at the wall temperature (g), Sec. 2.C
-            fc[i] = ld_ro(Fin + lat_opp(i) * plane + node);
-            if (THERMAL) {
+          for (int i = 0; i < 9; ++i) {
+            const int cxi = lat_cx(i), cyi = lat_cy(i);
+            if ((cyi == 1 && wlo) || (cyi == -1 && whi)) {
               Real dTw = dT_in;
               if (cyi == 1 && heat_bc) {
                 int sx = xn - cxi;
                 if (perx) sx = wrap_index(sx, nx);
-                if (sx >= hx0 && sx < hx1) dTw = dT_heat;
+                if (sx >= sI.heater_x0 && sx < sI.heater_x0 + sI.heater_len) dTw = sC.dT_heat;
               }
-              gc[i] = -ld_ro(Gin + lat_opp(i) * plane + node) + Real(2) * lat_w<Real>(i) * dTw;
-            } else {
-              gc[i] = Real(0);
+              gc[i] = -gc[i] + Real(2) * lat_w<Real>(i) * dTw;
             }
-          } else if (!unknown) {
-            const int sxx = cxi == 1 ? xm : (cxi == -1 ? xp : xn);
-            const int syy = cyi == 1 ? rm : (cyi == -1 ? rp : rn);
-            const long long src = (long long)syy * pitch + sxx;
-            fc[i] = ld_ro(Fin + i * plane + src);
-            gc[i] = THERMAL ? ld_ro(Gin + i * plane + src) : Real(0);
-          } else {
-            fc[i] = Real(0);
-            gc[i] = Real(0);
           }
         }
         if (inl) {
           // velocity inlet (Zou-He non-equilibrium bounce-back), u = (u_in, 0)
+          const Real u_in = sC.u_in;
           const Real S = fc[0] + fc[2] + fc[4] + Real(2) * (fc[3] + fc[6] + fc[7]);
           const Real rho_b = (S + rho_ref) / (Real(1) - u_in);
           const Real ru = rho_b * u_in;
@@ -269,6 +415,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
         }
         if (outl) {
           // pressure outlet (Zou-He), rho = rho_out, u_y = 0
+          const Real drho_out = sC.drho_out;
           if (wlo) {
             fc[7] = fc[2] + fc[5] + fc[6] - fc[4] - fc[8];
             fc[3] = drho_out - (fc[0] + fc[1] + fc[2] + fc[4] + fc[5] + fc[6] + fc[7] + fc[8]);
@@ -277,7 +424,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
             fc[3] = drho_out - (fc[0] + fc[1] + fc[2] + fc[4] + fc[5] + fc[6] + fc[7] + fc[8]);
           } else {
             const Real S = fc[0] + fc[2] + fc[4] + Real(2) * (fc[1] + fc[5] + fc[8]);
-            const Real ru = S + rho_ref - rho_out;  // rho_out * u_x
+            const Real ru = S - drho_out;  // rho_out * u_x
             const Real h = Real(0.5) * (fc[2] - fc[4]);
             fc[3] = fc[1] - Real(2.0 / 3.0) * ru;
             fc[7] = fc[5] + h - ru * Real(1.0 / 6.0);
@@ -285,11 +432,15 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
           }
           if (THERMAL) {
             // zero temperature gradient: the post-stream populations of node nx-2
-            const long long col = xn;
-            gc[3] = ld_ro(Gin + 3 * plane + (long long)rn * pitch + col);
-            if (!wlo) gc[6] = ld_ro(Gin + 6 * plane + (long long)(rn - 1) * pitch + col);
-            if (!whi) gc[7] = ld_ro(Gin + 7 * plane + (long long)(rn + 1) * pitch + col);
+            gc[3] = ld_ro(Gin + 3 * plane + node);
+            if (!wlo) gc[6] = ld_ro(Gin + 6 * plane + node - pitch);
+            if (!whi) gc[7] = ld_ro(Gin + 7 * plane + node + pitch);
           }
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          fs[i * NS] = fc[i];
+          if (THERMAL) gs[i * NS] = gc[i];
         }
       }
 
@@ -298,7 +449,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
       rho_c = rho_ref + drho_c;
       const Real jx = (fc[1] - fc[3]) + (fc[5] - fc[6]) + (fc[8] - fc[7]);
       const Real jy = (fc[2] - fc[4]) + (fc[5] + fc[6]) - (fc[7] + fc[8]);
-      const Real inv_rho = Real(1) / rho_c;
+      const Real inv_rho = fast_rcp(rho_c);
       ux_c = jx * inv_rho;
       uy_c = jy * inv_rho;
       if (THERMAL) {
@@ -306,45 +457,66 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
         T_c = T_ref + dT_c;
       }
 
-      // Peng-Robinson EOS (Eq. 12), pseudopotential (Eq. 11), (dp/dT)_rho
-      Real psi = Real(0), p = rho_c * Real(1.0 / 3.0), dpdT = Real(0);
+      // Peng-Robinson EOS (Eq. 12), pseudopotential (Eq. 11), (dp/dT)_rho.  The shared
+      // ring holds dpsi = psi - psi_ref: psi itself in FP64 (psi_ref = 0); in FP32 the
+      // deviation from the reference state, from exact difference forms of Eq. 12 in
+      // rho - rho_ref and T - T_ref, so that neighbour differences in the force keep
+      // their low-order bits.
+      Real dpsi = Real(0), p = rho_c * Real(1.0 / 3.0), dpdT = Real(0);
       bool bad = !(rho_c > Real(0));
       if (multiphase) {
+        const Real pa = sC.a, pb = sC.b, pR = sC.R, kappa = sC.kappa, inv_sqrtTc = sC.inv_sqrtTc;
         const Real br = pb * rho_c;
-        const Real inv1 = Real(1) / (Real(1) - br);
-        const Real rr_den = rho_c * rho_c / (Real(1) + br * (Real(2) - br));
-        Real alpha, sa = Real(0), sT = Real(0);
+        const Real inv1 = fast_rcp(Real(1) - br);
+        const Real invD = fast_rcp(Real(1) + br * (Real(2) - br));
+        const Real rr_den = rho_c * rho_c * invD;
+        Real alpha, sa = Real(0), inv_sT = Real(0), sT = Real(0);
         if (THERMAL) {
-          sT = sqrt(T_c);
+          inv_sT = fast_rsqrt(T_c);
+          sT = T_c * inv_sT;
           sa = Real(1) + kappa * (Real(1) - sT * inv_sqrtTc);
           alpha = sa * sa;
         } else {
-          alpha = alpha0;
+          alpha = sC.alpha0;
         }
-        p = rho_c * pR * T_c * inv1 - pa * alpha * rr_den;
-        const Real rad = (p - rho_c * Real(1.0 / 3.0)) * psi_scale;
+        Real rad;
+        if (sizeof(Real) == 4) {
+          const Real rr = rho_ref, inv_u1r = sC.inv_u1r;
+          const Real dA = pR * (drho_c * T_c * inv1 * inv_u1r + (THERMAL ? rr * dT_c * inv_u1r : Real(0)));
+          Real dB = pa * alpha * drho_c * (rho_c + rr + Real(2) * pb * rho_c * rr) * invD * sC.inv_Dr;
+          if (THERMAL) {
+            const Real dsa = -kappa * inv_sqrtTc * dT_c * fast_rcp(sT + sC.sqrtT_r);
+            dB += pa * dsa * (sa + sC.sa_r) * sC.rr2_Dr;
+          }
+          const Real dp = dA - dB;
+          const Real drad = (dp - drho_c * Real(1.0 / 3.0)) * sC.psi_scale;
+          rad = sC.rad_ref + drad;
+          const Real psi = fast_sqrt(fmax(rad, Real(0)));
+          const Real den = psi + sC.psi_ref;
+          dpsi = den > Real(0) ? drad * fast_rcp(den) : Real(0);
+          p = sC.p_ref + dp;
+        } else {
+          p = rho_c * pR * T_c * inv1 - pa * alpha * rr_den;
+          rad = (p - rho_c * Real(1.0 / 3.0)) * sC.psi_scale;
+          dpsi = fast_sqrt(fmax(rad, Real(0)));
+        }
         bad = bad || !(br < Real(1)) || !(rad >= Real(0));
-        psi = sqrt(fmax(rad, Real(0)));
         if (THERMAL) {
-          const Real dalpha = -kappa * sa / (sT * sqrtTc);
+          const Real dalpha = -kappa * sa * inv_sT * inv_sqrtTc;
           dpdT = rho_c * pR * inv1 - pa * dalpha * rr_den;
         }
       }
       if (THERMAL) {
         bad = bad || !isfinite(T_c);
-        coef_c = T_c * (Real(1) - dpdT * inv_rho * inv_cv);
+        coef_c = T_c * (Real(1) - dpdT * inv_rho * sC.inv_cv);
       }
       if (bad) atomicOr(&st->status, STATUS_UNSTABLE);
-      sPsi[k3][s] = psi;
-      if (THERMAL && MODE == MODE_STEP && tid < W) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) sG[k3][i][tid] = gc[i];
-      }
+      sPsi[f_cur * NS + s] = dpsi;
       const bool out_row = r >= tile.y0 && r < tile.y1;
       if ((MODE == MODE_STEP || MODE == MODE_MOMENTS) && out_col && out_row) {
-        acc[0] += (double)rho_c;
-        acc[1] += (double)T_c;
-        if (THERMAL && !pery && rn == 0 && xn >= hx0 && xn < hx1) acc[2] += (double)T_c;
+        acc_m += drho_c;
+        acc_e += dT_c;
+        if (THERMAL && !pery && rn == 0 && xn >= sI.heater_x0 && xn < sI.heater_x0 + sI.heater_len) acc_h += dT_c;
         if (MODE == MODE_STEP && channel && rn == ny / 2 && (xn == 1 || xn == nx - 2)) {
           if (xn == 1) st->p_probe[0] = (double)p;
           if (xn == nx - 2) st->p_probe[1] = (double)p;
@@ -352,7 +524,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
         }
       }
       if (MODE == MODE_POPS && out_col && out_row) {
-        const long long o = (long long)rn * pitch + xn;
+        const int o = rn * pitch + xn;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
           Fout[i * plane + o] = fc[i];
@@ -361,15 +533,14 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
       }
     }
     if (MODE == MODE_POPS || MODE == MODE_MOMENTS) {
-      k3 = (k3 == 2) ? 0 : k3 + 1;
+      f_cur = f_next;
+      g_cur = g_next;
       continue;
     }
     __syncthreads();
 
     // ============ Phase B: row q = r - 1: force, u_act, f collision ============
     const int q = r - 1;
-    const int k3m1 = (k3 == 0) ? 2 : k3 - 1;  // slot of row r-1
-    const int k3m2 = (k3m1 == 0) ? 2 : k3m1 - 1;  // slot of row r-2
     // STEP needs u_act from row y0 - 1 (divergence at y0); FIELDS only on its output rows
     const int qmin = (MODE == MODE_STEP) ? tile.y0 - 1 : tile.y0;
     if (q >= qmin) {
@@ -379,59 +550,70 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
         const bool sol_p = !pery && q == ny - 1;  // row q+1 is the top wall
         Real Fx = Real(0), Fy = Real(0);
         if (multiphase) {
-          const Real pc = sPsi[k3m1][s];
-          const Real pE = sPsi[k3m1][sp], pW = sPsi[k3m1][sm];
-          Real pN = Real(0), pNE = Real(0), pNW = Real(0), pS = Real(0), pSE = Real(0), pSW = Real(0);
+          // ring values are d = psi - psi_ref (psi_ref = 0 in FP64); solid neighbours carry d = 0
+          const Real* P0 = sPsi + f_prev * NS;
+          const Real dc = P0[s];
+          const Real dE = P0[sp], dW = P0[sm];
+          Real dN = Real(0), dNE = Real(0), dNW = Real(0), dS = Real(0), dSE = Real(0), dSW = Real(0);
           if (!sol_p) {
-            pN = sPsi[k3][s];
-            pNE = sPsi[k3][sp];
-            pNW = sPsi[k3][sm];
+            const Real* Pp = sPsi + f_cur * NS;
+            dN = Pp[s];
+            dNE = Pp[sp];
+            dNW = Pp[sm];
           }
           if (!sol_m) {
-            pS = sPsi[k3m2][s];
-            pSE = sPsi[k3m2][sp];
-            pSW = sPsi[k3m2][sm];
+            const Real* Pm = sPsi + f_prev2 * NS;
+            dS = Pm[s];
+            dSE = Pm[sp];
+            dSW = Pm[sm];
           }
-          // Eq. 9 sums over fluid neighbours: sum G_i psi(x1) c_i and sum G_i psi(x1)^2 c_i
-          const Real s1x = G2 * (pE - pW) + Gh * ((pNE - pNW) + (pSE - pSW));
-          const Real s1y = G2 * (pN - pS) + Gh * ((pNE + pNW) - (pSE + pSW));
-          const Real s2x = G2 * (pE * pE - pW * pW) + Gh * ((pNE * pNE - pNW * pNW) + (pSE * pSE - pSW * pSW));
-          const Real s2y = G2 * (pN * pN - pS * pS) + Gh * ((pNE * pNE + pNW * pNW) - (pSE * pSE + pSW * pSW));
-          const Real mix = Real(0.5) * (Real(1) - beta);
-          Fx = -beta * pc * s1x - mix * s2x;
-          Fy = -beta * pc * s1y - mix * s2y;
-          // Eq. 15: solid neighbours, sum_i w_i c_iy = -1/6 below, +1/6 above
-          Real wy = Real(0);
-          if (sol_m) wy -= Real(1.0 / 6.0);
-          if (sol_p) wy += Real(1.0 / 6.0);
-          Fy -= Gwet_psiw * pc * wy;
+          // Eq. 9 over fluid neighbours with psi = psi_ref + d: the beta-mixed sums reduce to
+          // F = -(psi_ref + beta d_c) t1 - (1 - beta)/2 t2, t1 = sum G_i d_i c_i,
+          // t2 = sum G_i d_i^2 c_i, plus the wall rows' reference parts with Eq. 15.
+          const Real G2 = sC.G2, Gh = sC.Gh;
+          const Real t1x = G2 * (dE - dW) + Gh * ((dNE - dNW) + (dSE - dSW));
+          const Real t1y = G2 * (dN - dS) + Gh * ((dNE + dNW) - (dSE + dSW));
+          const Real t2x = G2 * (dE - dW) * (dE + dW) + Gh * ((dNE - dNW) * (dNE + dNW) + (dSE - dSW) * (dSE + dSW));
+          const Real t2y = G2 * (dN - dS) * (dN + dS) + Gh * ((dNE - dSE) * (dNE + dSE) + (dNW - dSW) * (dNW + dSW));
+          const Real lead = sC.psi_ref + sC.beta * dc;
+          Fx = -lead * t1x - sC.mix * t2x;
+          Fy = -lead * t1y - sC.mix * t2y;
+          if (sol_m) Fy += sC.wall0 + dc * sC.wall1;
+          if (sol_p) Fy -= sC.wall0 + dc * sC.wall1;
         }
-        Fy -= (rho_p - rho_avg_prev) * g_a;  // Eq. 14, gravity along -y
-        const Real inv_rho = Real(1) / rho_p;
+        Fy -= (drho_p + sC.rho_ref_minus_avg) * sC.g_a;  // Eq. 14, gravity along -y
+        const Real inv_rho = fast_rcp(rho_p);
         const Real dux = Fx * inv_rho, duy = Fy * inv_rho;
         const Real uax = ux_p + Real(0.5) * dux, uay = uy_p + Real(0.5) * duy;  // Eq. 7
-        sUx[k3m1][s] = uax;
-        sUy[k3m1][s] = uay;
+        sUx[f_prev * NS + s] = uax;
+        sUy[f_prev * NS + s] = uay;
         const bool out_q = out_col && q >= tile.y0 && q < tile.y1;
         if (MODE == MODE_STEP && out_q) {
           // BGK toward f^eq(rho, u_eq) (Eqs. 2-3) plus the exact-difference term (Eq. 5),
-          // written as the difference of the two equilibria expanded in du
+          // written pairwise over opposite directions i, i': with cu = c_i.u, cd = c_i.du and
+          // cs = c_i.(2u + du), omega f^eq_i + F_i = w_i (K + 4.5 rho (omega cu^2 + cd cs))
+          // + 3 w_i rho (omega cu + cd), K = omega (drho - 1.5 rho u.u) - 1.5 rho du.(2u + du);
+          // the direction i' flips the sign of the second term only.
+          const Real omega_f = sC.omega_f;
           const Real sx = Real(2) * ux_p + dux, sy = Real(2) * uy_p + duy;
           const Real usq = ux_p * ux_p + uy_p * uy_p;
-          const Real dsum = dux * sx + duy * sy;
-          const long long o = (long long)q * pitch + xn;
-#pragma unroll
-          for (int i = 0; i < 9; ++i) {
-            const Real cu = Real(lat_cx(i)) * ux_p + Real(lat_cy(i)) * uy_p;
-            const Real cd = Real(lat_cx(i)) * dux + Real(lat_cy(i)) * duy;
-            const Real cs = Real(lat_cx(i)) * sx + Real(lat_cy(i)) * sy;
-            const Real wi = lat_w<Real>(i);
-            const Real feq = wi * (drho_p + rho_p * (Real(3) * cu + Real(4.5) * cu * cu - Real(1.5) * usq));
-            const Real Fi = wi * rho_p * (Real(3) * cd + Real(4.5) * cd * cs - Real(1.5) * dsum);
-            Fout[i * plane + o] = fp[i] + omega_f * (feq - fp[i]) + Fi;
-          }
-          if (channel && xn == 0) acc[3] += (double)rho_p * (double)uax;
-          if (channel && xn == nx - 1) acc[4] += (double)rho_p * (double)uax;
+          const Real K = omega_f * (drho_p - Real(1.5) * rho_p * usq) - Real(1.5) * rho_p * (dux * sx + duy * sy);
+          const Real r45 = Real(4.5) * rho_p, r3 = Real(3) * rho_p, keep = Real(1) - omega_f;
+          const Real* fs = sF + f_prev * 9 * NS + s;
+          Real* fo = Fout + (q * pitch + xn);
+          auto pair = [&](int i, int j, Real cu, Real cd, Real cs, Real w) {
+            const Real sym = w * (K + r45 * (omega_f * cu * cu + cd * cs));
+            const Real anti = w * r3 * (omega_f * cu + cd);
+            fo[i * plane] = keep * fs[i * NS] + sym + anti;
+            fo[j * plane] = keep * fs[j * NS] + sym - anti;
+          };
+          fo[0] = keep * fs[0] + lat_w<Real>(0) * K;
+          pair(1, 3, ux_p, dux, sx, lat_w<Real>(1));
+          pair(2, 4, uy_p, duy, sy, lat_w<Real>(2));
+          pair(5, 7, ux_p + uy_p, dux + duy, sx + sy, lat_w<Real>(5));
+          pair(6, 8, uy_p - ux_p, duy - dux, sy - sx, lat_w<Real>(6));
+          if (channel && xn == 0) acc_fi += rho_p * uax;
+          if (channel && xn == nx - 1) acc_fo += rho_p * uax;
         }
         if (MODE == MODE_FIELDS && out_q) {
           double* out = static_cast<double*>(sI.f[(step + 1) & 1]);
@@ -451,32 +633,38 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
       const int q2 = r - 2;
       if (out_col && q2 >= tile.y0 && q2 < tile.y1) {
         // second-order central differences of u_act; zero at solid rows, ghost copy at open ends
-        const Real uxE = sUx[k3m2][sp], uxW = sUx[k3m2][sm];
-        const Real uyN = (!pery && q2 == ny - 1) ? Real(0) : sUy[k3m1][s];
-        const int k3m3 = (k3m2 == 0) ? 2 : k3m2 - 1;
-        const Real uyS = (!pery && q2 == 0) ? Real(0) : sUy[k3m3][s];
+        const Real uxE = sUx[f_prev2 * NS + sp], uxW = sUx[f_prev2 * NS + sm];
+        const Real uyN = (!pery && q2 == ny - 1) ? Real(0) : sUy[f_prev * NS + s];
+        const Real uyS = (!pery && q2 == 0) ? Real(0) : sUy[f_cur * NS + s];  // slot of row r-3
         const Real divu = Real(0.5) * (uxE - uxW) + Real(0.5) * (uyN - uyS);
         const Real phi = coef_p2 * divu;  // second Eq. 19
-        const Real uax = sUx[k3m2][s], uay = sUy[k3m2][s];
+        const Real uax = sUx[f_prev2 * NS + s], uay = sUy[f_prev2 * NS + s];
+        // Eq. 16 with g^eq of Eq. 18, pairwise over opposite directions as for f:
+        // omega g^eq_i + w_i phi = w_i (Kg + 4.5 omega T cu^2) + 3 w_i omega T cu
+        const Real omega_g = sC.omega_g;
         const Real usq = uax * uax + uay * uay;
-        const long long o = (long long)q2 * pitch + xn;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          const Real cu = Real(lat_cx(i)) * uax + Real(lat_cy(i)) * uay;
-          const Real wi = lat_w<Real>(i);
-          const Real geq = wi * (dT_p2 + T_p2 * (Real(3) * cu + Real(4.5) * cu * cu - Real(1.5) * usq));
-          const Real gi = sG[k3m2][i][tid];
-          Gout[i * plane + o] = gi + omega_g * (geq - gi) + wi * phi;  // Eq. 16
-        }
+        const Real Kg = omega_g * (dT_p2 - Real(1.5) * T_p2 * usq) + phi;
+        const Real t45 = Real(4.5) * omega_g * T_p2, t3 = Real(3) * omega_g * T_p2, keep = Real(1) - omega_g;
+        const Real* gs = sG + g_prev2 * 9 * NS + s;
+        Real* go = Gout + (q2 * pitch + xn);
+        auto pair = [&](int i, int j, Real cu, Real w) {
+          const Real sym = w * (Kg + t45 * cu * cu);
+          const Real anti = w * t3 * cu;
+          go[i * plane] = keep * gs[i * NS] + sym + anti;
+          go[j * plane] = keep * gs[j * NS] + sym - anti;
+        };
+        go[0] = keep * gs[0] + lat_w<Real>(0) * Kg;
+        pair(1, 3, uax, lat_w<Real>(1));
+        pair(2, 4, uay, lat_w<Real>(2));
+        pair(5, 7, uax + uay, lat_w<Real>(5));
+        pair(6, 8, uay - uax, lat_w<Real>(6));
       }
     }
 
-    // rotate the carried rows
+    // rotate the carried rows and ring slots
     T_p2 = T_p;
     dT_p2 = dT_p;
     coef_p2 = coef_p;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) fp[i] = fc[i];
     rho_p = rho_c;
     drho_p = drho_c;
     ux_p = ux_c;
@@ -484,12 +672,14 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
     T_p = T_c;
     dT_p = dT_c;
     coef_p = coef_c;
-    k3 = (k3 == 2) ? 0 : k3 + 1;
+    f_cur = f_next;
+    g_cur = g_next;
   }
 
   if (MODE != MODE_STEP && MODE != MODE_MOMENTS) return;
 
   // ---------------- per-tile partials and the last-CTA fold ----------------
+  double acc[NPART] = {(double)acc_m, (double)acc_e, (double)acc_h, (double)acc_fi, (double)acc_fo};
   block_sum<BLOCK>(acc, sRed);
   if (tid == 0) {
     double* part = sI.partials + (long long)tile.local * NPART;
@@ -510,15 +700,18 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
   __syncthreads();
   block_sum<BLOCK>(tot, sRed);
   if (tid == 0) {
+    // the partials are sums of deviations from the storage references
     const double n = (double)nx * (double)ny;
-    const double mass = tot[0], energy = tot[1];
+    const double mass = tot[0] + n * sI.rho_ref;
+    const double energy = THERMAL ? tot[1] + n * sI.T_ref : n * sI.T0;
     if (MODE == MODE_STEP) {
       double dtstar = 0.0;
       const bool heat_now = THERMAL && sI.heater_len > 0 && step >= sI.heat_on_step && !pery;
       if (heat_now) {
+        const int hx0 = sI.heater_x0, hx1 = sI.heater_x0 + sI.heater_len;
         int lo = hx0 < 0 ? 0 : hx0, hi = hx1 > nx ? nx : hx1;
         if (hi > lo) {
-          const double tnb = tot[2] / (double)(hi - lo);
+          const double tnb = tot[2] / (double)(hi - lo) + sI.T_ref;
           dtstar = (sI.T_heat - tnb) / (sI.T_heat - energy / n);
         }
       }
@@ -605,17 +798,34 @@ __global__ void lbm_init_builtin_kernel(const Inst* __restrict__ insts, InitSpec
 // ---------------------------------------------------------------------------
 // Host launchers for one storage precision.
 // ---------------------------------------------------------------------------
-template <typename Real, bool THERMAL, int W>
-cudaError_t launch_cols(int mode, const Inst* d_inst, const Tile* d_tiles, int ntiles, cudaStream_t s) {
-  dim3 grid(ntiles), block(W + 32);
-  switch (mode) {
-    case MODE_STEP: lbm_fused_kernel<Real, THERMAL, W, MODE_STEP><<<grid, block, 0, s>>>(d_inst, d_tiles); break;
-    case MODE_FIELDS: lbm_fused_kernel<Real, THERMAL, W, MODE_FIELDS><<<grid, block, 0, s>>>(d_inst, d_tiles); break;
-    case MODE_POPS: lbm_fused_kernel<Real, THERMAL, W, MODE_POPS><<<grid, block, 0, s>>>(d_inst, d_tiles); break;
-    case MODE_MOMENTS: lbm_fused_kernel<Real, THERMAL, W, MODE_MOMENTS><<<grid, block, 0, s>>>(d_inst, d_tiles); break;
-    default: return cudaErrorInvalidValue;
+template <typename Real, bool THERMAL, int B, int MODE>
+cudaError_t launch_one(const Inst* d_inst, const Tile* d_tiles, int ntiles, cudaStream_t s) {
+  constexpr size_t smem = fused_smem_bytes<Real, THERMAL, B>();
+  // the dynamic shared-memory opt-in is per device; remember which devices have it
+  static unsigned long long configured = 0ull;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(configured & bit)) {
+    e = cudaFuncSetAttribute(lbm_fused_kernel<Real, THERMAL, B, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    configured |= bit;
   }
+  lbm_fused_kernel<Real, THERMAL, B, MODE><<<ntiles, B, smem, s>>>(d_inst, d_tiles);
   return cudaGetLastError();
+}
+
+template <typename Real, bool THERMAL, int B>
+cudaError_t launch_cols(int mode, const Inst* d_inst, const Tile* d_tiles, int ntiles, cudaStream_t s) {
+  switch (mode) {
+    case MODE_STEP: return launch_one<Real, THERMAL, B, MODE_STEP>(d_inst, d_tiles, ntiles, s);
+    case MODE_FIELDS: return launch_one<Real, THERMAL, B, MODE_FIELDS>(d_inst, d_tiles, ntiles, s);
+    case MODE_POPS: return launch_one<Real, THERMAL, B, MODE_POPS>(d_inst, d_tiles, ntiles, s);
+    case MODE_MOMENTS: return launch_one<Real, THERMAL, B, MODE_MOMENTS>(d_inst, d_tiles, ntiles, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <typename Real>
@@ -626,10 +836,7 @@ cudaError_t launch_precision(int thermal, int cols, int mode, const Inst* d_inst
     switch (cols) {
       case 64: return launch_cols<Real, true, 64>(mode, d_inst, d_tiles, ntiles, s);
       case 128: return launch_cols<Real, true, 128>(mode, d_inst, d_tiles, ntiles, s);
-      case 256:
-        // three rows of nine FP64 planes for 256 columns exceed the 48 KB static shared memory
-        if (sizeof(Real) == 8) return cudaErrorInvalidValue;
-        return launch_cols<Real, true, (sizeof(Real) == 8 ? 128 : 256)>(mode, d_inst, d_tiles, ntiles, s);
+      case 256: return launch_cols<Real, true, 256>(mode, d_inst, d_tiles, ntiles, s);
     }
   } else {
     switch (cols) {
