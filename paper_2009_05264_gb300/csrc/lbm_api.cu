@@ -88,10 +88,12 @@ double host_pressure(const lbm_params& p, double rho, double T) {
   return rho * p.R * T / (1.0 - p.b * rho) - p.a * s * s * rho * rho / (1.0 + 2.0 * p.b * rho - p.b * p.b * rho * rho);
 }
 
-// Tiles of a kernel with `cols` threads per CTA, each writing cols - 8 columns.
+// Output columns of one tile: a CTA of `cols` threads writes cols - 8 columns.
+int tile_cols(int cols) { return cols - 8; }
+
 void build_tiles(int nx, int ny, int cols, int rows, std::vector<Tile>& out) {
   out.clear();
-  const int w = cols - 8;
+  const int w = tile_cols(cols);
   const int strips = (nx + w - 1) / w;
   const int bands = (ny + rows - 1) / rows;
   const int n = strips * bands;
@@ -112,7 +114,7 @@ void build_tiles(int nx, int ny, int cols, int rows, std::vector<Tile>& out) {
 // Rows per band for a tile width: enough CTAs to fill 152 SMs a few times over
 // while keeping the 4-row band overhead small.
 int default_rows(int nx, int ny, int cols) {
-  const int strips = (nx + cols - 9) / (cols - 8);
+  const int strips = (nx + tile_cols(cols) - 1) / tile_cols(cols);
   const long long target = 152LL * 8;
   long long rows = ((long long)ny * strips + target - 1) / target;
   rows = std::max<long long>(rows, 16);

@@ -16,17 +16,19 @@
 // rest-state weights, f_i - w_i rho_ref and g_i - w_i T_ref, which keeps the
 // low-order bits for the small non-equilibrium parts.
 //
-// Work decomposition: a CTA owns W output columns [x0, x0 + W) and a band of
-// rows [y0, y1), and marches up the band one row per iteration.  The force at
-// a node needs psi on its 8 neighbours, and the divergence of u_act in the g
-// source needs u_act (hence the force) on the 4 neighbours, so psi is needed
-// two nodes out.  Each CTA therefore keeps three-row rings in shared memory
-// of psi and u_act over W + 4 columns; W threads own the output columns and 4
-// lanes of a fifth warp compute the 2-column halos on each side.  At iteration
-// k the CTA pulls row r = y0 - 2 + k, computes force, u_act and the f
-// collision of row r - 1, and the g collision of row r - 2.  Populations are
-// read once per CTA (plus the halo columns and 4 rows per band), all loads and
-// stores of a warp are to consecutive addresses.
+// Work decomposition: a CTA of B threads (64, 128 or 256) owns B - 8 output
+// columns [x0, x0 + B - 8) and a band of rows [y0, y1), and marches up the band
+// one row per iteration.  Its threads map to the columns [x0 - 2, x0 + B - 6): the
+// outputs plus two halo columns per side (the last 4 lanes idle, so every CTA's
+// output starts on a 32-byte sector).  The force at a node needs psi on its 8
+// neighbours and the divergence of u_act in the g source needs u_act (hence the
+// force) on the 4 neighbours, so psi is needed two nodes out: the CTA keeps
+// three-row rings of psi and u_act in shared memory.  At iteration k it pulls
+// row r = y0 - 2 + k (phase A: boundary fill, moments, EOS), computes force, u_act
+// and the f collision of row r - 1 (phase B) and the g collision of row r - 2
+// (phase C), with a barrier after A and after B.  Each thread's pulled
+// populations are staged in its own shared-memory ring by cp.async, one row ahead,
+// so the loads of the next row are in flight during the arithmetic of this one.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -190,10 +192,355 @@ __device__ __forceinline__ void fill_consts(KConst<Real>& c, const Inst& I, doub
 }
 
 // ---------------------------------------------------------------------------
-// The fused kernel.  MODE_STEP advances one step; MODE_FIELDS writes rho, u_act
-// and T (FP64) of the current state to the spare f buffer; MODE_POPS writes
-// the post-stream populations to the spare buffers; MODE_MOMENTS only folds
-// the mean density into the buoyancy slot of the previous step.
+// Node-level pieces of the step, shared by the kernels below.
+// ---------------------------------------------------------------------------
+
+// Where a node sits relative to the boundaries of Sec. 2.C.
+struct NodeBC {
+  bool wlo, whi;  // links with c_y = +1 / -1 come from the bottom / top wall
+  bool inl, outl; // velocity inlet (x = 0) / pressure outlet (x = nx - 1)
+};
+
+// Complete the pulled populations of a boundary node in place.  Wall links were
+// pulled from the node's own opposite population (halfway bounce-back); here g on
+// those links gets the anti-bounce-back sign flip and wall temperature, and the
+// links from outside an open end are set by the Zou-He conditions.
+template <typename Real, bool THERMAL>
+__device__ __forceinline__ void boundary_fill(Real (&fc)[9], Real (&gc)[9], const NodeBC& nb, const Inst& I,
+                                              const KConst<Real>& C, const Real* __restrict__ Gin, int plane,
+                                              int pitch, int node, int xn, bool perx, long long step) {
+  const Real rho_ref = C.rho_ref;
+  const Real dT_in = C.dT_in;
+  if (THERMAL && (nb.wlo || nb.whi)) {
+    // anti-bounce-back at the wall temperature (the heater heats the bottom wall
+    // once the boundary condition of step heat_on_step has been applied)
+    const bool heat_bc = I.heater_len > 0 && (step - 1) >= I.heat_on_step;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int cxi = lat_cx(i), cyi = lat_cy(i);
+      if ((cyi == 1 && nb.wlo) || (cyi == -1 && nb.whi)) {
+        Real dTw = dT_in;
+        if (cyi == 1 && heat_bc) {
+          int sx = xn - cxi;
+          if (perx) sx = wrap_index(sx, I.nx);
+          if (sx >= I.heater_x0 && sx < I.heater_x0 + I.heater_len) dTw = C.dT_heat;
+        }
+        gc[i] = -gc[i] + Real(2) * lat_w<Real>(i) * dTw;
+      }
+    }
+  }
+  if (nb.inl) {
+    // velocity inlet (Zou-He non-equilibrium bounce-back), u = (u_in, 0)
+    const Real u_in = C.u_in;
+    const Real S = fc[0] + fc[2] + fc[4] + Real(2) * (fc[3] + fc[6] + fc[7]);
+    const Real rho_b = (S + rho_ref) / (Real(1) - u_in);
+    const Real ru = rho_b * u_in;
+    if (nb.wlo) {
+      fc[8] = fc[2] + fc[5] + fc[6] - fc[4] - fc[7];
+      fc[1] = ru - fc[5] - fc[8] + fc[3] + fc[6] + fc[7];
+    } else if (nb.whi) {
+      fc[5] = fc[4] + fc[7] + fc[8] - fc[2] - fc[6];
+      fc[1] = ru - fc[5] - fc[8] + fc[3] + fc[6] + fc[7];
+    } else {
+      const Real h = Real(0.5) * (fc[2] - fc[4]);
+      fc[1] = fc[3] + Real(2.0 / 3.0) * ru;
+      fc[5] = fc[7] - h + ru * Real(1.0 / 6.0);
+      fc[8] = fc[6] + h + ru * Real(1.0 / 6.0);
+    }
+    if (THERMAL) {
+      // anti-bounce-back at the inlet temperature
+      if (!nb.wlo) gc[5] = -ld_ro(Gin + 7 * plane + node) + Real(2) * lat_w<Real>(5) * dT_in;
+      if (!nb.whi) gc[8] = -ld_ro(Gin + 6 * plane + node) + Real(2) * lat_w<Real>(8) * dT_in;
+      gc[1] = -ld_ro(Gin + 3 * plane + node) + Real(2) * lat_w<Real>(1) * dT_in;
+    }
+  }
+  if (nb.outl) {
+    // pressure outlet (Zou-He), rho = rho_out, u_y = 0
+    const Real drho_out = C.drho_out;
+    if (nb.wlo) {
+      fc[7] = fc[2] + fc[5] + fc[6] - fc[4] - fc[8];
+      fc[3] = drho_out - (fc[0] + fc[1] + fc[2] + fc[4] + fc[5] + fc[6] + fc[7] + fc[8]);
+    } else if (nb.whi) {
+      fc[6] = fc[4] + fc[7] + fc[8] - fc[2] - fc[5];
+      fc[3] = drho_out - (fc[0] + fc[1] + fc[2] + fc[4] + fc[5] + fc[6] + fc[7] + fc[8]);
+    } else {
+      const Real S = fc[0] + fc[2] + fc[4] + Real(2) * (fc[1] + fc[5] + fc[8]);
+      const Real ru = S - drho_out;  // rho_out * u_x
+      const Real h = Real(0.5) * (fc[2] - fc[4]);
+      fc[3] = fc[1] - Real(2.0 / 3.0) * ru;
+      fc[7] = fc[5] + h - ru * Real(1.0 / 6.0);
+      fc[6] = fc[8] - h - ru * Real(1.0 / 6.0);
+    }
+    if (THERMAL) {
+      // zero temperature gradient: the post-stream populations of node nx-2
+      gc[3] = ld_ro(Gin + 3 * plane + node);
+      if (!nb.wlo) gc[6] = ld_ro(Gin + 6 * plane + node - pitch);
+      if (!nb.whi) gc[7] = ld_ro(Gin + 7 * plane + node + pitch);
+    }
+  }
+}
+
+// Macroscopic state of one node (compute precision; deviations from the references).
+template <typename Real>
+struct NodeState {
+  Real rho, drho, ux, uy, T, dT, coef;  // coef = T (1 - (dp/dT)_rho / (rho c_v)) of the source
+  Real dpsi;                             // psi - psi_ref (psi itself in FP64)
+  Real p;                                // EOS pressure (diagnostics)
+  bool bad;                              // outside the EOS domain
+};
+
+// Moments (Eqs. 4, 6, 17), Peng-Robinson EOS (Eq. 12), pseudopotential (Eq. 11) and
+// (dp/dT)_rho of one node.  In FP32 psi is evaluated as psi - psi_ref from exact
+// difference forms of Eq. 12 in rho - rho_ref and T - T_ref, so that neighbour
+// differences in the force keep their low-order bits.
+template <typename Real, bool THERMAL>
+__device__ __forceinline__ NodeState<Real> node_state(const Real (&fc)[9], const Real (&gc)[9],
+                                                      const KConst<Real>& C, bool multiphase) {
+  NodeState<Real> o;
+  const Real rho_ref = C.rho_ref;
+  o.drho = ((fc[0] + fc[1]) + (fc[2] + fc[3])) + ((fc[4] + fc[5]) + (fc[6] + fc[7])) + fc[8];
+  o.rho = rho_ref + o.drho;
+  const Real jx = (fc[1] - fc[3]) + (fc[5] - fc[6]) + (fc[8] - fc[7]);
+  const Real jy = (fc[2] - fc[4]) + (fc[5] + fc[6]) - (fc[7] + fc[8]);
+  const Real inv_rho = fast_rcp(o.rho);
+  o.ux = jx * inv_rho;
+  o.uy = jy * inv_rho;
+  if (THERMAL) {
+    o.dT = ((gc[0] + gc[1]) + (gc[2] + gc[3])) + ((gc[4] + gc[5]) + (gc[6] + gc[7])) + gc[8];
+    o.T = C.T_ref + o.dT;
+  } else {
+    o.dT = Real(0);
+    o.T = C.T0;
+  }
+  o.dpsi = Real(0);
+  o.p = o.rho * Real(1.0 / 3.0);
+  o.coef = Real(0);
+  Real dpdT = Real(0);
+  bool bad = !(o.rho > Real(0));
+  if (multiphase) {
+    const Real pa = C.a, pb = C.b, pR = C.R, kappa = C.kappa, inv_sqrtTc = C.inv_sqrtTc;
+    const Real rho_c = o.rho, drho_c = o.drho, T_c = o.T, dT_c = o.dT;
+    const Real br = pb * rho_c;
+    const Real inv1 = fast_rcp(Real(1) - br);
+    const Real invD = fast_rcp(Real(1) + br * (Real(2) - br));
+    const Real rr_den = rho_c * rho_c * invD;
+    Real alpha, sa = Real(0), inv_sT = Real(0), sT = Real(0);
+    if (THERMAL) {
+      inv_sT = fast_rsqrt(T_c);
+      sT = T_c * inv_sT;
+      sa = Real(1) + kappa * (Real(1) - sT * inv_sqrtTc);
+      alpha = sa * sa;
+    } else {
+      alpha = C.alpha0;
+    }
+    Real rad;
+    if (sizeof(Real) == 4) {
+      const Real rr = rho_ref, inv_u1r = C.inv_u1r;
+      const Real dA = pR * (drho_c * T_c * inv1 * inv_u1r + (THERMAL ? rr * dT_c * inv_u1r : Real(0)));
+      Real dB = pa * alpha * drho_c * (rho_c + rr + Real(2) * pb * rho_c * rr) * invD * C.inv_Dr;
+      if (THERMAL) {
+        const Real dsa = -kappa * inv_sqrtTc * dT_c * fast_rcp(sT + C.sqrtT_r);
+        dB += pa * dsa * (sa + C.sa_r) * C.rr2_Dr;
+      }
+      const Real dp = dA - dB;
+      const Real drad = (dp - drho_c * Real(1.0 / 3.0)) * C.psi_scale;
+      rad = C.rad_ref + drad;
+      const Real psi = fast_sqrt(fmax(rad, Real(0)));
+      const Real den = psi + C.psi_ref;
+      o.dpsi = den > Real(0) ? drad * fast_rcp(den) : Real(0);
+      o.p = C.p_ref + dp;
+    } else {
+      o.p = rho_c * pR * T_c * inv1 - pa * alpha * rr_den;
+      rad = (o.p - rho_c * Real(1.0 / 3.0)) * C.psi_scale;
+      o.dpsi = fast_sqrt(fmax(rad, Real(0)));
+    }
+    bad = bad || !(br < Real(1)) || !(rad >= Real(0));
+    if (THERMAL) {
+      const Real dalpha = -kappa * sa * inv_sT * inv_sqrtTc;
+      dpdT = rho_c * pR * inv1 - pa * dalpha * rr_den;
+    }
+  }
+  if (THERMAL) {
+    bad = bad || !isfinite(o.T);
+    o.coef = o.T * (Real(1) - dpdT * inv_rho * C.inv_cv);
+  }
+  o.bad = bad;
+  return o;
+}
+
+// Interaction force of Eqs. 9, 10, 14, 15 from the neighbours' d = psi - psi_ref
+// (d = 0 for solid neighbours).  With psi = psi_ref + d the beta-mixed sums reduce to
+// F = -(psi_ref + beta d_c) t1 - (1 - beta)/2 t2, t1 = sum G_i d_i c_i,
+// t2 = sum G_i d_i^2 c_i, plus the wall rows' reference parts with Eq. 15.
+template <typename Real>
+__device__ __forceinline__ void sc_force(Real dc, Real dE, Real dW, Real dN, Real dNE, Real dNW, Real dS, Real dSE,
+                                         Real dSW, bool sol_m, bool sol_p, const KConst<Real>& C, Real& Fx,
+                                         Real& Fy) {
+  const Real G2 = C.G2, Gh = C.Gh;
+  const Real t1x = G2 * (dE - dW) + Gh * ((dNE - dNW) + (dSE - dSW));
+  const Real t1y = G2 * (dN - dS) + Gh * ((dNE + dNW) - (dSE + dSW));
+  const Real t2x = G2 * (dE - dW) * (dE + dW) + Gh * ((dNE - dNW) * (dNE + dNW) + (dSE - dSW) * (dSE + dSW));
+  const Real t2y = G2 * (dN - dS) * (dN + dS) + Gh * ((dNE - dSE) * (dNE + dSE) + (dNW - dSW) * (dNW + dSW));
+  const Real lead = C.psi_ref + C.beta * dc;
+  Fx = -lead * t1x - C.mix * t2x;
+  Fy = -lead * t1y - C.mix * t2y;
+  if (sol_m) Fy += C.wall0 + dc * C.wall1;
+  if (sol_p) Fy -= C.wall0 + dc * C.wall1;
+}
+
+// BGK toward f^eq(rho, u_eq) (Eqs. 2-3) plus the exact-difference term (Eq. 5),
+// written pairwise over opposite directions i, i': with cu = c_i.u, cd = c_i.du and
+// cs = c_i.(2u + du), omega f^eq_i + F_i = w_i (K + 4.5 rho (omega cu^2 + cd cs))
+// + 3 w_i rho (omega cu + cd), K = omega (drho - 1.5 rho u.u) - 1.5 rho du.(2u + du);
+// the direction i' flips the sign of the second term only.  fs: the 9 pulled
+// populations at stride fstride; fo: the node in the output buffer, planes `plane` apart.
+template <typename Real>
+__device__ __forceinline__ void collide_f(const Real* fs, int fstride, Real* __restrict__ fo, int plane, Real rho,
+                                          Real drho, Real ux, Real uy, Real dux, Real duy, Real omega_f) {
+  const Real sx = Real(2) * ux + dux, sy = Real(2) * uy + duy;
+  const Real usq = ux * ux + uy * uy;
+  const Real K = omega_f * (drho - Real(1.5) * rho * usq) - Real(1.5) * rho * (dux * sx + duy * sy);
+  const Real r45 = Real(4.5) * rho, r3 = Real(3) * rho, keep = Real(1) - omega_f;
+  auto pair = [&](int i, int j, Real cu, Real cd, Real cs, Real w) {
+    const Real sym = w * (K + r45 * (omega_f * cu * cu + cd * cs));
+    const Real anti = w * r3 * (omega_f * cu + cd);
+    fo[i * plane] = keep * fs[i * fstride] + sym + anti;
+    fo[j * plane] = keep * fs[j * fstride] + sym - anti;
+  };
+  fo[0] = keep * fs[0] + lat_w<Real>(0) * K;
+  pair(1, 3, ux, dux, sx, lat_w<Real>(1));
+  pair(2, 4, uy, duy, sy, lat_w<Real>(2));
+  pair(5, 7, ux + uy, dux + duy, sx + sy, lat_w<Real>(5));
+  pair(6, 8, uy - ux, duy - dux, sy - sx, lat_w<Real>(6));
+}
+
+// Eq. 16 with g^eq of Eq. 18 and the source phi (second Eq. 19), pairwise as for f:
+// omega g^eq_i + w_i phi = w_i (Kg + 4.5 omega T cu^2) + 3 w_i omega T cu.
+template <typename Real>
+__device__ __forceinline__ void collide_g(const Real* gs, int gstride, Real* __restrict__ go, int plane, Real T,
+                                          Real dT, Real uax, Real uay, Real phi, Real omega_g) {
+  const Real usq = uax * uax + uay * uay;
+  const Real Kg = omega_g * (dT - Real(1.5) * T * usq) + phi;
+  const Real t45 = Real(4.5) * omega_g * T, t3 = Real(3) * omega_g * T, keep = Real(1) - omega_g;
+  auto pair = [&](int i, int j, Real cu, Real w) {
+    const Real sym = w * (Kg + t45 * cu * cu);
+    const Real anti = w * t3 * cu;
+    go[i * plane] = keep * gs[i * gstride] + sym + anti;
+    go[j * plane] = keep * gs[j * gstride] + sym - anti;
+  };
+  go[0] = keep * gs[0] + lat_w<Real>(0) * Kg;
+  pair(1, 3, uax, lat_w<Real>(1));
+  pair(2, 4, uay, lat_w<Real>(2));
+  pair(5, 7, uax + uay, lat_w<Real>(5));
+  pair(6, 8, uay - uax, lat_w<Real>(6));
+}
+
+// Issue the asynchronous pull of one node's populations into f_dst/g_dst (stride
+// dstride).  Interior links copy f*_i(x - c_i); links from a wall row copy
+// f*_opp(x) (halfway bounce-back; boundary_fill applies the g sign flip and wall
+// temperature); links from outside an open end are left for boundary_fill.
+template <typename Real, bool THERMAL>
+__device__ __forceinline__ void pull_node(Real* f_dst, Real* g_dst, int dstride, const Real* __restrict__ Fin,
+                                          const Real* __restrict__ Gin, int plane, int pitch, int xn, int rn,
+                                          int nx, int ny, bool perx, bool pery, bool local, const NodeBC& nb) {
+  const int node = rn * pitch + xn;
+  if (local) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      cp_async_elem(f_dst + i * dstride, Fin + node + i * plane);
+      if (THERMAL) cp_async_elem(g_dst + i * dstride, Gin + node + i * plane);
+    }
+    return;
+  }
+  if (xn >= 1 && xn <= nx - 2 && rn >= 1 && rn <= ny - 2) {
+    // interior: the source of link i is node - c_iy * pitch - c_ix in plane i
+    const Real* fn = Fin + node;
+    const Real* gn = Gin + node;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int off = i * plane - lat_cy(i) * pitch - lat_cx(i);
+      cp_async_elem(f_dst + i * dstride, fn + off);
+      if (THERMAL) cp_async_elem(g_dst + i * dstride, gn + off);
+    }
+    return;
+  }
+  int xm = xn - 1, xp = xn + 1, rm = rn - 1, rp = rn + 1;
+  if (perx) {
+    if (xm < 0) xm += nx;
+    if (xp >= nx) xp -= nx;
+  }
+  if (pery) {
+    if (rm < 0) rm += ny;
+    if (rp >= ny) rp -= ny;
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int cxi = lat_cx(i), cyi = lat_cy(i);
+    const bool wall = (cyi == 1 && nb.wlo) || (cyi == -1 && nb.whi);
+    const bool unknown = (cxi == 1 && nb.inl) || (cxi == -1 && nb.outl);
+    int src;
+    int pl = i;
+    if (wall) {
+      src = node;
+      pl = lat_opp(i);
+    } else if (!unknown) {
+      src = (cyi == 1 ? rm : (cyi == -1 ? rp : rn)) * pitch + (cxi == 1 ? xm : (cxi == -1 ? xp : xn));
+    } else {
+      continue;
+    }
+    cp_async_elem(f_dst + i * dstride, Fin + pl * plane + src);
+    if (THERMAL) cp_async_elem(g_dst + i * dstride, Gin + pl * plane + src);
+  }
+}
+
+// Fold of the per-tile partials by the last tile of a launch: the diagnostics
+// record of the step, the domain-mean density for the next step's buoyancy, and the
+// step counter (tot: sums of deviations from the storage references).
+template <bool THERMAL, int MODE>
+__device__ __forceinline__ void finish_step(const Inst& I, InstState* st, const double (&tot)[NPART],
+                                            long long step) {
+  const double n = (double)I.nx * (double)I.ny;
+  const double mass = tot[0] + n * I.rho_ref;
+  const double energy = THERMAL ? tot[1] + n * I.T_ref : n * I.T0;
+  const bool channel = I.geometry == GEOM_CHANNEL;
+  if (MODE == MODE_STEP) {
+    double dtstar = 0.0;
+    const bool heat_now = THERMAL && I.heater_len > 0 && step >= I.heat_on_step && I.geometry != GEOM_PERIODIC;
+    if (heat_now) {
+      const int hx0 = I.heater_x0, hx1 = I.heater_x0 + I.heater_len;
+      const int lo = hx0 < 0 ? 0 : hx0, hi = hx1 > I.nx ? I.nx : hx1;
+      if (hi > lo) {
+        const double tnb = tot[2] / (double)(hi - lo) + I.T_ref;
+        dtstar = (I.T_heat - tnb) / (I.T_heat - energy / n);
+      }
+    }
+    double* rec = I.ring + (step % RING) * NDIAG;
+    rec[0] = (double)step;
+    rec[1] = mass;
+    rec[2] = energy;
+    rec[3] = mass / n;
+    rec[4] = channel ? __ldcg(&st->p_probe[0]) - __ldcg(&st->p_probe[1]) : 0.0;
+    rec[5] = dtstar;
+    rec[6] = channel ? tot[3] : 0.0;
+    rec[7] = channel ? tot[4] : 0.0;
+    st->rho_avg[step & 1] = mass / n;
+    st->step = step + 1;
+    st->local_read = 0;
+  } else {
+    st->rho_avg[(step - 1) & 1] = mass / n;
+  }
+  st->counter = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// Block form of the fused step.  MODE_STEP advances one step; MODE_FIELDS writes
+// rho, u_act and T (FP64) of the current state to the spare f buffer; MODE_POPS
+// writes the post-stream populations to the spare buffers; MODE_MOMENTS only
+// folds the mean density into the buoyancy slot of the previous step.
+// A CTA of B threads owns B - 8 output columns and a band of rows; psi and u_act
+// of three rows live in shared rings so that all threads see their neighbours,
+// with a barrier after each of phase A (pull, moments, EOS), phase B (force,
+// f collision of the row below) and before phase C (g collision two rows below).
 // ---------------------------------------------------------------------------
 template <typename Real, bool THERMAL, int B, int MODE>
 __global__ void __launch_bounds__(B, (sizeof(Real) == 4 ? (B <= 64 ? 10 : (B <= 128 ? 5 : 2))
@@ -233,19 +580,17 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
   const bool pery = sI.geometry == GEOM_PERIODIC;
   const bool channel = sI.geometry == GEOM_CHANNEL;
   const bool multiphase = sI.multiphase != 0;
-
   const Real* __restrict__ Fin = static_cast<const Real*>(sI.f[step & 1]);
   const Real* __restrict__ Gin = static_cast<const Real*>(sI.g[step & 1]);
   Real* __restrict__ Fout = static_cast<Real*>(sI.f[(step + 1) & 1]);
   Real* __restrict__ Gout = static_cast<Real*>(sI.g[(step + 1) & 1]);
-  const Real rho_ref = sC.rho_ref, T_ref = sC.T_ref, T0 = sC.T0;
+  const Real T0 = sC.T0;
 
   // column owned by this thread: x0 - 2 + tid (two halo columns on each side of the W outputs)
   const int s = tid < NS ? tid : 0;
   const int xc = tile.x0 - 2 + s;
-  const bool lane_used = tid < NS;
   int xn = xc;
-  bool col_ok = lane_used;
+  bool col_ok = tid < NS;
   if (perx) {
     xn = wrap_index(xc, nx);
   } else {
@@ -256,86 +601,29 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
   // shared-memory neighbours; at the open ends the ghost column repeats the end column
   const int sm = (!perx && xc == 0) ? s : s - 1;
   const int sp = (!perx && xc == nx - 1) ? s : s + 1;
-  int xm = xn - 1, xp = xn + 1;
-  if (perx) {
-    if (xm < 0) xm += nx;
-    if (xp >= nx) xp -= nx;
-  }
   const bool inl = channel && xn == 0;
   const bool outl = channel && xn == nx - 1;
-  const bool inner_col = xn >= 1 && xn <= nx - 2;  // no wrap and no open end on either side
 
   const int nrow = tile.y1 - tile.y0;
   const int kbeg = (MODE == MODE_STEP) ? 0 : (MODE == MODE_FIELDS ? 1 : 2);
   const int kend = (MODE == MODE_STEP) ? nrow + 4 : (MODE == MODE_FIELDS ? nrow + 3 : nrow + 2);
 
-  // Issue the asynchronous pull of row index k (row y0 - 2 + k) into ring slots
-  // (fslot, gslot).  Interior links copy f*_i(x - c_i); links from a wall row copy
-  // f*_opp(x) (halfway bounce-back; the g sign flip and wall temperature are
-  // applied when the row is read); links from outside an open end are filled at
-  // read time.
   auto issue_row = [&](int k, int fslot, int gslot) {
     if (col_ok && k < kend) {
       const int r = tile.y0 - 2 + k;
       if (pery || (r >= 0 && r < ny)) {
         const int rn = pery ? wrap_index(r, ny) : r;
-        Real* f_dst = sF + fslot * 9 * NS + s;
-        Real* g_dst = sG + gslot * 9 * NS + s;
-        const int node = rn * pitch + xn;
-        const Real* fn = Fin + node;
-        const Real* gn = Gin + node;
-        if (local) {
-#pragma unroll
-          for (int i = 0; i < 9; ++i) {
-            cp_async_elem(f_dst + i * NS, fn + i * plane);
-            if (THERMAL) cp_async_elem(g_dst + i * NS, gn + i * plane);
-          }
-        } else if (inner_col && rn >= 1 && rn <= ny - 2) {
-          // interior: the source of link i is node - c_iy * pitch - c_ix in plane i
-#pragma unroll
-          for (int i = 0; i < 9; ++i) {
-            const int off = i * plane - lat_cy(i) * pitch - lat_cx(i);
-            cp_async_elem(f_dst + i * NS, fn + off);
-            if (THERMAL) cp_async_elem(g_dst + i * NS, gn + off);
-          }
-        } else {
-          int rm = rn - 1, rp = rn + 1;
-          if (pery) {
-            if (rm < 0) rm += ny;
-            if (rp >= ny) rp -= ny;
-          }
-          const bool wlo = !pery && rn == 0;
-          const bool whi = !pery && rn == ny - 1;
-#pragma unroll
-          for (int i = 0; i < 9; ++i) {
-            const int cxi = lat_cx(i), cyi = lat_cy(i);
-            const bool wall = (cyi == 1 && wlo) || (cyi == -1 && whi);
-            const bool unknown = (cxi == 1 && inl) || (cxi == -1 && outl);
-            int src;
-            int pl = i;
-            if (wall) {
-              src = node;
-              pl = lat_opp(i);
-            } else if (!unknown) {
-              src = (cyi == 1 ? rm : (cyi == -1 ? rp : rn)) * pitch + (cxi == 1 ? xm : (cxi == -1 ? xp : xn));
-            } else {
-              continue;
-            }
-            cp_async_elem(f_dst + i * NS, Fin + pl * plane + src);
-            if (THERMAL) cp_async_elem(g_dst + i * NS, Gin + pl * plane + src);
-          }
-        }
+        const NodeBC nb{!pery && rn == 0, !pery && rn == ny - 1, inl, outl};
+        pull_node<Real, THERMAL>(sF + fslot * 9 * NS + s, sG + gslot * 9 * NS + s, NS, Fin, Gin, plane, pitch, xn,
+                                 rn, nx, ny, perx, pery, local, nb);
       }
     }
     cp_async_commit();
   };
 
-  // per-thread diagnostics partials over this band (in the compute precision)
   Real acc_m = Real(0), acc_e = Real(0), acc_h = Real(0), acc_fi = Real(0), acc_fo = Real(0);
-
-  // scalars carried between iterations: row r-1 (f collision), row r-2 (g collision)
-  Real rho_p = Real(1), drho_p = Real(0), ux_p = Real(0), uy_p = Real(0), T_p = T0, dT_p = Real(0),
-       coef_p = Real(0);
+  // node scalars carried between iterations: row r-1 (f collision), row r-2 (g collision)
+  Real rho_p = Real(1), drho_p = Real(0), ux_p = Real(0), uy_p = Real(0), T_p = T0, dT_p = Real(0), coef_p = Real(0);
   Real T_p2 = T0, dT_p2 = Real(0), coef_p2 = Real(0);
 
   // ring slots: f and psi/u rings have 3 slots (row index mod 3), g has 4 (mod 4)
@@ -344,18 +632,19 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
   for (int k = kbeg; k < kend; ++k) {
     const int r = tile.y0 - 2 + k;
     const int f_next = (f_cur == F_SLOTS - 1) ? 0 : f_cur + 1;
-    const int f_prev = (f_cur == 0) ? F_SLOTS - 1 : f_cur - 1;  // row r-1
+    const int f_prev = (f_cur == 0) ? F_SLOTS - 1 : f_cur - 1;      // row r-1
     const int f_prev2 = (f_prev == 0) ? F_SLOTS - 1 : f_prev - 1;  // row r-2 (= r+1)
     const int g_next = (g_cur + 1) & (G_SLOTS - 1);
     const int g_prev2 = (g_cur + 2) & (G_SLOTS - 1);  // row r-2
     issue_row(k + 1, f_next, g_next);
     cp_async_wait_1();  // this thread's copies of row k have landed
 
-    // ===================== Phase A: row r: boundary fill, moments, EOS =====================
+    // ===================== phase A: row r =====================
     const bool row_ok = pery || (r >= 0 && r < ny);
     const int rn = pery ? wrap_index(r, ny) : r;
-    Real rho_c = Real(1), drho_c = Real(0), ux_c = Real(0), uy_c = Real(0), T_c = T0, dT_c = Real(0),
-         coef_c = Real(0);
+    NodeState<Real> ns;
+    ns.rho = Real(1); ns.drho = Real(0); ns.ux = Real(0); ns.uy = Real(0);
+    ns.T = T0; ns.dT = Real(0); ns.coef = Real(0); ns.dpsi = Real(0);
     if (col_ok && row_ok) {
       Real* fs = sF + f_cur * 9 * NS + s;
       Real* gs = sG + g_cur * 9 * NS + s;
@@ -365,170 +654,37 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
         fc[i] = fs[i * NS];
         gc[i] = THERMAL ? gs[i * NS] : Real(0);
       }
-      const bool wlo = !pery && rn == 0;
-      const bool whi = !pery && rn == ny - 1;
-      if (!local && (wlo || whi || inl || outl)) {
-        const long long node = (long long)rn * pitch + xn;
-        const Real dT_in = sC.dT_in;
-        if (THERMAL && (wlo || whi)) {
-          // anti-bounce-back at the wall temperature (the heater heats the bottom wall
-          // once the boundary condition of step heat_on_step has been applied)
-          const bool heat_bc = sI.heater_len > 0 && (step - 1) >= sI.heat_on_step;
-#pragma unroll
-          for (int i = 0; i < 9; ++i) {
-            const int cxi = lat_cx(i), cyi = lat_cy(i);
-            if ((cyi == 1 && wlo) || (cyi == -1 && whi)) {
-              Real dTw = dT_in;
-              if (cyi == 1 && heat_bc) {
-                int sx = xn - cxi;
-                if (perx) sx = wrap_index(sx, nx);
-                if (sx >= sI.heater_x0 && sx < sI.heater_x0 + sI.heater_len) dTw = sC.dT_heat;
-              }
-              gc[i] = -gc[i] + Real(2) * lat_w<Real>(i) * dTw;
-            }
-          }
-        }
-        if (inl) {
-          // velocity inlet (Zou-He non-equilibrium bounce-back), u = (u_in, 0)
-          const Real u_in = sC.u_in;
-          const Real S = fc[0] + fc[2] + fc[4] + Real(2) * (fc[3] + fc[6] + fc[7]);
-          const Real rho_b = (S + rho_ref) / (Real(1) - u_in);
-          const Real ru = rho_b * u_in;
-          if (wlo) {
-            fc[8] = fc[2] + fc[5] + fc[6] - fc[4] - fc[7];
-            fc[1] = ru - fc[5] - fc[8] + fc[3] + fc[6] + fc[7];
-          } else if (whi) {
-            fc[5] = fc[4] + fc[7] + fc[8] - fc[2] - fc[6];
-            fc[1] = ru - fc[5] - fc[8] + fc[3] + fc[6] + fc[7];
-          } else {
-            const Real h = Real(0.5) * (fc[2] - fc[4]);
-            fc[1] = fc[3] + Real(2.0 / 3.0) * ru;
-            fc[5] = fc[7] - h + ru * Real(1.0 / 6.0);
-            fc[8] = fc[6] + h + ru * Real(1.0 / 6.0);
-          }
-          if (THERMAL) {
-            // anti-bounce-back at the inlet temperature
-            if (!wlo) gc[5] = -ld_ro(Gin + 7 * plane + node) + Real(2) * lat_w<Real>(5) * dT_in;
-            if (!whi) gc[8] = -ld_ro(Gin + 6 * plane + node) + Real(2) * lat_w<Real>(8) * dT_in;
-            gc[1] = -ld_ro(Gin + 3 * plane + node) + Real(2) * lat_w<Real>(1) * dT_in;
-          }
-        }
-        if (outl) {
-          // pressure outlet (Zou-He), rho = rho_out, u_y = 0
-          const Real drho_out = sC.drho_out;
-          if (wlo) {
-            fc[7] = fc[2] + fc[5] + fc[6] - fc[4] - fc[8];
-            fc[3] = drho_out - (fc[0] + fc[1] + fc[2] + fc[4] + fc[5] + fc[6] + fc[7] + fc[8]);
-          } else if (whi) {
-            fc[6] = fc[4] + fc[7] + fc[8] - fc[2] - fc[5];
-            fc[3] = drho_out - (fc[0] + fc[1] + fc[2] + fc[4] + fc[5] + fc[6] + fc[7] + fc[8]);
-          } else {
-            const Real S = fc[0] + fc[2] + fc[4] + Real(2) * (fc[1] + fc[5] + fc[8]);
-            const Real ru = S - drho_out;  // rho_out * u_x
-            const Real h = Real(0.5) * (fc[2] - fc[4]);
-            fc[3] = fc[1] - Real(2.0 / 3.0) * ru;
-            fc[7] = fc[5] + h - ru * Real(1.0 / 6.0);
-            fc[6] = fc[8] - h - ru * Real(1.0 / 6.0);
-          }
-          if (THERMAL) {
-            // zero temperature gradient: the post-stream populations of node nx-2
-            gc[3] = ld_ro(Gin + 3 * plane + node);
-            if (!wlo) gc[6] = ld_ro(Gin + 6 * plane + node - pitch);
-            if (!whi) gc[7] = ld_ro(Gin + 7 * plane + node + pitch);
-          }
-        }
+      const NodeBC nb{!pery && rn == 0, !pery && rn == ny - 1, inl, outl};
+      if (!local && (nb.wlo || nb.whi || inl || outl)) {
+        boundary_fill<Real, THERMAL>(fc, gc, nb, sI, sC, Gin, plane, pitch, rn * pitch + xn, xn, perx, step);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
           fs[i * NS] = fc[i];
           if (THERMAL) gs[i * NS] = gc[i];
         }
       }
-
-      // moments, Eqs. 4, 6, 17 (deviation sums; the rest-state parts carry no momentum)
-      drho_c = ((fc[0] + fc[1]) + (fc[2] + fc[3])) + ((fc[4] + fc[5]) + (fc[6] + fc[7])) + fc[8];
-      rho_c = rho_ref + drho_c;
-      const Real jx = (fc[1] - fc[3]) + (fc[5] - fc[6]) + (fc[8] - fc[7]);
-      const Real jy = (fc[2] - fc[4]) + (fc[5] + fc[6]) - (fc[7] + fc[8]);
-      const Real inv_rho = fast_rcp(rho_c);
-      ux_c = jx * inv_rho;
-      uy_c = jy * inv_rho;
-      if (THERMAL) {
-        dT_c = ((gc[0] + gc[1]) + (gc[2] + gc[3])) + ((gc[4] + gc[5]) + (gc[6] + gc[7])) + gc[8];
-        T_c = T_ref + dT_c;
-      }
-
-      // Peng-Robinson EOS (Eq. 12), pseudopotential (Eq. 11), (dp/dT)_rho.  The shared
-      // ring holds dpsi = psi - psi_ref: psi itself in FP64 (psi_ref = 0); in FP32 the
-      // deviation from the reference state, from exact difference forms of Eq. 12 in
-      // rho - rho_ref and T - T_ref, so that neighbour differences in the force keep
-      // their low-order bits.
-      Real dpsi = Real(0), p = rho_c * Real(1.0 / 3.0), dpdT = Real(0);
-      bool bad = !(rho_c > Real(0));
-      if (multiphase) {
-        const Real pa = sC.a, pb = sC.b, pR = sC.R, kappa = sC.kappa, inv_sqrtTc = sC.inv_sqrtTc;
-        const Real br = pb * rho_c;
-        const Real inv1 = fast_rcp(Real(1) - br);
-        const Real invD = fast_rcp(Real(1) + br * (Real(2) - br));
-        const Real rr_den = rho_c * rho_c * invD;
-        Real alpha, sa = Real(0), inv_sT = Real(0), sT = Real(0);
-        if (THERMAL) {
-          inv_sT = fast_rsqrt(T_c);
-          sT = T_c * inv_sT;
-          sa = Real(1) + kappa * (Real(1) - sT * inv_sqrtTc);
-          alpha = sa * sa;
-        } else {
-          alpha = sC.alpha0;
-        }
-        Real rad;
-        if (sizeof(Real) == 4) {
-          const Real rr = rho_ref, inv_u1r = sC.inv_u1r;
-          const Real dA = pR * (drho_c * T_c * inv1 * inv_u1r + (THERMAL ? rr * dT_c * inv_u1r : Real(0)));
-          Real dB = pa * alpha * drho_c * (rho_c + rr + Real(2) * pb * rho_c * rr) * invD * sC.inv_Dr;
-          if (THERMAL) {
-            const Real dsa = -kappa * inv_sqrtTc * dT_c * fast_rcp(sT + sC.sqrtT_r);
-            dB += pa * dsa * (sa + sC.sa_r) * sC.rr2_Dr;
-          }
-          const Real dp = dA - dB;
-          const Real drad = (dp - drho_c * Real(1.0 / 3.0)) * sC.psi_scale;
-          rad = sC.rad_ref + drad;
-          const Real psi = fast_sqrt(fmax(rad, Real(0)));
-          const Real den = psi + sC.psi_ref;
-          dpsi = den > Real(0) ? drad * fast_rcp(den) : Real(0);
-          p = sC.p_ref + dp;
-        } else {
-          p = rho_c * pR * T_c * inv1 - pa * alpha * rr_den;
-          rad = (p - rho_c * Real(1.0 / 3.0)) * sC.psi_scale;
-          dpsi = fast_sqrt(fmax(rad, Real(0)));
-        }
-        bad = bad || !(br < Real(1)) || !(rad >= Real(0));
-        if (THERMAL) {
-          const Real dalpha = -kappa * sa * inv_sT * inv_sqrtTc;
-          dpdT = rho_c * pR * inv1 - pa * dalpha * rr_den;
-        }
-      }
-      if (THERMAL) {
-        bad = bad || !isfinite(T_c);
-        coef_c = T_c * (Real(1) - dpdT * inv_rho * sC.inv_cv);
-      }
-      if (bad) atomicOr(&st->status, STATUS_UNSTABLE);
-      sPsi[f_cur * NS + s] = dpsi;
+      ns = node_state<Real, THERMAL>(fc, gc, sC, multiphase);
+      if (ns.bad) atomicOr(&st->status, STATUS_UNSTABLE);
+      sPsi[f_cur * NS + s] = ns.dpsi;
       const bool out_row = r >= tile.y0 && r < tile.y1;
       if ((MODE == MODE_STEP || MODE == MODE_MOMENTS) && out_col && out_row) {
-        acc_m += drho_c;
-        acc_e += dT_c;
-        if (THERMAL && !pery && rn == 0 && xn >= sI.heater_x0 && xn < sI.heater_x0 + sI.heater_len) acc_h += dT_c;
+        acc_m += ns.drho;
+        if (THERMAL) {
+          acc_e += ns.dT;
+          if (!pery && rn == 0 && xn >= sI.heater_x0 && xn < sI.heater_x0 + sI.heater_len) acc_h += ns.dT;
+        }
         if (MODE == MODE_STEP && channel && rn == ny / 2 && (xn == 1 || xn == nx - 2)) {
-          if (xn == 1) st->p_probe[0] = (double)p;
-          if (xn == nx - 2) st->p_probe[1] = (double)p;
+          if (xn == 1) st->p_probe[0] = (double)ns.p;
+          if (xn == nx - 2) st->p_probe[1] = (double)ns.p;
           __threadfence();
         }
       }
       if (MODE == MODE_POPS && out_col && out_row) {
-        const int o = rn * pitch + xn;
+        const int oo = rn * pitch + xn;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-          Fout[i * plane + o] = fc[i];
-          if (THERMAL) Gout[i * plane + o] = gc[i];
+          Fout[i * plane + oo] = fc[i];
+          if (THERMAL) Gout[i * plane + oo] = gc[i];
         }
       }
     }
@@ -539,96 +695,48 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
     }
     __syncthreads();
 
-    // ============ Phase B: row q = r - 1: force, u_act, f collision ============
+    // ===================== phase B: row q = r - 1 =====================
     const int q = r - 1;
     // STEP needs u_act from row y0 - 1 (divergence at y0); FIELDS only on its output rows
     const int qmin = (MODE == MODE_STEP) ? tile.y0 - 1 : tile.y0;
-    if (q >= qmin) {
-      const bool qrow_ok = pery || (q >= 0 && q < ny);
-      if (f_col && qrow_ok) {
-        const bool sol_m = !pery && q == 0;       // row q-1 is the bottom wall
-        const bool sol_p = !pery && q == ny - 1;  // row q+1 is the top wall
-        Real Fx = Real(0), Fy = Real(0);
-        if (multiphase) {
-          // ring values are d = psi - psi_ref (psi_ref = 0 in FP64); solid neighbours carry d = 0
-          const Real* P0 = sPsi + f_prev * NS;
-          const Real dc = P0[s];
-          const Real dE = P0[sp], dW = P0[sm];
-          Real dN = Real(0), dNE = Real(0), dNW = Real(0), dS = Real(0), dSE = Real(0), dSW = Real(0);
-          if (!sol_p) {
-            const Real* Pp = sPsi + f_cur * NS;
-            dN = Pp[s];
-            dNE = Pp[sp];
-            dNW = Pp[sm];
-          }
-          if (!sol_m) {
-            const Real* Pm = sPsi + f_prev2 * NS;
-            dS = Pm[s];
-            dSE = Pm[sp];
-            dSW = Pm[sm];
-          }
-          // Eq. 9 over fluid neighbours with psi = psi_ref + d: the beta-mixed sums reduce to
-          // F = -(psi_ref + beta d_c) t1 - (1 - beta)/2 t2, t1 = sum G_i d_i c_i,
-          // t2 = sum G_i d_i^2 c_i, plus the wall rows' reference parts with Eq. 15.
-          const Real G2 = sC.G2, Gh = sC.Gh;
-          const Real t1x = G2 * (dE - dW) + Gh * ((dNE - dNW) + (dSE - dSW));
-          const Real t1y = G2 * (dN - dS) + Gh * ((dNE + dNW) - (dSE + dSW));
-          const Real t2x = G2 * (dE - dW) * (dE + dW) + Gh * ((dNE - dNW) * (dNE + dNW) + (dSE - dSW) * (dSE + dSW));
-          const Real t2y = G2 * (dN - dS) * (dN + dS) + Gh * ((dNE - dSE) * (dNE + dSE) + (dNW - dSW) * (dNW + dSW));
-          const Real lead = sC.psi_ref + sC.beta * dc;
-          Fx = -lead * t1x - sC.mix * t2x;
-          Fy = -lead * t1y - sC.mix * t2y;
-          if (sol_m) Fy += sC.wall0 + dc * sC.wall1;
-          if (sol_p) Fy -= sC.wall0 + dc * sC.wall1;
-        }
-        Fy -= (drho_p + sC.rho_ref_minus_avg) * sC.g_a;  // Eq. 14, gravity along -y
-        const Real inv_rho = fast_rcp(rho_p);
-        const Real dux = Fx * inv_rho, duy = Fy * inv_rho;
-        const Real uax = ux_p + Real(0.5) * dux, uay = uy_p + Real(0.5) * duy;  // Eq. 7
-        sUx[f_prev * NS + s] = uax;
-        sUy[f_prev * NS + s] = uay;
-        const bool out_q = out_col && q >= tile.y0 && q < tile.y1;
-        if (MODE == MODE_STEP && out_q) {
-          // BGK toward f^eq(rho, u_eq) (Eqs. 2-3) plus the exact-difference term (Eq. 5),
-          // written pairwise over opposite directions i, i': with cu = c_i.u, cd = c_i.du and
-          // cs = c_i.(2u + du), omega f^eq_i + F_i = w_i (K + 4.5 rho (omega cu^2 + cd cs))
-          // + 3 w_i rho (omega cu + cd), K = omega (drho - 1.5 rho u.u) - 1.5 rho du.(2u + du);
-          // the direction i' flips the sign of the second term only.
-          const Real omega_f = sC.omega_f;
-          const Real sx = Real(2) * ux_p + dux, sy = Real(2) * uy_p + duy;
-          const Real usq = ux_p * ux_p + uy_p * uy_p;
-          const Real K = omega_f * (drho_p - Real(1.5) * rho_p * usq) - Real(1.5) * rho_p * (dux * sx + duy * sy);
-          const Real r45 = Real(4.5) * rho_p, r3 = Real(3) * rho_p, keep = Real(1) - omega_f;
-          const Real* fs = sF + f_prev * 9 * NS + s;
-          Real* fo = Fout + (q * pitch + xn);
-          auto pair = [&](int i, int j, Real cu, Real cd, Real cs, Real w) {
-            const Real sym = w * (K + r45 * (omega_f * cu * cu + cd * cs));
-            const Real anti = w * r3 * (omega_f * cu + cd);
-            fo[i * plane] = keep * fs[i * NS] + sym + anti;
-            fo[j * plane] = keep * fs[j * NS] + sym - anti;
-          };
-          fo[0] = keep * fs[0] + lat_w<Real>(0) * K;
-          pair(1, 3, ux_p, dux, sx, lat_w<Real>(1));
-          pair(2, 4, uy_p, duy, sy, lat_w<Real>(2));
-          pair(5, 7, ux_p + uy_p, dux + duy, sx + sy, lat_w<Real>(5));
-          pair(6, 8, uy_p - ux_p, duy - dux, sy - sx, lat_w<Real>(6));
-          if (channel && xn == 0) acc_fi += rho_p * uax;
-          if (channel && xn == nx - 1) acc_fo += rho_p * uax;
-        }
-        if (MODE == MODE_FIELDS && out_q) {
-          double* out = static_cast<double*>(sI.f[(step + 1) & 1]);
-          const long long n = (long long)nx * ny;
-          const long long o = (long long)q * nx + xn;
-          out[o] = (double)rho_p;
-          out[n + o] = (double)uax;
-          out[2 * n + o] = (double)uay;
-          out[3 * n + o] = (double)T_p;
-        }
+    if (q >= qmin && f_col && (pery || (q >= 0 && q < ny))) {
+      const bool sol_m = !pery && q == 0;       // row q-1 is the bottom wall
+      const bool sol_p = !pery && q == ny - 1;  // row q+1 is the top wall
+      Real Fx = Real(0), Fy = Real(0);
+      if (multiphase) {
+        const Real* P0 = sPsi + f_prev * NS;
+        const Real* Pp = sPsi + f_cur * NS;
+        const Real* Pm = sPsi + f_prev2 * NS;
+        sc_force<Real>(P0[s], P0[sp], P0[sm], sol_p ? Real(0) : Pp[s], sol_p ? Real(0) : Pp[sp],
+                       sol_p ? Real(0) : Pp[sm], sol_m ? Real(0) : Pm[s], sol_m ? Real(0) : Pm[sp],
+                       sol_m ? Real(0) : Pm[sm], sol_m, sol_p, sC, Fx, Fy);
+      }
+      Fy -= (drho_p + sC.rho_ref_minus_avg) * sC.g_a;  // Eq. 14, gravity along -y
+      const Real inv_rho = fast_rcp(rho_p);
+      const Real dux = Fx * inv_rho, duy = Fy * inv_rho;
+      const Real uax = ux_p + Real(0.5) * dux, uay = uy_p + Real(0.5) * duy;  // Eq. 7
+      sUx[f_prev * NS + s] = uax;
+      sUy[f_prev * NS + s] = uay;
+      const bool out_q = out_col && q >= tile.y0 && q < tile.y1;
+      if (MODE == MODE_STEP && out_q) {
+        collide_f<Real>(sF + f_prev * 9 * NS + s, NS, Fout + (q * pitch + xn), plane, rho_p, drho_p, ux_p, uy_p,
+                        dux, duy, sC.omega_f);
+        if (channel && xn == 0) acc_fi += rho_p * uax;
+        if (channel && xn == nx - 1) acc_fo += rho_p * uax;
+      }
+      if (MODE == MODE_FIELDS && out_q) {
+        double* out = static_cast<double*>(sI.f[(step + 1) & 1]);
+        const long long n = (long long)nx * ny;
+        const long long oo = (long long)q * nx + xn;
+        out[oo] = (double)rho_p;
+        out[n + oo] = (double)uax;
+        out[2 * n + oo] = (double)uay;
+        out[3 * n + oo] = (double)T_p;
       }
     }
     __syncthreads();
 
-    // ============ Phase C: row q2 = r - 2: source and g collision ============
+    // ===================== phase C: row q2 = r - 2 =====================
     if (THERMAL && MODE == MODE_STEP) {
       const int q2 = r - 2;
       if (out_col && q2 >= tile.y0 && q2 < tile.y1) {
@@ -637,41 +745,21 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
         const Real uyN = (!pery && q2 == ny - 1) ? Real(0) : sUy[f_prev * NS + s];
         const Real uyS = (!pery && q2 == 0) ? Real(0) : sUy[f_cur * NS + s];  // slot of row r-3
         const Real divu = Real(0.5) * (uxE - uxW) + Real(0.5) * (uyN - uyS);
-        const Real phi = coef_p2 * divu;  // second Eq. 19
-        const Real uax = sUx[f_prev2 * NS + s], uay = sUy[f_prev2 * NS + s];
-        // Eq. 16 with g^eq of Eq. 18, pairwise over opposite directions as for f:
-        // omega g^eq_i + w_i phi = w_i (Kg + 4.5 omega T cu^2) + 3 w_i omega T cu
-        const Real omega_g = sC.omega_g;
-        const Real usq = uax * uax + uay * uay;
-        const Real Kg = omega_g * (dT_p2 - Real(1.5) * T_p2 * usq) + phi;
-        const Real t45 = Real(4.5) * omega_g * T_p2, t3 = Real(3) * omega_g * T_p2, keep = Real(1) - omega_g;
-        const Real* gs = sG + g_prev2 * 9 * NS + s;
-        Real* go = Gout + (q2 * pitch + xn);
-        auto pair = [&](int i, int j, Real cu, Real w) {
-          const Real sym = w * (Kg + t45 * cu * cu);
-          const Real anti = w * t3 * cu;
-          go[i * plane] = keep * gs[i * NS] + sym + anti;
-          go[j * plane] = keep * gs[j * NS] + sym - anti;
-        };
-        go[0] = keep * gs[0] + lat_w<Real>(0) * Kg;
-        pair(1, 3, uax, lat_w<Real>(1));
-        pair(2, 4, uay, lat_w<Real>(2));
-        pair(5, 7, uax + uay, lat_w<Real>(5));
-        pair(6, 8, uay - uax, lat_w<Real>(6));
+        collide_g<Real>(sG + g_prev2 * 9 * NS + s, NS, Gout + (q2 * pitch + xn), plane, T_p2, dT_p2,
+                        sUx[f_prev2 * NS + s], sUy[f_prev2 * NS + s], coef_p2 * divu, sC.omega_g);
       }
     }
 
-    // rotate the carried rows and ring slots
     T_p2 = T_p;
     dT_p2 = dT_p;
     coef_p2 = coef_p;
-    rho_p = rho_c;
-    drho_p = drho_c;
-    ux_p = ux_c;
-    uy_p = uy_c;
-    T_p = T_c;
-    dT_p = dT_c;
-    coef_p = coef_c;
+    rho_p = ns.rho;
+    drho_p = ns.drho;
+    ux_p = ns.ux;
+    uy_p = ns.uy;
+    T_p = ns.T;
+    dT_p = ns.dT;
+    coef_p = ns.coef;
     f_cur = f_next;
     g_cur = g_next;
   }
@@ -699,39 +787,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
   }
   __syncthreads();
   block_sum<BLOCK>(tot, sRed);
-  if (tid == 0) {
-    // the partials are sums of deviations from the storage references
-    const double n = (double)nx * (double)ny;
-    const double mass = tot[0] + n * sI.rho_ref;
-    const double energy = THERMAL ? tot[1] + n * sI.T_ref : n * sI.T0;
-    if (MODE == MODE_STEP) {
-      double dtstar = 0.0;
-      const bool heat_now = THERMAL && sI.heater_len > 0 && step >= sI.heat_on_step && !pery;
-      if (heat_now) {
-        const int hx0 = sI.heater_x0, hx1 = sI.heater_x0 + sI.heater_len;
-        int lo = hx0 < 0 ? 0 : hx0, hi = hx1 > nx ? nx : hx1;
-        if (hi > lo) {
-          const double tnb = tot[2] / (double)(hi - lo) + sI.T_ref;
-          dtstar = (sI.T_heat - tnb) / (sI.T_heat - energy / n);
-        }
-      }
-      double* rec = sI.ring + (step % RING) * NDIAG;
-      rec[0] = (double)step;
-      rec[1] = mass;
-      rec[2] = energy;
-      rec[3] = mass / n;
-      rec[4] = channel ? __ldcg(&st->p_probe[0]) - __ldcg(&st->p_probe[1]) : 0.0;
-      rec[5] = dtstar;
-      rec[6] = channel ? tot[3] : 0.0;
-      rec[7] = channel ? tot[4] : 0.0;
-      st->rho_avg[step & 1] = mass / n;
-      st->step = step + 1;
-      st->local_read = 0;
-    } else {
-      st->rho_avg[(step - 1) & 1] = mass / n;
-    }
-    st->counter = 0u;
-  }
+  if (tid == 0) finish_step<THERMAL, MODE>(sI, st, tot, step);
 }
 
 // ---------------------------------------------------------------------------
