@@ -36,6 +36,116 @@ cudaError_t launch_init_builtin(int fp64, const Inst* d_inst, int nx, int ny, In
   return fp64 ? launch_init_builtin_f64(d_inst, nx, ny, spec, s) : launch_init_builtin_f32(d_inst, nx, ny, spec, s);
 }
 bool cols_supported(int cols) { return cols == 64 || cols == 128 || cols == 256; }
+
+const char* check_params(int nx, int ny, const lbm_params* p) {
+  if (!p) return "params is NULL";
+  if (p->size != sizeof(lbm_params)) return "params.size != sizeof(lbm_params)";
+  if (p->geometry < 0 || p->geometry > 2) return "geometry must be 0, 1 or 2";
+  if (p->geometry == LBM_GEOM_CHANNEL && (nx < 3 || ny < 2)) return "channel needs nx >= 3 and ny >= 2";
+  if (p->geometry == LBM_GEOM_WALLS && ny < 2) return "walls geometry needs ny >= 2";
+  if (p->thermal != 0 && p->thermal != 1) return "thermal must be 0 or 1";
+  if (p->multiphase != 0 && p->multiphase != 1) return "multiphase must be 0 or 1";
+  if (!(p->tau_f > 0.5) || !(p->tau_g > 0.5)) return "tau_f and tau_g must exceed 1/2";
+  if (!(p->a > 0) || !(p->b > 0) || !(p->R > 0)) return "a, b, R must be positive";
+  if (!(p->T0_R > 0) || !(p->Tin_R > 0) || !(p->Tin_R + p->dTheat_R > 0)) return "temperatures must be positive";
+  if (p->multiphase && (!(p->c0 > 0) || p->G == 0.0 || !std::isfinite(p->G))) return "c0 > 0 and G != 0 required";
+  if (p->thermal && !(p->c_v > 0)) return "c_v must be positive";
+  if (p->geometry == LBM_GEOM_CHANNEL && (!(p->rho_out > 0) || !(std::fabs(p->u_in) < 0.5)))
+    return "rho_out > 0 and |u_in| < 0.5 required";
+  if (p->heater_len < 0) return "heater_len must be >= 0";
+  if (p->init_kind != LBM_INIT_UNIFORM && p->init_kind != LBM_INIT_DISK) return "init_kind must be 0 or 1";
+  if (!(p->init_rho_out > 0) || (p->init_kind == LBM_INIT_DISK && (!(p->init_rho_in > 0) || !(p->init_width > 0))))
+    return "initial densities and width must be positive";
+  if (!std::isfinite(p->u_in) || !std::isfinite(p->g_a) || !std::isfinite(p->G_wet) || !std::isfinite(p->beta))
+    return "non-finite parameter";
+  return nullptr;
+}
+
+namespace {
+// Peng-Robinson pressure (Eq. 12) in double on the host, for psi(rho_w, T0).
+double host_pressure(const lbm_params& p, double rho, double T) {
+  const double Tc = 0.0778 * p.a / (0.45724 * p.b * p.R);
+  const double kappa = 0.37464 + 1.54226 * p.omega - 0.26992 * p.omega * p.omega;
+  const double s = 1.0 + kappa * (1.0 - std::sqrt(T / Tc));
+  return rho * p.R * T / (1.0 - p.b * rho) - p.a * s * s * rho * rho / (1.0 + 2.0 * p.b * rho - p.b * p.b * rho * rho);
+}
+}  // namespace
+
+const char* fill_inst(Inst& I, const lbm_params* p, int nx, int ny, int pitch, long long plane, int fp64) {
+  I = Inst{};
+  I.nx = nx;
+  I.ny = ny;
+  I.pitch = pitch;
+  I.geometry = p->geometry;
+  I.plane = plane;
+  I.multiphase = p->multiphase;
+  I.omega_f = 1.0 / p->tau_f;
+  I.omega_g = 1.0 / p->tau_g;
+  const double Tc = 0.0778 * p->a / (0.45724 * p->b * p->R);
+  I.a = p->a;
+  I.b = p->b;
+  I.R = p->R;
+  I.kappa = 0.37464 + 1.54226 * p->omega - 0.26992 * p->omega * p->omega;
+  I.sqrtTc = std::sqrt(Tc);
+  I.inv_sqrtTc = 1.0 / I.sqrtTc;
+  I.T0 = p->T0_R * Tc;
+  I.T_in = p->Tin_R * Tc;
+  I.T_heat = (p->Tin_R + p->dTheat_R) * Tc;
+  {
+    const double sa = 1.0 + I.kappa * (1.0 - std::sqrt(I.T0 / Tc));
+    I.alpha0 = sa * sa;
+  }
+  if (p->multiphase) {
+    I.psi_scale = 2.0 / (p->c0 * p->G);
+    const double rad = (host_pressure(*p, p->rho_w, I.T0) - p->rho_w / 3.0) * I.psi_scale;
+    if (!(rad >= 0.0)) return "psi(rho_w, T0) undefined: negative radicand (Eq. 11)";
+    I.Gwet_psiw = p->G_wet * std::sqrt(rad);
+    if (!(p->b * std::max(p->rho_w, p->init_rho_out) < 1.0)) return "density beyond 1/b";
+  }
+  I.beta = p->beta;
+  I.G2 = 2.0 * p->G;
+  I.Ghalf = 0.5 * p->G;
+  I.g_a = p->g_a;
+  I.inv_cv = p->thermal ? 1.0 / p->c_v : 0.0;
+  I.u_in = p->u_in;
+  I.rho_out = p->rho_out;
+  if (!fp64) {
+    I.rho_ref = p->geometry == LBM_GEOM_CHANNEL ? p->rho_out : p->init_rho_out;
+    I.T_ref = I.T0;
+  } else {
+    I.rho_ref = 0.0;
+    I.T_ref = 0.0;
+  }
+  if (!fp64 && p->multiphase) {
+    const double rr = I.rho_ref, Tr = I.T_ref;
+    const double u1r = 1.0 - p->b * rr, Dr = 1.0 + 2.0 * p->b * rr - p->b * p->b * rr * rr;
+    if (!(u1r > 0.0) || !(Dr > 0.0)) return "reference density beyond 1/b";
+    I.sa_r = 1.0 + I.kappa * (1.0 - std::sqrt(Tr / Tc));
+    I.p_ref = rr * p->R * Tr / u1r - p->a * I.sa_r * I.sa_r * rr * rr / Dr;
+    I.rad_ref = (I.p_ref - rr / 3.0) * I.psi_scale;
+    if (!(I.rad_ref >= 0.0)) return "psi undefined at the reference state (Eq. 11)";
+    I.psi_ref = std::sqrt(I.rad_ref);
+    I.inv_u1r = 1.0 / u1r;
+    I.inv_Dr = 1.0 / Dr;
+    I.sqrtT_r = std::sqrt(Tr);
+    I.rr2_Dr = rr * rr / Dr;
+  }
+  I.heater_x0 = p->heater_x0 < 0 ? nx / 5 : p->heater_x0;
+  I.heater_len = p->heater_len;
+  I.heat_on_step = p->heat_on_step;
+  return nullptr;
+}
+
+int default_band_rows(int nx, int ny, int cols) {
+  const int w = cols - 8;
+  const int strips = (nx + w - 1) / w;
+  const long long target = 152LL * 8;
+  long long rows = ((long long)ny * strips + target - 1) / target;
+  rows = std::max<long long>(rows, 16);
+  rows = std::min<long long>(rows, 128);
+  rows = std::min<long long>(rows, ny);
+  return (int)std::max<long long>(rows, 4 < ny ? 4 : ny);
+}
 }  // namespace pplbm
 
 using namespace pplbm;
@@ -80,14 +190,6 @@ Layout make_layout(int nx, int ny, lbm_precision prec) {
   return L;
 }
 
-// Peng-Robinson pressure (Eq. 12) in double on the host, for psi(rho_w, T0).
-double host_pressure(const lbm_params& p, double rho, double T) {
-  const double Tc = 0.0778 * p.a / (0.45724 * p.b * p.R);
-  const double kappa = 0.37464 + 1.54226 * p.omega - 0.26992 * p.omega * p.omega;
-  const double s = 1.0 + kappa * (1.0 - std::sqrt(T / Tc));
-  return rho * p.R * T / (1.0 - p.b * rho) - p.a * s * s * rho * rho / (1.0 + 2.0 * p.b * rho - p.b * p.b * rho * rho);
-}
-
 // Output columns of one tile: a CTA of `cols` threads writes cols - 8 columns.
 int tile_cols(int cols) { return cols - 8; }
 
@@ -113,15 +215,7 @@ void build_tiles(int nx, int ny, int cols, int rows, std::vector<Tile>& out) {
 
 // Rows per band for a tile width: enough CTAs to fill 152 SMs a few times over
 // while keeping the 4-row band overhead small.
-int default_rows(int nx, int ny, int cols) {
-  const int strips = (nx + tile_cols(cols) - 1) / tile_cols(cols);
-  const long long target = 152LL * 8;
-  long long rows = ((long long)ny * strips + target - 1) / target;
-  rows = std::max<long long>(rows, 16);
-  rows = std::min<long long>(rows, 128);
-  rows = std::min<long long>(rows, ny);
-  return (int)std::max<long long>(rows, kMinRows < ny ? kMinRows : ny);
-}
+int default_rows(int nx, int ny, int cols) { return default_band_rows(nx, ny, cols); }
 
 }  // namespace
 
@@ -214,102 +308,16 @@ lbm_status launch(lbm_ctx* c, int mode) {
   return LBM_OK;
 }
 
-lbm_status validate_params(const lbm_ctx* c, const lbm_params* p, std::string& why) {
-  if (!p) { why = "params is NULL"; return LBM_EINVAL; }
-  if (p->size != sizeof(lbm_params)) { why = "params.size != sizeof(lbm_params)"; return LBM_EINVAL; }
-  if (p->geometry < 0 || p->geometry > 2) { why = "geometry must be 0, 1 or 2"; return LBM_EINVAL; }
-  if (p->geometry == LBM_GEOM_CHANNEL && (c->nx < 3 || c->ny < 2)) { why = "channel needs nx >= 3 and ny >= 2"; return LBM_EINVAL; }
-  if (p->geometry == LBM_GEOM_WALLS && c->ny < 2) { why = "walls geometry needs ny >= 2"; return LBM_EINVAL; }
-  if (p->thermal != 0 && p->thermal != 1) { why = "thermal must be 0 or 1"; return LBM_EINVAL; }
-  if (p->multiphase != 0 && p->multiphase != 1) { why = "multiphase must be 0 or 1"; return LBM_EINVAL; }
-  if (!(p->tau_f > 0.5) || !(p->tau_g > 0.5)) { why = "tau_f and tau_g must exceed 1/2"; return LBM_EINVAL; }
-  if (!(p->a > 0) || !(p->b > 0) || !(p->R > 0)) { why = "a, b, R must be positive"; return LBM_EINVAL; }
-  if (!(p->T0_R > 0) || !(p->Tin_R > 0) || !(p->Tin_R + p->dTheat_R > 0)) { why = "temperatures must be positive"; return LBM_EINVAL; }
-  if (p->multiphase && (!(p->c0 > 0) || p->G == 0.0 || !std::isfinite(p->G))) { why = "c0 > 0 and G != 0 required"; return LBM_EINVAL; }
-  if (p->thermal && !(p->c_v > 0)) { why = "c_v must be positive"; return LBM_EINVAL; }
-  if (p->geometry == LBM_GEOM_CHANNEL && (!(p->rho_out > 0) || !(std::fabs(p->u_in) < 0.5))) { why = "rho_out > 0 and |u_in| < 0.5 required"; return LBM_EINVAL; }
-  if (p->heater_len < 0) { why = "heater_len must be >= 0"; return LBM_EINVAL; }
-  if (p->init_kind != LBM_INIT_UNIFORM && p->init_kind != LBM_INIT_DISK) { why = "init_kind must be 0 or 1"; return LBM_EINVAL; }
-  if (!(p->init_rho_out > 0) || (p->init_kind == LBM_INIT_DISK && (!(p->init_rho_in > 0) || !(p->init_width > 0)))) {
-    why = "initial densities and width must be positive"; return LBM_EINVAL;
-  }
-  if (!std::isfinite(p->u_in) || !std::isfinite(p->g_a) || !std::isfinite(p->G_wet) || !std::isfinite(p->beta)) {
-    why = "non-finite parameter"; return LBM_EINVAL;
-  }
-  return LBM_OK;
-}
-
 // Fill the device instance descriptor from validated parameters.
 lbm_status apply_params(lbm_ctx* c, const lbm_params* p) {
-  std::string why;
-  lbm_status s = validate_params(c, p, why);
-  if (s != LBM_OK) return fail(c, s, why);
+  if (const char* why = check_params(c->nx, c->ny, p)) return fail(c, LBM_EINVAL, why);
   Inst& I = c->hinst;
-  I = Inst{};
-  I.nx = c->nx;
-  I.ny = c->ny;
-  I.pitch = c->L.pitch;
-  I.geometry = p->geometry;
-  I.plane = c->L.plane;
+  if (const char* why = fill_inst(I, p, c->nx, c->ny, c->L.pitch, c->L.plane, c->prec == LBM_FP64))
+    return fail(c, LBM_EINVAL, why);
   for (int b = 0; b < 2; ++b) {
     I.f[b] = c->base + c->L.off_f[b];
     I.g[b] = c->base + c->L.off_g[b];
   }
-  I.multiphase = p->multiphase;
-  I.omega_f = 1.0 / p->tau_f;
-  I.omega_g = 1.0 / p->tau_g;
-  const double Tc = 0.0778 * p->a / (0.45724 * p->b * p->R);
-  I.a = p->a;
-  I.b = p->b;
-  I.R = p->R;
-  I.kappa = 0.37464 + 1.54226 * p->omega - 0.26992 * p->omega * p->omega;
-  I.sqrtTc = std::sqrt(Tc);
-  I.inv_sqrtTc = 1.0 / I.sqrtTc;
-  I.T0 = p->T0_R * Tc;
-  I.T_in = p->Tin_R * Tc;
-  I.T_heat = (p->Tin_R + p->dTheat_R) * Tc;
-  {
-    const double sa = 1.0 + I.kappa * (1.0 - std::sqrt(I.T0 / Tc));
-    I.alpha0 = sa * sa;
-  }
-  if (p->multiphase) {
-    I.psi_scale = 2.0 / (p->c0 * p->G);
-    const double rad = (host_pressure(*p, p->rho_w, I.T0) - p->rho_w / 3.0) * I.psi_scale;
-    if (!(rad >= 0.0)) return fail(c, LBM_EINVAL, "psi(rho_w, T0) undefined: negative radicand (Eq. 11)");
-    I.Gwet_psiw = p->G_wet * std::sqrt(rad);
-    if (!(p->b * std::max(p->rho_w, p->init_rho_out) < 1.0)) return fail(c, LBM_EINVAL, "density beyond 1/b");
-  }
-  I.beta = p->beta;
-  I.G2 = 2.0 * p->G;
-  I.Ghalf = 0.5 * p->G;
-  I.g_a = p->g_a;
-  I.inv_cv = p->thermal ? 1.0 / p->c_v : 0.0;
-  I.u_in = p->u_in;
-  I.rho_out = p->rho_out;
-  if (c->prec == LBM_FP32) {
-    I.rho_ref = p->geometry == LBM_GEOM_CHANNEL ? p->rho_out : p->init_rho_out;
-    I.T_ref = I.T0;
-  } else {
-    I.rho_ref = 0.0;
-    I.T_ref = 0.0;
-  }
-  if (c->prec == LBM_FP32 && p->multiphase) {
-    const double rr = I.rho_ref, Tr = I.T_ref;
-    const double u1r = 1.0 - p->b * rr, Dr = 1.0 + 2.0 * p->b * rr - p->b * p->b * rr * rr;
-    if (!(u1r > 0.0) || !(Dr > 0.0)) return fail(c, LBM_EINVAL, "reference density beyond 1/b");
-    I.sa_r = 1.0 + I.kappa * (1.0 - std::sqrt(Tr / Tc));
-    I.p_ref = rr * p->R * Tr / u1r - p->a * I.sa_r * I.sa_r * rr * rr / Dr;
-    I.rad_ref = (I.p_ref - rr / 3.0) * I.psi_scale;
-    if (!(I.rad_ref >= 0.0)) return fail(c, LBM_EINVAL, "psi undefined at the reference state (Eq. 11)");
-    I.psi_ref = std::sqrt(I.rad_ref);
-    I.inv_u1r = 1.0 / u1r;
-    I.inv_Dr = 1.0 / Dr;
-    I.sqrtT_r = std::sqrt(Tr);
-    I.rr2_Dr = rr * rr / Dr;
-  }
-  I.heater_x0 = p->heater_x0 < 0 ? c->nx / 5 : p->heater_x0;
-  I.heater_len = p->heater_len;
-  I.heat_on_step = p->heat_on_step;
   I.st = c->d_state;
   I.partials = reinterpret_cast<double*>(c->base + c->L.off_part);
   I.ring = reinterpret_cast<double*>(c->base + c->L.off_ring);

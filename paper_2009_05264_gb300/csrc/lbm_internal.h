@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "pplbm.h"
+
 namespace pplbm {
 
 // Per-tile partial sums folded by the last CTA of an instance:
@@ -77,5 +79,14 @@ struct InitSpec {
 cudaError_t launch_init_builtin(int fp64, const Inst* d_inst, int nx, int ny, InitSpec spec, cudaStream_t s);
 
 bool cols_supported(int cols);
+
+// Host helpers shared by the context API and the allocation-free step.
+// check_params: nullptr when p is valid for an nx x ny lattice, else the reason.
+const char* check_params(int nx, int ny, const lbm_params* p);
+// fill_inst: the physics part of an instance descriptor (buffer and scratch pointers
+// are left null); nullptr on success, else the reason.
+const char* fill_inst(Inst& I, const lbm_params* p, int nx, int ny, int pitch, long long plane, int fp64);
+// Rows per band of the default tiling for CTAs of `cols` threads.
+int default_band_rows(int nx, int ny, int cols);
 
 }  // namespace pplbm
