@@ -196,6 +196,41 @@ void* lbm_get_stream(const lbm_ctx* ctx);
 /* Critical temperature of the parameters' Eq. 12: Tc = 0.0778 a / (0.45724 b R). */
 double lbm_critical_temperature(const lbm_params* p);
 
+/* One fused step without any device allocation, for callers that cannot call
+ * cudaMalloc: code that runs inside a process whose device memory is owned by
+ * another allocator or budgeted to the last byte, or a plug-in that may only use
+ * the buffers its host hands it.  The paper has no counterpart; this is a calling
+ * convention of the library.
+ *
+ * Populations are caller-owned device arrays in the library's storage form:
+ * 9 planes of ny rows of nx elements (no padding), element type float for
+ * LBM_FP32 and double for LBM_FP64.  FP32 stores deviations from the rest state,
+ * f_i - w_i rho_ref and g_i - w_i T0 (rho_ref = p->rho_out for a channel, else
+ * p->init_rho_out; T0 = p->T0_R * Tc); FP64 stores the populations themselves.
+ * in_post_stream = 1: f_in, g_in hold post-stream populations f^n (an initial
+ * state); 0: they hold the previous call's output, which this call streams.
+ * f_out, g_out receive the post-collision populations of step `step` and must not
+ * alias the inputs; g_in and g_out may be NULL when p->thermal is 0.
+ * rho_avg_prev is the domain-mean density of step - 1 (buoyancy, Eq. 14);
+ * diag_out (host, LBM_D_COUNT doubles, may be NULL) receives this step's record,
+ * whose LBM_D_RHO_AVG is the rho_avg_prev of the next call.  The call waits for
+ * the step on cuda_stream (a cudaStream_t; NULL = the default stream).
+ *
+ * Scratch: a fixed 0.65 MB device array inside the library, which every GPU that
+ * loads the library holds until the process exits.  The first call on a device
+ * looks up that array's device address (once per device, with the device
+ * current); make that first call before capturing any CUDA graph.  Every call
+ * reuses the same array and overwrites the previous call's contents, so calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Sizes beyond the array's capacity are rejected:
+ * the lattice is cut into ceil(nx / 120) column strips and at most 8192 tiles,
+ * so nx > 983040, or 9 * nx * ny >= 2^31, returns LBM_EINVAL.
+ * Errors: LBM_EINVAL (invalid parameters, sizes, NULL or aliased buffers),
+ * LBM_EUNSTABLE (as lbm_step), LBM_ECUDA. */
+lbm_status lbm_step_noalloc(const lbm_params* p, int32_t nx, int32_t ny, lbm_precision prec, const void* f_in,
+                            const void* g_in, void* f_out, void* g_out, int32_t in_post_stream, int64_t step,
+                            double rho_avg_prev, double* diag_out, void* cuda_stream);
+
 /* Free the context and its device memory (not caller-provided memory).  NULL-safe. */
 lbm_status lbm_destroy(lbm_ctx* ctx);
 

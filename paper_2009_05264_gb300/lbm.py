@@ -30,7 +30,7 @@ EXPORTS = (
     "lbm_init_fields", "lbm_step", "lbm_step_async", "lbm_sync", "lbm_read_fields", "lbm_get_populations",
     "lbm_set_populations", "lbm_read_diagnostics", "lbm_state_bytes", "lbm_save_state", "lbm_load_state",
     "lbm_set_tiling", "lbm_get_step", "lbm_launch_count", "lbm_get_stream", "lbm_critical_temperature",
-    "lbm_destroy", "lbm_status_string", "lbm_last_error",
+    "lbm_destroy", "lbm_status_string", "lbm_last_error", "lbm_step_noalloc",
 )
 
 
@@ -97,6 +97,8 @@ def load(build_if_missing: bool = True):
         "lbm_destroy": (ctypes.c_int, [vp]),
         "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "lbm_last_error": (ctypes.c_char_p, [vp]),
+        "lbm_step_noalloc": (ctypes.c_int, [P, i32, i32, ctypes.c_int, vp, vp, vp, vp, i32, i64, ctypes.c_double,
+                                            dp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
