@@ -196,6 +196,52 @@ void* lbm_get_stream(const lbm_ctx* ctx);
 /* Critical temperature of the parameters' Eq. 12: Tc = 0.0778 a / (0.45724 b R). */
 double lbm_critical_temperature(const lbm_params* p);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent lattices of uneven size and parameters advanced
+ * together, one fused launch per step over all members' tiles (replayed from a
+ * captured CUDA graph in runs of 16 steps).  Members share the batch's precision,
+ * thermal flag, device and stream; each member is an lbm_ctx owned by the batch,
+ * reachable through lbm_batch_member() for initialisation and readback (do not
+ * step a member on its own while the batch is stepping it).  A member's results
+ * are those of the same lattice run alone with the batch's tiling.
+ * ------------------------------------------------------------------------- */
+
+/* Create an empty batch.  cuda_stream NULL: the batch creates and owns a stream. */
+lbm_status lbm_batch_create(lbm_batch** out, lbm_precision prec, int32_t thermal, int32_t device,
+                            void* cuda_stream);
+/* Add an nx x ny member with parameters p (p->thermal must match the batch), initialised
+ * as lbm_set_params does; *slot receives its index (freed slots are reused).
+ * Allocates the member's device memory (lbm_required_bytes). */
+lbm_status lbm_batch_add(lbm_batch* b, int32_t nx, int32_t ny, const lbm_params* p, int32_t* slot);
+/* Remove a member and free its device memory (waits for the batch's stream). */
+lbm_status lbm_batch_remove(lbm_batch* b, int32_t slot);
+/* The member's context, or NULL for a free slot.  Owned by the batch. */
+lbm_ctx* lbm_batch_member(lbm_batch* b, int32_t slot);
+int32_t lbm_batch_size(const lbm_batch* b);
+/* Tiling of the batched launch: threads per CTA (64, 128, 256) and rows per band
+ * (0 = each member's default, else >= 4). */
+lbm_status lbm_batch_set_tiling(lbm_batch* b, int32_t cols, int32_t rows);
+lbm_status lbm_batch_get_tiling(const lbm_batch* b, int32_t* cols, int32_t* rows);
+/* Time trial_steps of every candidate tiling on the current members and keep the
+ * fastest (reported in *cols, *rows; either may be NULL).  The trials advance the
+ * members: re-initialise them afterwards if their state matters. */
+lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, int32_t* cols, int32_t* rows);
+/* Advance every member nsteps steps, then wait and check every member's status
+ * (LBM_EUNSTABLE if any member left the EOS domain). */
+lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps);
+/* Enqueue without waiting; lbm_batch_sync waits, returns the first failing member's
+ * status and its slot in *unstable_slot (-1 if none; may be NULL). */
+lbm_status lbm_batch_step_async(lbm_batch* b, int64_t nsteps);
+lbm_status lbm_batch_sync(lbm_batch* b, int32_t* unstable_slot);
+/* lbm_read_fields of one member. */
+lbm_status lbm_batch_read_fields(lbm_batch* b, int32_t slot, double* rho, double* ux, double* uy, double* T,
+                                 size_t n);
+int64_t lbm_batch_launch_count(const lbm_batch* b);
+void* lbm_batch_get_stream(const lbm_batch* b);
+const char* lbm_batch_last_error(const lbm_batch* b);
+/* Destroy the batch and every member.  NULL-safe. */
+lbm_status lbm_batch_destroy(lbm_batch* b);
+
 /* One fused step without any device allocation, for callers that cannot call
  * cudaMalloc: code that runs inside a process whose device memory is owned by
  * another allocator or budgeted to the last byte, or a plug-in that may only use

@@ -241,6 +241,7 @@ struct lbm_ctx {
   int thermal = 0;
   long long launches = 0;
   long long step_host = 0;  // step count as last synchronised
+  unsigned long long params_gen = 0;  // bumped whenever the descriptor changes
   std::string err;
 };
 
@@ -325,6 +326,7 @@ lbm_status apply_params(lbm_ctx* c, const lbm_params* p) {
   c->params = *p;
   c->thermal = p->thermal;
   c->have_params = true;
+  ++c->params_gen;
   return LBM_OK;
 }
 
@@ -393,6 +395,11 @@ lbm_status create_impl(lbm_ctx** out, int32_t nx, int32_t ny, lbm_precision prec
 }
 
 }  // namespace
+
+namespace pplbm {
+Inst lbm_internal_inst(const lbm_ctx* c) { return c->hinst; }
+unsigned long long lbm_internal_params_gen(const lbm_ctx* c) { return c->params_gen; }
+}  // namespace pplbm
 
 extern "C" {
 

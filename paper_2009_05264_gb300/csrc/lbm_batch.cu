@@ -1,0 +1,388 @@
+// Batches of independent lattices advanced by one fused launch per step.
+//
+// A batch owns member contexts (each with its own populations, step state,
+// partial sums and diagnostics ring, created on the batch's stream) and a
+// concatenated tile table over all members; one launch of the fused kernel per
+// step covers every member's tiles, so lattices of uneven size and parameters
+// share the GPU in one grid.  Each member's partials are folded by that member's
+// last tile, so per-member results are those of the member run alone with the same
+// tiling.  Runs of steps are captured once into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+#include "pplbm.h"
+
+using namespace pplbm;
+
+namespace {
+
+constexpr int kGraphChunk = 16;  // steps per captured graph
+
+struct Member {
+  lbm_ctx* ctx = nullptr;
+  int nx = 0, ny = 0;
+  unsigned long long gen = 0;  // descriptor generation copied into the device table
+};
+
+}  // namespace
+
+struct lbm_batch {
+  lbm_precision prec = LBM_FP32;
+  int thermal = 1;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<Member> slots;  // empty ctx = free slot
+  int cols = 128, rows = 0;   // rows 0: each member's default band height
+  // device tables of the current membership
+  Inst* d_insts = nullptr;
+  Tile* d_tiles = nullptr;
+  size_t cap_insts = 0, cap_tiles = 0;
+  int ntiles = 0;
+  bool dirty = true;
+  cudaGraphExec_t graph = nullptr;
+  long long launches = 0;
+  std::string err;
+};
+
+namespace {
+
+lbm_status bfail(lbm_batch* b, lbm_status s, const std::string& msg) {
+  if (b) b->err = msg;
+  return s;
+}
+
+#define LBM_BCUDA(b, call)                                                                     \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return bfail(b, LBM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+void drop_graph(lbm_batch* b) {
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+}
+
+int member_rows(const lbm_batch* b, int nx, int ny) {
+  const int r = b->rows > 0 ? b->rows : default_band_rows(nx, ny, b->cols);
+  return std::max(1, std::min(r, ny));
+}
+
+// Upload the descriptors and the concatenated tile table of the active members.
+lbm_status rebuild(lbm_batch* b) {
+  std::vector<Inst> insts;
+  std::vector<Tile> tiles;
+  const int w = b->cols - 8;
+  for (Member& m : b->slots) {
+    if (!m.ctx) continue;
+    const int idx = (int)insts.size();
+    insts.push_back(lbm_internal_inst(m.ctx));
+    m.gen = lbm_internal_params_gen(m.ctx);
+    const int rows = member_rows(b, m.nx, m.ny);
+    const int strips = (m.nx + w - 1) / w, bands = (m.ny + rows - 1) / rows;
+    const int n = strips * bands;
+    int local = 0;
+    for (int bd = 0; bd < bands; ++bd)
+      for (int sx = 0; sx < strips; ++sx) {
+        Tile t{};
+        t.inst = idx;
+        t.x0 = sx * w;
+        t.y0 = bd * rows;
+        t.y1 = std::min(m.ny, (bd + 1) * rows);
+        t.local = local++;
+        t.ntiles = n;
+        tiles.push_back(t);
+      }
+  }
+  if (insts.size() > b->cap_insts) {
+    if (b->d_insts) cudaFree(b->d_insts);
+    b->d_insts = nullptr;
+    b->cap_insts = std::max<size_t>(insts.size(), 2 * b->cap_insts);
+    if (cudaMalloc(&b->d_insts, b->cap_insts * sizeof(Inst)) != cudaSuccess) {
+      b->cap_insts = 0;
+      return bfail(b, LBM_ENOMEM, "batch descriptor table");
+    }
+  }
+  if (tiles.size() > b->cap_tiles) {
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    b->d_tiles = nullptr;
+    b->cap_tiles = std::max<size_t>(tiles.size(), 2 * b->cap_tiles);
+    if (cudaMalloc(&b->d_tiles, b->cap_tiles * sizeof(Tile)) != cudaSuccess) {
+      b->cap_tiles = 0;
+      return bfail(b, LBM_ENOMEM, "batch tile table");
+    }
+  }
+  if (!insts.empty()) {
+    LBM_BCUDA(b, cudaMemcpyAsync(b->d_insts, insts.data(), insts.size() * sizeof(Inst), cudaMemcpyHostToDevice,
+                                 b->stream));
+    LBM_BCUDA(b, cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice,
+                                 b->stream));
+  }
+  LBM_BCUDA(b, cudaStreamSynchronize(b->stream));
+  b->ntiles = (int)tiles.size();
+  drop_graph(b);
+  b->dirty = false;
+  return LBM_OK;
+}
+
+lbm_status launch_steps(lbm_batch* b, int64_t n) {
+  for (int64_t k = 0; k < n; ++k) {
+    LBM_BCUDA(b, launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->d_insts, b->d_tiles, b->ntiles,
+                            b->stream));
+    ++b->launches;
+  }
+  return LBM_OK;
+}
+
+lbm_status capture_graph(lbm_batch* b) {
+  cudaGraph_t g = nullptr;
+  LBM_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  lbm_status s = LBM_OK;
+  for (int k = 0; k < kGraphChunk && s == LBM_OK; ++k) {
+    if (launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->d_insts, b->d_tiles, b->ntiles,
+                   b->stream) != cudaSuccess)
+      s = bfail(b, LBM_ECUDA, "launch during graph capture");
+  }
+  const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  if (s != LBM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return bfail(b, LBM_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  const cudaError_t ei = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    b->graph = nullptr;
+    return bfail(b, LBM_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei));
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_create(lbm_batch** out, lbm_precision prec, int32_t thermal, int32_t device, void* cuda_stream) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  if ((prec != LBM_FP32 && prec != LBM_FP64) || (thermal != 0 && thermal != 1)) return LBM_EINVAL;
+  lbm_batch* b = new (std::nothrow) lbm_batch();
+  if (!b) return LBM_ENOMEM;
+  b->prec = prec;
+  b->thermal = thermal;
+  b->device = device;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete b;
+    return LBM_ECUDA;
+  }
+  if (cuda_stream) {
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      if (prev >= 0) cudaSetDevice(prev);
+      return LBM_ECUDA;
+    }
+    b->own_stream = true;
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  *out = b;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_add(lbm_batch* b, int32_t nx, int32_t ny, const lbm_params* p, int32_t* slot) {
+  if (!b || !slot) return LBM_EINVAL;
+  if (!p || p->thermal != b->thermal) return bfail(b, LBM_EINVAL, "member must match the batch's thermal flag");
+  lbm_ctx* c = nullptr;
+  lbm_status s = lbm_create(&c, nx, ny, b->prec, b->device, b->stream);
+  if (s != LBM_OK) return bfail(b, s, "member creation failed");
+  s = lbm_set_params(c, p);
+  if (s != LBM_OK) {
+    b->err = lbm_last_error(c);
+    lbm_destroy(c);
+    return s;
+  }
+  int idx = -1;
+  for (size_t i = 0; i < b->slots.size(); ++i)
+    if (!b->slots[i].ctx) {
+      idx = (int)i;
+      break;
+    }
+  if (idx < 0) {
+    idx = (int)b->slots.size();
+    b->slots.push_back(Member{});
+  }
+  b->slots[idx].ctx = c;
+  b->slots[idx].nx = nx;
+  b->slots[idx].ny = ny;
+  b->dirty = true;
+  *slot = idx;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_remove(lbm_batch* b, int32_t slot) {
+  if (!b || slot < 0 || slot >= (int32_t)b->slots.size() || !b->slots[slot].ctx) return bfail(b, LBM_EINVAL, "no such slot");
+  cudaStreamSynchronize(b->stream);
+  lbm_destroy(b->slots[slot].ctx);
+  b->slots[slot] = Member{};
+  b->dirty = true;
+  return LBM_OK;
+}
+
+lbm_ctx* lbm_batch_member(lbm_batch* b, int32_t slot) {
+  if (!b || slot < 0 || slot >= (int32_t)b->slots.size()) return nullptr;
+  return b->slots[slot].ctx;
+}
+
+int32_t lbm_batch_size(const lbm_batch* b) {
+  if (!b) return 0;
+  int32_t n = 0;
+  for (const Member& m : b->slots) n += m.ctx != nullptr;
+  return n;
+}
+
+lbm_status lbm_batch_set_tiling(lbm_batch* b, int32_t cols, int32_t rows) {
+  if (!b) return LBM_EINVAL;
+  if (cols == 0) cols = 128;
+  if (!cols_supported(cols)) return bfail(b, LBM_EINVAL, "cols must be 64, 128 or 256");
+  if (rows < 0 || (rows > 0 && rows < 4)) return bfail(b, LBM_EINVAL, "rows must be 0 (per-member default) or >= 4");
+  b->cols = cols;
+  b->rows = rows;
+  b->dirty = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_get_tiling(const lbm_batch* b, int32_t* cols, int32_t* rows) {
+  if (!b || !cols || !rows) return LBM_EINVAL;
+  *cols = b->cols;
+  *rows = b->rows;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_step_async(lbm_batch* b, int64_t nsteps) {
+  if (!b || nsteps < 0) return LBM_EINVAL;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->device);
+  lbm_status s = LBM_OK;
+  for (const Member& m : b->slots)  // a member's parameters or state were replaced directly
+    if (m.ctx && m.gen != lbm_internal_params_gen(m.ctx)) b->dirty = true;
+  if (b->dirty) s = rebuild(b);
+  if (s == LBM_OK && b->ntiles > 0) {
+    int64_t left = nsteps;
+    if (left >= kGraphChunk && !b->graph) s = capture_graph(b);
+    while (s == LBM_OK && left >= kGraphChunk) {
+      const cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+      if (e != cudaSuccess) s = bfail(b, LBM_ECUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+      b->launches += kGraphChunk;
+      left -= kGraphChunk;
+    }
+    if (s == LBM_OK) s = launch_steps(b, left);
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  return s;
+}
+
+lbm_status lbm_batch_sync(lbm_batch* b, int32_t* unstable_slot) {
+  if (!b) return LBM_EINVAL;
+  if (unstable_slot) *unstable_slot = -1;
+  lbm_status worst = LBM_OK;
+  for (size_t i = 0; i < b->slots.size(); ++i) {
+    if (!b->slots[i].ctx) continue;
+    const lbm_status s = lbm_sync(b->slots[i].ctx);
+    if (s != LBM_OK && worst == LBM_OK) {
+      worst = s;
+      b->err = lbm_last_error(b->slots[i].ctx);
+      if (unstable_slot) *unstable_slot = (int32_t)i;
+    }
+  }
+  return worst;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps) {
+  const lbm_status s = lbm_batch_step_async(b, nsteps);
+  if (s != LBM_OK) return s;
+  return lbm_batch_sync(b, nullptr);
+}
+
+lbm_status lbm_batch_read_fields(lbm_batch* b, int32_t slot, double* rho, double* ux, double* uy, double* T,
+                                 size_t n) {
+  lbm_ctx* c = lbm_batch_member(b, slot);
+  if (!c) return bfail(b, LBM_EINVAL, "no such slot");
+  return lbm_read_fields(c, rho, ux, uy, T, n);
+}
+
+lbm_status lbm_batch_autotune(lbm_batch* b, int32_t trial_steps, int32_t* cols_out, int32_t* rows_out) {
+  if (!b || trial_steps < 1) return LBM_EINVAL;
+  static const int kCols[] = {64, 128, 256};
+  static const int kRows[] = {0, 16, 24, 32, 48, 64};
+  cudaEvent_t e0, e1;
+  LBM_BCUDA(b, cudaEventCreate(&e0));
+  LBM_BCUDA(b, cudaEventCreate(&e1));
+  float best = -1.0f;
+  int best_c = b->cols, best_r = b->rows;
+  lbm_status s = LBM_OK;
+  for (int c : kCols) {
+    for (int r : kRows) {
+      if ((s = lbm_batch_set_tiling(b, c, r)) != LBM_OK) break;
+      if ((s = lbm_batch_step_async(b, 2)) != LBM_OK) break;  // warm-up and table upload
+      cudaEventRecord(e0, b->stream);
+      if ((s = lbm_batch_step_async(b, trial_steps)) != LBM_OK) break;
+      cudaEventRecord(e1, b->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        s = bfail(b, LBM_ECUDA, "autotune timing");
+        break;
+      }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (best < 0.0f || ms < best) {
+        best = ms;
+        best_c = c;
+        best_r = r;
+      }
+    }
+    if (s != LBM_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != LBM_OK) return s;
+  lbm_batch_set_tiling(b, best_c, best_r);
+  if (cols_out) *cols_out = best_c;
+  if (rows_out) *rows_out = best_r;
+  return lbm_batch_sync(b, nullptr);
+}
+
+int64_t lbm_batch_launch_count(const lbm_batch* b) { return b ? b->launches : -1; }
+
+void* lbm_batch_get_stream(const lbm_batch* b) { return b ? static_cast<void*>(b->stream) : nullptr; }
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : "NULL batch"; }
+
+lbm_status lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return LBM_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->device);
+  cudaStreamSynchronize(b->stream);
+  drop_graph(b);
+  for (Member& m : b->slots)
+    if (m.ctx) lbm_destroy(m.ctx);
+  if (b->d_insts) cudaFree(b->d_insts);
+  if (b->d_tiles) cudaFree(b->d_tiles);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete b;
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -88,5 +88,9 @@ const char* check_params(int nx, int ny, const lbm_params* p);
 const char* fill_inst(Inst& I, const lbm_params* p, int nx, int ny, int pitch, long long plane, int fp64);
 // Rows per band of the default tiling for CTAs of `cols` threads.
 int default_band_rows(int nx, int ny, int cols);
+// The instance descriptor of a context (device pointers included), for batching.
+Inst lbm_internal_inst(const lbm_ctx* c);
+// Changes whenever the context's descriptor is rewritten (parameters or a loaded state).
+unsigned long long lbm_internal_params_gen(const lbm_ctx* c);
 
 }  // namespace pplbm

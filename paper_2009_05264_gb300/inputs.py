@@ -82,3 +82,18 @@ def smooth_random(nx: int, ny: int, rho0: float, T0: float, seed: int, drho: flo
     uy = du * np.sin(sx * x + ph[4]) * np.sin(sy * y + ph[5])
     T = T0 * (1.0 + dT * np.cos(sx * x + ph[6]) * np.sin(sy * y + ph[7]))
     return rho, ux, uy, T
+
+
+def sweep_draws(n: int, seed: int, nx_range=(400, 2000), ny_range=(50, 200), u_range=(0.01, 0.05),
+                dT_range=(0.03, 0.12), rho_w_range=(5.0, 6.2)):
+    """Seeded parameter draws of a channel sweep: lattice size (uniform integers,
+    inclusive), inlet velocity, heater superheat (in units of T_c) and wall density
+    rho_w (the wetting parameter), each uniform in its range.  Returns a list of dicts."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        out.append(dict(nx=int(rng.integers(nx_range[0], nx_range[1] + 1)),
+                        ny=int(rng.integers(ny_range[0], ny_range[1] + 1)),
+                        u_in=float(rng.uniform(*u_range)), dTheat_R=float(rng.uniform(*dT_range)),
+                        rho_w=float(rng.uniform(*rho_w_range))))
+    return out

@@ -31,6 +31,10 @@ EXPORTS = (
     "lbm_set_populations", "lbm_read_diagnostics", "lbm_state_bytes", "lbm_save_state", "lbm_load_state",
     "lbm_set_tiling", "lbm_get_step", "lbm_launch_count", "lbm_get_stream", "lbm_critical_temperature",
     "lbm_destroy", "lbm_status_string", "lbm_last_error", "lbm_step_noalloc",
+    "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_member", "lbm_batch_size",
+    "lbm_batch_set_tiling", "lbm_batch_get_tiling", "lbm_batch_autotune", "lbm_batch_step",
+    "lbm_batch_step_async", "lbm_batch_sync", "lbm_batch_read_fields", "lbm_batch_launch_count",
+    "lbm_batch_get_stream", "lbm_batch_last_error", "lbm_batch_destroy",
 )
 
 
@@ -99,6 +103,22 @@ def load(build_if_missing: bool = True):
         "lbm_last_error": (ctypes.c_char_p, [vp]),
         "lbm_step_noalloc": (ctypes.c_int, [P, i32, i32, ctypes.c_int, vp, vp, vp, vp, i32, i64, ctypes.c_double,
                                             dp, vp]),
+        "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, i32, i32, vp]),
+        "lbm_batch_add": (ctypes.c_int, [vp, i32, i32, P, ctypes.POINTER(i32)]),
+        "lbm_batch_remove": (ctypes.c_int, [vp, i32]),
+        "lbm_batch_member": (vp, [vp, i32]),
+        "lbm_batch_size": (i32, [vp]),
+        "lbm_batch_set_tiling": (ctypes.c_int, [vp, i32, i32]),
+        "lbm_batch_get_tiling": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "lbm_batch_autotune": (ctypes.c_int, [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "lbm_batch_step": (ctypes.c_int, [vp, i64]),
+        "lbm_batch_step_async": (ctypes.c_int, [vp, i64]),
+        "lbm_batch_sync": (ctypes.c_int, [vp, ctypes.POINTER(i32)]),
+        "lbm_batch_read_fields": (ctypes.c_int, [vp, i32, dp, dp, dp, dp, sz]),
+        "lbm_batch_launch_count": (i64, [vp]),
+        "lbm_batch_get_stream": (vp, [vp]),
+        "lbm_batch_last_error": (ctypes.c_char_p, [vp]),
+        "lbm_batch_destroy": (ctypes.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -263,3 +283,116 @@ class Lattice:
     def load_state(self, blob: bytes):
         buf = ctypes.create_string_buffer(blob, len(blob))
         self._check(self._L.lbm_load_state(self._h, buf, len(blob)))
+
+
+class Member(Lattice):
+    """A batch member: a lattice whose context the batch owns (never destroyed here)."""
+
+    def __init__(self, batch, slot: int, nx: int, ny: int):
+        self.nx, self.ny = int(nx), int(ny)
+        self.precision = batch.precision
+        self.device = batch.device
+        self._L = batch._L
+        self._h = ctypes.c_void_p(batch._L.lbm_batch_member(batch._h, slot))
+        self._mem = None
+        self._batch = batch  # keeps the batch (and so the context) alive
+        self.slot = slot
+        self.params = None
+
+    def close(self):
+        self._h = None
+
+    def set_params(self, p: dict):
+        raise LbmError(7, "a member's parameters are fixed when it is added to the batch")
+
+
+class Batch:
+    """Many independent lattices advanced by one fused launch per step (C ABI lbm_batch_*)."""
+
+    def __init__(self, precision: str = "fp32", thermal: bool = True, device: int = 0, stream=None):
+        self._L = load()
+        self.precision = FP64 if precision in ("fp64", "f64", FP64) else FP32
+        self.thermal = 1 if thermal else 0
+        self.device = int(device)
+        sptr = None
+        if stream is not None:
+            sptr = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        h = ctypes.c_void_p()
+        st = self._L.lbm_batch_create(ctypes.byref(h), self.precision, self.thermal, self.device, sptr)
+        if st != 0:
+            raise LbmError(st, "lbm_batch_create failed")
+        self._h = h
+        self.members = {}
+
+    def _check(self, st: int):
+        if st != 0:
+            raise LbmError(st, self._L.lbm_batch_last_error(self._h).decode())
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self.members.clear()
+            self._L.lbm_batch_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, nx: int, ny: int, p: dict) -> Member:
+        slot = ctypes.c_int32()
+        self._check(self._L.lbm_batch_add(self._h, int(nx), int(ny), ctypes.byref(make_params(p, nx)),
+                                          ctypes.byref(slot)))
+        m = Member(self, slot.value, nx, ny)
+        m.params = dict(p)
+        self.members[slot.value] = m
+        return m
+
+    def remove(self, slot: int):
+        self._check(self._L.lbm_batch_remove(self._h, int(slot)))
+        m = self.members.pop(slot, None)
+        if m is not None:
+            m.close()  # its context is gone
+
+    def __len__(self):
+        return int(self._L.lbm_batch_size(self._h))
+
+    def set_tiling(self, cols: int, rows: int = 0):
+        self._check(self._L.lbm_batch_set_tiling(self._h, int(cols), int(rows)))
+
+    @property
+    def tiling(self):
+        c, r = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._L.lbm_batch_get_tiling(self._h, ctypes.byref(c), ctypes.byref(r)))
+        return c.value, r.value
+
+    def autotune(self, trial_steps: int = 20):
+        c, r = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._L.lbm_batch_autotune(self._h, int(trial_steps), ctypes.byref(c), ctypes.byref(r)))
+        return c.value, r.value
+
+    def step(self, n: int = 1):
+        self.step_async(n)
+        self.sync()
+
+    def step_async(self, n: int = 1):
+        self._check(self._L.lbm_batch_step_async(self._h, int(n)))
+
+    def sync(self):
+        slot = ctypes.c_int32(-1)
+        st = self._L.lbm_batch_sync(self._h, ctypes.byref(slot))
+        if st != 0:
+            raise LbmError(st, f"member {slot.value}: " + self._L.lbm_batch_last_error(self._h).decode())
+
+    @property
+    def launches(self) -> int:
+        return int(self._L.lbm_batch_launch_count(self._h))
+
+    @property
+    def stream(self):
+        import torch
+
+        return torch.cuda.ExternalStream(int(self._L.lbm_batch_get_stream(self._h) or 0),
+                                         device=torch.device("cuda", self.device))

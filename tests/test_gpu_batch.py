@@ -1,0 +1,122 @@
+"""Batched launches: every member of a batch evolves exactly as the same lattice alone.
+
+A batch advances lattices of uneven size and parameters with one fused launch per
+step (replayed from a CUDA graph); each member's partial sums are folded by its
+own last tile, so with the same tiling a member's populations are bit-identical
+to a single-lattice run.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_05264_gb300 import inputs as I
+from paper_2009_05264_gb300 import params as PP
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def lbm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_05264_gb300 import lbm as L
+
+    return L
+
+
+def member_case(k, nx, ny):
+    rng = np.random.default_rng(100 + k)
+    p = PP.resolve(PP.default_params(geometry="channel", u_in=float(rng.uniform(0.01, 0.04)),
+                                     dTheat_R=float(rng.uniform(0.03, 0.12)), heat_on_step=5, heater_len=12,
+                                     rho_w=float(rng.uniform(5.0, 6.2)), g_a=1e-4), nx)
+    Tc = oracle.Tc(p)
+    fields = I.smooth_random(nx, ny, 5.95, 0.9 * Tc, seed=300 + k, drho=0.002, du=0.005, dT=0.002)
+    return p, fields
+
+
+def single_run(L, nx, ny, p, fields, prec, steps, tiling):
+    lat = L.Lattice(nx, ny, prec)
+    lat.set_params(p)
+    lat.set_tiling(*tiling)
+    lat.init_fields(*fields)
+    lat.step(steps)
+    return lat.populations()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batch_members_match_single_runs(prec):
+    L = lbm()
+    sizes = [(403, 57), (250, 121), (129, 50), (777, 64)]
+    b = L.Batch(prec, thermal=True)
+    cases = []
+    for k, (nx, ny) in enumerate(sizes):
+        p, fields = member_case(k, nx, ny)
+        m = b.add(nx, ny, p)
+        m.init_fields(*fields)
+        cases.append((m, nx, ny, p, fields))
+    steps = 37  # two captured 16-step graphs plus single launches
+    b.step(steps)
+    assert b.launches == steps
+    cols, rows = b.tiling
+    for m, nx, ny, p, fields in cases:
+        f_ref, g_ref = single_run(L, nx, ny, p, fields, prec, steps, (cols, rows or 0))
+        f, g = m.populations()
+        assert np.array_equal(f, f_ref) and np.array_equal(g, g_ref)
+        assert m.step_count == steps
+    b.close()
+
+
+def test_members_added_and_removed_mid_run():
+    L = lbm()
+    b = L.Batch("fp32", thermal=True)
+    p0, f0 = member_case(0, 300, 60)
+    p1, f1 = member_case(1, 180, 90)
+    m0 = b.add(300, 60, p0)
+    m0.init_fields(*f0)
+    b.step(20)
+    m1 = b.add(180, 90, p1)  # joins at its own step 0 while m0 is at step 20
+    m1.init_fields(*f1)
+    b.step(25)
+    b.remove(m0.slot)
+    b.step(10)
+    assert len(b) == 1 and m1.step_count == 35
+    f_ref, g_ref = single_run(L, 180, 90, p1, f1, "fp32", 35, (128, 0))
+    f, g = m1.populations()
+    assert np.array_equal(f, f_ref) and np.array_equal(g, g_ref)
+    b.close()
+
+
+def test_autotune_picks_a_valid_tiling_and_keeps_results():
+    L = lbm()
+    b = L.Batch("fp32", thermal=True)
+    cases = []
+    for k, (nx, ny) in enumerate([(500, 80), (260, 140)]):
+        p, fields = member_case(k, nx, ny)
+        m = b.add(nx, ny, p)
+        m.init_fields(*fields)
+        cases.append((m, nx, ny, p, fields))
+    cols, rows = b.autotune(trial_steps=3)
+    assert cols in (64, 128, 256) and (rows == 0 or rows >= 4)
+    for m, nx, ny, p, fields in cases:
+        m.init_fields(*fields)  # the trials advanced the members
+    b.step(20)
+    for m, nx, ny, p, fields in cases:
+        f_ref, _ = single_run(L, nx, ny, p, fields, "fp32", 20, (cols, rows))
+        assert np.array_equal(m.populations()[0], f_ref)
+    b.close()
+
+
+def test_unstable_member_is_reported_with_its_slot():
+    L = lbm()
+    b = L.Batch("fp64", thermal=True)
+    p, fields = member_case(0, 120, 40)
+    good = b.add(120, 40, p)
+    good.init_fields(*fields)
+    bad = b.add(120, 40, p)
+    rho = fields[0].copy()
+    rho[10, 60] = 11.0  # beyond 1/b
+    bad.init_fields(rho, fields[1], fields[2], fields[3])
+    with pytest.raises(L.LbmError) as e:
+        b.step(2)
+    assert e.value.status == 3 and f"member {bad.slot}" in str(e.value)
+    b.close()

@@ -1,0 +1,131 @@
+"""Host logic of the serving loop (admission, memory budget, chunking, latency) with a
+fake batch backend; no GPU."""
+import numpy as np
+import pytest
+
+from paper_2009_05264_gb300.serve import FakeClock, Request, Server, poisson_arrivals
+
+
+class FakeMember:
+    def __init__(self, slot, nx, ny):
+        self.slot, self.nx, self.ny = slot, nx, ny
+        self.steps = 0
+        self.inited = False
+        self.bad = False
+
+    def init_fields(self, *fields):
+        self.inited = True
+
+    def sync(self):
+        if self.bad:
+            raise RuntimeError(f"member {self.slot} unstable")
+
+    def fields(self):
+        return {"steps": self.steps}
+
+    def diagnostics(self):
+        return {"step": self.steps - 1}
+
+
+class FakeBatch:
+    def __init__(self):
+        self.members = {}
+        self.step_calls = []
+        self.max_resident = 0
+
+    def add(self, nx, ny, p):
+        slot = min(set(range(len(self.members) + 1)) - set(self.members))
+        m = FakeMember(slot, nx, ny)
+        self.members[slot] = m
+        self.max_resident = max(self.max_resident, len(self.members))
+        return m
+
+    def remove(self, slot):
+        del self.members[slot]
+
+    def step(self, n):
+        self.step_calls.append((n, sorted(self.members)))
+        for m in self.members.values():
+            m.steps += n
+        for m in self.members.values():
+            m.bad = m.bad or m.nx == 13  # a lattice of width 13 "diverges" on its first chunk
+        for m in self.members.values():
+            m.sync()
+
+
+def req(rid, nx, ny, steps, arrival=0.0):
+    return Request(rid, nx, ny, {}, (None, None, None, None), steps, arrival)
+
+
+def test_every_request_runs_exactly_its_steps_in_chunks():
+    b = FakeBatch()
+    s = Server(backend=b, chunk=100, clock=FakeClock())
+    for k, steps in enumerate([250, 100, 430]):
+        s.submit(req(k, 10, 10, steps))
+    done = s.run()
+    assert sorted(r.rid for r in done) == [0, 1, 2]
+    assert all(r.result["steps"] == r.steps for r in done)
+    assert all(n <= 100 for n, _ in b.step_calls)
+    assert s.node_updates == 100 * (250 + 100 + 430)
+
+
+def test_budget_admits_first_come_first_served_and_never_overcommits():
+    b = FakeBatch()
+    sizes = {0: 60, 1: 50, 2: 30, 3: 10}
+    bytes_of = lambda nx, ny: nx  # noqa: E731
+    s = Server(backend=b, chunk=50, clock=FakeClock(), hbm_budget=100, bytes_of=bytes_of)
+    for rid, sz in sizes.items():
+        s.submit(req(rid, sz, 1, 100 + 50 * rid))
+    usage = []
+    while not s.idle:
+        s.run_once()
+        usage.append(s.in_use)
+    assert max(usage) <= 100
+    order = [r.rid for r in sorted(s.finished, key=lambda r: r.admitted)]
+    assert order == [0, 1, 2, 3]  # request 2 (30) waits behind 1 (50) although it would fit
+    first = b.step_calls[0][1]
+    assert first == [0]  # 0 (60) alone: 1 (50) does not fit beside it
+
+
+def test_oversized_request_is_rejected_not_queued_forever():
+    s = Server(backend=FakeBatch(), chunk=10, clock=FakeClock(), hbm_budget=100, bytes_of=lambda nx, ny: nx)
+    s.submit(req(0, 500, 1, 10))
+    s.submit(req(1, 20, 1, 10))
+    done = {r.rid: r.status for r in s.run()}
+    assert done == {0: "rejected", 1: "done"}
+    assert s.stats()["rejected"] == 1
+
+
+def test_late_arrivals_join_a_running_batch():
+    clock = FakeClock(tick=1.0)
+    b = FakeBatch()
+    s = Server(backend=b, chunk=10, clock=clock)
+    s.submit(req(0, 10, 10, 100, arrival=0.0))
+    s.submit(req(1, 10, 10, 30, arrival=5.0))
+    s.submit(req(2, 10, 10, 10, arrival=1000.0))  # after everything else has finished
+    done = {r.rid: r for r in s.run()}
+    assert b.max_resident == 2
+    assert done[1].admitted >= 5.0 and done[1].done < done[0].done
+    assert done[2].admitted >= 1000.0
+    st = s.stats()
+    assert st["completed"] == 3 and st["p50_s"] <= st["p99_s"]
+
+
+def test_poisson_arrivals_have_the_requested_rate():
+    t = poisson_arrivals(4000, 2.0, seed=5)
+    assert np.all(np.diff(t) > 0)
+    assert 4000 / t[-1] == pytest.approx(2.0, rel=0.05)
+
+
+def test_a_diverging_member_fails_alone():
+    b = FakeBatch()
+    s = Server(backend=b, chunk=10, clock=FakeClock())
+    s.submit(req(0, 10, 10, 40))
+    s.submit(req(1, 13, 10, 40))
+    s.submit(req(2, 11, 10, 25))
+    done = {r.rid: r for r in s.run()}
+    assert done[1].status == "failed" and "unstable" in done[1].result["error"]
+    assert done[0].status == "done" and done[0].result["steps"] == 40
+    assert done[2].status == "done" and done[2].result["steps"] == 25
+    st = s.stats()
+    assert st["failed"] == 1 and st["completed"] == 2
