@@ -26,7 +26,14 @@
  *   alpha(T) of Eq. 12 with sqrt(T/Tc); Eq. 14 as F_y = -(rho - rho_avg) g_a with
  *   rho_avg the previous step's mean; Eq. 15 with D2Q9 weights w_i and
  *   psi_w = psi(rho_w, T0); Eq. 16 with the relaxation term -(g - g^eq)/tau_g;
- *   the second Eq. 19 (Gong-Cheng source) is the one used.
+ *   the second Eq. 19 (Gong-Cheng source) is the one used.  Sec. 2.C fixes no
+ *   discretisation of div u in that source nor of the outlet's zero temperature
+ *   gradient: div u is taken by central differences, except that on a row next to
+ *   a wall the wall-normal derivative is the one-sided difference over the two
+ *   fluid rows; the outlet node takes all nine post-stream g of the node upstream.
+ *   (With u = 0 at the solid site instead, a row-alternating u_y mode grows at the
+ *   walls, and with only the unknown g copied the outlet diverges, both within
+ *   about 10^4 steps.)
  */
 #include "lbm_oracle.h"
 
@@ -465,11 +472,9 @@ static void outlet_node(orc_lattice* L, const orc_params* P, int y) {
     L->fnew[pid(L, b, x, y)] = z[1];
   }
   if (P->thermal) {
-    /* zero temperature gradient: copy the post-stream populations one node upstream */
-    for (int k = 0; k < nu; ++k) {
-      int i = U[k];
-      L->gnew[pid(L, i, x, y)] = L->gnew[pid(L, i, x - 1, y)];
-    }
+    /* zero temperature gradient: the outlet node takes all post-stream populations
+     * of the node one upstream (their wall links already applied) */
+    for (int i = 0; i < 9; ++i) L->gnew[pid(L, i, x, y)] = L->gnew[pid(L, i, x - 1, y)];
   }
 }
 
@@ -504,7 +509,17 @@ static int one_step(orc_lattice* L, const orc_params* P) {
         uact_at(L, P, x - 1, y, &uxm, &t);
         uact_at(L, P, x, y + 1, &t, &uyp);
         uact_at(L, P, x, y - 1, &t, &uym);
-        double divu = 0.5 * (uxp - uxm) + 0.5 * (uyp - uym); /* second-order central differences */
+        /* second-order central differences; on a row next to a wall the wall-normal
+         * derivative is the one-sided difference over the two fluid rows */
+        double dyu = 0.5 * (uyp - uym);
+        if (P->geometry != ORC_PERIODIC && (y == 0 || y == ny - 1)) {
+          double uyc;
+          uact_at(L, P, x, y, &t, &uyc);
+          if (ny == 1) dyu = 0.0;
+          else if (y == 0) dyu = uyp - uyc;
+          else dyu = uyc - uym;
+        }
+        double divu = 0.5 * (uxp - uxm) + dyu;
         double T = L->T[k];
         double phi = T * (1.0 - L->dpdT[k] / (L->rho[k] * P->c_v)) * divu;
         L->phi[k] = phi;

@@ -247,6 +247,41 @@ def test_open_boundary_moments():
         np.testing.assert_allclose(jy[:, 0], 0.0, atol=1e-13)
         np.testing.assert_allclose(rho[:, -1], 5.9, rtol=1e-14)
         np.testing.assert_allclose(jy[:, -1], 0.0, atol=1e-13)
+        # zero temperature gradient at the exit plane: T(nx-1) = T(nx-2) on every row
+        Tn = O.populations()[1].sum(axis=0)
+        np.testing.assert_allclose(Tn[:, -1], Tn[:, -2], rtol=1e-15)
+        assert np.ptp(Tn[:, -2]) > 1e-6  # the outlet column is not uniform: the check has teeth
+
+
+def test_source_divergence_is_exact_for_a_linear_velocity_field():
+    """The source of the second Eq. 19 needs div u_act.  For u = (0, a (y - y_m)) between
+    walls every row, the two next to the walls included, must see div u = a exactly, so
+    with an ideal-gas EOS ((dp/dT)_rho = 0, phi = T div u) the step's total source is
+    a T nx ny."""
+    nx, ny, a = 6, 12, 1e-3
+    p = prm(nx, geometry="walls", thermal=1, multiphase=0, g_a=0.0, heater_len=0)
+    T = 0.9 * oracle.Tc(p)
+    rho, ux, uy, TT = I.uniform(nx, ny, 1.0, T)
+    uy = a * (np.arange(ny, dtype=np.float64)[:, None] - 0.5 * (ny - 1)) * np.ones((1, nx))
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(rho, ux, uy, TT)
+    assert O.step(1) == 0
+    assert O.last_diag()["source"] == pytest.approx(a * T * nx * ny, rel=1e-12)
+
+
+def test_thermal_liquid_between_walls_is_quiet():
+    """A saturated liquid at rest between isothermal walls (Sec. 2.C) with a small seeded
+    perturbation relaxes: its velocity decays instead of growing into a wall mode."""
+    nx, ny = 8, 40
+    p = prm(nx, geometry="walls", thermal=1, g_a=0.0, heater_len=0)
+    Tc = oracle.Tc(p)
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(*I.smooth_random(nx, ny, 5.95, 0.9 * Tc, seed=7, drho=0.002, du=0.005, dT=0.002))
+    amp = []
+    for _ in range(3):
+        assert O.step(2000) == 0
+        amp.append(np.abs(O.fields()["uy"]).max())
+    assert amp[2] < amp[1] < amp[0] < 1e-6
 
 
 def test_steady_conduction_between_walls():
