@@ -10,6 +10,13 @@ Under torchrun each rank advances its own independent channel (replicas; no
 data-path collective), so `value` is the total node updates of all ranks per
 second ("weak" scaling).
 
+Three sub-measurements ride on the same JSON line (rank 0, single process only):
+"fp64", the same channel in FP64; "batch", a seeded sweep of 64 channels of
+uneven size and parameters advanced together (one fused launch per step, CUDA
+graph replay, autotuned tiles) against the same 64 solved one at a time; and
+"serve", Poisson arrivals of channel solves through the continuous-batching
+server with p50/p99 time-to-result.
+
 --impl reference times the FP64 CPU oracle (the plain restatement of the
 paper used by the tests) on the host cores, on a bounded sample of the same
 channel: a 1000 x 800 band of it per step.
@@ -24,6 +31,8 @@ import subprocess
 import sys
 import threading
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -111,6 +120,145 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def channel_params(nx: int, u_in: float, dTheat_R: float, rho_w: float | None = None):
+    from paper_2009_05264_gb300 import params as PP
+
+    kw = dict(geometry="channel", u_in=u_in, dTheat_R=dTheat_R, heater_len=40, heat_on_step=0, rho_out=5.95)
+    if rho_w is not None:
+        kw["rho_w"] = rho_w
+    return PP.resolve(PP.default_params(**kw), nx)
+
+
+def channel_fields(nx: int, ny: int, Tc: float, seed: int, instance: int = 0):
+    from paper_2009_05264_gb300 import inputs as I
+
+    return I.smooth_random(nx, ny, 5.95, 0.9 * Tc, seed=seed, drho=0.002, du=0.005, dT=0.002, instance=instance)
+
+
+def run_fp64(steps: int):
+    """The same 8000 x 800 channel with FP64 populations: MLUPS and roofline fraction."""
+    import torch
+
+    from paper_2009_05264_gb300 import lbm
+
+    p = workload_params("fp64")
+    lat = lbm.Lattice(NX, NY, "fp64")
+    lat.set_params(p)
+    lat.init_fields(*channel_fields(NX, NY, lbm.critical_temperature(p), SEED))
+    lat.step(3)
+    st = lat.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    lat.step_async(steps)
+    e1.record(st)
+    lat.sync()
+    ms = e0.elapsed_time(e1)
+    nodes = NX * NY
+    peak, kind = read_peaks()
+    gbs = bytes_per_node("fp64") * nodes * steps / (ms * 1e-3) / 1e9
+    out = {"value": nodes * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "steps": steps, "ms_per_step": ms / steps,
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                        "peak_source": f"{kind} HBM copy bandwidth", "algorithmic_bytes_per_node": bytes_per_node("fp64")}}
+    lat.close()
+    return out
+
+
+def run_batch(steps: int, trial_steps: int = 4, n: int = 64, seed: int = SEED + 4):
+    """64 seeded channels (Nx U{400..2000}, Ny U{50..200}, u_in U[0.01,0.05], superheat U[0.03,0.12] Tc,
+    rho_w U[2.2,4.0] i.e. contact angles of about 137 to 46 degrees), FP32: one batch (autotuned tiles, graph replay) against one at a time."""
+    import torch
+
+    from paper_2009_05264_gb300 import inputs as I
+    from paper_2009_05264_gb300 import lbm
+
+    draws = I.sweep_draws(n, seed)
+    b = lbm.Batch("fp32", thermal=True)
+    members = []
+    for k, d in enumerate(draws):
+        p = channel_params(d["nx"], d["u_in"], d["dTheat_R"], d["rho_w"])
+        m = b.add(d["nx"], d["ny"], p)
+        m.init_fields(*channel_fields(d["nx"], d["ny"], lbm.critical_temperature(p), seed, instance=k))
+        members.append(m)
+    nodes = sum(d["nx"] * d["ny"] for d in draws)
+    t0 = time.perf_counter()
+    cols, rows = b.autotune(trial_steps=trial_steps)
+    tune_s = time.perf_counter() - t0
+    b.step(3)
+    st = b.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = b.launches
+    e0.record(st)
+    b.step_async(steps)
+    e1.record(st)
+    b.sync()
+    ms_b = e0.elapsed_time(e1)
+    launches = b.launches - l0
+    # the same lattices one at a time through the single-lattice call (each on its own default tiling)
+    e0.record(st)
+    for m in members:
+        m.step_async(steps)
+    e1.record(st)
+    for m in members:
+        m.sync()
+    ms_s = e0.elapsed_time(e1)
+    ok = all(np.isfinite(m.fields()["rho"]).all() for m in members[:4])
+    b.close()
+    batched = nodes * steps / (ms_b * 1e-3) / 1e6
+    seq = nodes * steps / (ms_s * 1e-3) / 1e6
+    peak, kind = read_peaks()
+    gbs = bytes_per_node("fp32") * nodes * steps / (ms_b * 1e-3) / 1e9
+    return {"workload": f"{n} channels, seeded sweep (seed {seed}), {nodes} nodes in total, FP32", "instances": n,
+            "nodes": nodes, "steps": steps, "value": batched, "unit": "MLUPS", "ms_per_step": ms_b / steps,
+            "sequential": {"value": seq, "unit": "MLUPS", "ms_per_step": ms_s / steps,
+                           "how": "each lattice alone through lbm_step_async, one after another"},
+            "speedup_vs_sequential": batched / seq, "tiling": f"{cols}x{rows}", "autotune_s": tune_s,
+            "gpu_launches": launches, "launches_sequential": n * steps, "finite": bool(ok),
+            "solves_per_hour_50k_steps": n * 3600.0 / (50000 * ms_b * 1e-3 / steps),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "peak_source": f"{kind} HBM copy bandwidth"}}
+
+
+def run_serve(n_requests: int, steps: int, rate: float = 2.0, seed: int = SEED + 5, tiling=None,
+              hbm_budget: int = 32 << 30, chunk: int = 500):
+    """Poisson arrivals (rate per second) of channel solves, 80 % sweep draws and 20 % 4000 x 400,
+    through the continuous-batching server on the wall clock."""
+    from paper_2009_05264_gb300 import inputs as I
+    from paper_2009_05264_gb300 import lbm
+    from paper_2009_05264_gb300.serve import Request, Server, poisson_arrivals
+
+    rng = np.random.default_rng(seed)
+    arrivals = poisson_arrivals(n_requests, rate, seed)
+    draws = I.sweep_draws(n_requests, seed + 1)
+    reqs = []
+    for k in range(n_requests):
+        d = draws[k]
+        if rng.random() < 0.2:
+            d = dict(d, nx=4000, ny=400)
+        p = channel_params(d["nx"], d["u_in"], d["dTheat_R"], d["rho_w"])
+        fields = channel_fields(d["nx"], d["ny"], lbm.critical_temperature(p), seed, instance=k)
+        reqs.append(Request(k, d["nx"], d["ny"], p, fields, steps, float(arrivals[k])))
+    srv = Server("fp32", hbm_budget=hbm_budget, chunk=chunk, tiling=tiling)
+    t0 = time.monotonic()
+    for r in reqs:
+        r.arrival += t0
+        srv.submit(r)
+    done = srv.run()
+    wall = max(r.done for r in done if r.done is not None) - t0
+    st = srv.stats()
+    finite = all(np.isfinite(r.result["rho"]).all() for r in done if r.status == "done")
+    peak_resident = srv.peak_resident
+    srv.batch.close()
+    return {"workload": f"{n_requests} Poisson arrivals at {rate}/s (seed {seed}): 80 % sweep draws, "
+                        f"20 % 4000x400; {steps} steps each; FP32", "requests": n_requests, "steps_each": steps,
+            "completed": st["completed"], "failed": st["failed"], "rejected": st["rejected"],
+            "p50_s": st["p50_s"], "p99_s": st["p99_s"], "unit_latency": "s (arrival to fields on the host)",
+            "value": st["node_updates"] / wall / 1e6, "unit": "MLUPS", "wall_s": wall,
+            "gpu_busy_frac": st["gpu_busy_s"] / wall, "offered_mlups": float(
+                sum(r.nx * r.ny for r in reqs) * steps * rate / n_requests / 1e6),
+            "solves_per_hour": st["completed"] * 3600.0 / wall, "peak_resident": peak_resident,
+            "hbm_budget_bytes": hbm_budget, "chunk_steps": chunk, "finite": bool(finite)}
 
 
 def dist_env():
@@ -272,6 +420,12 @@ def run_ours(args):
             "gpu_launches": gpu_launches,
             "clocks": clocks,
         }
+        if world == 1 and not args.no_extras:
+            lat.close()
+            line["fp64"] = run_fp64(max(10, args.steps // 10))
+            line["batch"] = run_batch(args.batch_steps)
+            line["serve"] = run_serve(args.serve_requests, args.serve_steps,
+                                      tiling=tuple(int(x) for x in line["batch"]["tiling"].split("x")))
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
@@ -290,6 +444,10 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--tiling", default=None, help="COLSxROWS, e.g. 128x32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the fp64, batch and serve measurements")
+    ap.add_argument("--batch-steps", type=int, default=300)
+    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-steps", type=int, default=20000)
     ap.add_argument("--nx", type=int, default=None, help="profiling only: smaller channel length")
     ap.add_argument("--ny", type=int, default=None, help="profiling only: smaller channel height")
     args = ap.parse_args()

@@ -272,10 +272,22 @@ __device__ __forceinline__ void boundary_fill(Real (&fc)[9], Real (&gc)[9], cons
       fc[6] = fc[8] - h - ru * Real(1.0 / 6.0);
     }
     if (THERMAL) {
-      // zero temperature gradient: the post-stream populations of node nx-2
-      gc[3] = ld_ro(Gin + 3 * plane + node);
-      if (!nb.wlo) gc[6] = ld_ro(Gin + 6 * plane + node - pitch);
-      if (!nb.whi) gc[7] = ld_ro(Gin + 7 * plane + node + pitch);
+      // zero temperature gradient: all nine post-stream populations of node nx-2, its
+      // wall links (anti-bounce-back at the wall temperature) included
+      const int xu = xn - 1;
+      const bool heat_bc = I.heater_len > 0 && (step - 1) >= I.heat_on_step;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const int cxi = lat_cx(i), cyi = lat_cy(i);
+        if ((cyi == 1 && nb.wlo) || (cyi == -1 && nb.whi)) {
+          const int sx = xu - cxi;
+          const Real dTw = (cyi == 1 && heat_bc && sx >= I.heater_x0 && sx < I.heater_x0 + I.heater_len)
+                               ? C.dT_heat : dT_in;
+          gc[i] = -ld_ro(Gin + lat_opp(i) * plane + node - 1) + Real(2) * lat_w<Real>(i) * dTw;
+        } else {
+          gc[i] = ld_ro(Gin + i * plane + node - 1 - cyi * pitch - cxi);
+        }
+      }
     }
   }
 }
@@ -740,11 +752,18 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
     if (THERMAL && MODE == MODE_STEP) {
       const int q2 = r - 2;
       if (out_col && q2 >= tile.y0 && q2 < tile.y1) {
-        // second-order central differences of u_act; zero at solid rows, ghost copy at open ends
+        // second-order central differences of u_act (ghost copy at open ends); on a row next
+        // to a wall the wall-normal derivative is the one-sided difference over the fluid rows
         const Real uxE = sUx[f_prev2 * NS + sp], uxW = sUx[f_prev2 * NS + sm];
-        const Real uyN = (!pery && q2 == ny - 1) ? Real(0) : sUy[f_prev * NS + s];
-        const Real uyS = (!pery && q2 == 0) ? Real(0) : sUy[f_cur * NS + s];  // slot of row r-3
-        const Real divu = Real(0.5) * (uxE - uxW) + Real(0.5) * (uyN - uyS);
+        const Real uyN = sUy[f_prev * NS + s];
+        const Real uyS = sUy[f_cur * NS + s];  // slot of row r-3
+        const bool wall_lo = !pery && q2 == 0, wall_hi = !pery && q2 == ny - 1;
+        Real dyu = Real(0.5) * (uyN - uyS);
+        if (wall_lo || wall_hi) {
+          const Real uyC = sUy[f_prev2 * NS + s];
+          dyu = (wall_lo && wall_hi) ? Real(0) : (wall_lo ? uyN - uyC : uyC - uyS);
+        }
+        const Real divu = Real(0.5) * (uxE - uxW) + dyu;
         collide_g<Real>(sG + g_prev2 * 9 * NS + s, NS, Gout + (q2 * pitch + xn), plane, T_p2, dT_p2,
                         sUx[f_prev2 * NS + s], sUy[f_prev2 * NS + s], coef_p2 * divu, sC.omega_g);
       }
