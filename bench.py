@@ -338,6 +338,7 @@ def run_ours(args):
     if args.tiling:
         c, r = (int(x) for x in args.tiling.split("x"))
         lat.set_tiling(c, r)
+    lat.set_kernel(args.kernel)
     lat.init_fields(*fields)
     stream = lat.stream
     nodes = NX * NY
@@ -408,12 +409,15 @@ def run_ours(args):
             "config": {"workload": WORKLOAD if prec == "fp32" else WORKLOAD.replace("FP32", "FP64"),
                        "nx": NX, "ny": NY, "nodes_per_gpu": nodes, "precision": prec,
                        "tiling": args.tiling or "default (128 columns, rows by heuristic)",
+                       "kernel": args.kernel if prec == "fp32" else "scalar (FP64)",
                        "l2": "inputs larger than L2: 2 x 0.92 GB population buffers vs 129 MB L2",
                        "parallelism": f"{world} independent channel replicas"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
                          "peak_source": f"{peak_kind} HBM copy bandwidth",
-                         "algorithmic_bytes_per_node": bpn, "kernel": "lbm_fused_kernel (MODE_STEP)"},
+                         "algorithmic_bytes_per_node": bpn,
+                         "kernel": ("lbm_fused_kernel (MODE_STEP)" if prec == "fp64" or args.kernel == "scalar"
+                                    else "lbm_pair_kernel (two columns per thread, packed FP32)")},
             "e2e": {"value": e2e_value, "unit": "MLUPS",
                     "h2d_bytes_per_step": 4 * nodes * 8 / e2e_steps, "d2h_bytes_per_step": 4 * nodes * 8 / e2e_steps,
                     "note": f"init_fields from pinned host arrays + {e2e_steps} steps + read_fields to host"},
@@ -443,6 +447,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--tiling", default=None, help="COLSxROWS, e.g. 128x32")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "scalar", "paired"], help="FP32 step kernel form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the fp64, batch and serve measurements")
     ap.add_argument("--batch-steps", type=int, default=300)

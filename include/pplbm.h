@@ -182,11 +182,24 @@ size_t lbm_state_bytes(const lbm_ctx* ctx);
 lbm_status lbm_save_state(lbm_ctx* ctx, void* host_buf, size_t bytes);
 lbm_status lbm_load_state(lbm_ctx* ctx, const void* host_buf, size_t bytes);
 
-/* Tile shape of the fused kernel: threads per CTA (64, 128 or 256; a CTA writes
- * cols - 8 columns, the other 8 lanes cover halo columns) and rows per CTA (>= 4, or
- * the full height).  Results do not depend on the shape except through
- * the summation order of the domain-mean density (Eq. 14); only speed differs.  0 = default. */
+/* Tile shape of the fused kernel: columns per CTA (64, 128 or 256; a CTA writes
+ * cols - 8 columns, the other 8 cover halo columns; the scalar kernel runs cols
+ * threads, the paired kernel cols / 2) and rows per CTA (>= 4, or the full height).
+ * Results do not depend on the shape except through the summation order of the
+ * domain-mean density (Eq. 14); only speed differs.  0 = default. */
 lbm_status lbm_set_tiling(lbm_ctx* ctx, int32_t cols, int32_t rows);
+
+/* Form of the FP32 step kernel.  LBM_KERNEL_SCALAR (and LBM_KERNEL_AUTO, the
+ * default): one column per thread.  LBM_KERNEL_PAIRED: each thread updates two
+ * adjacent columns with packed FP32 arithmetic (two nodes per add / multiply / fused
+ * multiply-add instruction) and 8-byte stores; it executes about 40 % fewer
+ * instructions per node but holds fewer warps per SM, and on GB300 runs slower.  Both compute the same step and agree
+ * to FP32 rounding (a few additions and multiply-add contractions are ordered
+ * differently).  FP64 lattices, and lbm_step_noalloc on caller-laid-out buffers,
+ * always use the scalar form.  LBM_EINVAL for other
+ * values. */
+enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_SCALAR = 1, LBM_KERNEL_PAIRED = 2 };
+lbm_status lbm_set_kernel(lbm_ctx* ctx, int32_t kernel);
 
 int64_t lbm_get_step(const lbm_ctx* ctx);
 /* Kernel launches enqueued by this context since creation (all kinds). */
@@ -218,9 +231,11 @@ lbm_status lbm_batch_remove(lbm_batch* b, int32_t slot);
 /* The member's context, or NULL for a free slot.  Owned by the batch. */
 lbm_ctx* lbm_batch_member(lbm_batch* b, int32_t slot);
 int32_t lbm_batch_size(const lbm_batch* b);
-/* Tiling of the batched launch: threads per CTA (64, 128, 256) and rows per band
+/* Tiling of the batched launch: columns per CTA (64, 128, 256) and rows per band
  * (0 = each member's default, else >= 4). */
 lbm_status lbm_batch_set_tiling(lbm_batch* b, int32_t cols, int32_t rows);
+/* Step kernel form of the batched launch (as lbm_set_kernel). */
+lbm_status lbm_batch_set_kernel(lbm_batch* b, int32_t kernel);
 lbm_status lbm_batch_get_tiling(const lbm_batch* b, int32_t* cols, int32_t* rows);
 /* Time trial_steps of every candidate tiling on the current members and keep the
  * fastest (reported in *cols, *rows; either may be NULL).  The trials advance the

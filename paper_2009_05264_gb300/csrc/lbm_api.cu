@@ -15,17 +15,17 @@
 #include "pplbm.h"
 
 namespace pplbm {
-cudaError_t launch_lbm_f32(int, int, int, const Inst*, const Tile*, int, cudaStream_t);
+cudaError_t launch_lbm_f32(int, int, int, int, const Inst*, const Tile*, int, cudaStream_t);
 cudaError_t launch_lbm_f64(int, int, int, const Inst*, const Tile*, int, cudaStream_t);
 cudaError_t launch_init_from_fields_f32(const Inst*, int, int, const double*, int, cudaStream_t);
 cudaError_t launch_init_from_fields_f64(const Inst*, int, int, const double*, int, cudaStream_t);
 cudaError_t launch_init_builtin_f32(const Inst*, int, int, InitSpec, cudaStream_t);
 cudaError_t launch_init_builtin_f64(const Inst*, int, int, InitSpec, cudaStream_t);
 
-cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, const Inst* d_inst, const Tile* d_tiles,
+cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, int kernel, const Inst* d_inst, const Tile* d_tiles,
                        int ntiles, cudaStream_t s) {
   return fp64 ? launch_lbm_f64(thermal, cols, mode, d_inst, d_tiles, ntiles, s)
-              : launch_lbm_f32(thermal, cols, mode, d_inst, d_tiles, ntiles, s);
+              : launch_lbm_f32(thermal, cols, mode, kernel, d_inst, d_tiles, ntiles, s);
 }
 cudaError_t launch_init_from_fields(int fp64, const Inst* d_inst, int nx, int ny, const double* d_fields,
                                     int has_T, cudaStream_t s) {
@@ -136,15 +136,35 @@ const char* fill_inst(Inst& I, const lbm_params* p, int nx, int ny, int pitch, l
   return nullptr;
 }
 
-int default_band_rows(int nx, int ny, int cols) {
+int default_band_rows(int nx, int ny, int cols, long long slots) {
   const int w = cols - 8;
-  const int strips = (nx + w - 1) / w;
-  const long long target = 152LL * 8;
-  long long rows = ((long long)ny * strips + target - 1) / target;
-  rows = std::max<long long>(rows, 16);
-  rows = std::min<long long>(rows, 128);
-  rows = std::min<long long>(rows, ny);
-  return (int)std::max<long long>(rows, 4 < ny ? 4 : ny);
+  const long long strips = (nx + w - 1) / w;
+  if (slots < 1) slots = 1;
+  if (ny <= 4) return ny;
+  int best_rows = ny;
+  double best_cost = -1.0;
+  // candidate band counts: every distinct balanced band height from ny down to 4 rows
+  for (int bands = 1; bands <= ny; ++bands) {
+    const int rows = (ny + bands - 1) / bands;
+    if (rows < 4) break;
+    if (bands > 1 && rows == (ny + bands - 2) / (bands - 1)) continue;  // same height as bands - 1
+    const long long tiles = strips * ((ny + rows - 1) / rows);
+    // row-iterations per CTA slot: the work spread over all slots plus, with the block
+    // scheduler refilling slots as tiles finish, about half a tile of tail
+    const double cost = (double)tiles * (rows + 5) / (double)slots + 0.5 * (rows + 5);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best_rows = rows;
+    }
+  }
+  return best_rows;
+}
+
+long long step_wave_slots(int fp64, int thermal, int cols, int kernel) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = fp64 ? resident_ctas_f64(thermal, cols) : resident_ctas_f32(thermal, cols, kernel);
+  return (long long)sms * (per_sm > 0 ? per_sm : 1);
 }
 }  // namespace pplbm
 
@@ -213,9 +233,6 @@ void build_tiles(int nx, int ny, int cols, int rows, std::vector<Tile>& out) {
     }
 }
 
-// Rows per band for a tile width: enough CTAs to fill 152 SMs a few times over
-// while keeping the 4-row band overhead small.
-int default_rows(int nx, int ny, int cols) { return default_band_rows(nx, ny, cols); }
 
 }  // namespace
 
@@ -233,6 +250,7 @@ struct lbm_ctx {
   InstState* d_state = nullptr;
   InstState* h_state = nullptr;  // pinned mirror
   int cols = 128, rows = 16;
+  bool rows_default = true;  // band height chosen by default_band_rows (re-chosen on changes)
   int ntiles_step = 0, ntiles_aux = 0;
   Tile* d_tiles_step = nullptr;
   Tile* d_tiles_aux = nullptr;
@@ -242,6 +260,7 @@ struct lbm_ctx {
   long long launches = 0;
   long long step_host = 0;  // step count as last synchronised
   unsigned long long params_gen = 0;  // bumped whenever the descriptor changes
+  int kernel = LBM_KERNEL_AUTO;        // step kernel form (FP32: scalar or paired columns)
   std::string err;
 };
 
@@ -299,9 +318,17 @@ lbm_status set_tiling(lbm_ctx* c, int cols, int rows) {
   return LBM_OK;
 }
 
+// Re-choose the default band height for the current kernel, precision and thermal flag.
+lbm_status retile_default(lbm_ctx* c, int cols) {
+  const long long slots = step_wave_slots(c->prec == LBM_FP64, c->have_params ? c->thermal : 1, cols, c->kernel);
+  const lbm_status s = set_tiling(c, cols, default_band_rows(c->nx, c->ny, cols, slots));
+  if (s == LBM_OK) c->rows_default = true;
+  return s;
+}
+
 lbm_status launch(lbm_ctx* c, int mode) {
   const bool step_tiles = mode == MODE_STEP;
-  cudaError_t e = launch_lbm(c->prec == LBM_FP64, c->thermal, step_tiles ? c->cols : kAuxCols, mode, c->d_inst,
+  cudaError_t e = launch_lbm(c->prec == LBM_FP64, c->thermal, step_tiles ? c->cols : kAuxCols, mode, c->kernel, c->d_inst,
                              step_tiles ? c->d_tiles_step : c->d_tiles_aux,
                              step_tiles ? c->ntiles_step : c->ntiles_aux, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
@@ -388,8 +415,7 @@ lbm_status create_impl(lbm_ctx** out, int32_t nx, int32_t ny, lbm_precision prec
     lbm_destroy(c);
     return LBM_ECUDA;
   }
-  const int rows = default_rows(nx, ny, 128);
-  if (set_tiling(c, 128, rows) != LBM_OK) { lbm_destroy(c); return LBM_ECUDA; }
+  if (retile_default(c, 128) != LBM_OK) { lbm_destroy(c); return LBM_ECUDA; }
   *out = c;
   return LBM_OK;
 }
@@ -460,6 +486,7 @@ lbm_status lbm_set_params(lbm_ctx* c, const lbm_params* p) {
   DeviceGuard g(c->device);
   lbm_status s = apply_params(c, p);
   if (s != LBM_OK) return s;
+  if (c->rows_default && (s = retile_default(c, c->cols)) != LBM_OK) return s;
   InitSpec spec{};
   spec.kind = p->init_kind;
   spec.rho_in = p->init_rho_in;
@@ -716,17 +743,30 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t bytes) {
   return LBM_OK;
 }
 
+lbm_status lbm_set_kernel(lbm_ctx* c, int32_t kernel) {
+  if (!c) return LBM_EINVAL;
+  if (kernel != LBM_KERNEL_AUTO && kernel != LBM_KERNEL_SCALAR && kernel != LBM_KERNEL_PAIRED)
+    return fail(c, LBM_EINVAL, "kernel must be LBM_KERNEL_AUTO, _SCALAR or _PAIRED");
+  c->kernel = kernel;
+  if (!c->rows_default) return LBM_OK;
+  DeviceGuard g(c->device);
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return retile_default(c, c->cols);
+}
+
 lbm_status lbm_set_tiling(lbm_ctx* c, int32_t cols, int32_t rows) {
   if (!c) return LBM_EINVAL;
   if (cols == 0) cols = 128;
   if (!cols_supported(cols)) return fail(c, LBM_EINVAL, "cols must be 64, 128 or 256");
-  if (rows == 0) rows = default_rows(c->nx, c->ny, cols);
-  if (rows < 1) return fail(c, LBM_EINVAL, "rows must be >= 1");
-  rows = std::min(rows, c->ny);
-  if (rows < kMinRows && rows < c->ny) return fail(c, LBM_EINVAL, "rows must be >= 4 (or the full height)");
+  if (rows < 0) return fail(c, LBM_EINVAL, "rows must be >= 0");
   DeviceGuard g(c->device);
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
-  return set_tiling(c, cols, rows);
+  if (rows == 0) return retile_default(c, cols);
+  rows = std::min(rows, c->ny);
+  if (rows < kMinRows && rows < c->ny) return fail(c, LBM_EINVAL, "rows must be >= 4 (or the full height)");
+  const lbm_status s = set_tiling(c, cols, rows);
+  if (s == LBM_OK) c->rows_default = false;
+  return s;
 }
 
 int64_t lbm_get_step(const lbm_ctx* c) { return c ? c->step_host : -1; }

@@ -40,6 +40,7 @@ struct lbm_batch {
   bool own_stream = false;
   std::vector<Member> slots;  // empty ctx = free slot
   int cols = 128, rows = 0;   // rows 0: each member's default band height
+  int kernel = LBM_KERNEL_AUTO;
   // device tables of the current membership
   Inst* d_insts = nullptr;
   Tile* d_tiles = nullptr;
@@ -71,8 +72,11 @@ void drop_graph(lbm_batch* b) {
   }
 }
 
-int member_rows(const lbm_batch* b, int nx, int ny) {
-  const int r = b->rows > 0 ? b->rows : default_band_rows(nx, ny, b->cols);
+// Default band height of a member: its share of one wave's CTA slots, in proportion
+// to its share of the batch's nodes.
+int member_rows(const lbm_batch* b, int nx, int ny, long long slots, double share) {
+  const long long member_slots = std::max<long long>(1, (long long)(slots * share + 0.5));
+  const int r = b->rows > 0 ? b->rows : default_band_rows(nx, ny, b->cols, member_slots);
   return std::max(1, std::min(r, ny));
 }
 
@@ -81,12 +85,16 @@ lbm_status rebuild(lbm_batch* b) {
   std::vector<Inst> insts;
   std::vector<Tile> tiles;
   const int w = b->cols - 8;
+  double total = 0.0;
+  for (const Member& m : b->slots)
+    if (m.ctx) total += (double)m.nx * m.ny;
+  const long long slots = step_wave_slots(b->prec == LBM_FP64, b->thermal, b->cols, b->kernel);
   for (Member& m : b->slots) {
     if (!m.ctx) continue;
     const int idx = (int)insts.size();
     insts.push_back(lbm_internal_inst(m.ctx));
     m.gen = lbm_internal_params_gen(m.ctx);
-    const int rows = member_rows(b, m.nx, m.ny);
+    const int rows = member_rows(b, m.nx, m.ny, slots, total > 0.0 ? (double)m.nx * m.ny / total : 1.0);
     const int strips = (m.nx + w - 1) / w, bands = (m.ny + rows - 1) / rows;
     const int n = strips * bands;
     int local = 0;
@@ -135,7 +143,7 @@ lbm_status rebuild(lbm_batch* b) {
 
 lbm_status launch_steps(lbm_batch* b, int64_t n) {
   for (int64_t k = 0; k < n; ++k) {
-    LBM_BCUDA(b, launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->d_insts, b->d_tiles, b->ntiles,
+    LBM_BCUDA(b, launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->kernel, b->d_insts, b->d_tiles, b->ntiles,
                             b->stream));
     ++b->launches;
   }
@@ -147,7 +155,7 @@ lbm_status capture_graph(lbm_batch* b) {
   LBM_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   lbm_status s = LBM_OK;
   for (int k = 0; k < kGraphChunk && s == LBM_OK; ++k) {
-    if (launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->d_insts, b->d_tiles, b->ntiles,
+    if (launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->kernel, b->d_insts, b->d_tiles, b->ntiles,
                    b->stream) != cudaSuccess)
       s = bfail(b, LBM_ECUDA, "launch during graph capture");
   }
@@ -259,6 +267,15 @@ lbm_status lbm_batch_set_tiling(lbm_batch* b, int32_t cols, int32_t rows) {
   b->cols = cols;
   b->rows = rows;
   b->dirty = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_set_kernel(lbm_batch* b, int32_t kernel) {
+  if (!b) return LBM_EINVAL;
+  if (kernel != LBM_KERNEL_AUTO && kernel != LBM_KERNEL_SCALAR && kernel != LBM_KERNEL_PAIRED)
+    return bfail(b, LBM_EINVAL, "kernel must be LBM_KERNEL_AUTO, _SCALAR or _PAIRED");
+  b->kernel = kernel;
+  b->dirty = true;  // default band heights depend on the kernel's occupancy; the graph names the kernel
   return LBM_OK;
 }
 

@@ -1,11 +1,17 @@
 // Kernel instantiations for float storage and arithmetic.
 #include "lbm_kernels.cuh"
+#include "lbm_pair.cuh"
 
 namespace pplbm {
 
-cudaError_t launch_lbm_f32(int thermal, int cols, int mode, const Inst* d_inst, const Tile* d_tiles, int ntiles,
-                          cudaStream_t s) {
+cudaError_t launch_lbm_f32(int thermal, int cols, int mode, int kernel, const Inst* d_inst, const Tile* d_tiles,
+                          int ntiles, cudaStream_t s) {
+  if (mode == MODE_STEP && kernel == LBM_KERNEL_PAIRED) return launch_pair(thermal, cols, d_inst, d_tiles, ntiles, s);
   return launch_precision<float>(thermal, cols, mode, d_inst, d_tiles, ntiles, s);
+}
+
+int resident_ctas_f32(int thermal, int cols, int kernel) {
+  return kernel == LBM_KERNEL_PAIRED ? resident_pair(thermal, cols) : resident_precision<float>(thermal, cols);
 }
 
 cudaError_t launch_init_from_fields_f32(const Inst* d_inst, int nx, int ny, const double* d_fields, int has_T,

@@ -8,6 +8,8 @@ cudaError_t launch_lbm_f64(int thermal, int cols, int mode, const Inst* d_inst, 
   return launch_precision<double>(thermal, cols, mode, d_inst, d_tiles, ntiles, s);
 }
 
+int resident_ctas_f64(int thermal, int cols) { return resident_precision<double>(thermal, cols); }
+
 cudaError_t launch_init_from_fields_f64(const Inst* d_inst, int nx, int ny, const double* d_fields, int has_T,
                                        cudaStream_t s) {
   return launch_init_fields_t<double>(d_inst, nx, ny, d_fields, has_T, s);

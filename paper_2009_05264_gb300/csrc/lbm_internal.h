@@ -64,7 +64,8 @@ struct Tile {
 };
 
 // Launchers (defined per precision).  Tiles must have been built for `cols`.
-cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, const Inst* d_inst, const Tile* d_tiles,
+// kernel: LBM_KERNEL_AUTO / _SCALAR / _PAIRED (pplbm.h); only the FP32 step has a paired form.
+cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, int kernel, const Inst* d_inst, const Tile* d_tiles,
                        int ntiles, cudaStream_t s);
 // f = f^eq(rho,u), g = g^eq(T,u) into buffer 0 from 4 planes of nx*ny doubles (rho, ux, uy, T).
 cudaError_t launch_init_from_fields(int fp64, const Inst* d_inst, int nx, int ny, const double* d_fields,
@@ -87,7 +88,16 @@ const char* check_params(int nx, int ny, const lbm_params* p);
 // are left null); nullptr on success, else the reason.
 const char* fill_inst(Inst& I, const lbm_params* p, int nx, int ny, int pitch, long long plane, int fp64);
 // Rows per band of the default tiling for CTAs of `cols` threads.
-int default_band_rows(int nx, int ny, int cols);
+// Rows per band of a cols-wide step tiling of an nx x ny lattice: the band height
+// that covers the lattice in the fewest row-iterations per CTA slot, counting the 4
+// halo rows (plus about one row of fixed cost) every band adds, the `slots` CTAs one
+// wave holds and half a tile of tail.  Never below 4 rows unless the lattice is lower.
+int default_band_rows(int nx, int ny, int cols, long long slots);
+// CTAs of the step kernel (storage precision, thermal flag, tile columns, kernel
+// form) that one wave of the current device holds: SMs x resident CTAs per SM.
+long long step_wave_slots(int fp64, int thermal, int cols, int kernel);
+int resident_ctas_f32(int thermal, int cols, int kernel);
+int resident_ctas_f64(int thermal, int cols);
 // The instance descriptor of a context (device pointers included), for batching.
 Inst lbm_internal_inst(const lbm_ctx* c);
 // Changes whenever the context's descriptor is rewritten (parameters or a loaded state).

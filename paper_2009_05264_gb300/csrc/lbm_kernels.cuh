@@ -892,6 +892,36 @@ cudaError_t launch_one(const Inst* d_inst, const Tile* d_tiles, int ntiles, cuda
   return cudaGetLastError();
 }
 
+// Step-kernel CTAs resident per SM on the current device (at least 1).
+template <typename Real, bool THERMAL, int B>
+int resident_one() {
+  constexpr size_t smem = fused_smem_bytes<Real, THERMAL, B>();
+  auto fn = lbm_fused_kernel<Real, THERMAL, B, MODE_STEP>;
+  int n = 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, B, smem) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
+}
+
+template <typename Real>
+int resident_precision(int thermal, int cols) {
+  if (thermal) {
+    switch (cols) {
+      case 64: return resident_one<Real, true, 64>();
+      case 128: return resident_one<Real, true, 128>();
+      case 256: return resident_one<Real, true, 256>();
+    }
+  } else {
+    switch (cols) {
+      case 64: return resident_one<Real, false, 64>();
+      case 128: return resident_one<Real, false, 128>();
+      case 256: return resident_one<Real, false, 256>();
+    }
+  }
+  return 1;
+}
+
 template <typename Real, bool THERMAL, int B>
 cudaError_t launch_cols(int mode, const Inst* d_inst, const Tile* d_tiles, int ntiles, cudaStream_t s) {
   switch (mode) {

@@ -93,7 +93,8 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, int32_t nx, int32_t 
   const int w = kNoAllocCols - 8;
   const int strips = (nx + w - 1) / w;
   if (strips > kNoAllocMaxTiles) return LBM_EINVAL;
-  int rows = default_band_rows(nx, ny, kNoAllocCols);
+  int rows = default_band_rows(nx, ny, kNoAllocCols, step_wave_slots(prec == LBM_FP64, p->thermal, kNoAllocCols,
+                                                                   LBM_KERNEL_SCALAR));
   while ((long long)strips * ((ny + rows - 1) / rows) > kNoAllocMaxTiles) rows *= 2;
   rows = std::min(rows, ny);
   const int ntiles = strips * ((ny + rows - 1) / rows);
@@ -127,8 +128,10 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, int32_t nx, int32_t 
   Tile* tiles = reinterpret_cast<Tile*>(base + kOffTiles);
   fill_tiles_kernel<<<(ntiles + 255) / 256, 256, 0, s>>>(tiles, nx, ny, w, rows, strips, ntiles);
   if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
-  if (launch_lbm(prec == LBM_FP64, p->thermal, kNoAllocCols, MODE_STEP, reinterpret_cast<const Inst*>(base + kOffInst),
-                 tiles, ntiles, s) != cudaSuccess)
+  // The caller's buffers are dense (pitch nx, any nx) and only element-aligned, so the
+  // paired kernel's 8-byte accesses are not valid here: always the one-column form.
+  if (launch_lbm(prec == LBM_FP64, p->thermal, kNoAllocCols, MODE_STEP, LBM_KERNEL_SCALAR,
+                 reinterpret_cast<const Inst*>(base + kOffInst), tiles, ntiles, s) != cudaSuccess)
     return LBM_ECUDA;
   InstState out;
   double rec[NDIAG];

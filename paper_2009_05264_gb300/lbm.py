@@ -29,13 +29,16 @@ EXPORTS = (
     "lbm_default_params", "lbm_required_bytes", "lbm_create", "lbm_create_ex", "lbm_set_params",
     "lbm_init_fields", "lbm_step", "lbm_step_async", "lbm_sync", "lbm_read_fields", "lbm_get_populations",
     "lbm_set_populations", "lbm_read_diagnostics", "lbm_state_bytes", "lbm_save_state", "lbm_load_state",
-    "lbm_set_tiling", "lbm_get_step", "lbm_launch_count", "lbm_get_stream", "lbm_critical_temperature",
+    "lbm_set_tiling", "lbm_set_kernel", "lbm_get_step", "lbm_launch_count", "lbm_get_stream", "lbm_critical_temperature",
     "lbm_destroy", "lbm_status_string", "lbm_last_error", "lbm_step_noalloc",
     "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_member", "lbm_batch_size",
-    "lbm_batch_set_tiling", "lbm_batch_get_tiling", "lbm_batch_autotune", "lbm_batch_step",
+    "lbm_batch_set_tiling", "lbm_batch_set_kernel", "lbm_batch_get_tiling", "lbm_batch_autotune", "lbm_batch_step",
     "lbm_batch_step_async", "lbm_batch_sync", "lbm_batch_read_fields", "lbm_batch_launch_count",
     "lbm_batch_get_stream", "lbm_batch_last_error", "lbm_batch_destroy",
 )
+
+
+KERNELS = {"auto": 0, "scalar": 1, "paired": 2}
 
 
 class LbmParams(ctypes.Structure):
@@ -94,6 +97,7 @@ def load(build_if_missing: bool = True):
         "lbm_save_state": (ctypes.c_int, [vp, vp, sz]),
         "lbm_load_state": (ctypes.c_int, [vp, vp, sz]),
         "lbm_set_tiling": (ctypes.c_int, [vp, i32, i32]),
+        "lbm_set_kernel": (ctypes.c_int, [vp, i32]),
         "lbm_get_step": (i64, [vp]),
         "lbm_launch_count": (i64, [vp]),
         "lbm_get_stream": (vp, [vp]),
@@ -109,6 +113,7 @@ def load(build_if_missing: bool = True):
         "lbm_batch_member": (vp, [vp, i32]),
         "lbm_batch_size": (i32, [vp]),
         "lbm_batch_set_tiling": (ctypes.c_int, [vp, i32, i32]),
+        "lbm_batch_set_kernel": (ctypes.c_int, [vp, i32]),
         "lbm_batch_get_tiling": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "lbm_batch_autotune": (ctypes.c_int, [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "lbm_batch_step": (ctypes.c_int, [vp, i64]),
@@ -219,6 +224,10 @@ class Lattice:
 
     def set_tiling(self, cols: int, rows: int):
         self._check(self._L.lbm_set_tiling(self._h, int(cols), int(rows)))
+
+    def set_kernel(self, kernel: str):
+        """FP32 step kernel form: "auto", "scalar" or "paired"."""
+        self._check(self._L.lbm_set_kernel(self._h, KERNELS[kernel]))
 
     # --- stepping ---------------------------------------------------------
     def step(self, n: int = 1):
@@ -361,6 +370,9 @@ class Batch:
 
     def set_tiling(self, cols: int, rows: int = 0):
         self._check(self._L.lbm_batch_set_tiling(self._h, int(cols), int(rows)))
+
+    def set_kernel(self, kernel: str):
+        self._check(self._L.lbm_batch_set_kernel(self._h, KERNELS[kernel]))
 
     @property
     def tiling(self):

@@ -39,10 +39,11 @@ def rel_err(got, ref, key):
     return np.abs(got[key] - ref[key]).max() / scale
 
 
-def run_pair(nx, ny, p, fields, steps, precision="fp64", tiling=None, chunks=1):
+def run_pair(nx, ny, p, fields, steps, precision="fp64", tiling=None, chunks=1, kernel="auto"):
     L = lbm()
     lat = L.Lattice(nx, ny, precision)
     lat.set_params(p)
+    lat.set_kernel(kernel)
     if tiling:
         lat.set_tiling(*tiling)
     lat.init_fields(*fields)
@@ -141,11 +142,12 @@ def test_fp64_single_phase_poiseuille():
         assert rel_err(got, ref, k) < FP64_TOL, k
 
 
+@pytest.mark.parametrize("kernel", ["paired", "scalar"])
 @pytest.mark.parametrize("tiling", [(128, 16), (64, 4), (256, 37)])
-def test_fp32_channel_thermal_1000_steps(tiling):
+def test_fp32_channel_thermal_1000_steps(tiling, kernel):
     nx, ny = 300, 37
     p, fields = channel_case(nx, ny, heat_on_step=200)
-    lat, orc = run_pair(nx, ny, p, fields, 1000, "fp32", tiling)
+    lat, orc = run_pair(nx, ny, p, fields, 1000, "fp32", tiling, kernel=kernel)
     got, ref = lat.fields(), orc.fields()
     for k in ("rho", "ux", "uy", "T"):
         assert rel_err(got, ref, k) < FP32_TOL, k
@@ -168,7 +170,8 @@ def two_phase_fp32_checks(got, ref, lat_mass, orc_mass):
     assert abs(lat_mass - orc_mass) < FP32_TOL * orc_mass
 
 
-def test_fp32_periodic_droplet_1000_steps():
+@pytest.mark.parametrize("kernel", ["paired", "scalar"])
+def test_fp32_periodic_droplet_1000_steps(kernel):
     nx, ny = 64, 64
     p = prm(nx, geometry="periodic", thermal=0, g_a=0.0)
     T = 0.86 * oracle.Tc(p)
@@ -176,24 +179,61 @@ def test_fp32_periodic_droplet_1000_steps():
     rv, rl, _ = oracle.maxwell(p, T)
     fields = I.disk(nx, ny, 25 * 64 / 128, rl, rv, T, seed=2009052640, amp=1e-3)
     p["init_rho_out"] = rl  # FP32 storage and pseudopotential reference: the liquid
-    lat, orc = run_pair(nx, ny, p, fields, 1000, "fp32")
+    lat, orc = run_pair(nx, ny, p, fields, 1000, "fp32", kernel=kernel)
     got, ref = lat.fields(), orc.fields()
     two_phase_fp32_checks(got, ref, lat.diagnostics()["mass"], orc.last_diag()["mass"])
 
 
-def test_fp32_thermal_droplet_1000_steps():
+@pytest.mark.parametrize("kernel", ["paired", "scalar"])
+def test_fp32_thermal_droplet_1000_steps(kernel):
     nx, ny = 40, 40
     p = prm(nx, geometry="periodic", thermal=1, g_a=1e-4)
     T = 0.9 * oracle.Tc(p)
     rv, rl, _ = oracle.maxwell(p, T)
     p["init_rho_out"] = rl
     fields = I.disk(nx, ny, 10, rl, rv, T, seed=9, amp=1e-3)
-    lat, orc = run_pair(nx, ny, p, fields, 1000, "fp32")
+    lat, orc = run_pair(nx, ny, p, fields, 1000, "fp32", kernel=kernel)
     got, ref = lat.fields(), orc.fields()
     two_phase_fp32_checks(got, ref, lat.diagnostics()["mass"], orc.last_diag()["mass"])
     # flow here is buoyancy- and phase-change-driven, not only spurious currents
     for k in ("ux", "uy"):
         assert rel_err(got, ref, k) < 1e-4, k
+
+
+@pytest.mark.parametrize("nx,ny,geometry,tiling", [(151, 37, "channel", (128, 16)), (57, 23, "channel", (64, 5)),
+                                                   (63, 30, "walls", (128, 8)), (37, 41, "periodic", (64, 6))])
+def test_fp32_paired_kernel_odd_and_periodic_edges(nx, ny, geometry, tiling):
+    """The paired kernel's edge cases: an odd width (the last pair half outside the
+    domain), open ends inside a pair, and wrap-around pairs in periodic directions."""
+    if geometry == "channel":
+        p, fields = channel_case(nx, ny, heat_on_step=20)
+    else:
+        p = prm(nx, geometry=geometry, thermal=1, g_a=1e-4, heater_x0=3, heater_len=7, heat_on_step=10)
+        fields = I.smooth_random(nx, ny, 5.95, 0.9 * oracle.Tc(p), seed=nx + 7 * ny, drho=0.002, du=0.005, dT=0.002)
+    lat, orc = run_pair(nx, ny, p, fields, 300, "fp32", tiling, kernel="paired")
+    got, ref = lat.fields(), orc.fields()
+    for k in ("rho", "ux", "uy", "T"):
+        assert rel_err(got, ref, k) < FP32_TOL, k
+    assert lat.diagnostics()["mass"] == pytest.approx(orc.last_diag()["mass"], rel=FP32_TOL)
+
+
+def test_fp32_paired_and_scalar_kernels_agree():
+    """The two FP32 step forms compute the same update; they differ only in the
+    order of a few roundings, so after 200 steps their populations agree to ~1e-6."""
+    L = lbm()
+    nx, ny = 260, 41
+    p, fields = channel_case(nx, ny, heat_on_step=10)
+    pops = {}
+    for kernel in ("paired", "scalar"):
+        lat = L.Lattice(nx, ny, "fp32")
+        lat.set_params(p)
+        lat.set_kernel(kernel)
+        lat.init_fields(*fields)
+        lat.step(200)
+        pops[kernel] = lat.populations()
+    for a, b in zip(pops["paired"], pops["scalar"]):
+        assert np.abs(a - b).max() < 1e-5 * np.abs(b).max()
+    assert L.load().lbm_set_kernel(lat._h, 7) == 1  # LBM_EINVAL
 
 
 def test_tiling_does_not_change_results():

@@ -28,7 +28,7 @@ def test_results_alone_and_in_the_mix_agree():
         fields = I.smooth_random(nx, ny, 5.95, 0.9 * Tc, seed=500 + k, drho=0.002, du=0.005, dT=0.002)
         reqs.append(Request(k, nx, ny, p, fields, steps=int(rng.integers(40, 120)), arrival=3.0 * k))
     clock = FakeClock(tick=1.0)
-    srv = Server("fp32", chunk=16, clock=clock)
+    srv = Server("fp32", chunk=16, clock=clock, tiling=(128, 16))
     for r in reqs:
         srv.submit(r)
     done = {r.rid: r for r in srv.run()}
@@ -40,7 +40,7 @@ def test_results_alone_and_in_the_mix_agree():
     for r in reqs:
         lat = lbm.Lattice(r.nx, r.ny, "fp32")
         lat.set_params(r.params)
-        lat.set_tiling(128, 0)
+        lat.set_tiling(128, 16)
         lat.init_fields(*r.fields)
         lat.step(r.steps)
         alone = lat.fields()
