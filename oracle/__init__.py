@@ -18,7 +18,8 @@ _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 GEOMETRY = {"periodic": 0, "channel": 1, "walls": 2}
-DIAG_NAMES = ("step", "mass", "energy", "rho_avg", "dp", "dtstar", "flux_in", "flux_out", "source")
+DIAG_NAMES = ("step", "mass", "energy", "rho_avg", "dp", "dtstar", "flux_in", "flux_out", "source",
+              "vapor_area", "wall_vapor", "heater_vapor")
 
 
 class OrcParams(ctypes.Structure):
@@ -47,6 +48,7 @@ class OrcParams(ctypes.Structure):
         ("heater_x0", ctypes.c_int32),
         ("heater_len", ctypes.c_int32),
         ("heat_on_step", ctypes.c_int64),
+        ("rho_vapor", ctypes.c_double),
     ]
 
 

@@ -40,12 +40,17 @@ typedef struct orc_params {
   double u_in, rho_out, rho_w, G_wet, g_a, c_v;
   int32_t heater_x0, heater_len;
   int64_t heat_on_step;
+  double rho_vapor;   /* density below which a node counts as vapour (bubble diagnostics) */
 } orc_params;
 
 /* Diagnostics of one step, computed from that step's moments. */
 enum {
   ORC_D_STEP = 0, ORC_D_MASS, ORC_D_ENERGY, ORC_D_RHO_AVG, ORC_D_DP, ORC_D_DTSTAR,
-  ORC_D_FLUX_IN, ORC_D_FLUX_OUT, ORC_D_SOURCE, ORC_D_COUNT
+  ORC_D_FLUX_IN, ORC_D_FLUX_OUT, ORC_D_SOURCE,
+  ORC_D_VAPOR_AREA,   /* nodes with rho < rho_vapor (bubble area, lattice units) */
+  ORC_D_WALL_VAPOR,   /* of those, nodes on the row next to the bottom wall (vapour footprint) */
+  ORC_D_HEATER_VAPOR, /* of those, nodes above heater sites x_h <= x < x_h + n_h */
+  ORC_D_COUNT
 };
 
 typedef struct orc_lattice orc_lattice;

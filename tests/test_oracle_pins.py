@@ -284,6 +284,25 @@ def test_thermal_liquid_between_walls_is_quiet():
     assert amp[2] < amp[1] < amp[0] < 1e-6
 
 
+def test_vapour_diagnostics_count_the_bubble():
+    """Bubble area, its footprint on the bottom wall and over the heater (Sec. 3.A,
+    Figs. 7-8) are node counts of rho < rho_vapor; the first step's record counts the
+    moments of the initial state, i.e. exactly the input field."""
+    nx, ny, R = 60, 30, 11
+    p = prm(nx, geometry="walls", thermal=1, g_a=0.0, heater_x0=25, heater_len=7, heat_on_step=0)
+    T = 0.9 * oracle.Tc(p)
+    rv, rl, _ = oracle.maxwell(p, T)
+    fields = I.sessile(nx, ny, R, rv, rl, T)  # a vapour half-disk on the bottom wall
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(*fields)
+    assert O.step(1) == 0
+    d = O.last_diag()
+    vap = fields[0] < p["rho_vapor"]
+    assert d["vapor_area"] == vap.sum() and d["wall_vapor"] == vap[0].sum()
+    assert d["heater_vapor"] == vap[0, 25:32].sum()
+    assert 0.4 * np.pi * R * R < d["vapor_area"] < 0.6 * np.pi * R * R and d["heater_vapor"] == 7
+
+
 def test_steady_conduction_between_walls():
     """With u = 0 anti-bounce-back (Sec. 2.C) and g^eq (Eq. 18) reduce to pure
     diffusion: the steady profile between a heated bottom wall at y = -1/2 and the
