@@ -19,7 +19,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 GEOMETRY = {"periodic": 0, "channel": 1, "walls": 2}
 DIAG_NAMES = ("step", "mass", "energy", "rho_avg", "dp", "dtstar", "flux_in", "flux_out", "source",
-              "vapor_area", "wall_vapor", "heater_vapor")
+              "vapor_area", "wall_vapor", "heater_vapor", "zone_vapor")
 
 
 class OrcParams(ctypes.Structure):

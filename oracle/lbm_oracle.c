@@ -13,7 +13,8 @@
  *   5. f collision        BGK (Eq. 2) toward f^eq (Eq. 3) plus exact-difference forcing (Eq. 5)
  *   6. g collision        BGK toward g^eq(T, u_act) (Eq. 18) plus source phi (second Eq. 19)
  *   7. diagnostics        mass, energy, domain-mean density for the next step's buoyancy;
- *                         vapour area, its footprint on the bottom wall and over the heater
+ *                         vapour area, its footprint on the bottom wall and over the heater,
+ *                         and the vapour in the columns around the heater
  *   8. streaming (Eqs. 1, 16) and the boundary conditions of Sec. 2.C: halfway
  *      bounce-back walls, anti-bounce-back wall/heater/inlet temperature,
  *      non-equilibrium bounce-back (Zou-He) velocity inlet and pressure outlet,
@@ -573,11 +574,12 @@ static int one_step(orc_lattice* L, const orc_params* P) {
   L->diag[ORC_D_FLUX_OUT] = flux_out;
   L->diag[ORC_D_SOURCE] = source_total;
   /* Bubble diagnostics (vapour: rho below rho_vapor), from this step's moments */
-  double area = 0, wall = 0, heat = 0;
+  double area = 0, wall = 0, heat = 0, zone = 0;
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       if (!(L->rho[nid(L, x, y)] < P->rho_vapor)) continue;
       area += 1.0;
+      if (x >= P->heater_x0 - P->heater_len && x < P->heater_x0 + 2 * P->heater_len) zone += 1.0;
       if (y == 0 && P->geometry != ORC_PERIODIC) {
         wall += 1.0;
         if (x >= P->heater_x0 && x < P->heater_x0 + P->heater_len) heat += 1.0;
@@ -586,6 +588,7 @@ static int one_step(orc_lattice* L, const orc_params* P) {
   L->diag[ORC_D_VAPOR_AREA] = area;
   L->diag[ORC_D_WALL_VAPOR] = wall;
   L->diag[ORC_D_HEATER_VAPOR] = heat;
+  L->diag[ORC_D_ZONE_VAPOR] = zone;
 
   /* Streaming (Eqs. 1, 16) with the wall rules; open-end unknowns marked */
   memset(L->unknown, 0, 9 * n);

@@ -50,6 +50,7 @@ enum {
   ORC_D_VAPOR_AREA,   /* nodes with rho < rho_vapor (bubble area, lattice units) */
   ORC_D_WALL_VAPOR,   /* of those, nodes on the row next to the bottom wall (vapour footprint) */
   ORC_D_HEATER_VAPOR, /* of those, nodes above heater sites x_h <= x < x_h + n_h */
+  ORC_D_ZONE_VAPOR,   /* vapour nodes in the columns x_h - n_h <= x < x_h + 2 n_h (the bubble at the heater) */
   ORC_D_COUNT
 };
 

@@ -300,6 +300,7 @@ def test_vapour_diagnostics_count_the_bubble():
     vap = fields[0] < p["rho_vapor"]
     assert d["vapor_area"] == vap.sum() and d["wall_vapor"] == vap[0].sum()
     assert d["heater_vapor"] == vap[0, 25:32].sum()
+    assert d["zone_vapor"] == vap[:, 18:39].sum()
     assert 0.4 * np.pi * R * R < d["vapor_area"] < 0.6 * np.pi * R * R and d["heater_vapor"] == 7
 
 
