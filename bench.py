@@ -261,6 +261,38 @@ def run_serve(n_requests: int, steps: int, rate: float = 2.0, seed: int = SEED +
             "hbm_budget_bytes": hbm_budget, "chunk_steps": chunk, "finite": bool(finite)}
 
 
+STEP_SOURCES = ("paper_2009_05264_gb300/csrc/lbm_kernels.cuh", "paper_2009_05264_gb300/csrc/lbm_internal.h")
+PROFILE = "profiles/lbm_fused_step_fp32_channel.md"
+
+
+def step_source_digest() -> str:
+    """Digest of the FP32 step kernel's sources: ties a profiled DRAM traffic figure to
+    the code it was measured on."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in STEP_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic_per_node():
+    """DRAM bytes per node update of the step kernel from the committed ncu summary, or
+    (None, reason) when the summary was taken on other kernel sources."""
+    import re
+
+    path = os.path.join(ROOT, PROFILE)
+    if not os.path.exists(path):
+        return None, "no profile summary"
+    m = re.search(r"traffic-per-node:\s*([0-9.]+)\s*B\s*\(source digest ([0-9a-f]+)", open(path).read())
+    if not m:
+        return None, "profile summary has no traffic line"
+    if m.group(2) != step_source_digest():
+        return None, "kernel sources changed since the profile"
+    return float(m.group(1)), f"ncu dram__bytes_read+write per node ({PROFILE})"
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -401,6 +433,7 @@ def run_ours(args):
         bpn = bytes_per_node(prec)
         avg_launch_ms = statistics.mean(per_launch)
         achieved = bpn * nodes / (avg_launch_ms * 1e-3) / 1e9
+        tpn, tsrc = profiled_traffic_per_node() if prec == "fp32" and args.kernel != "paired" else (None, "not profiled")
         line = {
             "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -413,11 +446,12 @@ def run_ours(args):
                        "l2": "inputs larger than L2: 2 x 0.92 GB population buffers vs 129 MB L2",
                        "parallelism": f"{world} independent channel replicas"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": tpn * nodes if tpn else None,
+                         "traffic_source": tsrc,
                          "peak_source": f"{peak_kind} HBM copy bandwidth",
                          "algorithmic_bytes_per_node": bpn,
-                         "kernel": ("lbm_fused_kernel (MODE_STEP)" if prec == "fp64" or args.kernel == "scalar"
-                                    else "lbm_pair_kernel (two columns per thread, packed FP32)")},
+                         "kernel": ("lbm_pair_kernel (two columns per thread, packed FP32)"
+                                    if prec == "fp32" and args.kernel == "paired" else "lbm_fused_kernel (MODE_STEP)")},
             "e2e": {"value": e2e_value, "unit": "MLUPS",
                     "h2d_bytes_per_step": 4 * nodes * 8 / e2e_steps, "d2h_bytes_per_step": 4 * nodes * 8 / e2e_steps,
                     "note": f"init_fields from pinned host arrays + {e2e_steps} steps + read_fields to host"},

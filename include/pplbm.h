@@ -69,6 +69,12 @@ enum {
   LBM_D_DTSTAR,      /* (T_wall - T_next_to_heater)/(T_wall - T_bulk) (Sec. 3.B, Fig. 12c); 0 if heater off */
   LBM_D_FLUX_IN,     /* sum over y of rho * u_act,x at x = 0 */
   LBM_D_FLUX_OUT,    /* sum over y of rho * u_act,x at x = nx-1 */
+  LBM_D_VAPOR_AREA,  /* nodes with rho < rho_vapor: bubble area (Sec. 3.A, Fig. 8) */
+  LBM_D_WALL_VAPOR,  /* of those, nodes on the row next to the bottom wall: the vapour footprint,
+                        i.e. the contact-line extent in 2D (Sec. 3.E, Fig. 17) */
+  LBM_D_HEATER_VAPOR,/* of those, nodes above heater sites: non-zero while a bubble sits on the heater */
+  LBM_D_ZONE_VAPOR,  /* vapour nodes in the columns x_h - n_h <= x < x_h + 2 n_h: the bubble at the heater,
+                        without the earlier bubbles the stream has carried off */
   LBM_D_COUNT
 };
 
@@ -109,6 +115,8 @@ typedef struct lbm_params {
   int32_t reserved0;
   double init_rho_in, init_rho_out, init_radius, init_width, perturb_amp;
   uint64_t seed;
+  double rho_vapor;   /* bubble diagnostics count a node as vapour when rho < rho_vapor: 3.2
+                         (about the midpoint of the coexisting densities 0.59 and 5.88 at 0.9 Tc) */
 } lbm_params;
 
 /* Fill *p with the defaults listed above (and p->size). */
@@ -174,6 +182,12 @@ lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f, const double* g, s
 
 /* Diagnostics record of the most recent step: out[LBM_D_COUNT]. */
 lbm_status lbm_read_diagnostics(lbm_ctx* ctx, double* out, size_t n);
+
+/* Records of the steps first, first + 1, ..., first + count - 1 (oldest first) into the
+ * host array out[count][LBM_D_COUNT].  The context keeps the records of its last 1024
+ * steps; LBM_EINVAL if a requested step is not held (not yet taken, or more than 1024
+ * steps back) or count < 0.  Waits for the context's stream. */
+lbm_status lbm_read_diagnostics_range(lbm_ctx* ctx, int64_t first, int64_t count, double* out);
 
 /* Checkpoint / resume: raw state (populations in storage precision, step,
  * buoyancy mean, parameters).  lbm_state_bytes() gives the buffer size; resume

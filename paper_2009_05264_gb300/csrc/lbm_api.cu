@@ -133,6 +133,7 @@ const char* fill_inst(Inst& I, const lbm_params* p, int nx, int ny, int pitch, l
   I.heater_x0 = p->heater_x0 < 0 ? nx / 5 : p->heater_x0;
   I.heater_len = p->heater_len;
   I.heat_on_step = p->heat_on_step;
+  I.rho_vapor = p->rho_vapor;
   return nullptr;
 }
 
@@ -464,6 +465,7 @@ void lbm_default_params(lbm_params* p) {
   p->init_width = 2.0;
   p->perturb_amp = 0.0;
   p->seed = 0;
+  p->rho_vapor = 3.2;
 }
 
 size_t lbm_required_bytes(int32_t nx, int32_t ny, lbm_precision prec) {
@@ -767,6 +769,29 @@ lbm_status lbm_set_tiling(lbm_ctx* c, int32_t cols, int32_t rows) {
   const lbm_status s = set_tiling(c, cols, rows);
   if (s == LBM_OK) c->rows_default = false;
   return s;
+}
+
+lbm_status lbm_read_diagnostics_range(lbm_ctx* c, int64_t first, int64_t count, double* out) {
+  if (!c) return LBM_EINVAL;
+  if (count < 0 || (count > 0 && !out)) return fail(c, LBM_EINVAL, "count < 0 or NULL out");
+  DeviceGuard g(c->device);
+  lbm_status s = fetch_state(c);
+  if (s != LBM_OK) return s;
+  if (count == 0) return LBM_OK;
+  const long long oldest = std::max<long long>(0, c->step_host - RING);
+  if (first < oldest || first + count > c->step_host)
+    return fail(c, LBM_EINVAL, "requested steps are not in the diagnostics ring");
+  const double* ring = reinterpret_cast<const double*>(c->base + c->L.off_ring);
+  long long done = 0;
+  while (done < count) {  // at most two contiguous pieces of the ring
+    const long long slot = (first + done) % RING;
+    const long long n = std::min<long long>(count - done, RING - slot);
+    LBM_CUDA(c, cudaMemcpyAsync(out + done * NDIAG, ring + slot * NDIAG, (size_t)n * NDIAG * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream));
+    done += n;
+  }
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
 }
 
 int64_t lbm_get_step(const lbm_ctx* c) { return c ? c->step_host : -1; }

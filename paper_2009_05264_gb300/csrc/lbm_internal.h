@@ -10,8 +10,8 @@ namespace pplbm {
 
 // Per-tile partial sums folded by the last CTA of an instance:
 // mass, energy, T summed over the heater-adjacent row, inlet flux, outlet flux.
-constexpr int NPART = 5;
-constexpr int NDIAG = 8;  // LBM_D_COUNT
+constexpr int NPART = 9;  // mass, energy, heater row T, inflow, outflow, vapour area, wall / heater / zone vapour
+constexpr int NDIAG = 12;  // LBM_D_COUNT
 constexpr int RING = 1024;  // diagnostics records kept per instance
 
 enum : int { GEOM_PERIODIC = 0, GEOM_CHANNEL = 1, GEOM_WALLS = 2 };
@@ -50,6 +50,7 @@ struct Inst {
   double psi_ref, rad_ref, p_ref, inv_u1r, inv_Dr, sa_r, sqrtT_r, rr2_Dr;
   int heater_x0, heater_len;
   long long heat_on_step;
+  double rho_vapor;                 // vapour threshold of the bubble diagnostics
   InstState* st;
   double* partials;                 // NPART per tile of this instance
   double* ring;                     // RING records of NDIAG doubles

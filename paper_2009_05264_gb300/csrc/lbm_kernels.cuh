@@ -147,6 +147,7 @@ struct KConst {
   // force on a row next to the bottom wall: wall0 + d * wall1 (the top wall: minus that)
   Real wall0, wall1;
   Real rho_ref_minus_avg;  // rho_ref - rho_avg of the previous step (buoyancy, Eq. 14)
+  Real drho_vapor;         // rho_vapor - rho_ref: vapour when drho < drho_vapor
 };
 
 template <typename Real>
@@ -189,6 +190,7 @@ __device__ __forceinline__ void fill_consts(KConst<Real>& c, const Inst& I, doub
   c.wall0 = Real(-G3 * (I.beta + mixd) * pr * pr + I.Gwet_psiw * pr / 6.0);
   c.wall1 = Real(-G3 * I.beta * pr + I.Gwet_psiw / 6.0);
   c.rho_ref_minus_avg = Real(I.rho_ref - rho_avg_prev);
+  c.drho_vapor = Real(I.rho_vapor - I.rho_ref);
 }
 
 // ---------------------------------------------------------------------------
@@ -535,6 +537,10 @@ __device__ __forceinline__ void finish_step(const Inst& I, InstState* st, const 
     rec[5] = dtstar;
     rec[6] = channel ? tot[3] : 0.0;
     rec[7] = channel ? tot[4] : 0.0;
+    rec[8] = tot[5];
+    rec[9] = tot[6];
+    rec[10] = tot[7];
+    rec[11] = tot[8];
     st->rho_avg[step & 1] = mass / n;
     st->step = step + 1;
     st->local_read = 0;
@@ -634,6 +640,8 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
   };
 
   Real acc_m = Real(0), acc_e = Real(0), acc_h = Real(0), acc_fi = Real(0), acc_fo = Real(0);
+  float acc_va = 0.0f, acc_wv = 0.0f, acc_hv = 0.0f, acc_zv = 0.0f;  // vapour node counts (exact in FP32)
+  const bool zone_col = xn >= sI.heater_x0 - sI.heater_len && xn < sI.heater_x0 + 2 * sI.heater_len;
   // node scalars carried between iterations: row r-1 (f collision), row r-2 (g collision)
   Real rho_p = Real(1), drho_p = Real(0), ux_p = Real(0), uy_p = Real(0), T_p = T0, dT_p = Real(0), coef_p = Real(0);
   Real T_p2 = T0, dT_p2 = Real(0), coef_p2 = Real(0);
@@ -684,6 +692,14 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
         if (THERMAL) {
           acc_e += ns.dT;
           if (!pery && rn == 0 && xn >= sI.heater_x0 && xn < sI.heater_x0 + sI.heater_len) acc_h += ns.dT;
+        }
+        if (ns.drho < sC.drho_vapor) {
+          acc_va += 1.0f;
+          if (zone_col) acc_zv += 1.0f;
+          if (!pery && rn == 0) {
+            acc_wv += 1.0f;
+            if (xn >= sI.heater_x0 && xn < sI.heater_x0 + sI.heater_len) acc_hv += 1.0f;
+          }
         }
         if (MODE == MODE_STEP && channel && rn == ny / 2 && (xn == 1 || xn == nx - 2)) {
           if (xn == 1) st->p_probe[0] = (double)ns.p;
@@ -786,7 +802,8 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
   if (MODE != MODE_STEP && MODE != MODE_MOMENTS) return;
 
   // ---------------- per-tile partials and the last-CTA fold ----------------
-  double acc[NPART] = {(double)acc_m, (double)acc_e, (double)acc_h, (double)acc_fi, (double)acc_fo};
+  double acc[NPART] = {(double)acc_m,  (double)acc_e,  (double)acc_h,  (double)acc_fi, (double)acc_fo,
+                       (double)acc_va, (double)acc_wv, (double)acc_hv, (double)acc_zv};
   block_sum<BLOCK>(acc, sRed);
   if (tid == 0) {
     double* part = sI.partials + (long long)tile.local * NPART;
@@ -799,7 +816,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
   __syncthreads();
   if (!sLast) return;
   __threadfence();
-  double tot[NPART] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double tot[NPART] = {};
   for (int t = tid; t < tile.ntiles; t += BLOCK) {
 #pragma unroll
     for (int j = 0; j < NPART; ++j) tot[j] += __ldcg(sI.partials + (long long)t * NPART + j);
@@ -816,16 +833,21 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
 template <typename Real>
 __device__ __forceinline__ void write_equilibrium(const Inst& I, long long node, double rho, double ux,
                                                   double uy, double T) {
+  // The reference parts are taken off in FP64; the rest is computed in the storage
+  // precision (FP32 storage keeps FP32 rounding of the deviations either way, and FP64
+  // arithmetic is scarce on this GPU).
   Real* F = static_cast<Real*>(I.f[0]);
   Real* Gb = static_cast<Real*>(I.g[0]);
-  const double usq = ux * ux + uy * uy;
+  const Real drho = Real(rho - I.rho_ref), dT = Real(T - I.T_ref);
+  const Real r = Real(rho), t = Real(T), vx = Real(ux), vy = Real(uy);
+  const Real usq = vx * vx + vy * vy;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const double cu = lat_cx(i) * ux + lat_cy(i) * uy;
-    const double w = lat_w<double>(i);
-    const double poly = 3.0 * cu + 4.5 * cu * cu - 1.5 * usq;
-    F[i * I.plane + node] = Real(w * ((rho - I.rho_ref) + rho * poly));
-    Gb[i * I.plane + node] = Real(w * ((T - I.T_ref) + T * poly));
+    const Real cu = Real(lat_cx(i)) * vx + Real(lat_cy(i)) * vy;
+    const Real w = lat_w<Real>(i);
+    const Real poly = Real(3) * cu + Real(4.5) * cu * cu - Real(1.5) * usq;
+    F[i * I.plane + node] = w * (drho + r * poly);
+    Gb[i * I.plane + node] = w * (dT + t * poly);
   }
 }
 

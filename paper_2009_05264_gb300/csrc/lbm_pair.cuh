@@ -343,7 +343,8 @@ lbm_pair_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) 
   };
 
   float2 acc_m = p_bc(0.0f), acc_e = p_bc(0.0f);
-  float acc_h = 0.0f, acc_fi = 0.0f, acc_fo = 0.0f;
+  float acc_h = 0.0f, acc_fi = 0.0f, acc_fo = 0.0f, acc_va = 0.0f, acc_wv = 0.0f, acc_hv = 0.0f, acc_zv = 0.0f;
+  const int zlo = sI.heater_x0 - sI.heater_len, zhi = sI.heater_x0 + 2 * sI.heater_len;
   float2 rho_p = p_bc(1.0f), drho_p = p_bc(0.0f), ux_p = p_bc(0.0f), uy_p = p_bc(0.0f), T_p = p_bc(T0),
          dT_p = p_bc(0.0f), coef_p = p_bc(0.0f);
   float2 T_p2 = p_bc(T0), dT_p2 = p_bc(0.0f), coef_p2 = p_bc(0.0f);
@@ -416,6 +417,18 @@ lbm_pair_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) 
           if (wlo) {
             if (xn0 >= sI.heater_x0 && xn0 < sI.heater_x0 + sI.heater_len) acc_h += ns.dT.x;
             if (out1 && xn1 >= sI.heater_x0 && xn1 < sI.heater_x0 + sI.heater_len) acc_h += ns.dT.y;
+          }
+        }
+        {
+          const float v0 = ns.drho.x < sC.drho_vapor ? 1.0f : 0.0f;
+          const float v1 = (out1 && ns.drho.y < sC.drho_vapor) ? 1.0f : 0.0f;
+          acc_va += v0 + v1;
+          if (xn0 >= zlo && xn0 < zhi) acc_zv += v0;
+          if (xn1 >= zlo && xn1 < zhi) acc_zv += v1;
+          if (wlo) {
+            acc_wv += v0 + v1;
+            if (xn0 >= sI.heater_x0 && xn0 < sI.heater_x0 + sI.heater_len) acc_hv += v0;
+            if (xn1 >= sI.heater_x0 && xn1 < sI.heater_x0 + sI.heater_len) acc_hv += v1;
           }
         }
         if (channel && rn == ny / 2) {
@@ -515,7 +528,8 @@ lbm_pair_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) 
 
   // ---------------- per-tile partials and the last-CTA fold ----------------
   double acc[NPART] = {(double)acc_m.x + (double)acc_m.y, (double)acc_e.x + (double)acc_e.y, (double)acc_h,
-                       (double)acc_fi, (double)acc_fo};
+                       (double)acc_fi, (double)acc_fo, (double)acc_va, (double)acc_wv, (double)acc_hv,
+                       (double)acc_zv};
   block_sum<B>(acc, sRed);
   if (tid == 0) {
     double* part = sI.partials + (long long)tile.local * NPART;
@@ -528,7 +542,7 @@ lbm_pair_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) 
   __syncthreads();
   if (!sLast) return;
   __threadfence();
-  double tot[NPART] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double tot[NPART] = {};
   for (int tt = tid; tt < tile.ntiles; tt += B) {
 #pragma unroll
     for (int j = 0; j < NPART; ++j) tot[j] += __ldcg(sI.partials + (long long)tt * NPART + j);

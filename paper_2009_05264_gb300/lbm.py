@@ -22,13 +22,15 @@ _lib = None
 STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_EUNSTABLE", 4: "LBM_ETIMEOUT",
           5: "LBM_ECUDA", 6: "LBM_EBUDGET", 7: "LBM_ESTATE"}
 FP32, FP64 = 0, 1
-DIAG_NAMES = ("step", "mass", "energy", "rho_avg", "dp", "dtstar", "flux_in", "flux_out")
+DIAG_NAMES = ("step", "mass", "energy", "rho_avg", "dp", "dtstar", "flux_in", "flux_out", "vapor_area",
+              "wall_vapor", "heater_vapor", "zone_vapor")
 
 # Every function the header declares (checked against the shared library's exports).
 EXPORTS = (
     "lbm_default_params", "lbm_required_bytes", "lbm_create", "lbm_create_ex", "lbm_set_params",
     "lbm_init_fields", "lbm_step", "lbm_step_async", "lbm_sync", "lbm_read_fields", "lbm_get_populations",
-    "lbm_set_populations", "lbm_read_diagnostics", "lbm_state_bytes", "lbm_save_state", "lbm_load_state",
+    "lbm_set_populations", "lbm_read_diagnostics", "lbm_read_diagnostics_range", "lbm_state_bytes",
+    "lbm_save_state", "lbm_load_state",
     "lbm_set_tiling", "lbm_set_kernel", "lbm_get_step", "lbm_launch_count", "lbm_get_stream", "lbm_critical_temperature",
     "lbm_destroy", "lbm_status_string", "lbm_last_error", "lbm_step_noalloc",
     "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_member", "lbm_batch_size",
@@ -53,7 +55,7 @@ class LbmParams(ctypes.Structure):
         ("heater_len", ctypes.c_int32), ("heat_on_step", ctypes.c_int64), ("init_kind", ctypes.c_int32),
         ("reserved0", ctypes.c_int32), ("init_rho_in", ctypes.c_double), ("init_rho_out", ctypes.c_double),
         ("init_radius", ctypes.c_double), ("init_width", ctypes.c_double), ("perturb_amp", ctypes.c_double),
-        ("seed", ctypes.c_uint64),
+        ("seed", ctypes.c_uint64), ("rho_vapor", ctypes.c_double),
     ]
 
 
@@ -93,6 +95,7 @@ def load(build_if_missing: bool = True):
         "lbm_get_populations": (ctypes.c_int, [vp, dp, dp, sz]),
         "lbm_set_populations": (ctypes.c_int, [vp, dp, dp, sz, i64, ctypes.c_double]),
         "lbm_read_diagnostics": (ctypes.c_int, [vp, dp, sz]),
+        "lbm_read_diagnostics_range": (ctypes.c_int, [vp, i64, i64, dp]),
         "lbm_state_bytes": (sz, [vp]),
         "lbm_save_state": (ctypes.c_int, [vp, vp, sz]),
         "lbm_load_state": (ctypes.c_int, [vp, vp, sz]),
@@ -281,6 +284,13 @@ class Lattice:
         d = np.empty(len(DIAG_NAMES))
         self._check(self._L.lbm_read_diagnostics(self._h, _dptr(d), d.size))
         return dict(zip(DIAG_NAMES, d.tolist()))
+
+    def diagnostics_range(self, first: int, count: int) -> np.ndarray:
+        """Records of steps first .. first + count - 1 as a (count, len(DIAG_NAMES)) array
+        (columns in DIAG_NAMES order); the context holds its last 1024 steps."""
+        out = np.empty((int(count), len(DIAG_NAMES)))
+        self._check(self._L.lbm_read_diagnostics_range(self._h, int(first), int(count), _dptr(out)))
+        return out
 
     # --- checkpoint -------------------------------------------------------
     def save_state(self) -> bytes:

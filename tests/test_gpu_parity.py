@@ -236,6 +236,63 @@ def test_fp32_paired_and_scalar_kernels_agree():
     assert L.load().lbm_set_kernel(lat._h, 7) == 1  # LBM_EINVAL
 
 
+@pytest.mark.parametrize("precision,slack", [("fp64", 1), ("fp32", 3)])
+def test_bubble_diagnostics_match_oracle(precision, slack):
+    """Vapour area and its wall / heater footprints of a heated sessile bubble, every
+    50 steps, against the oracle's counts (node counts; FP32 may move a few interface
+    nodes across the threshold)."""
+    L = lbm()
+    nx, ny, R = 90, 40, 14
+    p = prm(nx, geometry="walls", thermal=1, g_a=5e-5, heater_x0=40, heater_len=10, heat_on_step=0, dTheat_R=0.3)
+    T = 0.9 * oracle.Tc(p)
+    rv, rl, _ = oracle.maxwell(p, T)
+    p["init_rho_out"] = rl
+    fields = I.sessile(nx, ny, R, rv, rl, T)
+    lat = L.Lattice(nx, ny, precision)
+    lat.set_params(p)
+    lat.init_fields(*fields)
+    orc = oracle.Oracle(nx, ny, p)
+    orc.init_fields(*fields)
+    for _ in range(4):
+        lat.step(25)
+        assert orc.step(25) == 0
+        got, ref = lat.diagnostics(), orc.last_diag()
+        assert got["step"] == ref["step"]
+        for k in ("vapor_area", "wall_vapor", "heater_vapor", "zone_vapor"):
+            assert abs(got[k] - ref[k]) <= slack, (k, got[k], ref[k])
+        assert ref["vapor_area"] > 250 and ref["heater_vapor"] > 0  # the bubble is still on the heater
+
+
+def test_diagnostics_range_returns_every_step_record():
+    L = lbm()
+    nx, ny = 120, 30
+    p, fields = channel_case(nx, ny, heat_on_step=5)
+    lat = L.Lattice(nx, ny, "fp64")
+    lat.set_params(p)
+    lat.init_fields(*fields)
+    orc = oracle.Oracle(nx, ny, p)
+    orc.init_fields(*fields)
+    ref = []
+    for _ in range(40):
+        assert orc.step(1) == 0
+        ref.append(orc.last_diag())
+    lat.step(40)
+    rec = lat.diagnostics_range(0, 40)
+    assert np.array_equal(rec[:, 0], np.arange(40))
+    assert np.array_equal(rec[-1], np.array(list(lat.diagnostics().values())))
+    names = L.DIAG_NAMES
+    for k in ("mass", "energy", "dp", "dtstar", "flux_in", "flux_out"):
+        got = rec[:, names.index(k)]
+        want = np.array([r[k] for r in ref])
+        assert np.abs(got - want).max() <= 1e-11 * max(np.abs(want).max(), 1e-300), k
+    with pytest.raises(L.LbmError):
+        lat.diagnostics_range(30, 20)  # step 49 not taken yet
+    lat.step(1100)
+    with pytest.raises(L.LbmError):
+        lat.diagnostics_range(0, 10)  # older than the 1024-record ring
+    assert lat.diagnostics_range(1140 - 1024, 1024).shape == (1024, len(names))
+
+
 def test_tiling_does_not_change_results():
     """Per-node arithmetic does not depend on the band height: without buoyancy (no global
     sum in the update) every band height gives bit-identical populations for one column

@@ -60,7 +60,7 @@ def test_noalloc_step_matches_context_step_twice(prec):
     bufs = [torch.from_numpy(f0).to(dev), torch.from_numpy(g0).to(dev)]
     outs = [torch.empty(9 * nx * ny, dtype=dt, device=dev) for _ in range(2)]
     torch.cuda.synchronize()
-    diag = np.zeros(8)
+    diag = np.zeros(len(lbm.DIAG_NAMES))
     for call in range(2):
         st = L.lbm_step_noalloc(ctypes.byref(cp), nx, ny, prec_code, ctypes.c_void_p(bufs[0].data_ptr()),
                                 ctypes.c_void_p(bufs[1].data_ptr()), ctypes.c_void_p(outs[0].data_ptr()),
