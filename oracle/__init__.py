@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-GEOMETRY = {"periodic": 0, "channel": 1, "walls": 2}
+GEOMETRY = {"periodic": 0, "channel": 1, "walls": 2, "pool": 3}
 DIAG_NAMES = ("step", "mass", "energy", "rho_avg", "dp", "dtstar", "flux_in", "flux_out", "source",
               "vapor_area", "wall_vapor", "heater_vapor", "zone_vapor")
 

@@ -239,15 +239,17 @@ static double equilibrium(int i, double m, double ux, double uy) {
  * Lattice sites.  site() maps a lattice site to the fluid node whose values it
  * carries, or reports a solid node.  Channel walls are the rows y = -1 and
  * y = ny; the open ends carry zero-gradient ghost columns x = -1 and x = nx
- * that repeat the first and last fluid column.
+ * that repeat the first and last fluid column.  The pool's open top carries a
+ * zero-gradient ghost row y = ny that repeats row ny - 1.
  * ------------------------------------------------------------------------- */
 static int site(const orc_lattice* L, const orc_params* P, int x, int y, size_t* idx) {
   if (P->geometry == ORC_PERIODIC) {
     x = wrap(x, L->nx);
     y = wrap(y, L->ny);
   } else {
+    if (P->geometry == ORC_POOL && y >= L->ny) y = L->ny - 1;
     if (y < 0 || y >= L->ny) return 0;
-    if (P->geometry == ORC_WALLS) {
+    if (P->geometry == ORC_WALLS || P->geometry == ORC_POOL) {
       x = wrap(x, L->nx);
     } else {
       if (x < 0) x = 0;
@@ -266,7 +268,7 @@ static int heater_on(const orc_params* P, int64_t step) {
  * superheated once switched on; every other wall point is at T_in. */
 static double wall_T(const orc_lattice* L, const orc_params* P, int sx, int sy, int64_t step) {
   double Tc = orc_Tc(P);
-  if (P->geometry == ORC_WALLS) sx = wrap(sx, L->nx);
+  if (P->geometry == ORC_WALLS || P->geometry == ORC_POOL) sx = wrap(sx, L->nx);
   if (sy < 0 && heater_on(P, step) && sx >= P->heater_x0 && sx < P->heater_x0 + P->heater_len)
     return (P->Tin_R + P->dTheat_R) * Tc;
   return P->Tin_R * Tc;
@@ -480,6 +482,33 @@ static void outlet_node(orc_lattice* L, const orc_params* P, int y) {
   }
 }
 
+/* Pool top y = ny-1 (free surface of Sec. 2.D, a constant-pressure boundary): Zou-He
+ * with rho = rho_out and u_x = 0 for the three populations streaming would bring from
+ * above (c_y = -1), and zero temperature gradient (all nine g of the row below). */
+static void top_node(orc_lattice* L, const orc_params* P, int x) {
+  const int y = L->ny - 1;
+  const double rho = P->rho_out;
+  double Kr = 0, Ky = 0, Kx = 0;
+  for (int i = 0; i < 9; ++i) {
+    if (CY[i] == -1) continue;
+    double fi = L->fnew[pid(L, i, x, y)];
+    Kr += fi;
+    Kx += fi * CX[i];
+    Ky += fi * CY[i];
+  }
+  /* unknowns 4, 7, 8 carry c_y = -1: sum f = rho and sum f c_y = rho u_y give u_y */
+  double u = (Ky - (rho - Kr)) / rho;
+  double f4 = L->fnew[pid(L, 2, x, y)] - (equilibrium(2, rho, 0.0, u) - equilibrium(4, rho, 0.0, u));
+  /* remaining two from sum f c_y = rho u_y and sum f c_x = 0 */
+  double f7 = 0.5 * (Ky - rho * u - f4 + Kx); /* c_7 = (-1, -1) */
+  double f8 = 0.5 * (Ky - rho * u - f4 - Kx); /* c_8 = (1, -1) */
+  L->fnew[pid(L, 4, x, y)] = f4;
+  L->fnew[pid(L, 7, x, y)] = f7;
+  L->fnew[pid(L, 8, x, y)] = f8;
+  if (P->thermal)
+    for (int i = 0; i < 9; ++i) L->gnew[pid(L, i, x, y)] = L->gnew[pid(L, i, x, y - 1)];
+}
+
 static int one_step(orc_lattice* L, const orc_params* P) {
   const int nx = L->nx, ny = L->ny;
   const size_t n = nodes(L);
@@ -514,10 +543,12 @@ static int one_step(orc_lattice* L, const orc_params* P) {
         /* second-order central differences; on a row next to a wall the wall-normal
          * derivative is the one-sided difference over the two fluid rows */
         double dyu = 0.5 * (uyp - uym);
-        if (P->geometry != ORC_PERIODIC && (y == 0 || y == ny - 1)) {
+        const int wall_row = P->geometry != ORC_PERIODIC &&
+                             (y == 0 || (y == ny - 1 && P->geometry != ORC_POOL)); /* pool top: open */
+        if (wall_row) {
           double uyc;
           uact_at(L, P, x, y, &t, &uyc);
-          if (ny == 1) dyu = 0.0;
+          if (ny == 1 && P->geometry != ORC_POOL) dyu = 0.0;
           else if (y == 0) dyu = uyp - uyc;
           else dyu = uyc - uym;
         }
@@ -600,13 +631,16 @@ static int one_step(orc_lattice* L, const orc_params* P) {
         if (P->geometry == ORC_PERIODIC) {
           sx = wrap(sx, nx);
           sy = wrap(sy, ny);
+        } else if (P->geometry == ORC_POOL && sy >= ny) {
+          L->unknown[dst] = 1; /* link from above the open top: set by top_node */
+          continue;
         } else if (sy < 0 || sy >= ny) {
           /* link from a wall row: halfway bounce-back for f, anti-bounce-back for g */
           L->fnew[dst] = L->fpost[pid(L, OPP[i], x, y)];
           if (P->thermal)
             L->gnew[dst] = -L->gpost[pid(L, OPP[i], x, y)] + 2.0 * WT[i] * wall_T(L, P, sx, sy, L->step);
           continue;
-        } else if (P->geometry == ORC_WALLS) {
+        } else if (P->geometry == ORC_WALLS || P->geometry == ORC_POOL) {
           sx = wrap(sx, nx);
         } else if (sx < 0 || sx >= nx) {
           L->unknown[dst] = 1; /* set by the inlet/outlet conditions below */
@@ -619,6 +653,8 @@ static int one_step(orc_lattice* L, const orc_params* P) {
     for (int y = 0; y < ny; ++y) inlet_node(L, P, y);
     for (int y = 0; y < ny; ++y) outlet_node(L, P, y);
   }
+  if (P->geometry == ORC_POOL)
+    for (int x = 0; x < nx; ++x) top_node(L, P, x);
 
   double* t = L->f; L->f = L->fnew; L->fnew = t;
   t = L->g; L->g = L->gnew; L->gnew = t;
@@ -630,7 +666,8 @@ static int one_step(orc_lattice* L, const orc_params* P) {
 static int check_geometry(const orc_lattice* L, const orc_params* P) {
   if (P->geometry == ORC_CHANNEL && (L->nx < 3 || L->ny < 2)) return ORC_BAD_ARG;
   if (P->geometry == ORC_WALLS && L->ny < 2) return ORC_BAD_ARG;
-  if (P->geometry < 0 || P->geometry > 2) return ORC_BAD_ARG;
+  if (P->geometry == ORC_POOL && L->ny < 3) return ORC_BAD_ARG;
+  if (P->geometry < 0 || P->geometry > 3) return ORC_BAD_ARG;
   return ORC_OK;
 }
 

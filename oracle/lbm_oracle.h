@@ -22,7 +22,8 @@
 extern "C" {
 #endif
 
-enum { ORC_PERIODIC = 0, ORC_CHANNEL = 1, ORC_WALLS = 2 };
+enum { ORC_PERIODIC = 0, ORC_CHANNEL = 1, ORC_WALLS = 2,
+       ORC_POOL = 3 /* pool boiling (Sec. 2.D): periodic x, bottom wall, pressure top (rho_out) */ };
 
 enum {
   ORC_OK = 0,
@@ -31,7 +32,8 @@ enum {
 };
 
 typedef struct orc_params {
-  int32_t geometry;   /* ORC_PERIODIC, ORC_CHANNEL (inlet/outlet + walls), ORC_WALLS (walls, periodic x) */
+  int32_t geometry;   /* ORC_PERIODIC, ORC_CHANNEL (inlet/outlet + walls), ORC_WALLS (walls, periodic x),
+                         ORC_POOL (bottom wall, periodic x, constant-pressure top) */
   int32_t thermal;    /* 1: evolve g (Eq. 16); 0: T frozen at T0 */
   int32_t multiphase; /* 1: Shan-Chen + wetting forces (Eqs. 9, 15); 0: single-phase, p = rho/3 */
   double tau_f, tau_g;

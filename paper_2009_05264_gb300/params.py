@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import math
 
-GEOMETRY = {"periodic": 0, "channel": 1, "walls": 2}
+GEOMETRY = {"periodic": 0, "channel": 1, "walls": 2, "pool": 3}
 
 
 def default_params(**overrides) -> dict:

@@ -405,6 +405,47 @@ def test_bubble_rises_under_buoyancy():
     assert y1 > y0 + 1.5
 
 
+def test_pool_top_is_a_constant_pressure_surface():
+    """Pool boiling domain (Sec. 2.D): periodic sides, heated bottom wall, and a top read
+    as a free surface, i.e. a constant-pressure boundary: after every step the top row
+    has rho = rho_out and no tangential momentum (Zou-He), and the temperature of the row
+    below (zero gradient)."""
+    nx, ny = 24, 12
+    p = prm(nx, geometry="pool", thermal=1, g_a=1e-4, heater_x0=9, heater_len=5, heat_on_step=0, dTheat_R=0.15,
+            rho_out=5.9)
+    T = 0.9 * oracle.Tc(p)
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(*I.smooth_random(nx, ny, 5.9, T, seed=3, drho=0.01, du=0.01, dT=0.01))
+    for _ in range(3):
+        assert O.step(5) == 0
+        f, g = O.populations()
+        np.testing.assert_allclose(f[:, -1, :].sum(axis=0), 5.9, rtol=1e-14)
+        np.testing.assert_allclose((f[:, -1, :] * CX[:, None]).sum(axis=0), 0.0, atol=1e-13)
+        np.testing.assert_array_equal(g[:, -1, :], g[:, -2, :])
+    assert np.ptp(g[:, -2, :].sum(axis=0)) > 0  # the temperature is not trivially uniform
+
+
+def test_pool_bubble_is_lifted_by_buoyancy():
+    """Eq. 14 in the pool: with gravity the vapour moves up; without, it does not.
+    (An unheated bubble in liquid held at the saturation pressure is a critical nucleus and
+    condenses over ~10^3 steps, so the test compares early rise velocities.)"""
+    nx, ny = 48, 80
+    rise = {}
+    for ga in (0.0, 1e-4):
+        p = prm(nx, geometry="pool", thermal=0, g_a=ga, heater_len=0)
+        T = 0.9 * oracle.Tc(p)
+        rv, rl, _ = oracle.maxwell(p, T)
+        p["rho_out"] = rl
+        O = oracle.Oracle(nx, ny, p)
+        O.init_fields(*I.disk(nx, ny, 14, rv, rl, T, cy=30.0))
+        assert O.step(150) == 0
+        F = O.fields()
+        vap = F["rho"] < 0.5 * (rl + rv)
+        assert vap.sum() > 400
+        rise[ga] = F["uy"][vap].mean()
+    assert abs(rise[0.0]) < 0.005 and rise[1e-4] > rise[0.0] + 0.02
+
+
 @pytest.mark.slow
 def test_contact_angle_decreases_with_wall_density():
     """Sec. 3.E, Fig. 15: a false wall density nearer the liquid value wets more
