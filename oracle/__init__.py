@@ -49,6 +49,8 @@ class OrcParams(ctypes.Structure):
         ("heater_len", ctypes.c_int32),
         ("heat_on_step", ctypes.c_int64),
         ("rho_vapor", ctypes.c_double),
+        ("source_model", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
     ]
 
 

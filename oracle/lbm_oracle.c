@@ -11,7 +11,8 @@
  *   3. body force         Shan-Chen (Eqs. 9-10), wetting (Eq. 15), buoyancy (Eq. 14)
  *   4. velocities         du = F/rho (Eq. 5), u_act = u_eq + F/(2 rho) (Eq. 7)
  *   5. f collision        BGK (Eq. 2) toward f^eq (Eq. 3) plus exact-difference forcing (Eq. 5)
- *   6. g collision        BGK toward g^eq(T, u_act) (Eq. 18) plus source phi (second Eq. 19)
+ *   6. g collision        BGK toward g^eq(T, u_act) (Eq. 18) plus source phi (second Eq. 19, or the
+ *                         first with rho^n - rho^(n-1) for its temporal density gradient)
  *   7. diagnostics        mass, energy, domain-mean density for the next step's buoyancy;
  *                         vapour area, its footprint on the bottom wall and over the heater,
  *                         and the vapour in the columns around the heater
@@ -56,6 +57,7 @@ struct orc_lattice {
   double* f; /* post-stream f^n */
   double* g; /* post-stream g^n */
   double rho_avg_prev;
+  double* rho_prev; /* rho^(n-1) per node (the Hazi-Markus source's time derivative) */
   int64_t step;
   double diag[ORC_D_COUNT];
   /* per-node work arrays of one step */
@@ -86,7 +88,7 @@ orc_lattice* orc_create(int32_t nx, int32_t ny) {
   L->gnew = calloc(9 * n, sizeof(double));
   L->unknown = calloc(9 * n, 1);
   double** scalars[] = {&L->rho, &L->ux, &L->uy, &L->T, &L->psi, &L->dpdT,
-                        &L->Fx,  &L->Fy, &L->uax, &L->uay, &L->phi};
+                        &L->Fx,  &L->Fy, &L->uax, &L->uay, &L->phi, &L->rho_prev};
   int ok = L->f && L->g && L->fpost && L->gpost && L->fnew && L->gnew && L->unknown;
   for (size_t k = 0; k < sizeof(scalars) / sizeof(scalars[0]); ++k) {
     *scalars[k] = calloc(n, sizeof(double));
@@ -104,7 +106,7 @@ void orc_destroy(orc_lattice* L) {
   free(L->f); free(L->g); free(L->fpost); free(L->gpost); free(L->fnew); free(L->gnew);
   free(L->unknown);
   free(L->rho); free(L->ux); free(L->uy); free(L->T); free(L->psi); free(L->dpdT);
-  free(L->Fx); free(L->Fy); free(L->uax); free(L->uay); free(L->phi);
+  free(L->Fx); free(L->Fy); free(L->uax); free(L->uay); free(L->phi); free(L->rho_prev);
   free(L);
 }
 
@@ -554,7 +556,15 @@ static int one_step(orc_lattice* L, const orc_params* P) {
         }
         double divu = 0.5 * (uxp - uxm) + dyu;
         double T = L->T[k];
-        double phi = T * (1.0 - L->dpdT[k] / (L->rho[k] * P->c_v)) * divu;
+        double phi;
+        if (P->source_model == 1) {
+          /* first Eq. 19 (Hazi-Markus): T/(rho^2 c_v) (dp/dT)_rho drho/dt + T div u, the
+           * temporal density gradient by the two-level difference rho^n - rho^(n-1) */
+          double rho = L->rho[k];
+          phi = T / (rho * rho * P->c_v) * L->dpdT[k] * (rho - L->rho_prev[k]) + T * divu;
+        } else {
+          phi = T * (1.0 - L->dpdT[k] / (L->rho[k] * P->c_v)) * divu;
+        }
         L->phi[k] = phi;
         for (int i = 0; i < 9; ++i) {
           double gi = L->g[pid(L, i, x, y)];
@@ -620,6 +630,7 @@ static int one_step(orc_lattice* L, const orc_params* P) {
   L->diag[ORC_D_WALL_VAPOR] = wall;
   L->diag[ORC_D_HEATER_VAPOR] = heat;
   L->diag[ORC_D_ZONE_VAPOR] = zone;
+  memcpy(L->rho_prev, L->rho, n * sizeof(double)); /* rho^n becomes the next step's rho^(n-1) */
 
   /* Streaming (Eqs. 1, 16) with the wall rules; open-end unknowns marked */
   memset(L->unknown, 0, 9 * n);
@@ -696,6 +707,7 @@ int orc_init_fields(orc_lattice* L, const orc_params* P, const double* rho, cons
       mass += rho[k];
     }
   L->rho_avg_prev = mass / (double)n;
+  memcpy(L->rho_prev, rho, n * sizeof(double)); /* no density change before the first step */
   L->step = 0;
   memset(L->diag, 0, sizeof(L->diag));
   return ORC_OK;
@@ -709,6 +721,11 @@ int orc_set_populations(orc_lattice* L, const double* f, const double* g, int64_
   if (g) memcpy(L->g, g, 9 * n * sizeof(double));
   L->step = step;
   L->rho_avg_prev = rho_avg_prev;
+  for (size_t k = 0; k < n; ++k) { /* injected state: no density change before its first step */
+    double r = 0.0;
+    for (int i = 0; i < 9; ++i) r += L->f[(size_t)i * n + k];
+    L->rho_prev[k] = r;
+  }
   return ORC_OK;
 }
 

@@ -43,6 +43,8 @@ typedef struct orc_params {
   int32_t heater_x0, heater_len;
   int64_t heat_on_step;
   double rho_vapor;   /* density below which a node counts as vapour (bubble diagnostics) */
+  int32_t source_model; /* energy source: 0 = Gong-Cheng (second Eq. 19), 1 = Hazi-Markus (first Eq. 19) */
+  int32_t reserved0;
 } orc_params;
 
 /* Diagnostics of one step, computed from that step's moments. */

@@ -181,11 +181,12 @@ def test_mass_and_momentum_conservation_periodic():
     assert d["mass"] == pytest.approx(m0, rel=1e-13)
 
 
-def test_energy_budget_equals_source():
+@pytest.mark.parametrize("source_model", [0, 1])
+def test_energy_budget_equals_source(source_model):
     """Eq. 16 conserves sum g except for the source: in a periodic domain
-    sum T^{n+1} - sum T^n = sum phi^n (second Eq. 19)."""
+    sum T^{n+1} - sum T^n = sum phi^n (either Eq. 19)."""
     nx, ny = 32, 24
-    p = prm(nx, geometry="periodic", thermal=1, g_a=0.0)
+    p = prm(nx, geometry="periodic", thermal=1, g_a=0.0, source_model=source_model)
     T = 0.9 * oracle.Tc(p)
     O = oracle.Oracle(nx, ny, p)
     O.init_fields(*I.smooth_random(nx, ny, 5.5, T, seed=7, drho=0.02, du=0.02, dT=0.01))
@@ -196,6 +197,52 @@ def test_energy_budget_equals_source():
         e1 = O.last_diag()
         assert abs(e1["energy"] - e0["energy"] - e0["source"]) < 1e-13 * e0["energy"]
     assert abs(e0["source"]) > 1e-9  # the budget test is not vacuous
+
+
+def test_hazi_markus_source_reduces_to_t_div_u_without_density_change():
+    """First Eq. 19: phi = T/(rho^2 c_v) (dp/dT)_rho drho/dt + T div u.  On the first step
+    after a state is injected rho^(n-1) = rho^n, so phi = T div u, which the second Eq. 19
+    also gives when c_v -> infinity; once the density moves the two differ."""
+    nx, ny = 30, 20
+    fields = None
+    out = {}
+    for name, kw in (("hm", dict(source_model=1)), ("gc_inf", dict(source_model=0, c_v=1e300))):
+        p = prm(nx, geometry="periodic", thermal=1, g_a=0.0, **kw)
+        T = 0.9 * oracle.Tc(p)
+        fields = I.smooth_random(nx, ny, 5.5, T, seed=21, drho=0.02, du=0.02, dT=0.01)
+        O = oracle.Oracle(nx, ny, p)
+        O.init_fields(*fields)
+        assert O.step(1) == 0
+        out[name] = (O.last_diag()["source"], O.populations())
+        assert O.step(1) == 0
+        out[name + "2"] = O.last_diag()["source"]
+    # (rho^0 = sum f^eq(rho) equals the input density only to rounding, ~1e-16)
+    assert out["hm"][0] == pytest.approx(out["gc_inf"][0], rel=1e-10)
+    np.testing.assert_allclose(out["hm"][1][1], out["gc_inf"][1][1], rtol=1e-13, atol=1e-17)
+    assert abs(out["hm2"] - out["gc_inf2"]) > 1e-6 * abs(out["gc_inf2"])  # drho/dt now acts
+
+
+def test_both_sources_give_the_same_compression_heating_in_a_sound_wave():
+    """The two Eq. 19 forms are one energy equation (with continuity, drho/dt = -rho div u
+    to first order in a small-amplitude wave, where u . grad rho is second order): in a
+    standing sound wave they heat and cool the liquid alike, and far more than T div u
+    alone would."""
+    nx, ny = 64, 4
+    res = {}
+    for name, kw in (("gc", dict(source_model=0)), ("hm", dict(source_model=1)),
+                     ("no_work", dict(source_model=0, c_v=1e300))):
+        p = prm(nx, geometry="periodic", thermal=1, g_a=0.0, **kw)
+        T0 = 0.9 * oracle.Tc(p)
+        x = np.arange(nx)[None, :] * np.ones((ny, 1))
+        rho = 5.5 * (1 + 0.002 * np.sin(2 * np.pi * x / nx))
+        O = oracle.Oracle(nx, ny, p)
+        O.init_fields(rho, np.zeros_like(rho), np.zeros_like(rho), np.full_like(rho, T0))
+        assert O.step(80) == 0
+        res[name] = O.fields()["T"][0] - T0
+    gc, hm = res["gc"], res["hm"]
+    assert np.corrcoef(gc, hm)[0, 1] > 0.999
+    assert np.linalg.norm(hm - gc) < 0.05 * np.linalg.norm(gc)
+    assert np.abs(gc).max() > 10 * np.abs(res["no_work"]).max()
 
 
 def test_poiseuille_profile():
