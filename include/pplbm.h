@@ -54,7 +54,10 @@ typedef enum { LBM_FP32 = 0, LBM_FP64 = 1 } lbm_precision;
 enum {
   LBM_GEOM_PERIODIC = 0, /* periodic in x and y (static droplet / bubble tests) */
   LBM_GEOM_CHANNEL = 1,  /* Sec. 2.C: velocity inlet x = 0, pressure outlet x = nx-1, walls */
-  LBM_GEOM_WALLS = 2     /* walls at y = -1 and y = ny, periodic in x */
+  LBM_GEOM_WALLS = 2,    /* walls at y = -1 and y = ny, periodic in x */
+  LBM_GEOM_POOL = 3      /* pool boiling (Sec. 2.D): periodic in x, bottom wall (heater) at y = -1, and a
+                            free-surface top read as a constant-pressure boundary: Zou-He rho = rho_out,
+                            u_x = 0 on row ny-1, zero temperature gradient; needs ny >= 3 */
 };
 
 enum { LBM_INIT_UNIFORM = 0, LBM_INIT_DISK = 1 };
@@ -69,7 +72,8 @@ enum {
   LBM_D_DTSTAR,      /* (T_wall - T_next_to_heater)/(T_wall - T_bulk) (Sec. 3.B, Fig. 12c); 0 if heater off */
   LBM_D_FLUX_IN,     /* sum over y of rho * u_act,x at x = 0 */
   LBM_D_FLUX_OUT,    /* sum over y of rho * u_act,x at x = nx-1 */
-  LBM_D_VAPOR_AREA,  /* nodes with rho < rho_vapor: bubble area (Sec. 3.A, Fig. 8) */
+  LBM_D_VAPOR_AREA,  /* nodes with rho < rho_vapor: bubble area (Sec. 3.A, Fig. 8); this and the next
+                        three records need params.bubble_stats = 1 */
   LBM_D_WALL_VAPOR,  /* of those, nodes on the row next to the bottom wall: the vapour footprint,
                         i.e. the contact-line extent in 2D (Sec. 3.E, Fig. 17) */
   LBM_D_HEATER_VAPOR,/* of those, nodes above heater sites: non-zero while a bubble sits on the heater */
@@ -98,7 +102,7 @@ typedef struct lbm_params {
   double Tin_R;       /* inlet and wall temperature / Tc: 0.9 */
   double dTheat_R;    /* heater superheat / Tc: 0.3 (Sec. 3.A) */
   double u_in;        /* inlet velocity (x) */
-  double rho_out;     /* outlet density */
+  double rho_out;     /* outlet density (channel), top density (pool) */
   double rho_w;       /* false wall density of Eq. 15 (sets the contact angle): 5.95 */
   double G_wet;       /* wetting strength of Eq. 15: 9 (1 + beta) G, so that a wall whose false density
                          equals the fluid's exerts no net force on uniform fluid under the beta-mixed
@@ -117,7 +121,15 @@ typedef struct lbm_params {
   uint64_t seed;
   double rho_vapor;   /* bubble diagnostics count a node as vapour when rho < rho_vapor: 3.2
                          (about the midpoint of the coexisting densities 0.59 and 5.88 at 0.9 Tc) */
+  int32_t source_model; /* energy source of Eq. 16: LBM_SOURCE_GONG_CHENG (second Eq. 19, the paper's
+                           choice, default) or LBM_SOURCE_HAZI_MARKUS (first Eq. 19, with the temporal
+                           density gradient rho^n - rho^(n-1); the context keeps rho^(n-1) per node,
+                           equal to the initial or injected density before the first step) */
+  int32_t bubble_stats; /* 1: count vapour nodes every step (the LBM_D_*_VAPOR records); 0 (default):
+                           those records stay 0 and the step runs its leaner form */
 } lbm_params;
+
+enum { LBM_SOURCE_GONG_CHENG = 0, LBM_SOURCE_HAZI_MARKUS = 1 };
 
 /* Fill *p with the defaults listed above (and p->size). */
 void lbm_default_params(lbm_params* p);
@@ -189,9 +201,10 @@ lbm_status lbm_read_diagnostics(lbm_ctx* ctx, double* out, size_t n);
  * steps back) or count < 0.  Waits for the context's stream. */
 lbm_status lbm_read_diagnostics_range(lbm_ctx* ctx, int64_t first, int64_t count, double* out);
 
-/* Checkpoint / resume: raw state (populations in storage precision, step,
- * buoyancy mean, parameters).  lbm_state_bytes() gives the buffer size; resume
- * is bitwise. */
+/* Checkpoint / resume: raw state (a header with the step, buoyancy mean and
+ * parameters; then f and g as 9 planes of ny x nx each in storage precision; then the
+ * per-node density history of the Hazi-Markus source, 1 plane).  lbm_state_bytes()
+ * gives the buffer size; resume is bitwise. */
 size_t lbm_state_bytes(const lbm_ctx* ctx);
 lbm_status lbm_save_state(lbm_ctx* ctx, void* host_buf, size_t bytes);
 lbm_status lbm_load_state(lbm_ctx* ctx, const void* host_buf, size_t bytes);

@@ -89,7 +89,8 @@ def fit_sine(t: np.ndarray, y: np.ndarray) -> dict:
 
 def record(lattice, steps: int, chunk: int = 1000) -> np.ndarray:
     """Advance a lattice by `steps` steps and return every step's diagnostics record
-    (read back every `chunk` <= 1024 steps, before the ring overwrites them)."""
+    (read back every `chunk` <= 1024 steps, before the ring overwrites them).  The
+    vapour columns are counted only for lattices created with bubble_stats = 1."""
     if not 1 <= chunk <= 1024:
         raise ValueError("chunk must be within the 1024-record ring")
     rows = []

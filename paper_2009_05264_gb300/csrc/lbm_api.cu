@@ -15,17 +15,17 @@
 #include "pplbm.h"
 
 namespace pplbm {
-cudaError_t launch_lbm_f32(int, int, int, int, const Inst*, const Tile*, int, cudaStream_t);
-cudaError_t launch_lbm_f64(int, int, int, const Inst*, const Tile*, int, cudaStream_t);
+cudaError_t launch_lbm_f32(int, int, int, int, bool, const Inst*, const Tile*, int, cudaStream_t);
+cudaError_t launch_lbm_f64(int, int, int, bool, const Inst*, const Tile*, int, cudaStream_t);
 cudaError_t launch_init_from_fields_f32(const Inst*, int, int, const double*, int, cudaStream_t);
 cudaError_t launch_init_from_fields_f64(const Inst*, int, int, const double*, int, cudaStream_t);
 cudaError_t launch_init_builtin_f32(const Inst*, int, int, InitSpec, cudaStream_t);
 cudaError_t launch_init_builtin_f64(const Inst*, int, int, InitSpec, cudaStream_t);
 
-cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, int kernel, const Inst* d_inst, const Tile* d_tiles,
-                       int ntiles, cudaStream_t s) {
-  return fp64 ? launch_lbm_f64(thermal, cols, mode, d_inst, d_tiles, ntiles, s)
-              : launch_lbm_f32(thermal, cols, mode, kernel, d_inst, d_tiles, ntiles, s);
+cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, int kernel, bool full, const Inst* d_inst,
+                       const Tile* d_tiles, int ntiles, cudaStream_t s) {
+  return fp64 ? launch_lbm_f64(thermal, cols, mode, full, d_inst, d_tiles, ntiles, s)
+              : launch_lbm_f32(thermal, cols, mode, kernel, full, d_inst, d_tiles, ntiles, s);
 }
 cudaError_t launch_init_from_fields(int fp64, const Inst* d_inst, int nx, int ny, const double* d_fields,
                                     int has_T, cudaStream_t s) {
@@ -40,7 +40,12 @@ bool cols_supported(int cols) { return cols == 64 || cols == 128 || cols == 256;
 const char* check_params(int nx, int ny, const lbm_params* p) {
   if (!p) return "params is NULL";
   if (p->size != sizeof(lbm_params)) return "params.size != sizeof(lbm_params)";
-  if (p->geometry < 0 || p->geometry > 2) return "geometry must be 0, 1 or 2";
+  if (p->geometry < 0 || p->geometry > 3) return "geometry must be 0, 1, 2 or 3";
+  if (p->source_model != LBM_SOURCE_GONG_CHENG && p->source_model != LBM_SOURCE_HAZI_MARKUS)
+    return "source_model must be LBM_SOURCE_GONG_CHENG or LBM_SOURCE_HAZI_MARKUS";
+  if (p->bubble_stats != 0 && p->bubble_stats != 1) return "bubble_stats must be 0 or 1";
+  if (p->geometry == LBM_GEOM_POOL && ny < 3) return "pool geometry needs ny >= 3";
+  if (p->geometry == LBM_GEOM_POOL && !(p->rho_out > 0)) return "pool geometry needs rho_out > 0";
   if (p->geometry == LBM_GEOM_CHANNEL && (nx < 3 || ny < 2)) return "channel needs nx >= 3 and ny >= 2";
   if (p->geometry == LBM_GEOM_WALLS && ny < 2) return "walls geometry needs ny >= 2";
   if (p->thermal != 0 && p->thermal != 1) return "thermal must be 0 or 1";
@@ -134,6 +139,8 @@ const char* fill_inst(Inst& I, const lbm_params* p, int nx, int ny, int pitch, l
   I.heater_len = p->heater_len;
   I.heat_on_step = p->heat_on_step;
   I.rho_vapor = p->rho_vapor;
+  I.source_model = p->source_model;
+  I.bubble_stats = p->bubble_stats;
   return nullptr;
 }
 
@@ -186,7 +193,8 @@ struct Layout {
   long long plane;
   size_t pop_bytes;  // one 9-plane buffer
   int max_tiles;
-  size_t off_f[2], off_g[2], off_inst, off_state, off_part, off_ring, off_tiles_step, off_tiles_aux, total;
+  size_t off_f[2], off_g[2], off_rho_prev, off_inst, off_state, off_part, off_ring, off_tiles_step, off_tiles_aux,
+      total;
 };
 
 Layout make_layout(int nx, int ny, lbm_precision prec) {
@@ -201,6 +209,7 @@ Layout make_layout(int nx, int ny, lbm_precision prec) {
   size_t off = 0;
   for (int b = 0; b < 2; ++b) { L.off_f[b] = off; off += L.pop_bytes; }
   for (int b = 0; b < 2; ++b) { L.off_g[b] = off; off += L.pop_bytes; }
+  L.off_rho_prev = off; off += align_up((size_t)L.plane * elt);
   L.off_inst = off; off += align_up(sizeof(Inst));
   L.off_state = off; off += align_up(sizeof(InstState));
   L.off_part = off; off += align_up((size_t)L.max_tiles * NPART * sizeof(double));
@@ -329,7 +338,10 @@ lbm_status retile_default(lbm_ctx* c, int cols) {
 
 lbm_status launch(lbm_ctx* c, int mode) {
   const bool step_tiles = mode == MODE_STEP;
-  cudaError_t e = launch_lbm(c->prec == LBM_FP64, c->thermal, step_tiles ? c->cols : kAuxCols, mode, c->kernel, c->d_inst,
+  // the paired kernel has no Hazi-Markus source: such lattices always take the one-column form
+  const int kernel = c->params.source_model == LBM_SOURCE_HAZI_MARKUS ? LBM_KERNEL_SCALAR : c->kernel;
+  cudaError_t e = launch_lbm(c->prec == LBM_FP64, c->thermal, step_tiles ? c->cols : kAuxCols, mode, kernel,
+                             needs_full_step(c->hinst), c->d_inst,
                              step_tiles ? c->d_tiles_step : c->d_tiles_aux,
                              step_tiles ? c->ntiles_step : c->ntiles_aux, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
@@ -347,6 +359,7 @@ lbm_status apply_params(lbm_ctx* c, const lbm_params* p) {
     I.f[b] = c->base + c->L.off_f[b];
     I.g[b] = c->base + c->L.off_g[b];
   }
+  I.rho_prev = c->base + c->L.off_rho_prev;
   I.st = c->d_state;
   I.partials = reinterpret_cast<double*>(c->base + c->L.off_part);
   I.ring = reinterpret_cast<double*>(c->base + c->L.off_ring);
@@ -466,6 +479,8 @@ void lbm_default_params(lbm_params* p) {
   p->perturb_amp = 0.0;
   p->seed = 0;
   p->rho_vapor = 3.2;
+  p->source_model = LBM_SOURCE_GONG_CHENG;
+  p->bubble_stats = 0;
 }
 
 size_t lbm_required_bytes(int32_t nx, int32_t ny, lbm_precision prec) {
@@ -653,7 +668,13 @@ lbm_status lbm_set_populations(lbm_ctx* c, const double* f, const double* gin, s
   reset_state_mirror(c, step, 1, need_mean ? 0.0 : rho_avg_prev);
   lbm_status s = upload_state(c);
   if (s != LBM_OK) return s;
-  if (need_mean && (s = launch(c, MODE_MOMENTS)) != LBM_OK) return s;
+  // the moments pass also sets rho^(n-1) of the Hazi-Markus source to the injected density
+  if ((need_mean || c->params.source_model == LBM_SOURCE_HAZI_MARKUS) && (s = launch(c, MODE_MOMENTS)) != LBM_OK)
+    return s;
+  if (!need_mean) {  // the moments pass overwrote the caller's mean: put it back
+    reset_state_mirror(c, step, 1, rho_avg_prev);
+    if ((s = upload_state(c)) != LBM_OK) return s;
+  }
   return fetch_state(c);
 }
 
@@ -682,7 +703,7 @@ struct StateHeader {
 
 size_t lbm_state_bytes(const lbm_ctx* c) {
   if (!c) return 0;
-  return sizeof(StateHeader) + 2 * 9 * (size_t)c->nx * c->ny * elt_size(c);
+  return sizeof(StateHeader) + (2 * 9 + 1) * (size_t)c->nx * c->ny * elt_size(c);
 }
 
 lbm_status lbm_save_state(lbm_ctx* c, void* host_buf, size_t bytes) {
@@ -712,6 +733,9 @@ lbm_status lbm_save_state(lbm_ctx* c, void* host_buf, size_t bytes) {
                                   9 * (size_t)c->ny, cudaMemcpyDeviceToHost, c->stream));
     dst += 9 * (size_t)c->nx * c->ny * elt;
   }
+  // rho^(n-1) of the Hazi-Markus source (kept in every state: resume is bitwise either way)
+  LBM_CUDA(c, cudaMemcpy2DAsync(dst, c->nx * elt, c->base + c->L.off_rho_prev, c->L.pitch * elt, c->nx * elt,
+                                (size_t)c->ny, cudaMemcpyDeviceToHost, c->stream));
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
   return LBM_OK;
 }
@@ -740,6 +764,8 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t bytes) {
                                   9 * (size_t)c->ny, cudaMemcpyHostToDevice, c->stream));
     src += 9 * (size_t)c->nx * c->ny * elt;
   }
+  LBM_CUDA(c, cudaMemcpy2DAsync(c->base + c->L.off_rho_prev, c->L.pitch * elt, src, c->nx * elt, c->nx * elt,
+                                (size_t)c->ny, cudaMemcpyHostToDevice, c->stream));
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
   c->step_host = h.state.step;
   return LBM_OK;

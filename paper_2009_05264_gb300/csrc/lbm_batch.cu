@@ -41,6 +41,8 @@ struct lbm_batch {
   std::vector<Member> slots;  // empty ctx = free slot
   int cols = 128, rows = 0;   // rows 0: each member's default band height
   int kernel = LBM_KERNEL_AUTO;
+  bool any_hazi = false;  // a member uses the Hazi-Markus source: one-column kernel for the batch
+  bool any_full = false;  // a member needs the step's full form (pool, Hazi-Markus, bubble statistics)
   // device tables of the current membership
   Inst* d_insts = nullptr;
   Tile* d_tiles = nullptr;
@@ -84,6 +86,8 @@ int member_rows(const lbm_batch* b, int nx, int ny, long long slots, double shar
 lbm_status rebuild(lbm_batch* b) {
   std::vector<Inst> insts;
   std::vector<Tile> tiles;
+  bool any_hazi = false;
+  bool any_full = false;
   const int w = b->cols - 8;
   double total = 0.0;
   for (const Member& m : b->slots)
@@ -94,6 +98,8 @@ lbm_status rebuild(lbm_batch* b) {
     const int idx = (int)insts.size();
     insts.push_back(lbm_internal_inst(m.ctx));
     m.gen = lbm_internal_params_gen(m.ctx);
+    if (insts.back().source_model == LBM_SOURCE_HAZI_MARKUS) any_hazi = true;
+    if (needs_full_step(insts.back())) any_full = true;
     const int rows = member_rows(b, m.nx, m.ny, slots, total > 0.0 ? (double)m.nx * m.ny / total : 1.0);
     const int strips = (m.nx + w - 1) / w, bands = (m.ny + rows - 1) / rows;
     const int n = strips * bands;
@@ -136,6 +142,8 @@ lbm_status rebuild(lbm_batch* b) {
   }
   LBM_BCUDA(b, cudaStreamSynchronize(b->stream));
   b->ntiles = (int)tiles.size();
+  b->any_hazi = any_hazi;
+  b->any_full = any_full;
   drop_graph(b);
   b->dirty = false;
   return LBM_OK;
@@ -143,7 +151,7 @@ lbm_status rebuild(lbm_batch* b) {
 
 lbm_status launch_steps(lbm_batch* b, int64_t n) {
   for (int64_t k = 0; k < n; ++k) {
-    LBM_BCUDA(b, launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->kernel, b->d_insts, b->d_tiles, b->ntiles,
+    LBM_BCUDA(b, launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->any_hazi ? LBM_KERNEL_SCALAR : b->kernel, b->any_full, b->d_insts, b->d_tiles, b->ntiles,
                             b->stream));
     ++b->launches;
   }
@@ -155,7 +163,7 @@ lbm_status capture_graph(lbm_batch* b) {
   LBM_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   lbm_status s = LBM_OK;
   for (int k = 0; k < kGraphChunk && s == LBM_OK; ++k) {
-    if (launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->kernel, b->d_insts, b->d_tiles, b->ntiles,
+    if (launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->any_hazi ? LBM_KERNEL_SCALAR : b->kernel, b->any_full, b->d_insts, b->d_tiles, b->ntiles,
                    b->stream) != cudaSuccess)
       s = bfail(b, LBM_ECUDA, "launch during graph capture");
   }

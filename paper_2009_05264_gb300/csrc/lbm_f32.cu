@@ -4,10 +4,10 @@
 
 namespace pplbm {
 
-cudaError_t launch_lbm_f32(int thermal, int cols, int mode, int kernel, const Inst* d_inst, const Tile* d_tiles,
-                          int ntiles, cudaStream_t s) {
+cudaError_t launch_lbm_f32(int thermal, int cols, int mode, int kernel, bool full, const Inst* d_inst,
+                          const Tile* d_tiles, int ntiles, cudaStream_t s) {
   if (mode == MODE_STEP && kernel == LBM_KERNEL_PAIRED) return launch_pair(thermal, cols, d_inst, d_tiles, ntiles, s);
-  return launch_precision<float>(thermal, cols, mode, d_inst, d_tiles, ntiles, s);
+  return launch_precision<float>(thermal, cols, mode, full, d_inst, d_tiles, ntiles, s);
 }
 
 int resident_ctas_f32(int thermal, int cols, int kernel) {

@@ -14,7 +14,7 @@ constexpr int NPART = 9;  // mass, energy, heater row T, inflow, outflow, vapour
 constexpr int NDIAG = 12;  // LBM_D_COUNT
 constexpr int RING = 1024;  // diagnostics records kept per instance
 
-enum : int { GEOM_PERIODIC = 0, GEOM_CHANNEL = 1, GEOM_WALLS = 2 };
+enum : int { GEOM_PERIODIC = 0, GEOM_CHANNEL = 1, GEOM_WALLS = 2, GEOM_POOL = 3 };
 enum : int { MODE_STEP = 0, MODE_FIELDS = 1, MODE_POPS = 2, MODE_MOMENTS = 3 };
 enum : unsigned { STATUS_UNSTABLE = 1u };
 
@@ -51,6 +51,8 @@ struct Inst {
   int heater_x0, heater_len;
   long long heat_on_step;
   double rho_vapor;                 // vapour threshold of the bubble diagnostics
+  int source_model, bubble_stats;   // 0 Gong-Cheng, 1 Hazi-Markus (first Eq. 19); count vapour nodes
+  void* rho_prev;                   // rho^(n-1) - rho_ref per node (storage precision, pitch layout)
   InstState* st;
   double* partials;                 // NPART per tile of this instance
   double* ring;                     // RING records of NDIAG doubles
@@ -66,8 +68,14 @@ struct Tile {
 
 // Launchers (defined per precision).  Tiles must have been built for `cols`.
 // kernel: LBM_KERNEL_AUTO / _SCALAR / _PAIRED (pplbm.h); only the FP32 step has a paired form.
-cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, int kernel, const Inst* d_inst, const Tile* d_tiles,
-                       int ntiles, cudaStream_t s);
+// full: the instances use the pool geometry, the Hazi-Markus source or bubble statistics, which
+// only the step's full form handles (the lean form leaves them out of the hot loop).
+cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, int kernel, bool full, const Inst* d_inst,
+                       const Tile* d_tiles, int ntiles, cudaStream_t s);
+// Whether an instance needs the step's full form.
+inline bool needs_full_step(const Inst& I) {
+  return I.geometry == GEOM_POOL || I.source_model != 0 || I.bubble_stats != 0;
+}
 // f = f^eq(rho,u), g = g^eq(T,u) into buffer 0 from 4 planes of nx*ny doubles (rho, ux, uy, T).
 cudaError_t launch_init_from_fields(int fp64, const Inst* d_inst, int nx, int ny, const double* d_fields,
                                     int has_T, cudaStream_t s);

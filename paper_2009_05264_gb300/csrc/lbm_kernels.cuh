@@ -97,6 +97,30 @@ __device__ __forceinline__ void block_sum(double (&v)[NPART], double (*red)[NPAR
   }
 }
 
+// Sum of the per-tile partials of one instance into tot, each thread taking tiles
+// tid, tid + BLOCK, tid + 2 BLOCK, ... in that order (the order fixes the rounding, so the
+// result is deterministic for a given tiling).  Four tiles' loads are issued before their
+// sums so the last CTA's fold is not one L2 round trip per tile.
+template <int BLOCK>
+__device__ __forceinline__ void fold_partials(const double* __restrict__ partials, int ntiles, double (&tot)[NPART]) {
+  int t = threadIdx.x;
+  for (; t + 3 * BLOCK < ntiles; t += 4 * BLOCK) {
+    double v[4][NPART];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int j = 0; j < NPART; ++j) v[u][j] = __ldcg(partials + (long long)(t + u * BLOCK) * NPART + j);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int j = 0; j < NPART; ++j) tot[j] += v[u][j];
+  }
+  for (; t < ntiles; t += BLOCK) {
+#pragma unroll
+    for (int j = 0; j < NPART; ++j) tot[j] += __ldcg(partials + (long long)t * NPART + j);
+  }
+}
+
 // Reciprocal and reciprocal square root: MUFU approximations (about 2 ulp) in
 // FP32, IEEE operations in FP64 (the FP64 path matches the oracle to round-off).
 __device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
@@ -201,6 +225,7 @@ __device__ __forceinline__ void fill_consts(KConst<Real>& c, const Inst& I, doub
 struct NodeBC {
   bool wlo, whi;  // links with c_y = +1 / -1 come from the bottom / top wall
   bool inl, outl; // velocity inlet (x = 0) / pressure outlet (x = nx - 1)
+  bool top;       // pool top row: links with c_y = -1 come from above the free surface
 };
 
 // Complete the pulled populations of a boundary node in place.  Wall links were
@@ -292,12 +317,32 @@ __device__ __forceinline__ void boundary_fill(Real (&fc)[9], Real (&gc)[9], cons
       }
     }
   }
+  if (nb.top) {
+    // pool top (free surface): Zou-He with rho = rho_out, u_x = 0 for the populations from
+    // above (c_y = -1: 4, 7, 8), then zero temperature gradient: every g of the node below
+    const Real drho_top = C.drho_out;
+    const Real S = fc[0] + fc[1] + fc[3] + Real(2) * (fc[2] + fc[5] + fc[6]);
+    const Real ru = S - drho_top;  // rho_out * u_y
+    const Real h = Real(0.5) * (fc[1] - fc[3]);
+    fc[4] = fc[2] - Real(2.0 / 3.0) * ru;
+    fc[7] = fc[5] + h - ru * Real(1.0 / 6.0);
+    fc[8] = fc[6] - h - ru * Real(1.0 / 6.0);
+    if (THERMAL) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        int sx = xn - lat_cx(i);
+        if (perx) sx = wrap_index(sx, I.nx);
+        gc[i] = ld_ro(Gin + i * plane + (node - pitch) - xn + sx - lat_cy(i) * pitch);
+      }
+    }
+  }
 }
 
 // Macroscopic state of one node (compute precision; deviations from the references).
 template <typename Real>
 struct NodeState {
   Real rho, drho, ux, uy, T, dT, coef;  // coef = T (1 - (dp/dT)_rho / (rho c_v)) of the source
+  Real hmc;                              // Hazi-Markus form: T (dp/dT)_rho / (rho^2 c_v); coef is then T
   Real dpsi;                             // psi - psi_ref (psi itself in FP64)
   Real p;                                // EOS pressure (diagnostics)
   bool bad;                              // outside the EOS domain
@@ -309,8 +354,9 @@ struct NodeState {
 // differences in the force keep their low-order bits.
 template <typename Real, bool THERMAL>
 __device__ __forceinline__ NodeState<Real> node_state(const Real (&fc)[9], const Real (&gc)[9],
-                                                      const KConst<Real>& C, bool multiphase) {
+                                                      const KConst<Real>& C, bool multiphase, bool hazi = false) {
   NodeState<Real> o;
+  o.hmc = Real(0);
   const Real rho_ref = C.rho_ref;
   o.drho = ((fc[0] + fc[1]) + (fc[2] + fc[3])) + ((fc[4] + fc[5]) + (fc[6] + fc[7])) + fc[8];
   o.rho = rho_ref + o.drho;
@@ -376,7 +422,12 @@ __device__ __forceinline__ NodeState<Real> node_state(const Real (&fc)[9], const
   }
   if (THERMAL) {
     bad = bad || !isfinite(o.T);
-    o.coef = o.T * (Real(1) - dpdT * inv_rho * C.inv_cv);
+    if (hazi) {  // first Eq. 19: T div u + T (dp/dT)_rho / (rho^2 c_v) drho/dt
+      o.coef = o.T;
+      o.hmc = o.T * dpdT * inv_rho * inv_rho * C.inv_cv;
+    } else {     // second Eq. 19
+      o.coef = o.T * (Real(1) - dpdT * inv_rho * C.inv_cv);
+    }
   }
   o.bad = bad;
   return o;
@@ -491,7 +542,7 @@ __device__ __forceinline__ void pull_node(Real* f_dst, Real* g_dst, int dstride,
   for (int i = 0; i < 9; ++i) {
     const int cxi = lat_cx(i), cyi = lat_cy(i);
     const bool wall = (cyi == 1 && nb.wlo) || (cyi == -1 && nb.whi);
-    const bool unknown = (cxi == 1 && nb.inl) || (cxi == -1 && nb.outl);
+    const bool unknown = (cxi == 1 && nb.inl) || (cxi == -1 && nb.outl) || (cyi == -1 && nb.top);
     int src;
     int pl = i;
     if (wall) {
@@ -560,7 +611,10 @@ __device__ __forceinline__ void finish_step(const Inst& I, InstState* st, const 
 // with a barrier after each of phase A (pull, moments, EOS), phase B (force,
 // f collision of the row below) and before phase C (g collision two rows below).
 // ---------------------------------------------------------------------------
-template <typename Real, bool THERMAL, int B, int MODE>
+// FULL: the full form, which handles the pool geometry, the Hazi-Markus source and the bubble
+// statistics; the lean form (FULL = false, step mode only) compiles them out of the hot loop and
+// is launched only for instances that use none of them.
+template <typename Real, bool THERMAL, int B, int MODE, bool FULL = true>
 __global__ void __launch_bounds__(B, (sizeof(Real) == 4 ? (B <= 64 ? 10 : (B <= 128 ? 5 : 2))
                                                         : (B <= 64 ? 4 : (B <= 128 ? 2 : 1))))
 lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) {
@@ -597,7 +651,11 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
   const bool perx = sI.geometry != GEOM_CHANNEL;
   const bool pery = sI.geometry == GEOM_PERIODIC;
   const bool channel = sI.geometry == GEOM_CHANNEL;
+  const bool pool = FULL && sI.geometry == GEOM_POOL;
   const bool multiphase = sI.multiphase != 0;
+  const bool hazi = FULL && THERMAL && sI.source_model == 1;
+  const bool bubbles = FULL && sI.bubble_stats != 0;
+  Real* __restrict__ rho_prev = static_cast<Real*>(sI.rho_prev);
   const Real* __restrict__ Fin = static_cast<const Real*>(sI.f[step & 1]);
   const Real* __restrict__ Gin = static_cast<const Real*>(sI.g[step & 1]);
   Real* __restrict__ Fout = static_cast<Real*>(sI.f[(step + 1) & 1]);
@@ -631,7 +689,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
       const int r = tile.y0 - 2 + k;
       if (pery || (r >= 0 && r < ny)) {
         const int rn = pery ? wrap_index(r, ny) : r;
-        const NodeBC nb{!pery && rn == 0, !pery && rn == ny - 1, inl, outl};
+        const NodeBC nb{!pery && rn == 0, !pery && !pool && rn == ny - 1, inl, outl, pool && rn == ny - 1};
         pull_node<Real, THERMAL>(sF + fslot * 9 * NS + s, sG + gslot * 9 * NS + s, NS, Fin, Gin, plane, pitch, xn,
                                  rn, nx, ny, perx, pery, local, nb);
       }
@@ -645,6 +703,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
   // node scalars carried between iterations: row r-1 (f collision), row r-2 (g collision)
   Real rho_p = Real(1), drho_p = Real(0), ux_p = Real(0), uy_p = Real(0), T_p = T0, dT_p = Real(0), coef_p = Real(0);
   Real T_p2 = T0, dT_p2 = Real(0), coef_p2 = Real(0);
+  Real hm_p = Real(0), hm_p2 = Real(0);  // Hazi-Markus source term of rows r-1 and r-2
 
   // ring slots: f and psi/u rings have 3 slots (row index mod 3), g has 4 (mod 4)
   int f_cur = kbeg % F_SLOTS, g_cur = kbeg % G_SLOTS;
@@ -674,8 +733,8 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
         fc[i] = fs[i * NS];
         gc[i] = THERMAL ? gs[i * NS] : Real(0);
       }
-      const NodeBC nb{!pery && rn == 0, !pery && rn == ny - 1, inl, outl};
-      if (!local && (nb.wlo || nb.whi || inl || outl)) {
+      const NodeBC nb{!pery && rn == 0, !pery && !pool && rn == ny - 1, inl, outl, pool && rn == ny - 1};
+      if (!local && (nb.wlo || nb.whi || inl || outl || nb.top)) {
         boundary_fill<Real, THERMAL>(fc, gc, nb, sI, sC, Gin, plane, pitch, rn * pitch + xn, xn, perx, step);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -683,17 +742,26 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
           if (THERMAL) gs[i * NS] = gc[i];
         }
       }
-      ns = node_state<Real, THERMAL>(fc, gc, sC, multiphase);
+      ns = node_state<Real, THERMAL>(fc, gc, sC, multiphase, hazi);
       if (ns.bad) atomicOr(&st->status, STATUS_UNSTABLE);
       sPsi[f_cur * NS + s] = ns.dpsi;
       const bool out_row = r >= tile.y0 && r < tile.y1;
+      const Real hmc = ns.hmc;
+      ns.hmc = Real(0);  // becomes the source term of this node (output nodes of the step only)
+      if (hazi && out_col && out_row) {
+        // temporal density gradient rho^n - rho^(n-1), both as deviations from rho_ref; this
+        // thread owns the node's history (read, then overwritten with rho^n)
+        Real* rp = rho_prev + (rn * pitch + xn);
+        if (MODE == MODE_STEP) ns.hmc = hmc * (ns.drho - *rp);
+        if (MODE == MODE_STEP || MODE == MODE_MOMENTS) *rp = ns.drho;
+      }
       if ((MODE == MODE_STEP || MODE == MODE_MOMENTS) && out_col && out_row) {
         acc_m += ns.drho;
         if (THERMAL) {
           acc_e += ns.dT;
           if (!pery && rn == 0 && xn >= sI.heater_x0 && xn < sI.heater_x0 + sI.heater_len) acc_h += ns.dT;
         }
-        if (ns.drho < sC.drho_vapor) {
+        if (bubbles && ns.drho < sC.drho_vapor) {
           acc_va += 1.0f;
           if (zone_col) acc_zv += 1.0f;
           if (!pery && rn == 0) {
@@ -728,12 +796,13 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
     // STEP needs u_act from row y0 - 1 (divergence at y0); FIELDS only on its output rows
     const int qmin = (MODE == MODE_STEP) ? tile.y0 - 1 : tile.y0;
     if (q >= qmin && f_col && (pery || (q >= 0 && q < ny))) {
-      const bool sol_m = !pery && q == 0;       // row q-1 is the bottom wall
-      const bool sol_p = !pery && q == ny - 1;  // row q+1 is the top wall
+      const bool sol_m = !pery && q == 0;                // row q-1 is the bottom wall
+      const bool sol_p = !pery && !pool && q == ny - 1;  // row q+1 is the top wall
       Real Fx = Real(0), Fy = Real(0);
       if (multiphase) {
         const Real* P0 = sPsi + f_prev * NS;
-        const Real* Pp = sPsi + f_cur * NS;
+        // above the pool's top row: the zero-gradient ghost row repeats row q
+        const Real* Pp = (pool && q == ny - 1) ? P0 : sPsi + f_cur * NS;
         const Real* Pm = sPsi + f_prev2 * NS;
         sc_force<Real>(P0[s], P0[sp], P0[sm], sol_p ? Real(0) : Pp[s], sol_p ? Real(0) : Pp[sp],
                        sol_p ? Real(0) : Pp[sm], sol_m ? Real(0) : Pm[s], sol_m ? Real(0) : Pm[sp],
@@ -771,23 +840,30 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
         // second-order central differences of u_act (ghost copy at open ends); on a row next
         // to a wall the wall-normal derivative is the one-sided difference over the fluid rows
         const Real uxE = sUx[f_prev2 * NS + sp], uxW = sUx[f_prev2 * NS + sm];
-        const Real uyN = sUy[f_prev * NS + s];
+        Real uyN = sUy[f_prev * NS + s];
+        if (pool && q2 == ny - 1) uyN = sUy[f_prev2 * NS + s];  // pool top: the ghost row repeats row q2
         const Real uyS = sUy[f_cur * NS + s];  // slot of row r-3
-        const bool wall_lo = !pery && q2 == 0, wall_hi = !pery && q2 == ny - 1;
+        const bool wall_lo = !pery && q2 == 0, wall_hi = !pery && !pool && q2 == ny - 1;
         Real dyu = Real(0.5) * (uyN - uyS);
         if (wall_lo || wall_hi) {
           const Real uyC = sUy[f_prev2 * NS + s];
           dyu = (wall_lo && wall_hi) ? Real(0) : (wall_lo ? uyN - uyC : uyC - uyS);
         }
         const Real divu = Real(0.5) * (uxE - uxW) + dyu;
+        Real phi = coef_p2 * divu;
+        if (hazi) phi += hm_p2;
         collide_g<Real>(sG + g_prev2 * 9 * NS + s, NS, Gout + (q2 * pitch + xn), plane, T_p2, dT_p2,
-                        sUx[f_prev2 * NS + s], sUy[f_prev2 * NS + s], coef_p2 * divu, sC.omega_g);
+                        sUx[f_prev2 * NS + s], sUy[f_prev2 * NS + s], phi, sC.omega_g);
       }
     }
 
     T_p2 = T_p;
     dT_p2 = dT_p;
     coef_p2 = coef_p;
+    if (hazi) {
+      hm_p2 = hm_p;
+      hm_p = ns.hmc;
+    }
     rho_p = ns.rho;
     drho_p = ns.drho;
     ux_p = ns.ux;
@@ -817,10 +893,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
   if (!sLast) return;
   __threadfence();
   double tot[NPART] = {};
-  for (int t = tid; t < tile.ntiles; t += BLOCK) {
-#pragma unroll
-    for (int j = 0; j < NPART; ++j) tot[j] += __ldcg(sI.partials + (long long)t * NPART + j);
-  }
+  fold_partials<BLOCK>(sI.partials, tile.ntiles, tot);
   __syncthreads();
   block_sum<BLOCK>(tot, sRed);
   if (tid == 0) finish_step<THERMAL, MODE>(sI, st, tot, step);
@@ -839,6 +912,7 @@ __device__ __forceinline__ void write_equilibrium(const Inst& I, long long node,
   Real* F = static_cast<Real*>(I.f[0]);
   Real* Gb = static_cast<Real*>(I.g[0]);
   const Real drho = Real(rho - I.rho_ref), dT = Real(T - I.T_ref);
+  static_cast<Real*>(I.rho_prev)[node] = drho;  // no density change before the first step
   const Real r = Real(rho), t = Real(T), vx = Real(ux), vy = Real(uy);
   const Real usq = vx * vx + vy * vy;
 #pragma unroll
@@ -895,7 +969,7 @@ __global__ void lbm_init_builtin_kernel(const Inst* __restrict__ insts, InitSpec
 // ---------------------------------------------------------------------------
 // Host launchers for one storage precision.
 // ---------------------------------------------------------------------------
-template <typename Real, bool THERMAL, int B, int MODE>
+template <typename Real, bool THERMAL, int B, int MODE, bool FULL>
 cudaError_t launch_one(const Inst* d_inst, const Tile* d_tiles, int ntiles, cudaStream_t s) {
   constexpr size_t smem = fused_smem_bytes<Real, THERMAL, B>();
   // the dynamic shared-memory opt-in is per device; remember which devices have it
@@ -905,12 +979,12 @@ cudaError_t launch_one(const Inst* d_inst, const Tile* d_tiles, int ntiles, cuda
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(configured & bit)) {
-    e = cudaFuncSetAttribute(lbm_fused_kernel<Real, THERMAL, B, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(lbm_fused_kernel<Real, THERMAL, B, MODE, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
     configured |= bit;
   }
-  lbm_fused_kernel<Real, THERMAL, B, MODE><<<ntiles, B, smem, s>>>(d_inst, d_tiles);
+  lbm_fused_kernel<Real, THERMAL, B, MODE, FULL><<<ntiles, B, smem, s>>>(d_inst, d_tiles);
   return cudaGetLastError();
 }
 
@@ -918,7 +992,7 @@ cudaError_t launch_one(const Inst* d_inst, const Tile* d_tiles, int ntiles, cuda
 template <typename Real, bool THERMAL, int B>
 int resident_one() {
   constexpr size_t smem = fused_smem_bytes<Real, THERMAL, B>();
-  auto fn = lbm_fused_kernel<Real, THERMAL, B, MODE_STEP>;
+  auto fn = lbm_fused_kernel<Real, THERMAL, B, MODE_STEP, false>;
   int n = 0;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, B, smem) != cudaSuccess)
@@ -945,31 +1019,33 @@ int resident_precision(int thermal, int cols) {
 }
 
 template <typename Real, bool THERMAL, int B>
-cudaError_t launch_cols(int mode, const Inst* d_inst, const Tile* d_tiles, int ntiles, cudaStream_t s) {
+cudaError_t launch_cols(int mode, bool full, const Inst* d_inst, const Tile* d_tiles, int ntiles, cudaStream_t s) {
   switch (mode) {
-    case MODE_STEP: return launch_one<Real, THERMAL, B, MODE_STEP>(d_inst, d_tiles, ntiles, s);
-    case MODE_FIELDS: return launch_one<Real, THERMAL, B, MODE_FIELDS>(d_inst, d_tiles, ntiles, s);
-    case MODE_POPS: return launch_one<Real, THERMAL, B, MODE_POPS>(d_inst, d_tiles, ntiles, s);
-    case MODE_MOMENTS: return launch_one<Real, THERMAL, B, MODE_MOMENTS>(d_inst, d_tiles, ntiles, s);
+    case MODE_STEP:
+      return full ? launch_one<Real, THERMAL, B, MODE_STEP, true>(d_inst, d_tiles, ntiles, s)
+                  : launch_one<Real, THERMAL, B, MODE_STEP, false>(d_inst, d_tiles, ntiles, s);
+    case MODE_FIELDS: return launch_one<Real, THERMAL, B, MODE_FIELDS, true>(d_inst, d_tiles, ntiles, s);
+    case MODE_POPS: return launch_one<Real, THERMAL, B, MODE_POPS, true>(d_inst, d_tiles, ntiles, s);
+    case MODE_MOMENTS: return launch_one<Real, THERMAL, B, MODE_MOMENTS, true>(d_inst, d_tiles, ntiles, s);
   }
   return cudaErrorInvalidValue;
 }
 
 template <typename Real>
-cudaError_t launch_precision(int thermal, int cols, int mode, const Inst* d_inst, const Tile* d_tiles, int ntiles,
-                             cudaStream_t s) {
+cudaError_t launch_precision(int thermal, int cols, int mode, bool full, const Inst* d_inst, const Tile* d_tiles,
+                             int ntiles, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   if (thermal) {
     switch (cols) {
-      case 64: return launch_cols<Real, true, 64>(mode, d_inst, d_tiles, ntiles, s);
-      case 128: return launch_cols<Real, true, 128>(mode, d_inst, d_tiles, ntiles, s);
-      case 256: return launch_cols<Real, true, 256>(mode, d_inst, d_tiles, ntiles, s);
+      case 64: return launch_cols<Real, true, 64>(mode, full, d_inst, d_tiles, ntiles, s);
+      case 128: return launch_cols<Real, true, 128>(mode, full, d_inst, d_tiles, ntiles, s);
+      case 256: return launch_cols<Real, true, 256>(mode, full, d_inst, d_tiles, ntiles, s);
     }
   } else {
     switch (cols) {
-      case 64: return launch_cols<Real, false, 64>(mode, d_inst, d_tiles, ntiles, s);
-      case 128: return launch_cols<Real, false, 128>(mode, d_inst, d_tiles, ntiles, s);
-      case 256: return launch_cols<Real, false, 256>(mode, d_inst, d_tiles, ntiles, s);
+      case 64: return launch_cols<Real, false, 64>(mode, full, d_inst, d_tiles, ntiles, s);
+      case 128: return launch_cols<Real, false, 128>(mode, full, d_inst, d_tiles, ntiles, s);
+      case 256: return launch_cols<Real, false, 256>(mode, full, d_inst, d_tiles, ntiles, s);
     }
   }
   return cudaErrorInvalidValue;

@@ -85,6 +85,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, int32_t nx, int32_t 
                                        void* cuda_stream) {
   if (nx < 1 || ny < 1 || (prec != LBM_FP32 && prec != LBM_FP64) || step < 0) return LBM_EINVAL;
   if (check_params(nx, ny, p) != nullptr) return LBM_EINVAL;
+  if (p->source_model != LBM_SOURCE_GONG_CHENG) return LBM_EINVAL;  // needs a rho^(n-1) history buffer
   if (!f_in || !f_out || f_in == f_out) return LBM_EINVAL;
   if (p->thermal && (!g_in || !g_out || g_in == g_out)) return LBM_EINVAL;
   const long long plane = (long long)nx * ny;
@@ -107,6 +108,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, int32_t nx, int32_t 
 
   Inst I;
   if (fill_inst(I, p, nx, ny, nx, plane, prec == LBM_FP64) != nullptr) return LBM_EINVAL;
+  I.rho_prev = nullptr;
   // buffer (step & 1) is read and ((step + 1) & 1) written by the kernel
   I.f[step & 1] = const_cast<void*>(f_in);
   I.f[(step + 1) & 1] = f_out;
@@ -130,7 +132,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, int32_t nx, int32_t 
   if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
   // The caller's buffers are dense (pitch nx, any nx) and only element-aligned, so the
   // paired kernel's 8-byte accesses are not valid here: always the one-column form.
-  if (launch_lbm(prec == LBM_FP64, p->thermal, kNoAllocCols, MODE_STEP, LBM_KERNEL_SCALAR,
+  if (launch_lbm(prec == LBM_FP64, p->thermal, kNoAllocCols, MODE_STEP, LBM_KERNEL_SCALAR, needs_full_step(I),
                  reinterpret_cast<const Inst*>(base + kOffInst), tiles, ntiles, s) != cudaSuccess)
     return LBM_ECUDA;
   InstState out;

@@ -210,7 +210,7 @@ __device__ __forceinline__ void cp_async_pair(float2* smem, const float* gmem) {
 template <bool THERMAL>
 __device__ __forceinline__ void pair_pull(float2* f_dst, float2* g_dst, int stride, const float* __restrict__ Fin,
                                           const float* __restrict__ Gin, int plane, int pitch, int x, int rn, int nx,
-                                          int ny, bool perx, bool pery, bool local, bool wlo, bool whi) {
+                                          int ny, bool perx, bool pery, bool local, bool wlo, bool whi, bool top) {
   const bool interior = !local && x >= 1 && x + 2 <= nx - 1 && rn >= 1 && rn <= ny - 2;
   if (interior) {
     const int node = rn * pitch + x;
@@ -250,7 +250,7 @@ __device__ __forceinline__ void pair_pull(float2* f_dst, float2* g_dst, int stri
         int sx = xl - cxi, sy = rn - cyi;
         if (perx) sx = wrap_index(sx, nx);
         if (pery) sy = wrap_index(sy, ny);
-        if (sx < 0 || sx >= nx) continue;  // unknown link at an open end
+        if (sx < 0 || sx >= nx || (top && cyi == -1)) continue;  // unknown link at an open end
         src = sy * pitch + sx;
       }
       cp_async_elem(reinterpret_cast<float*>(f_dst + i * stride) + lane, Fin + pl * plane + src);
@@ -299,6 +299,7 @@ lbm_pair_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) 
   const bool perx = sI.geometry != GEOM_CHANNEL;
   const bool pery = sI.geometry == GEOM_PERIODIC;
   const bool channel = sI.geometry == GEOM_CHANNEL;
+  const bool pool = sI.geometry == GEOM_POOL;
   const bool multiphase = sI.multiphase != 0;
   const float* __restrict__ Fin = static_cast<const float*>(sI.f[step & 1]);
   const float* __restrict__ Gin = static_cast<const float*>(sI.g[step & 1]);
@@ -336,7 +337,8 @@ lbm_pair_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) 
       if (pery || (r >= 0 && r < ny)) {
         const int rn = pery ? wrap_index(r, ny) : r;
         pair_pull<THERMAL>(sF + fslot * 9 * B + t, sG + gslot * 9 * B + t, B, Fin, Gin, plane, pitch, xa, rn, nx, ny,
-                           perx, pery, local, !pery && rn == 0, !pery && rn == ny - 1);
+                           perx, pery, local, !pery && rn == 0, !pery && !pool && rn == ny - 1,
+                           pool && rn == ny - 1);
       }
     }
     cp_async_commit();
@@ -376,15 +378,15 @@ lbm_pair_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) 
         fc[i] = fs[i * B];
         gc[i] = THERMAL ? gs[i * B] : p_bc(0.0f);
       }
-      const bool wlo = !pery && rn == 0, whi = !pery && rn == ny - 1;
-      if (!local && (wlo || whi || edge)) {
+      const bool wlo = !pery && rn == 0, whi = !pery && !pool && rn == ny - 1, top = pool && rn == ny - 1;
+      if (!local && (wlo || whi || edge || top)) {
         // boundary nodes: the scalar boundary fill, lane by lane, written back to the ring
 #pragma unroll
         for (int lane = 0; lane < 2; ++lane) {
           const int xl = lane ? xn1 : xn0;
           if (!(lane ? in1 : in0)) continue;
-          const NodeBC nb{wlo, whi, channel && xl == 0, channel && xl == nx - 1};
-          if (!(nb.wlo || nb.whi || nb.inl || nb.outl)) continue;
+          const NodeBC nb{wlo, whi, channel && xl == 0, channel && xl == nx - 1, top};
+          if (!(nb.wlo || nb.whi || nb.inl || nb.outl || nb.top)) continue;
           float f1[9], g1[9];
 #pragma unroll
           for (int i = 0; i < 9; ++i) {
@@ -419,7 +421,7 @@ lbm_pair_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) 
             if (out1 && xn1 >= sI.heater_x0 && xn1 < sI.heater_x0 + sI.heater_len) acc_h += ns.dT.y;
           }
         }
-        {
+        if (sI.bubble_stats) {
           const float v0 = ns.drho.x < sC.drho_vapor ? 1.0f : 0.0f;
           const float v1 = (out1 && ns.drho.y < sC.drho_vapor) ? 1.0f : 0.0f;
           acc_va += v0 + v1;
@@ -446,11 +448,11 @@ lbm_pair_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) 
     const int q = r - 1;
     if (q >= tile.y0 - 1 && f_thread && (pery || (q >= 0 && q < ny))) {
       const bool sol_m = !pery && q == 0;
-      const bool sol_p = !pery && q == ny - 1;
+      const bool sol_p = !pery && !pool && q == ny - 1;
       float2 Fx = p_bc(0.0f), Fy = p_bc(0.0f);
       if (multiphase) {
         const float* P0 = sPsi + f_prev * NC;
-        const float* Pp = sPsi + f_cur * NC;
+        const float* Pp = (pool && q == ny - 1) ? P0 : sPsi + f_cur * NC;  // pool top: ghost row
         const float* Pm = sPsi + f_prev2 * NC;
         const float2 zc = p_bc(0.0f);
         const float2 dc = *reinterpret_cast<const float2*>(P0 + c0);
@@ -495,10 +497,10 @@ lbm_pair_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) 
       if (out_thread && q2 >= tile.y0 && q2 < tile.y1) {
         const float* Ux = sUx + f_prev2 * NC;
         const float2 uxE = make_float2(Ux[iE0], Ux[iE1]), uxW = make_float2(Ux[iW0], Ux[iW1]);
-        const float2 uyN = *reinterpret_cast<const float2*>(sUy + f_prev * NC + c0);
-        const float2 uyS = *reinterpret_cast<const float2*>(sUy + f_cur * NC + c0);  // slot of row r-3
         const float2 uyC = *reinterpret_cast<const float2*>(sUy + f_prev2 * NC + c0);
-        const bool wall_lo = !pery && q2 == 0, wall_hi = !pery && q2 == ny - 1;
+        const float2 uyN = (pool && q2 == ny - 1) ? uyC : *reinterpret_cast<const float2*>(sUy + f_prev * NC + c0);
+        const float2 uyS = *reinterpret_cast<const float2*>(sUy + f_cur * NC + c0);  // slot of row r-3
+        const bool wall_lo = !pery && q2 == 0, wall_hi = !pery && !pool && q2 == ny - 1;
         float2 dyu = p_mul(p_bc(0.5f), p_sub(uyN, uyS));
         if (wall_lo || wall_hi) dyu = (wall_lo && wall_hi) ? p_bc(0.0f) : (wall_lo ? p_sub(uyN, uyC) : p_sub(uyC, uyS));
         const float2 divu = p_fma(p_bc(0.5f), p_sub(uxE, uxW), dyu);
@@ -543,10 +545,7 @@ lbm_pair_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) 
   if (!sLast) return;
   __threadfence();
   double tot[NPART] = {};
-  for (int tt = tid; tt < tile.ntiles; tt += B) {
-#pragma unroll
-    for (int j = 0; j < NPART; ++j) tot[j] += __ldcg(sI.partials + (long long)tt * NPART + j);
-  }
+  fold_partials<B>(sI.partials, tile.ntiles, tot);
   __syncthreads();
   block_sum<B>(tot, sRed);
   if (tid == 0) finish_step<THERMAL, MODE_STEP>(sI, st, tot, step);

@@ -55,7 +55,8 @@ class LbmParams(ctypes.Structure):
         ("heater_len", ctypes.c_int32), ("heat_on_step", ctypes.c_int64), ("init_kind", ctypes.c_int32),
         ("reserved0", ctypes.c_int32), ("init_rho_in", ctypes.c_double), ("init_rho_out", ctypes.c_double),
         ("init_radius", ctypes.c_double), ("init_width", ctypes.c_double), ("perturb_amp", ctypes.c_double),
-        ("seed", ctypes.c_uint64), ("rho_vapor", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("rho_vapor", ctypes.c_double), ("source_model", ctypes.c_int32),
+        ("bubble_stats", ctypes.c_int32),
     ]
 
 

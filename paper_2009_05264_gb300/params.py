@@ -41,6 +41,7 @@ def default_params(**overrides) -> dict:
         heat_on_step=10000,  # heater switched on after 10000 steps (Sec. 2.C)
         source_model=0,      # energy source: 0 Gong-Cheng (second Eq. 19, the paper's), 1 Hazi-Markus (first)
         reserved0=0,
+        bubble_stats=0,      # 1: the library counts vapour nodes every step (bubble diagnostics)
         rho_vapor=3.2,       # vapour below this density in the bubble diagnostics: about the
                              # midpoint of the coexisting densities (0.59, 5.88) at 0.9 Tc
         init_kind=0,         # 0 uniform, 1 disk

@@ -23,10 +23,11 @@ TOL = {"fp64": 1e-12, "fp32": 1e-5}
 
 
 def raw_state(lat, elt):
-    """Storage-form populations (f, g) of a context, from its checkpoint blob."""
+    """Storage-form populations (f, g) of a context, from its checkpoint blob
+    (header, 9 planes of f, 9 of g, 1 of the density history)."""
     blob = lat.save_state()
     n = 9 * lat.nx * lat.ny
-    hdr = len(blob) - 2 * n * elt
+    hdr = len(blob) - (2 * n + lat.nx * lat.ny) * elt
     dt = np.float64 if elt == 8 else np.float32
     f = np.frombuffer(blob, dtype=dt, count=n, offset=hdr)
     g = np.frombuffer(blob, dtype=dt, count=n, offset=hdr + n * elt)
