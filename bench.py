@@ -159,8 +159,17 @@ def run_fp64(steps: int):
     peak, kind = read_peaks()
     gbs = bytes_per_node("fp64") * nodes * steps / (ms * 1e-3) / 1e9
     out = {"value": nodes * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "steps": steps, "ms_per_step": ms / steps,
-           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                        "peak_source": f"{kind} HBM copy bandwidth", "algorithmic_bytes_per_node": bytes_per_node("fp64")}}
+           "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                   "peak_source": f"{kind} HBM copy bandwidth", "algorithmic_bytes_per_node": bytes_per_node("fp64")}}
+    fpn = profiled_fp64_flops_per_node()
+    if fpn:  # FP64 arithmetic, not HBM, bounds this form on GB300
+        tf = fpn * nodes * steps / (ms * 1e-3) / 1e12
+        out["roofline"] = {"bound": "alu", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                           "frac": tf / FP64_NOMINAL_TFLOPS, "flops_per_node": fpn,
+                           "peak_source": "nominal GB300 FP64 (non-tensor) rate",
+                           "flops_source": f"ncu DADD + DMUL + 2 DFMA per node ({FP64_PROFILE})"}
+    else:
+        out["roofline"] = dict(out["hbm"], bound="hbm")
     lat.close()
     return out
 
@@ -277,6 +286,24 @@ def step_source_digest() -> str:
     return h.hexdigest()[:16]
 
 
+FP64_PROFILE = "profiles/lbm_fused_step_fp64_channel.md"
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate; no measured figure on this machine
+
+
+def profiled_fp64_flops_per_node():
+    """FP64 floating-point operations per node update of the step kernel (DADD + DMUL + 2 DFMA,
+    counted by ncu), or None when the summary was taken on other kernel sources."""
+    import re
+
+    path = os.path.join(ROOT, FP64_PROFILE)
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"fp64-flops-per-node:\s*([0-9.]+)\s*\(source digest ([0-9a-f]+)", open(path).read())
+    if not m or m.group(2) != step_source_digest():
+        return None
+    return float(m.group(1))
+
+
 def profiled_traffic_per_node():
     """DRAM bytes per node update of the step kernel from the committed ncu summary, or
     (None, reason) when the summary was taken on other kernel sources."""
@@ -291,6 +318,23 @@ def profiled_traffic_per_node():
     if m.group(2) != step_source_digest():
         return None, "kernel sources changed since the profile"
     return float(m.group(1)), f"ncu dram__bytes_read+write per node ({PROFILE})"
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest of every rank's value (the slowest rank's time); the value itself on one rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(nodes_per_rank: int, steps: int, world: int, seconds: float) -> float:
+    """Node updates of all ranks per second (weak scaling: every rank advances its own lattice)."""
+    return nodes_per_rank * steps * world / seconds / 1e6
 
 
 def dist_env():
@@ -398,12 +442,10 @@ def run_ours(args):
     total_ms = events[0].elapsed_time(events[-1])
     per_launch = [events[k].elapsed_time(events[k + 1]) for k in range(args.steps)]
     clocks = sampler.stop() if sampler else None
-    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
     if world > 1:
         dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = nodes * args.steps * world / (total_ms * 1e-3) / 1e6
+    total_ms = max_over_ranks(total_ms, world, dev)
+    value = whole_job_mlups(nodes, args.steps, world, total_ms * 1e-3)
 
     # ---- end to end through the public API with host buffers ----
     pinned = [torch.empty((NY, NX), dtype=torch.float64).pin_memory() for _ in range(4)]
@@ -421,10 +463,7 @@ def run_ours(args):
     for o, k in zip(outs, ("rho", "ux", "uy", "T")):
         o.numpy()[...] = got[k]
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = nodes * e2e_steps * world / float(te.item()) / 1e6
+    e2e_value = whole_job_mlups(nodes, e2e_steps, world, max_over_ranks(e2e_s, world, dev))
     if not np.isfinite(got["rho"]).all():
         raise RuntimeError("non-finite density after the e2e run")
 
