@@ -270,17 +270,23 @@ def run_serve(n_requests: int, steps: int, rate: float = 2.0, seed: int = SEED +
             "hbm_budget_bytes": hbm_budget, "chunk_steps": chunk, "finite": bool(finite)}
 
 
-STEP_SOURCES = ("paper_2009_05264_gb300/csrc/lbm_kernels.cuh", "paper_2009_05264_gb300/csrc/lbm_internal.h")
-PROFILE = "profiles/lbm_fused_step_fp32_channel.md"
+_CSRC = "paper_2009_05264_gb300/csrc/"
+# sources of each step-kernel form (scalar: also the FP64 step) and its ncu summary
+STEP_SOURCES = {"scalar": (_CSRC + "lbm_kernels.cuh", _CSRC + "lbm_internal.h"),
+                "tma": (_CSRC + "lbm_kernels.cuh", _CSRC + "lbm_internal.h", _CSRC + "lbm_tma.cuh")}
+PROFILES = {"scalar": "profiles/lbm_fused_step_fp32_channel.md", "tma": "profiles/lbm_tma_step_fp32_channel.md"}
+KERNEL_LABELS = {"scalar": "lbm_fused_kernel (MODE_STEP)",
+                 "paired": "lbm_pair_kernel (two columns per thread, packed FP32)",
+                 "tma": "lbm_tma_kernel (MODE_STEP, rows staged by bulk tensor copies)"}
 
 
-def step_source_digest() -> str:
-    """Digest of the FP32 step kernel's sources: ties a profiled DRAM traffic figure to
-    the code it was measured on."""
+def step_source_digest(kernel: str = "scalar") -> str:
+    """Digest of a step kernel's sources: ties a profiled DRAM traffic figure to the
+    code it was measured on."""
     import hashlib
 
     h = hashlib.sha256()
-    for rel in STEP_SOURCES:
+    for rel in STEP_SOURCES[kernel]:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -304,20 +310,22 @@ def profiled_fp64_flops_per_node():
     return float(m.group(1))
 
 
-def profiled_traffic_per_node():
-    """DRAM bytes per node update of the step kernel from the committed ncu summary, or
-    (None, reason) when the summary was taken on other kernel sources."""
+def profiled_traffic_per_node(kernel: str):
+    """DRAM bytes per node update of a step kernel form from its committed ncu summary, or
+    (None, reason) when there is none or it was taken on other kernel sources."""
     import re
 
-    path = os.path.join(ROOT, PROFILE)
+    if kernel not in PROFILES:
+        return None, "not profiled"
+    path = os.path.join(ROOT, PROFILES[kernel])
     if not os.path.exists(path):
         return None, "no profile summary"
     m = re.search(r"traffic-per-node:\s*([0-9.]+)\s*B\s*\(source digest ([0-9a-f]+)", open(path).read())
     if not m:
         return None, "profile summary has no traffic line"
-    if m.group(2) != step_source_digest():
+    if m.group(2) != step_source_digest(kernel):
         return None, "kernel sources changed since the profile"
-    return float(m.group(1)), f"ncu dram__bytes_read+write per node ({PROFILE})"
+    return float(m.group(1)), f"ncu dram__bytes_read+write per node ({PROFILES[kernel]})"
 
 
 def max_over_ranks(value: float, world: int, device=None) -> float:
@@ -415,6 +423,7 @@ def run_ours(args):
         c, r = (int(x) for x in args.tiling.split("x"))
         lat.set_tiling(c, r)
     lat.set_kernel(args.kernel)
+    step_kernel = lat.step_kernel  # the form the timed launches take
     lat.init_fields(*fields)
     stream = lat.stream
     nodes = NX * NY
@@ -472,7 +481,7 @@ def run_ours(args):
         bpn = bytes_per_node(prec)
         avg_launch_ms = statistics.mean(per_launch)
         achieved = bpn * nodes / (avg_launch_ms * 1e-3) / 1e9
-        tpn, tsrc = profiled_traffic_per_node() if prec == "fp32" and args.kernel != "paired" else (None, "not profiled")
+        tpn, tsrc = profiled_traffic_per_node(step_kernel)
         line = {
             "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -481,7 +490,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD if prec == "fp32" else WORKLOAD.replace("FP32", "FP64"),
                        "nx": NX, "ny": NY, "nodes_per_gpu": nodes, "precision": prec,
                        "tiling": args.tiling or "default (128 columns, rows by heuristic)",
-                       "kernel": args.kernel if prec == "fp32" else "scalar (FP64)",
+                       "kernel": f"{step_kernel} (requested {args.kernel})" if prec == "fp32" else "scalar (FP64)",
                        "l2": "inputs larger than L2: 2 x 0.92 GB population buffers vs 129 MB L2",
                        "parallelism": f"{world} independent channel replicas"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -489,8 +498,7 @@ def run_ours(args):
                          "traffic_source": tsrc,
                          "peak_source": f"{peak_kind} HBM copy bandwidth",
                          "algorithmic_bytes_per_node": bpn,
-                         "kernel": ("lbm_pair_kernel (two columns per thread, packed FP32)"
-                                    if prec == "fp32" and args.kernel == "paired" else "lbm_fused_kernel (MODE_STEP)")},
+                         "kernel": KERNEL_LABELS[step_kernel]},
             "e2e": {"value": e2e_value, "unit": "MLUPS",
                     "h2d_bytes_per_step": 4 * nodes * 8 / e2e_steps, "d2h_bytes_per_step": 4 * nodes * 8 / e2e_steps,
                     "note": f"init_fields from pinned host arrays + {e2e_steps} steps + read_fields to host"},
@@ -520,7 +528,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--tiling", default=None, help="COLSxROWS, e.g. 128x32")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "scalar", "paired"], help="FP32 step kernel form")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "scalar", "paired", "tma"], help="FP32 step kernel form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the fp64, batch and serve measurements")
     ap.add_argument("--batch-steps", type=int, default=300)

@@ -216,17 +216,30 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* host_buf, size_t bytes);
  * domain-mean density (Eq. 14); only speed differs.  0 = default. */
 lbm_status lbm_set_tiling(lbm_ctx* ctx, int32_t cols, int32_t rows);
 
-/* Form of the FP32 step kernel.  LBM_KERNEL_SCALAR (and LBM_KERNEL_AUTO, the
- * default): one column per thread.  LBM_KERNEL_PAIRED: each thread updates two
- * adjacent columns with packed FP32 arithmetic (two nodes per add / multiply / fused
- * multiply-add instruction) and 8-byte stores; it executes about 40 % fewer
- * instructions per node but holds fewer warps per SM, and on GB300 runs slower.  Both compute the same step and agree
- * to FP32 rounding (a few additions and multiply-add contractions are ordered
- * differently).  FP64 lattices, and lbm_step_noalloc on caller-laid-out buffers,
- * always use the scalar form.  LBM_EINVAL for other
- * values. */
-enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_SCALAR = 1, LBM_KERNEL_PAIRED = 2 };
+/* Form of the FP32 step kernel.  All forms compute the same step (Sec. 2; boundary
+ * conditions of Sec. 2.C) and agree to FP32 rounding.
+ *   LBM_KERNEL_SCALAR (and LBM_KERNEL_AUTO, the default): one column per thread; each
+ *     thread stages the populations it pulls with per-element asynchronous copies
+ *     (cp.async).  Handles every option.  The fastest form on GB300.
+ *   LBM_KERNEL_PAIRED: each thread updates two adjacent columns with packed FP32
+ *     arithmetic (two nodes per add / multiply / fused multiply-add) and 8-byte stores;
+ *     about 40 % fewer instructions per node but fewer warps per SM, slower on GB300.
+ *     Lattices with the Hazi-Markus source take the scalar form.
+ *   LBM_KERNEL_TMA: one column per thread; one thread per CTA stages whole rows of
+ *     every population plane with bulk tensor copies (cp.async.bulk.tensor, completion
+ *     on mbarriers), which removes the per-thread copy work from the step.  Needs
+ *     128-column tiles and the step's lean form (no pool geometry, Hazi-Markus source
+ *     or bubble statistics); other lattices take the scalar form.  A bulk copy that does
+ *     not complete within a bounded wait makes lbm_sync return LBM_ETIMEOUT.  Its results
+ *     are bit-identical to the scalar form's; on GB300 it runs about 10 % slower (its
+ *     warps wait on rows that arrive later than the per-thread copies do).
+ * FP64 lattices, and lbm_step_noalloc on caller-laid-out buffers, always use the scalar
+ * form.  LBM_EINVAL for other values. */
+enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_SCALAR = 1, LBM_KERNEL_PAIRED = 2, LBM_KERNEL_TMA = 3 };
 lbm_status lbm_set_kernel(lbm_ctx* ctx, int32_t kernel);
+/* The form (LBM_KERNEL_SCALAR, _PAIRED or _TMA) the context's step launches take
+ * with its current kernel request, precision, parameters and tiling; -1 if ctx is NULL. */
+int32_t lbm_step_kernel(const lbm_ctx* ctx);
 
 int64_t lbm_get_step(const lbm_ctx* ctx);
 /* Kernel launches enqueued by this context since creation (all kinds). */

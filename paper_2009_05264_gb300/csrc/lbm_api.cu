@@ -1,6 +1,7 @@
 // Host side of the pplbm C ABI: contexts, parameter validation, device memory
 // layout, launches and readback.  Every exported function returns a status and
 // never throws.
+#include <cuda.h>  // CUtensorMap and its encoder's types (the encoder is fetched at run time)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -193,7 +194,7 @@ struct Layout {
   long long plane;
   size_t pop_bytes;  // one 9-plane buffer
   int max_tiles;
-  size_t off_f[2], off_g[2], off_rho_prev, off_inst, off_state, off_part, off_ring, off_tiles_step, off_tiles_aux,
+  size_t off_f[2], off_g[2], off_rho_prev, off_tmaps, off_inst, off_state, off_part, off_ring, off_tiles_step, off_tiles_aux,
       total;
 };
 
@@ -210,6 +211,7 @@ Layout make_layout(int nx, int ny, lbm_precision prec) {
   for (int b = 0; b < 2; ++b) { L.off_f[b] = off; off += L.pop_bytes; }
   for (int b = 0; b < 2; ++b) { L.off_g[b] = off; off += L.pop_bytes; }
   L.off_rho_prev = off; off += align_up((size_t)L.plane * elt);
+  L.off_tmaps = off; off += align_up(4 * sizeof(CUtensorMap));
   L.off_inst = off; off += align_up(sizeof(Inst));
   L.off_state = off; off += align_up(sizeof(InstState));
   L.off_part = off; off += align_up((size_t)L.max_tiles * NPART * sizeof(double));
@@ -243,6 +245,40 @@ void build_tiles(int nx, int ny, int cols, int rows, std::vector<Tile>& out) {
     }
 }
 
+// cuTensorMapEncodeTiled, fetched from the driver at run time (the library does not
+// link the driver API).  Null when the driver does not provide it.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// The TMA step kernel's view of one FP32 population buffer: a 3-D tensor (x: nx columns,
+// y: ny rows `pitch` apart, z: 9 planes `plane` apart) read in boxes of one 128-column
+// row of one plane; boxes reaching outside the tensor read zeros.
+bool encode_pop_map(CUtensorMap* m, void* base, int nx, int ny, int pitch, long long plane) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 9};
+  const cuuint64_t strides[2] = {(cuuint64_t)pitch * sizeof(float), (cuuint64_t)plane * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)TMA_TILE_COLS, 1, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 
 }  // namespace
 
@@ -270,7 +306,8 @@ struct lbm_ctx {
   long long launches = 0;
   long long step_host = 0;  // step count as last synchronised
   unsigned long long params_gen = 0;  // bumped whenever the descriptor changes
-  int kernel = LBM_KERNEL_AUTO;        // step kernel form (FP32: scalar or paired columns)
+  int kernel = LBM_KERNEL_AUTO;        // requested step kernel form (resolve_kernel picks the one launched)
+  bool have_tmaps = false;             // FP32: the tensor maps of the population buffers are on the device
   std::string err;
 };
 
@@ -329,8 +366,14 @@ lbm_status set_tiling(lbm_ctx* c, int cols, int rows) {
 }
 
 // Re-choose the default band height for the current kernel, precision and thermal flag.
+int step_kernel(const lbm_ctx* c, int cols) {
+  return resolve_kernel(c->kernel, c->prec == LBM_FP64, needs_full_step(c->hinst),
+                        c->params.source_model == LBM_SOURCE_HAZI_MARKUS, c->have_tmaps, cols);
+}
+
 lbm_status retile_default(lbm_ctx* c, int cols) {
-  const long long slots = step_wave_slots(c->prec == LBM_FP64, c->have_params ? c->thermal : 1, cols, c->kernel);
+  const long long slots =
+      step_wave_slots(c->prec == LBM_FP64, c->have_params ? c->thermal : 1, cols, step_kernel(c, cols));
   const lbm_status s = set_tiling(c, cols, default_band_rows(c->nx, c->ny, cols, slots));
   if (s == LBM_OK) c->rows_default = true;
   return s;
@@ -338,8 +381,7 @@ lbm_status retile_default(lbm_ctx* c, int cols) {
 
 lbm_status launch(lbm_ctx* c, int mode) {
   const bool step_tiles = mode == MODE_STEP;
-  // the paired kernel has no Hazi-Markus source: such lattices always take the one-column form
-  const int kernel = c->params.source_model == LBM_SOURCE_HAZI_MARKUS ? LBM_KERNEL_SCALAR : c->kernel;
+  const int kernel = step_tiles ? step_kernel(c, c->cols) : LBM_KERNEL_SCALAR;
   cudaError_t e = launch_lbm(c->prec == LBM_FP64, c->thermal, step_tiles ? c->cols : kAuxCols, mode, kernel,
                              needs_full_step(c->hinst), c->d_inst,
                              step_tiles ? c->d_tiles_step : c->d_tiles_aux,
@@ -360,6 +402,7 @@ lbm_status apply_params(lbm_ctx* c, const lbm_params* p) {
     I.g[b] = c->base + c->L.off_g[b];
   }
   I.rho_prev = c->base + c->L.off_rho_prev;
+  I.tmaps = c->have_tmaps ? c->base + c->L.off_tmaps : nullptr;
   I.st = c->d_state;
   I.partials = reinterpret_cast<double*>(c->base + c->L.off_part);
   I.ring = reinterpret_cast<double*>(c->base + c->L.off_ring);
@@ -420,6 +463,25 @@ lbm_status create_impl(lbm_ctx** out, int32_t nx, int32_t ny, lbm_precision prec
   c->d_state = reinterpret_cast<InstState*>(c->base + c->L.off_state);
   c->d_tiles_step = reinterpret_cast<Tile*>(c->base + c->L.off_tiles_step);
   c->d_tiles_aux = reinterpret_cast<Tile*>(c->base + c->L.off_tiles_aux);
+  if (prec == LBM_FP32) {
+    // tensor maps of f and g, both buffers, for the TMA step kernel (without them the
+    // scalar kernel runs)
+    CUtensorMap maps[4];
+    bool ok = true;
+    for (int b = 0; b < 2; ++b) {
+      ok = ok && encode_pop_map(&maps[b], c->base + c->L.off_f[b], nx, ny, c->L.pitch, c->L.plane);
+      ok = ok && encode_pop_map(&maps[2 + b], c->base + c->L.off_g[b], nx, ny, c->L.pitch, c->L.plane);
+    }
+    if (ok) {
+      if (cudaMemcpyAsync(c->base + c->L.off_tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, c->stream) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        lbm_destroy(c);
+        return LBM_ECUDA;
+      }
+      c->have_tmaps = true;
+    }
+  }
   std::vector<Tile> t;
   build_tiles(nx, ny, kAuxCols, std::min(kAuxRows, ny), t);
   c->ntiles_aux = (int)t.size();
@@ -565,6 +627,8 @@ lbm_status lbm_sync(lbm_ctx* c) {
   DeviceGuard g(c->device);
   lbm_status s = fetch_state(c);
   if (s != LBM_OK) return s;
+  if (c->h_state->status & STATUS_TIMEOUT)
+    return fail(c, LBM_ETIMEOUT, "a bulk tensor copy of the step did not complete within its bounded wait");
   if (c->h_state->status & STATUS_UNSTABLE)
     return fail(c, LBM_EUNSTABLE, "lattice left the EOS domain (rho <= 0, rho >= 1/b, NaN or psi radicand < 0)");
   return LBM_OK;
@@ -773,14 +837,17 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t bytes) {
 
 lbm_status lbm_set_kernel(lbm_ctx* c, int32_t kernel) {
   if (!c) return LBM_EINVAL;
-  if (kernel != LBM_KERNEL_AUTO && kernel != LBM_KERNEL_SCALAR && kernel != LBM_KERNEL_PAIRED)
-    return fail(c, LBM_EINVAL, "kernel must be LBM_KERNEL_AUTO, _SCALAR or _PAIRED");
+  if (kernel != LBM_KERNEL_AUTO && kernel != LBM_KERNEL_SCALAR && kernel != LBM_KERNEL_PAIRED &&
+      kernel != LBM_KERNEL_TMA)
+    return fail(c, LBM_EINVAL, "kernel must be LBM_KERNEL_AUTO, _SCALAR, _PAIRED or _TMA");
   c->kernel = kernel;
   if (!c->rows_default) return LBM_OK;
   DeviceGuard g(c->device);
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
   return retile_default(c, c->cols);
 }
+
+int32_t lbm_step_kernel(const lbm_ctx* c) { return c ? step_kernel(c, c->cols) : -1; }
 
 lbm_status lbm_set_tiling(lbm_ctx* c, int32_t cols, int32_t rows) {
   if (!c) return LBM_EINVAL;

@@ -40,8 +40,8 @@ struct lbm_batch {
   bool own_stream = false;
   std::vector<Member> slots;  // empty ctx = free slot
   int cols = 128, rows = 0;   // rows 0: each member's default band height
-  int kernel = LBM_KERNEL_AUTO;
-  bool any_hazi = false;  // a member uses the Hazi-Markus source: one-column kernel for the batch
+  int kernel = LBM_KERNEL_AUTO;         // requested step kernel form
+  int launch_kernel = LBM_KERNEL_SCALAR; // the form the batch's launches take (resolve_kernel)
   bool any_full = false;  // a member needs the step's full form (pool, Hazi-Markus, bubble statistics)
   // device tables of the current membership
   Inst* d_insts = nullptr;
@@ -86,20 +86,26 @@ int member_rows(const lbm_batch* b, int nx, int ny, long long slots, double shar
 lbm_status rebuild(lbm_batch* b) {
   std::vector<Inst> insts;
   std::vector<Tile> tiles;
-  bool any_hazi = false;
+  bool any_hazi = false;  // a member uses the Hazi-Markus source (no paired form)
   bool any_full = false;
+  bool all_tmaps = true;  // every member has the tensor maps of the TMA kernel
   const int w = b->cols - 8;
   double total = 0.0;
-  for (const Member& m : b->slots)
-    if (m.ctx) total += (double)m.nx * m.ny;
-  const long long slots = step_wave_slots(b->prec == LBM_FP64, b->thermal, b->cols, b->kernel);
+  for (const Member& m : b->slots) {
+    if (!m.ctx) continue;
+    total += (double)m.nx * m.ny;
+    const Inst I = lbm_internal_inst(m.ctx);
+    any_hazi = any_hazi || I.source_model == LBM_SOURCE_HAZI_MARKUS;
+    any_full = any_full || needs_full_step(I);
+    all_tmaps = all_tmaps && I.tmaps != nullptr;
+  }
+  const int launch_kernel = resolve_kernel(b->kernel, b->prec == LBM_FP64, any_full, any_hazi, all_tmaps, b->cols);
+  const long long slots = step_wave_slots(b->prec == LBM_FP64, b->thermal, b->cols, launch_kernel);
   for (Member& m : b->slots) {
     if (!m.ctx) continue;
     const int idx = (int)insts.size();
     insts.push_back(lbm_internal_inst(m.ctx));
     m.gen = lbm_internal_params_gen(m.ctx);
-    if (insts.back().source_model == LBM_SOURCE_HAZI_MARKUS) any_hazi = true;
-    if (needs_full_step(insts.back())) any_full = true;
     const int rows = member_rows(b, m.nx, m.ny, slots, total > 0.0 ? (double)m.nx * m.ny / total : 1.0);
     const int strips = (m.nx + w - 1) / w, bands = (m.ny + rows - 1) / rows;
     const int n = strips * bands;
@@ -142,7 +148,7 @@ lbm_status rebuild(lbm_batch* b) {
   }
   LBM_BCUDA(b, cudaStreamSynchronize(b->stream));
   b->ntiles = (int)tiles.size();
-  b->any_hazi = any_hazi;
+  b->launch_kernel = launch_kernel;
   b->any_full = any_full;
   drop_graph(b);
   b->dirty = false;
@@ -151,7 +157,7 @@ lbm_status rebuild(lbm_batch* b) {
 
 lbm_status launch_steps(lbm_batch* b, int64_t n) {
   for (int64_t k = 0; k < n; ++k) {
-    LBM_BCUDA(b, launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->any_hazi ? LBM_KERNEL_SCALAR : b->kernel, b->any_full, b->d_insts, b->d_tiles, b->ntiles,
+    LBM_BCUDA(b, launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->launch_kernel, b->any_full, b->d_insts, b->d_tiles, b->ntiles,
                             b->stream));
     ++b->launches;
   }
@@ -163,7 +169,7 @@ lbm_status capture_graph(lbm_batch* b) {
   LBM_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   lbm_status s = LBM_OK;
   for (int k = 0; k < kGraphChunk && s == LBM_OK; ++k) {
-    if (launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->any_hazi ? LBM_KERNEL_SCALAR : b->kernel, b->any_full, b->d_insts, b->d_tiles, b->ntiles,
+    if (launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->launch_kernel, b->any_full, b->d_insts, b->d_tiles, b->ntiles,
                    b->stream) != cudaSuccess)
       s = bfail(b, LBM_ECUDA, "launch during graph capture");
   }
@@ -280,8 +286,9 @@ lbm_status lbm_batch_set_tiling(lbm_batch* b, int32_t cols, int32_t rows) {
 
 lbm_status lbm_batch_set_kernel(lbm_batch* b, int32_t kernel) {
   if (!b) return LBM_EINVAL;
-  if (kernel != LBM_KERNEL_AUTO && kernel != LBM_KERNEL_SCALAR && kernel != LBM_KERNEL_PAIRED)
-    return bfail(b, LBM_EINVAL, "kernel must be LBM_KERNEL_AUTO, _SCALAR or _PAIRED");
+  if (kernel != LBM_KERNEL_AUTO && kernel != LBM_KERNEL_SCALAR && kernel != LBM_KERNEL_PAIRED &&
+      kernel != LBM_KERNEL_TMA)
+    return bfail(b, LBM_EINVAL, "kernel must be LBM_KERNEL_AUTO, _SCALAR, _PAIRED or _TMA");
   b->kernel = kernel;
   b->dirty = true;  // default band heights depend on the kernel's occupancy; the graph names the kernel
   return LBM_OK;

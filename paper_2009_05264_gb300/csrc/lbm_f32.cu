@@ -1,17 +1,21 @@
 // Kernel instantiations for float storage and arithmetic.
 #include "lbm_kernels.cuh"
 #include "lbm_pair.cuh"
+#include "lbm_tma.cuh"
 
 namespace pplbm {
 
 cudaError_t launch_lbm_f32(int thermal, int cols, int mode, int kernel, bool full, const Inst* d_inst,
                           const Tile* d_tiles, int ntiles, cudaStream_t s) {
   if (mode == MODE_STEP && kernel == LBM_KERNEL_PAIRED) return launch_pair(thermal, cols, d_inst, d_tiles, ntiles, s);
+  if (mode == MODE_STEP && kernel == LBM_KERNEL_TMA) return launch_tma(thermal, cols, d_inst, d_tiles, ntiles, s);
   return launch_precision<float>(thermal, cols, mode, full, d_inst, d_tiles, ntiles, s);
 }
 
 int resident_ctas_f32(int thermal, int cols, int kernel) {
-  return kernel == LBM_KERNEL_PAIRED ? resident_pair(thermal, cols) : resident_precision<float>(thermal, cols);
+  if (kernel == LBM_KERNEL_PAIRED) return resident_pair(thermal, cols);
+  if (kernel == LBM_KERNEL_TMA && cols == TMA_COLS) return resident_tma(thermal);
+  return resident_precision<float>(thermal, cols);
 }
 
 cudaError_t launch_init_from_fields_f32(const Inst* d_inst, int nx, int ny, const double* d_fields, int has_T,

@@ -16,7 +16,7 @@ constexpr int RING = 1024;  // diagnostics records kept per instance
 
 enum : int { GEOM_PERIODIC = 0, GEOM_CHANNEL = 1, GEOM_WALLS = 2, GEOM_POOL = 3 };
 enum : int { MODE_STEP = 0, MODE_FIELDS = 1, MODE_POPS = 2, MODE_MOMENTS = 3 };
-enum : unsigned { STATUS_UNSTABLE = 1u };
+enum : unsigned { STATUS_UNSTABLE = 1u, STATUS_TIMEOUT = 2u };
 
 // Device-resident mutable state of one lattice instance.
 struct InstState {
@@ -53,6 +53,7 @@ struct Inst {
   double rho_vapor;                 // vapour threshold of the bubble diagnostics
   int source_model, bubble_stats;   // 0 Gong-Cheng, 1 Hazi-Markus (first Eq. 19); count vapour nodes
   void* rho_prev;                   // rho^(n-1) - rho_ref per node (storage precision, pitch layout)
+  const void* tmaps;                // FP32: 4 tensor maps of 128 bytes (f of buffers 0, 1, then g); or null
   InstState* st;
   double* partials;                 // NPART per tile of this instance
   double* ring;                     // RING records of NDIAG doubles
@@ -67,7 +68,7 @@ struct Tile {
 };
 
 // Launchers (defined per precision).  Tiles must have been built for `cols`.
-// kernel: LBM_KERNEL_AUTO / _SCALAR / _PAIRED (pplbm.h); only the FP32 step has a paired form.
+// kernel: a resolved form (resolve_kernel): LBM_KERNEL_SCALAR, _PAIRED or _TMA.
 // full: the instances use the pool geometry, the Hazi-Markus source or bubble statistics, which
 // only the step's full form handles (the lean form leaves them out of the hot loop).
 cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, int kernel, bool full, const Inst* d_inst,
@@ -75,6 +76,18 @@ cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, int kernel, bo
 // Whether an instance needs the step's full form.
 inline bool needs_full_step(const Inst& I) {
   return I.geometry == GEOM_POOL || I.source_model != 0 || I.bubble_stats != 0;
+}
+// The step-kernel form a launch takes for a requested LBM_KERNEL_* value: FP64 has only
+// the scalar kernel; the paired kernel has no Hazi-Markus source; the TMA kernel needs
+// 128-column tiles, the step's lean form and the instances' tensor maps (tmaps: all
+// instances of the launch have them).  LBM_KERNEL_AUTO takes the scalar kernel, the
+// fastest form on GB300.
+constexpr int TMA_TILE_COLS = 128;
+inline int resolve_kernel(int requested, int fp64, bool full, bool hazi, bool tmaps, int cols) {
+  if (fp64) return LBM_KERNEL_SCALAR;
+  if (requested == LBM_KERNEL_PAIRED) return hazi ? LBM_KERNEL_SCALAR : LBM_KERNEL_PAIRED;
+  if (requested == LBM_KERNEL_TMA && !full && tmaps && cols == TMA_TILE_COLS) return LBM_KERNEL_TMA;
+  return LBM_KERNEL_SCALAR;
 }
 // f = f^eq(rho,u), g = g^eq(T,u) into buffer 0 from 4 planes of nx*ny doubles (rho, ux, uy, T).
 cudaError_t launch_init_from_fields(int fp64, const Inst* d_inst, int nx, int ny, const double* d_fields,

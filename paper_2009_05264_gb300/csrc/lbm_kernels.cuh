@@ -453,14 +453,22 @@ __device__ __forceinline__ void sc_force(Real dc, Real dE, Real dW, Real dN, Rea
   if (sol_p) Fy -= C.wall0 + dc * C.wall1;
 }
 
+// The 9 staged populations of one node, population i at p[i * stride].
+template <typename Real>
+struct StridedPops {
+  const Real* p;
+  int stride;
+  __device__ __forceinline__ Real operator()(int i) const { return p[i * stride]; }
+};
+
 // BGK toward f^eq(rho, u_eq) (Eqs. 2-3) plus the exact-difference term (Eq. 5),
 // written pairwise over opposite directions i, i': with cu = c_i.u, cd = c_i.du and
 // cs = c_i.(2u + du), omega f^eq_i + F_i = w_i (K + 4.5 rho (omega cu^2 + cd cs))
 // + 3 w_i rho (omega cu + cd), K = omega (drho - 1.5 rho u.u) - 1.5 rho du.(2u + du);
-// the direction i' flips the sign of the second term only.  fs: the 9 pulled
-// populations at stride fstride; fo: the node in the output buffer, planes `plane` apart.
-template <typename Real>
-__device__ __forceinline__ void collide_f(const Real* fs, int fstride, Real* __restrict__ fo, int plane, Real rho,
+// the direction i' flips the sign of the second term only.  fs(i): the pulled
+// population i of the node; fo: the node in the output buffer, planes `plane` apart.
+template <typename Real, typename Pops>
+__device__ __forceinline__ void collide_f(const Pops& fs, Real* __restrict__ fo, int plane, Real rho,
                                           Real drho, Real ux, Real uy, Real dux, Real duy, Real omega_f) {
   const Real sx = Real(2) * ux + dux, sy = Real(2) * uy + duy;
   const Real usq = ux * ux + uy * uy;
@@ -469,10 +477,10 @@ __device__ __forceinline__ void collide_f(const Real* fs, int fstride, Real* __r
   auto pair = [&](int i, int j, Real cu, Real cd, Real cs, Real w) {
     const Real sym = w * (K + r45 * (omega_f * cu * cu + cd * cs));
     const Real anti = w * r3 * (omega_f * cu + cd);
-    fo[i * plane] = keep * fs[i * fstride] + sym + anti;
-    fo[j * plane] = keep * fs[j * fstride] + sym - anti;
+    fo[i * plane] = keep * fs(i) + sym + anti;
+    fo[j * plane] = keep * fs(j) + sym - anti;
   };
-  fo[0] = keep * fs[0] + lat_w<Real>(0) * K;
+  fo[0] = keep * fs(0) + lat_w<Real>(0) * K;
   pair(1, 3, ux, dux, sx, lat_w<Real>(1));
   pair(2, 4, uy, duy, sy, lat_w<Real>(2));
   pair(5, 7, ux + uy, dux + duy, sx + sy, lat_w<Real>(5));
@@ -481,8 +489,8 @@ __device__ __forceinline__ void collide_f(const Real* fs, int fstride, Real* __r
 
 // Eq. 16 with g^eq of Eq. 18 and the source phi (second Eq. 19), pairwise as for f:
 // omega g^eq_i + w_i phi = w_i (Kg + 4.5 omega T cu^2) + 3 w_i omega T cu.
-template <typename Real>
-__device__ __forceinline__ void collide_g(const Real* gs, int gstride, Real* __restrict__ go, int plane, Real T,
+template <typename Real, typename Pops>
+__device__ __forceinline__ void collide_g(const Pops& gs, Real* __restrict__ go, int plane, Real T,
                                           Real dT, Real uax, Real uay, Real phi, Real omega_g) {
   const Real usq = uax * uax + uay * uay;
   const Real Kg = omega_g * (dT - Real(1.5) * T * usq) + phi;
@@ -490,10 +498,10 @@ __device__ __forceinline__ void collide_g(const Real* gs, int gstride, Real* __r
   auto pair = [&](int i, int j, Real cu, Real w) {
     const Real sym = w * (Kg + t45 * cu * cu);
     const Real anti = w * t3 * cu;
-    go[i * plane] = keep * gs[i * gstride] + sym + anti;
-    go[j * plane] = keep * gs[j * gstride] + sym - anti;
+    go[i * plane] = keep * gs(i) + sym + anti;
+    go[j * plane] = keep * gs(j) + sym - anti;
   };
-  go[0] = keep * gs[0] + lat_w<Real>(0) * Kg;
+  go[0] = keep * gs(0) + lat_w<Real>(0) * Kg;
   pair(1, 3, uax, lat_w<Real>(1));
   pair(2, 4, uay, lat_w<Real>(2));
   pair(5, 7, uax + uay, lat_w<Real>(5));
@@ -816,7 +824,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
       sUy[f_prev * NS + s] = uay;
       const bool out_q = out_col && q >= tile.y0 && q < tile.y1;
       if (MODE == MODE_STEP && out_q) {
-        collide_f<Real>(sF + f_prev * 9 * NS + s, NS, Fout + (q * pitch + xn), plane, rho_p, drho_p, ux_p, uy_p,
+        collide_f<Real>(StridedPops<Real>{sF + f_prev * 9 * NS + s, NS}, Fout + (q * pitch + xn), plane, rho_p, drho_p, ux_p, uy_p,
                         dux, duy, sC.omega_f);
         if (channel && xn == 0) acc_fi += rho_p * uax;
         if (channel && xn == nx - 1) acc_fo += rho_p * uax;
@@ -852,7 +860,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
         const Real divu = Real(0.5) * (uxE - uxW) + dyu;
         Real phi = coef_p2 * divu;
         if (hazi) phi += hm_p2;
-        collide_g<Real>(sG + g_prev2 * 9 * NS + s, NS, Gout + (q2 * pitch + xn), plane, T_p2, dT_p2,
+        collide_g<Real>(StridedPops<Real>{sG + g_prev2 * 9 * NS + s, NS}, Gout + (q2 * pitch + xn), plane, T_p2, dT_p2,
                         sUx[f_prev2 * NS + s], sUy[f_prev2 * NS + s], phi, sC.omega_g);
       }
     }

@@ -31,7 +31,7 @@ EXPORTS = (
     "lbm_init_fields", "lbm_step", "lbm_step_async", "lbm_sync", "lbm_read_fields", "lbm_get_populations",
     "lbm_set_populations", "lbm_read_diagnostics", "lbm_read_diagnostics_range", "lbm_state_bytes",
     "lbm_save_state", "lbm_load_state",
-    "lbm_set_tiling", "lbm_set_kernel", "lbm_get_step", "lbm_launch_count", "lbm_get_stream", "lbm_critical_temperature",
+    "lbm_set_tiling", "lbm_set_kernel", "lbm_step_kernel", "lbm_get_step", "lbm_launch_count", "lbm_get_stream", "lbm_critical_temperature",
     "lbm_destroy", "lbm_status_string", "lbm_last_error", "lbm_step_noalloc",
     "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_member", "lbm_batch_size",
     "lbm_batch_set_tiling", "lbm_batch_set_kernel", "lbm_batch_get_tiling", "lbm_batch_autotune", "lbm_batch_step",
@@ -40,7 +40,8 @@ EXPORTS = (
 )
 
 
-KERNELS = {"auto": 0, "scalar": 1, "paired": 2}
+KERNELS = {"auto": 0, "scalar": 1, "paired": 2, "tma": 3}
+KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
 
 
 class LbmParams(ctypes.Structure):
@@ -102,6 +103,7 @@ def load(build_if_missing: bool = True):
         "lbm_load_state": (ctypes.c_int, [vp, vp, sz]),
         "lbm_set_tiling": (ctypes.c_int, [vp, i32, i32]),
         "lbm_set_kernel": (ctypes.c_int, [vp, i32]),
+        "lbm_step_kernel": (i32, [vp]),
         "lbm_get_step": (i64, [vp]),
         "lbm_launch_count": (i64, [vp]),
         "lbm_get_stream": (vp, [vp]),
@@ -230,8 +232,13 @@ class Lattice:
         self._check(self._L.lbm_set_tiling(self._h, int(cols), int(rows)))
 
     def set_kernel(self, kernel: str):
-        """FP32 step kernel form: "auto", "scalar" or "paired"."""
+        """FP32 step kernel form: "auto", "scalar", "paired" or "tma"."""
         self._check(self._L.lbm_set_kernel(self._h, KERNELS[kernel]))
+
+    @property
+    def step_kernel(self) -> str:
+        """The kernel form the step launches take ("scalar", "paired" or "tma")."""
+        return KERNEL_NAMES[int(self._L.lbm_step_kernel(self._h))]
 
     # --- stepping ---------------------------------------------------------
     def step(self, n: int = 1):

@@ -142,7 +142,7 @@ def test_fp64_single_phase_poiseuille():
         assert rel_err(got, ref, k) < FP64_TOL, k
 
 
-@pytest.mark.parametrize("kernel", ["paired", "scalar"])
+@pytest.mark.parametrize("kernel", ["paired", "scalar", "tma"])
 @pytest.mark.parametrize("tiling", [(128, 16), (64, 4), (256, 37)])
 def test_fp32_channel_thermal_1000_steps(tiling, kernel):
     nx, ny = 300, 37
@@ -170,7 +170,7 @@ def two_phase_fp32_checks(got, ref, lat_mass, orc_mass):
     assert abs(lat_mass - orc_mass) < FP32_TOL * orc_mass
 
 
-@pytest.mark.parametrize("kernel", ["paired", "scalar"])
+@pytest.mark.parametrize("kernel", ["paired", "scalar", "tma"])
 def test_fp32_periodic_droplet_1000_steps(kernel):
     nx, ny = 64, 64
     p = prm(nx, geometry="periodic", thermal=0, g_a=0.0)
@@ -184,7 +184,7 @@ def test_fp32_periodic_droplet_1000_steps(kernel):
     two_phase_fp32_checks(got, ref, lat.diagnostics()["mass"], orc.last_diag()["mass"])
 
 
-@pytest.mark.parametrize("kernel", ["paired", "scalar"])
+@pytest.mark.parametrize("kernel", ["paired", "scalar", "tma"])
 def test_fp32_thermal_droplet_1000_steps(kernel):
     nx, ny = 40, 40
     p = prm(nx, geometry="periodic", thermal=1, g_a=1e-4)
@@ -200,40 +200,80 @@ def test_fp32_thermal_droplet_1000_steps(kernel):
         assert rel_err(got, ref, k) < 1e-4, k
 
 
+@pytest.mark.parametrize("kernel", ["paired", "tma"])
 @pytest.mark.parametrize("nx,ny,geometry,tiling", [(151, 37, "channel", (128, 16)), (57, 23, "channel", (64, 5)),
-                                                   (63, 30, "walls", (128, 8)), (37, 41, "periodic", (64, 6))])
-def test_fp32_paired_kernel_odd_and_periodic_edges(nx, ny, geometry, tiling):
-    """The paired kernel's edge cases: an odd width (the last pair half outside the
-    domain), open ends inside a pair, and wrap-around pairs in periodic directions."""
+                                                   (63, 30, "walls", (128, 8)), (37, 41, "periodic", (64, 6)),
+                                                   (245, 17, "walls", (128, 4)), (121, 30, "periodic", (128, 4)),
+                                                   (3, 2, "channel", (128, 4))])
+def test_fp32_kernel_odd_and_periodic_edges(nx, ny, geometry, tiling, kernel):
+    """Edge cases of the paired and TMA step forms: an odd width (the last pair half
+    outside the domain), open ends inside a pair or a staged box, wrap-around in
+    periodic directions, a width that is an exact multiple of the 120-column tile
+    plus a ragged tail, bands of 4 rows, and the smallest channel (3 x 2)."""
     if geometry == "channel":
         p, fields = channel_case(nx, ny, heat_on_step=20)
     else:
         p = prm(nx, geometry=geometry, thermal=1, g_a=1e-4, heater_x0=3, heater_len=7, heat_on_step=10)
         fields = I.smooth_random(nx, ny, 5.95, 0.9 * oracle.Tc(p), seed=nx + 7 * ny, drho=0.002, du=0.005, dT=0.002)
-    lat, orc = run_pair(nx, ny, p, fields, 300, "fp32", tiling, kernel="paired")
+    lat, orc = run_pair(nx, ny, p, fields, 300, "fp32", tiling, kernel=kernel)
+    if kernel == "tma" and tiling[0] == 128:
+        assert lat.step_kernel == "tma"
     got, ref = lat.fields(), orc.fields()
     for k in ("rho", "ux", "uy", "T"):
         assert rel_err(got, ref, k) < FP32_TOL, k
     assert lat.diagnostics()["mass"] == pytest.approx(orc.last_diag()["mass"], rel=FP32_TOL)
 
 
-def test_fp32_paired_and_scalar_kernels_agree():
-    """The two FP32 step forms compute the same update; they differ only in the
-    order of a few roundings, so after 200 steps their populations agree to ~1e-6."""
+def test_fp32_step_kernel_forms_agree():
+    """The FP32 step forms compute the same update.  The TMA form does the scalar form's
+    arithmetic in the same order (only the staging of the pulled populations differs), so
+    their populations agree bit for bit; the paired form orders a few roundings
+    differently, so after 200 steps it agrees to ~1e-6."""
     L = lbm()
     nx, ny = 260, 41
     p, fields = channel_case(nx, ny, heat_on_step=10)
     pops = {}
-    for kernel in ("paired", "scalar"):
+    for kernel in ("paired", "scalar", "tma"):
         lat = L.Lattice(nx, ny, "fp32")
         lat.set_params(p)
         lat.set_kernel(kernel)
+        assert lat.step_kernel == kernel
         lat.init_fields(*fields)
         lat.step(200)
         pops[kernel] = lat.populations()
     for a, b in zip(pops["paired"], pops["scalar"]):
         assert np.abs(a - b).max() < 1e-5 * np.abs(b).max()
+    for a, b in zip(pops["tma"], pops["scalar"]):
+        assert np.array_equal(a, b)
     assert L.load().lbm_set_kernel(lat._h, 7) == 1  # LBM_EINVAL
+
+
+def test_step_kernel_resolution():
+    """LBM_KERNEL_AUTO takes the scalar form; a TMA request takes the TMA form for a lean
+    FP32 lattice on 128-column tiles and the scalar form where the TMA form does not apply."""
+    L = lbm()
+    nx, ny = 130, 20
+    p, _ = channel_case(nx, ny)
+    lat = L.Lattice(nx, ny, "fp32")
+    lat.set_params(p)
+    assert lat.step_kernel == "scalar"
+    lat.set_kernel("tma")
+    assert lat.step_kernel == "tma"
+    lat.set_tiling(64, 8)
+    assert lat.step_kernel == "scalar"
+    lat.set_tiling(128, 0)
+    lat.set_params(dict(p, bubble_stats=1))  # full form
+    assert lat.step_kernel == "scalar"
+    lat.set_params(dict(p, source_model=1))
+    assert lat.step_kernel == "scalar"
+    lat.set_kernel("paired")
+    assert lat.step_kernel == "scalar"  # no paired Hazi-Markus form
+    lat.set_params(p)
+    assert lat.step_kernel == "paired"
+    lat64 = L.Lattice(nx, ny, "fp64")
+    lat64.set_params(p)
+    lat64.set_kernel("tma")
+    assert lat64.step_kernel == "scalar"
 
 
 @pytest.mark.parametrize("precision,slack", [("fp64", 1), ("fp32", 3)])
