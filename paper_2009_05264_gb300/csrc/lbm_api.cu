@@ -16,17 +16,17 @@
 #include "pplbm.h"
 
 namespace pplbm {
-cudaError_t launch_lbm_f32(int, int, int, int, bool, const Inst*, const Tile*, int, cudaStream_t);
-cudaError_t launch_lbm_f64(int, int, int, bool, const Inst*, const Tile*, int, cudaStream_t);
+cudaError_t launch_lbm_f32(int, int, int, int, bool, const Inst*, const Tile*, int, cudaStream_t, const Inst*);
+cudaError_t launch_lbm_f64(int, int, int, bool, const Inst*, const Tile*, int, cudaStream_t, const Inst*);
 cudaError_t launch_init_from_fields_f32(const Inst*, int, int, const double*, int, cudaStream_t);
 cudaError_t launch_init_from_fields_f64(const Inst*, int, int, const double*, int, cudaStream_t);
 cudaError_t launch_init_builtin_f32(const Inst*, int, int, InitSpec, cudaStream_t);
 cudaError_t launch_init_builtin_f64(const Inst*, int, int, InitSpec, cudaStream_t);
 
 cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, int kernel, bool full, const Inst* d_inst,
-                       const Tile* d_tiles, int ntiles, cudaStream_t s) {
-  return fp64 ? launch_lbm_f64(thermal, cols, mode, full, d_inst, d_tiles, ntiles, s)
-              : launch_lbm_f32(thermal, cols, mode, kernel, full, d_inst, d_tiles, ntiles, s);
+                       const Tile* d_tiles, int ntiles, cudaStream_t s, const Inst* h_inst) {
+  return fp64 ? launch_lbm_f64(thermal, cols, mode, full, d_inst, d_tiles, ntiles, s, h_inst)
+              : launch_lbm_f32(thermal, cols, mode, kernel, full, d_inst, d_tiles, ntiles, s, h_inst);
 }
 cudaError_t launch_init_from_fields(int fp64, const Inst* d_inst, int nx, int ny, const double* d_fields,
                                     int has_T, cudaStream_t s) {
@@ -385,7 +385,7 @@ lbm_status launch(lbm_ctx* c, int mode) {
   cudaError_t e = launch_lbm(c->prec == LBM_FP64, c->thermal, step_tiles ? c->cols : kAuxCols, mode, kernel,
                              needs_full_step(c->hinst), c->d_inst,
                              step_tiles ? c->d_tiles_step : c->d_tiles_aux,
-                             step_tiles ? c->ntiles_step : c->ntiles_aux, c->stream);
+                             step_tiles ? c->ntiles_step : c->ntiles_aux, c->stream, &c->hinst);
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
   ++c->launches;
   return LBM_OK;

@@ -4,8 +4,8 @@
 namespace pplbm {
 
 cudaError_t launch_lbm_f64(int thermal, int cols, int mode, bool full, const Inst* d_inst, const Tile* d_tiles,
-                          int ntiles, cudaStream_t s) {
-  return launch_precision<double>(thermal, cols, mode, full, d_inst, d_tiles, ntiles, s);
+                          int ntiles, cudaStream_t s, const Inst* h_inst) {
+  return launch_precision<double>(thermal, cols, mode, full, d_inst, d_tiles, ntiles, s, h_inst);
 }
 
 int resident_ctas_f64(int thermal, int cols) { return resident_precision<double>(thermal, cols); }

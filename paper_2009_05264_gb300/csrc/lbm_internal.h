@@ -71,8 +71,10 @@ struct Tile {
 // kernel: a resolved form (resolve_kernel): LBM_KERNEL_SCALAR, _PAIRED or _TMA.
 // full: the instances use the pool geometry, the Hazi-Markus source or bubble statistics, which
 // only the step's full form handles (the lean form leaves them out of the hot loop).
+// h_inst: host copy of the launch's only instance (the lean scalar step then takes its
+// constants as a kernel parameter), or null for launches over several instances.
 cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, int kernel, bool full, const Inst* d_inst,
-                       const Tile* d_tiles, int ntiles, cudaStream_t s);
+                       const Tile* d_tiles, int ntiles, cudaStream_t s, const Inst* h_inst = nullptr);
 // Whether an instance needs the step's full form.
 inline bool needs_full_step(const Inst& I) {
   return I.geometry == GEOM_POOL || I.source_model != 0 || I.bubble_stats != 0;

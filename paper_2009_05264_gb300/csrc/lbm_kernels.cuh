@@ -175,7 +175,7 @@ struct KConst {
 };
 
 template <typename Real>
-__device__ __forceinline__ void fill_consts(KConst<Real>& c, const Inst& I, double rho_avg_prev) {
+__host__ __device__ inline void fill_consts(KConst<Real>& c, const Inst& I, double rho_avg_prev) {
   c.omega_f = Real(I.omega_f);
   c.omega_g = Real(I.omega_g);
   c.a = Real(I.a);
@@ -622,10 +622,15 @@ __device__ __forceinline__ void finish_step(const Inst& I, InstState* st, const 
 // FULL: the full form, which handles the pool geometry, the Hazi-Markus source and the bubble
 // statistics; the lean form (FULL = false, step mode only) compiles them out of the hot loop and
 // is launched only for instances that use none of them.
-template <typename Real, bool THERMAL, int B, int MODE, bool FULL = true>
+// PCONST: the launch covers one instance whose constants arrive as the kernel parameter kc
+// (read as constant-bank operands by the arithmetic instead of shared-memory loads); the
+// buoyancy reference rho_ref - rho_avg, which depends on the previous step, is still formed
+// on the device.  Otherwise every CTA converts its instance's constants into shared memory.
+template <typename Real, bool THERMAL, int B, int MODE, bool FULL = true, bool PCONST = false>
 __global__ void __launch_bounds__(B, (sizeof(Real) == 4 ? (B <= 64 ? 10 : (B <= 128 ? 5 : 2))
                                                         : (B <= 64 ? 4 : (B <= 128 ? 2 : 1))))
-lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) {
+lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
+                 const __grid_constant__ KConst<Real> kc) {
   constexpr int BLOCK = B;
   constexpr int W = out_cols<B>();
   constexpr int NS = B - 4;
@@ -636,7 +641,8 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
   Real* const sUx = sPsi + 3 * NS;                                  // [3][NS]
   Real* const sUy = sUx + 3 * NS;                                   // [3][NS]
   __shared__ Inst sI;
-  __shared__ KConst<Real> sC;
+  __shared__ KConst<Real> sCv;
+  __shared__ Real sRra;  // rho_ref - rho_avg of the previous step (buoyancy, Eq. 14)
   __shared__ double sRed[BLOCK / 32][NPART];
   __shared__ int sLast;
 
@@ -650,8 +656,13 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
   __syncthreads();
   InstState* st = sI.st;
   const long long step = st->step;
-  if (tid == 0) fill_consts<Real>(sC, sI, st->rho_avg[(step - 1) & 1]);
+  if (tid == 0) {
+    const double rho_avg_prev = st->rho_avg[(step - 1) & 1];
+    if (!PCONST) fill_consts<Real>(sCv, sI, rho_avg_prev);
+    sRra = Real(sI.rho_ref - rho_avg_prev);
+  }
   __syncthreads();
+  const KConst<Real>& sC = PCONST ? kc : sCv;
 
   const int nx = sI.nx, ny = sI.ny, pitch = sI.pitch;
   const int plane = (int)sI.plane;  // the host guarantees 9 * plane < 2^31
@@ -816,7 +827,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles)
                        sol_p ? Real(0) : Pp[sm], sol_m ? Real(0) : Pm[s], sol_m ? Real(0) : Pm[sp],
                        sol_m ? Real(0) : Pm[sm], sol_m, sol_p, sC, Fx, Fy);
       }
-      Fy -= (drho_p + sC.rho_ref_minus_avg) * sC.g_a;  // Eq. 14, gravity along -y
+      Fy -= (drho_p + sRra) * sC.g_a;  // Eq. 14, gravity along -y
       const Real inv_rho = fast_rcp(rho_p);
       const Real dux = Fx * inv_rho, duy = Fy * inv_rho;
       const Real uax = ux_p + Real(0.5) * dux, uay = uy_p + Real(0.5) * duy;  // Eq. 7
@@ -977,8 +988,9 @@ __global__ void lbm_init_builtin_kernel(const Inst* __restrict__ insts, InitSpec
 // ---------------------------------------------------------------------------
 // Host launchers for one storage precision.
 // ---------------------------------------------------------------------------
-template <typename Real, bool THERMAL, int B, int MODE, bool FULL>
-cudaError_t launch_one(const Inst* d_inst, const Tile* d_tiles, int ntiles, cudaStream_t s) {
+template <typename Real, bool THERMAL, int B, int MODE, bool FULL, bool PCONST = false>
+cudaError_t launch_one(const Inst* d_inst, const Tile* d_tiles, int ntiles, cudaStream_t s,
+                       const KConst<Real>& kc = KConst<Real>{}) {
   constexpr size_t smem = fused_smem_bytes<Real, THERMAL, B>();
   // the dynamic shared-memory opt-in is per device; remember which devices have it
   static unsigned long long configured = 0ull;
@@ -987,12 +999,12 @@ cudaError_t launch_one(const Inst* d_inst, const Tile* d_tiles, int ntiles, cuda
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(configured & bit)) {
-    e = cudaFuncSetAttribute(lbm_fused_kernel<Real, THERMAL, B, MODE, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+    e = cudaFuncSetAttribute(lbm_fused_kernel<Real, THERMAL, B, MODE, FULL, PCONST>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured |= bit;
   }
-  lbm_fused_kernel<Real, THERMAL, B, MODE, FULL><<<ntiles, B, smem, s>>>(d_inst, d_tiles);
+  lbm_fused_kernel<Real, THERMAL, B, MODE, FULL, PCONST><<<ntiles, B, smem, s>>>(d_inst, d_tiles, kc);
   return cudaGetLastError();
 }
 
@@ -1026,12 +1038,20 @@ int resident_precision(int thermal, int cols) {
   return 1;
 }
 
+// h_inst: the host copy of the launch's only instance (its constants then travel as a kernel
+// parameter to the lean step), or null for launches over several instances.
 template <typename Real, bool THERMAL, int B>
-cudaError_t launch_cols(int mode, bool full, const Inst* d_inst, const Tile* d_tiles, int ntiles, cudaStream_t s) {
+cudaError_t launch_cols(int mode, bool full, const Inst* d_inst, const Tile* d_tiles, int ntiles, cudaStream_t s,
+                        const Inst* h_inst) {
   switch (mode) {
     case MODE_STEP:
-      return full ? launch_one<Real, THERMAL, B, MODE_STEP, true>(d_inst, d_tiles, ntiles, s)
-                  : launch_one<Real, THERMAL, B, MODE_STEP, false>(d_inst, d_tiles, ntiles, s);
+      if (full) return launch_one<Real, THERMAL, B, MODE_STEP, true>(d_inst, d_tiles, ntiles, s);
+      if (h_inst) {
+        KConst<Real> kc;
+        fill_consts<Real>(kc, *h_inst, h_inst->rho_ref);
+        return launch_one<Real, THERMAL, B, MODE_STEP, false, true>(d_inst, d_tiles, ntiles, s, kc);
+      }
+      return launch_one<Real, THERMAL, B, MODE_STEP, false>(d_inst, d_tiles, ntiles, s);
     case MODE_FIELDS: return launch_one<Real, THERMAL, B, MODE_FIELDS, true>(d_inst, d_tiles, ntiles, s);
     case MODE_POPS: return launch_one<Real, THERMAL, B, MODE_POPS, true>(d_inst, d_tiles, ntiles, s);
     case MODE_MOMENTS: return launch_one<Real, THERMAL, B, MODE_MOMENTS, true>(d_inst, d_tiles, ntiles, s);
@@ -1041,19 +1061,19 @@ cudaError_t launch_cols(int mode, bool full, const Inst* d_inst, const Tile* d_t
 
 template <typename Real>
 cudaError_t launch_precision(int thermal, int cols, int mode, bool full, const Inst* d_inst, const Tile* d_tiles,
-                             int ntiles, cudaStream_t s) {
+                             int ntiles, cudaStream_t s, const Inst* h_inst) {
   if (ntiles <= 0) return cudaSuccess;
   if (thermal) {
     switch (cols) {
-      case 64: return launch_cols<Real, true, 64>(mode, full, d_inst, d_tiles, ntiles, s);
-      case 128: return launch_cols<Real, true, 128>(mode, full, d_inst, d_tiles, ntiles, s);
-      case 256: return launch_cols<Real, true, 256>(mode, full, d_inst, d_tiles, ntiles, s);
+      case 64: return launch_cols<Real, true, 64>(mode, full, d_inst, d_tiles, ntiles, s, h_inst);
+      case 128: return launch_cols<Real, true, 128>(mode, full, d_inst, d_tiles, ntiles, s, h_inst);
+      case 256: return launch_cols<Real, true, 256>(mode, full, d_inst, d_tiles, ntiles, s, h_inst);
     }
   } else {
     switch (cols) {
-      case 64: return launch_cols<Real, false, 64>(mode, full, d_inst, d_tiles, ntiles, s);
-      case 128: return launch_cols<Real, false, 128>(mode, full, d_inst, d_tiles, ntiles, s);
-      case 256: return launch_cols<Real, false, 256>(mode, full, d_inst, d_tiles, ntiles, s);
+      case 64: return launch_cols<Real, false, 64>(mode, full, d_inst, d_tiles, ntiles, s, h_inst);
+      case 128: return launch_cols<Real, false, 128>(mode, full, d_inst, d_tiles, ntiles, s, h_inst);
+      case 256: return launch_cols<Real, false, 256>(mode, full, d_inst, d_tiles, ntiles, s, h_inst);
     }
   }
   return cudaErrorInvalidValue;
