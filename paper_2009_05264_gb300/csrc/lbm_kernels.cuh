@@ -217,6 +217,13 @@ __host__ __device__ inline void fill_consts(KConst<Real>& c, const Inst& I, doub
   c.drho_vapor = Real(I.rho_vapor - I.rho_ref);
 }
 
+// Kernel parameter of a launch over one instance: its descriptor and converted constants.
+template <typename Real>
+struct KParams {
+  Inst I;
+  KConst<Real> C;
+};
+
 // ---------------------------------------------------------------------------
 // Node-level pieces of the step, shared by the kernels below.
 // ---------------------------------------------------------------------------
@@ -622,15 +629,16 @@ __device__ __forceinline__ void finish_step(const Inst& I, InstState* st, const 
 // FULL: the full form, which handles the pool geometry, the Hazi-Markus source and the bubble
 // statistics; the lean form (FULL = false, step mode only) compiles them out of the hot loop and
 // is launched only for instances that use none of them.
-// PCONST: the launch covers one instance whose constants arrive as the kernel parameter kc
-// (read as constant-bank operands by the arithmetic instead of shared-memory loads); the
-// buoyancy reference rho_ref - rho_avg, which depends on the previous step, is still formed
-// on the device.  Otherwise every CTA converts its instance's constants into shared memory.
+// PCONST: the launch covers one instance whose descriptor and converted constants arrive as
+// the kernel parameter kp (read as constant-bank operands instead of shared-memory loads, and
+// rematerialised from there instead of held in registers); the buoyancy reference
+// rho_ref - rho_avg, which depends on the previous step, is still formed on the device.
+// Otherwise every CTA copies its instance's descriptor and constants into shared memory.
 template <typename Real, bool THERMAL, int B, int MODE, bool FULL = true, bool PCONST = false>
 __global__ void __launch_bounds__(B, (sizeof(Real) == 4 ? (B <= 64 ? 10 : (B <= 128 ? 5 : 2))
                                                         : (B <= 64 ? 4 : (B <= 128 ? 2 : 1))))
 lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
-                 const __grid_constant__ KConst<Real> kc) {
+                 const __grid_constant__ KParams<Real> kp) {
   constexpr int BLOCK = B;
   constexpr int W = out_cols<B>();
   constexpr int NS = B - 4;
@@ -648,37 +656,38 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
 
   const int tid = threadIdx.x;
   const Tile tile = tiles[blockIdx.x];
-  {
+  if (!PCONST) {
     const int* src = reinterpret_cast<const int*>(insts + tile.inst);
     int* dst = reinterpret_cast<int*>(&sI);
     for (int k = tid; k < (int)(sizeof(Inst) / 4); k += BLOCK) dst[k] = src[k];
+    __syncthreads();
   }
-  __syncthreads();
-  InstState* st = sI.st;
+  const Inst& I = PCONST ? kp.I : sI;
+  InstState* st = I.st;
   const long long step = st->step;
   if (tid == 0) {
     const double rho_avg_prev = st->rho_avg[(step - 1) & 1];
-    if (!PCONST) fill_consts<Real>(sCv, sI, rho_avg_prev);
-    sRra = Real(sI.rho_ref - rho_avg_prev);
+    if (!PCONST) fill_consts<Real>(sCv, I, rho_avg_prev);
+    sRra = Real(I.rho_ref - rho_avg_prev);
   }
   __syncthreads();
-  const KConst<Real>& sC = PCONST ? kc : sCv;
+  const KConst<Real>& sC = PCONST ? kp.C : sCv;
 
-  const int nx = sI.nx, ny = sI.ny, pitch = sI.pitch;
-  const int plane = (int)sI.plane;  // the host guarantees 9 * plane < 2^31
+  const int nx = I.nx, ny = I.ny, pitch = I.pitch;
+  const int plane = (int)I.plane;  // the host guarantees 9 * plane < 2^31
   const bool local = st->local_read != 0;
-  const bool perx = sI.geometry != GEOM_CHANNEL;
-  const bool pery = sI.geometry == GEOM_PERIODIC;
-  const bool channel = sI.geometry == GEOM_CHANNEL;
-  const bool pool = FULL && sI.geometry == GEOM_POOL;
-  const bool multiphase = sI.multiphase != 0;
-  const bool hazi = FULL && THERMAL && sI.source_model == 1;
-  const bool bubbles = FULL && sI.bubble_stats != 0;
-  Real* __restrict__ rho_prev = static_cast<Real*>(sI.rho_prev);
-  const Real* __restrict__ Fin = static_cast<const Real*>(sI.f[step & 1]);
-  const Real* __restrict__ Gin = static_cast<const Real*>(sI.g[step & 1]);
-  Real* __restrict__ Fout = static_cast<Real*>(sI.f[(step + 1) & 1]);
-  Real* __restrict__ Gout = static_cast<Real*>(sI.g[(step + 1) & 1]);
+  const bool perx = I.geometry != GEOM_CHANNEL;
+  const bool pery = I.geometry == GEOM_PERIODIC;
+  const bool channel = I.geometry == GEOM_CHANNEL;
+  const bool pool = FULL && I.geometry == GEOM_POOL;
+  const bool multiphase = I.multiphase != 0;
+  const bool hazi = FULL && THERMAL && I.source_model == 1;
+  const bool bubbles = FULL && I.bubble_stats != 0;
+  Real* __restrict__ rho_prev = static_cast<Real*>(I.rho_prev);
+  const Real* __restrict__ Fin = static_cast<const Real*>(I.f[step & 1]);
+  const Real* __restrict__ Gin = static_cast<const Real*>(I.g[step & 1]);
+  Real* __restrict__ Fout = static_cast<Real*>(I.f[(step + 1) & 1]);
+  Real* __restrict__ Gout = static_cast<Real*>(I.g[(step + 1) & 1]);
   const Real T0 = sC.T0;
 
   // column owned by this thread: x0 - 2 + tid (two halo columns on each side of the W outputs)
@@ -718,7 +727,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
 
   Real acc_m = Real(0), acc_e = Real(0), acc_h = Real(0), acc_fi = Real(0), acc_fo = Real(0);
   float acc_va = 0.0f, acc_wv = 0.0f, acc_hv = 0.0f, acc_zv = 0.0f;  // vapour node counts (exact in FP32)
-  const bool zone_col = xn >= sI.heater_x0 - sI.heater_len && xn < sI.heater_x0 + 2 * sI.heater_len;
+  const bool zone_col = xn >= I.heater_x0 - I.heater_len && xn < I.heater_x0 + 2 * I.heater_len;
   // node scalars carried between iterations: row r-1 (f collision), row r-2 (g collision)
   Real rho_p = Real(1), drho_p = Real(0), ux_p = Real(0), uy_p = Real(0), T_p = T0, dT_p = Real(0), coef_p = Real(0);
   Real T_p2 = T0, dT_p2 = Real(0), coef_p2 = Real(0);
@@ -754,7 +763,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
       }
       const NodeBC nb{!pery && rn == 0, !pery && !pool && rn == ny - 1, inl, outl, pool && rn == ny - 1};
       if (!local && (nb.wlo || nb.whi || inl || outl || nb.top)) {
-        boundary_fill<Real, THERMAL>(fc, gc, nb, sI, sC, Gin, plane, pitch, rn * pitch + xn, xn, perx, step);
+        boundary_fill<Real, THERMAL>(fc, gc, nb, I, sC, Gin, plane, pitch, rn * pitch + xn, xn, perx, step);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
           fs[i * NS] = fc[i];
@@ -778,14 +787,14 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
         acc_m += ns.drho;
         if (THERMAL) {
           acc_e += ns.dT;
-          if (!pery && rn == 0 && xn >= sI.heater_x0 && xn < sI.heater_x0 + sI.heater_len) acc_h += ns.dT;
+          if (!pery && rn == 0 && xn >= I.heater_x0 && xn < I.heater_x0 + I.heater_len) acc_h += ns.dT;
         }
         if (bubbles && ns.drho < sC.drho_vapor) {
           acc_va += 1.0f;
           if (zone_col) acc_zv += 1.0f;
           if (!pery && rn == 0) {
             acc_wv += 1.0f;
-            if (xn >= sI.heater_x0 && xn < sI.heater_x0 + sI.heater_len) acc_hv += 1.0f;
+            if (xn >= I.heater_x0 && xn < I.heater_x0 + I.heater_len) acc_hv += 1.0f;
           }
         }
         if (MODE == MODE_STEP && channel && rn == ny / 2 && (xn == 1 || xn == nx - 2)) {
@@ -841,7 +850,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
         if (channel && xn == nx - 1) acc_fo += rho_p * uax;
       }
       if (MODE == MODE_FIELDS && out_q) {
-        double* out = static_cast<double*>(sI.f[(step + 1) & 1]);
+        double* out = static_cast<double*>(I.f[(step + 1) & 1]);
         const long long n = (long long)nx * ny;
         const long long oo = (long long)q * nx + xn;
         out[oo] = (double)rho_p;
@@ -901,7 +910,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
                        (double)acc_va, (double)acc_wv, (double)acc_hv, (double)acc_zv};
   block_sum<BLOCK>(acc, sRed);
   if (tid == 0) {
-    double* part = sI.partials + (long long)tile.local * NPART;
+    double* part = I.partials + (long long)tile.local * NPART;
 #pragma unroll
     for (int j = 0; j < NPART; ++j) part[j] = acc[j];
     __threadfence();
@@ -912,10 +921,10 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
   if (!sLast) return;
   __threadfence();
   double tot[NPART] = {};
-  fold_partials<BLOCK>(sI.partials, tile.ntiles, tot);
+  fold_partials<BLOCK>(I.partials, tile.ntiles, tot);
   __syncthreads();
   block_sum<BLOCK>(tot, sRed);
-  if (tid == 0) finish_step<THERMAL, MODE>(sI, st, tot, step);
+  if (tid == 0) finish_step<THERMAL, MODE>(I, st, tot, step);
 }
 
 // ---------------------------------------------------------------------------
@@ -990,7 +999,7 @@ __global__ void lbm_init_builtin_kernel(const Inst* __restrict__ insts, InitSpec
 // ---------------------------------------------------------------------------
 template <typename Real, bool THERMAL, int B, int MODE, bool FULL, bool PCONST = false>
 cudaError_t launch_one(const Inst* d_inst, const Tile* d_tiles, int ntiles, cudaStream_t s,
-                       const KConst<Real>& kc = KConst<Real>{}) {
+                       const KParams<Real>& kp = KParams<Real>{}) {
   constexpr size_t smem = fused_smem_bytes<Real, THERMAL, B>();
   // the dynamic shared-memory opt-in is per device; remember which devices have it
   static unsigned long long configured = 0ull;
@@ -1004,7 +1013,7 @@ cudaError_t launch_one(const Inst* d_inst, const Tile* d_tiles, int ntiles, cuda
     if (e != cudaSuccess) return e;
     configured |= bit;
   }
-  lbm_fused_kernel<Real, THERMAL, B, MODE, FULL, PCONST><<<ntiles, B, smem, s>>>(d_inst, d_tiles, kc);
+  lbm_fused_kernel<Real, THERMAL, B, MODE, FULL, PCONST><<<ntiles, B, smem, s>>>(d_inst, d_tiles, kp);
   return cudaGetLastError();
 }
 
@@ -1047,9 +1056,10 @@ cudaError_t launch_cols(int mode, bool full, const Inst* d_inst, const Tile* d_t
     case MODE_STEP:
       if (full) return launch_one<Real, THERMAL, B, MODE_STEP, true>(d_inst, d_tiles, ntiles, s);
       if (h_inst) {
-        KConst<Real> kc;
-        fill_consts<Real>(kc, *h_inst, h_inst->rho_ref);
-        return launch_one<Real, THERMAL, B, MODE_STEP, false, true>(d_inst, d_tiles, ntiles, s, kc);
+        KParams<Real> kp;
+        kp.I = *h_inst;
+        fill_consts<Real>(kp.C, *h_inst, h_inst->rho_ref);
+        return launch_one<Real, THERMAL, B, MODE_STEP, false, true>(d_inst, d_tiles, ntiles, s, kp);
       }
       return launch_one<Real, THERMAL, B, MODE_STEP, false>(d_inst, d_tiles, ntiles, s);
     case MODE_FIELDS: return launch_one<Real, THERMAL, B, MODE_FIELDS, true>(d_inst, d_tiles, ntiles, s);
