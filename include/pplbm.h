@@ -231,7 +231,7 @@ lbm_status lbm_set_tiling(lbm_ctx* ctx, int32_t cols, int32_t rows);
  *     128-column tiles and the step's lean form (no pool geometry, Hazi-Markus source
  *     or bubble statistics); other lattices take the scalar form.  A bulk copy that does
  *     not complete within a bounded wait makes lbm_sync return LBM_ETIMEOUT.  Its results
- *     are bit-identical to the scalar form's; on GB300 it runs about 10 % slower (its
+ *     are bit-identical to the scalar form's; on GB300 it runs about 6 % slower (its
  *     warps wait on rows that arrive later than the per-thread copies do).
  * FP64 lattices, and lbm_step_noalloc on caller-laid-out buffers, always use the scalar
  * form.  LBM_EINVAL for other values. */

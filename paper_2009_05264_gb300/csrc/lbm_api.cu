@@ -837,8 +837,7 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t bytes) {
 
 lbm_status lbm_set_kernel(lbm_ctx* c, int32_t kernel) {
   if (!c) return LBM_EINVAL;
-  if (kernel != LBM_KERNEL_AUTO && kernel != LBM_KERNEL_SCALAR && kernel != LBM_KERNEL_PAIRED &&
-      kernel != LBM_KERNEL_TMA)
+  if (kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_TMA)
     return fail(c, LBM_EINVAL, "kernel must be LBM_KERNEL_AUTO, _SCALAR, _PAIRED or _TMA");
   c->kernel = kernel;
   if (!c->rows_default) return LBM_OK;

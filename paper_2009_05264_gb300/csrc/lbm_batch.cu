@@ -286,8 +286,7 @@ lbm_status lbm_batch_set_tiling(lbm_batch* b, int32_t cols, int32_t rows) {
 
 lbm_status lbm_batch_set_kernel(lbm_batch* b, int32_t kernel) {
   if (!b) return LBM_EINVAL;
-  if (kernel != LBM_KERNEL_AUTO && kernel != LBM_KERNEL_SCALAR && kernel != LBM_KERNEL_PAIRED &&
-      kernel != LBM_KERNEL_TMA)
+  if (kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_TMA)
     return bfail(b, LBM_EINVAL, "kernel must be LBM_KERNEL_AUTO, _SCALAR, _PAIRED or _TMA");
   b->kernel = kernel;
   b->dirty = true;  // default band heights depend on the kernel's occupancy; the graph names the kernel

@@ -8,13 +8,13 @@ namespace pplbm {
 cudaError_t launch_lbm_f32(int thermal, int cols, int mode, int kernel, bool full, const Inst* d_inst,
                           const Tile* d_tiles, int ntiles, cudaStream_t s, const Inst* h_inst) {
   if (mode == MODE_STEP && kernel == LBM_KERNEL_PAIRED) return launch_pair(thermal, cols, d_inst, d_tiles, ntiles, s);
-  if (mode == MODE_STEP && kernel == LBM_KERNEL_TMA) return launch_tma(thermal, cols, d_inst, d_tiles, ntiles, s);
+  if (mode == MODE_STEP && kernel == LBM_KERNEL_TMA) return launch_tma(thermal, cols, d_inst, d_tiles, ntiles, s, h_inst);
   return launch_precision<float>(thermal, cols, mode, full, d_inst, d_tiles, ntiles, s, h_inst);
 }
 
 int resident_ctas_f32(int thermal, int cols, int kernel) {
   if (kernel == LBM_KERNEL_PAIRED) return resident_pair(thermal, cols);
-  if (kernel == LBM_KERNEL_TMA && cols == TMA_COLS) return resident_tma(thermal);
+  if (kernel == LBM_KERNEL_TMA && cols == ST_COLS) return resident_tma(thermal);
   return resident_precision<float>(thermal, cols);
 }
 

@@ -1,52 +1,47 @@
 // FP32 fused step with its populations staged by the Tensor Memory Accelerator.
 //
 // Same time step as lbm_fused_kernel (Sec. 2 of Mukherjee, Basu & Mondal, arXiv
-// 2009.05264, boundary conditions of Sec. 2.C), lean form, 128 threads per CTA.
-// The scalar kernel stages each node's 18 pulled populations with 18 per-thread
-// cp.async copies, each with its own address arithmetic.  Here one thread of the CTA
-// issues, per row, one bulk tensor copy (cp.async.bulk.tensor) per population
-// plane: a 128-column box of plane i taken from row r - c_iy, starting at column
-// x0 - 4, into a shared-memory row of the ring; the pull shift along x is then a
-// constant offset of the shared-memory read (node x of plane i sits at position
-// x - x0 + 4 - c_ix).  Completion is tracked by one mbarrier per ring slot
-// (expect-tx of the 9 boxes' bytes), so the per-thread address and issue work of
-// the copies disappears from the hot loop.
+// 2009.05264, boundary conditions of Sec. 2.C), lean form, 128 threads per CTA.  The
+// scalar kernel stages, per thread, the 18 populations its node pulls, with one
+// 4-byte cp.async each (18 copies and their address arithmetic per node).  Here the CTA
+// stages, per row, the 128 columns [x0 - 4, x0 + 124) of each population plane i taken
+// from row r - c_iy into a shared-memory row of a ring; the pull's shift along x is then
+// a constant offset of the shared-memory read (node x of plane i sits at position
+// x - x0 + 4 - c_ix).  One thread issues one bulk tensor copy (cp.async.bulk.tensor.3d)
+// per plane-row; completion is one mbarrier per ring slot (expect-tx of the 9 boxes'
+// bytes), and every thread waits on the slot's barrier (bounded).
 //
-// Nodes whose pull leaves the tensor box or needs a boundary condition (the two
-// outermost rows and columns of the lattice, periodic wrap-around, and the first
-// step after an initialisation, whose buffer holds post-stream populations) are
-// "special": their thread pulls them with plain loads as the scalar kernel does,
-// completes them with boundary_fill, and writes the result back into its own
-// positions of the staged rows (one position per plane per node, so no two threads
-// write the same element), followed by a generic-to-async proxy fence before the
-// slot is refilled.
+// Nodes whose pull leaves the staged box or needs a boundary condition (the two
+// outermost rows and columns of the lattice, periodic wrap-around, and the first step
+// after an initialisation, whose buffer holds post-stream populations) are "special":
+// their thread pulls them with plain loads as the scalar kernel does, completes them
+// with boundary_fill, and writes the result back into its own positions of the staged
+// rows (one position per plane per node, so no two threads write the same element),
+// then fences its generic-proxy writes before the slot is refilled by the async proxy.
 //
-// Ring slots: f of rows r + 1 (in flight), r and r - 1 (3 slots); g of rows r + 1
-// down to r - 3 (5 slots).  Row r + 1 is issued at the top of iteration r with no
-// barrier since the previous iteration's phase C, which still reads g of row r - 3,
-// so that slot must not be the one refilled.
-// Every wait on an mbarrier is bounded; a wait that gives up sets STATUS_TIMEOUT,
-// the CTA leaves the row loop, drains its copies in flight (again bounded) and
-// still posts its partials, so the launch ends and the host reports LBM_ETIMEOUT.
+// Ring slots: f of rows r + 1 (in flight), r and r - 1 (3 slots); g of rows r + 1 down
+// to r - 3 (5 slots).  Row r + 1 is issued at the top of iteration r with no barrier
+// since the previous iteration's phase C, which still reads g of row r - 3, so that slot
+// must not be the one refilled.  Every mbarrier wait is bounded; a wait that gives up sets STATUS_TIMEOUT, the CTA leaves the row loop, drains its copies in
+// flight (again bounded) and still posts its partials, so the launch ends and the host
+// reports LBM_ETIMEOUT.
 #pragma once
 
 #include "lbm_kernels.cuh"
 
 namespace pplbm {
 
-constexpr int TMA_COLS = 128;                              // threads per CTA and columns per staged box
-constexpr int TMA_AHEAD = 1;                               // rows in flight ahead of the row pulled
-constexpr int TMA_ISSUERS = 1;                             // warps whose lane 0 issues a row's copies
-constexpr int TMA_FS = 2 + TMA_AHEAD;                      // f ring slots: rows r + AHEAD .. r - 1
-constexpr int TMA_GS = 4 + TMA_AHEAD;                      // g ring slots: rows r + AHEAD .. r - 3
-constexpr int TMA_RW = 9 * TMA_COLS;                       // floats per staged row of one population set
-constexpr unsigned TMA_ROW_BYTES = TMA_RW * sizeof(float); // bytes the 9 boxes of one row deliver
-constexpr long long TMA_WAIT_LIMIT = 1ll << 22;            // polls of a bounded mbarrier wait
+constexpr int ST_COLS = 128;                             // threads per CTA and columns per staged row
+constexpr int ST_FS = 3;                                 // f ring slots
+constexpr int ST_GS = 5;                                 // g ring slots
+constexpr int ST_RW = 9 * ST_COLS;                       // floats per staged row of one population set
+constexpr unsigned ST_ROW_BYTES = ST_RW * sizeof(float); // bytes of one row of one population set
+constexpr long long TMA_WAIT_LIMIT = 1ll << 22;          // polls of a bounded mbarrier wait
 
 template <bool THERMAL>
 constexpr size_t tma_smem_bytes() {
   // 128 bytes of slack to align the rings to 128 bytes
-  return 128 + sizeof(float) * ((size_t)TMA_RW * (TMA_FS + (THERMAL ? TMA_GS : 0)) + 9 * (TMA_COLS - 4));
+  return 128 + sizeof(float) * ((size_t)ST_RW * (ST_FS + (THERMAL ? ST_GS : 0)) + 9 * (ST_COLS - 4));
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -97,12 +92,11 @@ __device__ __forceinline__ void tma_load_3d(float* dst, const void* tmap, int x,
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
-
 // The pulled populations of one node in a staged row: plane i at the node's column
 // shifted by -c_ix (row points at the node's unshifted position in plane 0).
 struct ShiftedPops {
   const float* row;
-  __device__ __forceinline__ float operator()(int i) const { return row[i * TMA_COLS - lat_cx(i)]; }
+  __device__ __forceinline__ float operator()(int i) const { return row[i * ST_COLS - lat_cx(i)]; }
 };
 
 // Plain-load pull of one node (the scalar kernel's pull, synchronous): interior and
@@ -150,64 +144,69 @@ __device__ __forceinline__ void pull_direct(float (&fc)[9], float (&gc)[9], cons
   }
 }
 
-// Lean FP32 step (no pool geometry, Hazi-Markus source or bubble counters), one
-// step of every tile of the launch.  Tiles must be 120 columns wide (x0 a multiple
-// of 120) and each instance must carry its four tensor maps (f and g, both buffers).
-template <bool THERMAL>
-__global__ void __launch_bounds__(TMA_COLS, 5)
-lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) {
-  constexpr int B = TMA_COLS;
+// Lean FP32 step (no pool geometry, Hazi-Markus source or bubble counters), one step of
+// every tile of the launch.  Tiles must be 120 columns wide (x0 a multiple of 120) and each
+// instance must carry its four tensor maps (f and g, both buffers).  PCONST: the launch
+// covers one instance whose descriptor and converted constants arrive as the kernel
+// parameter kp (as in lbm_fused_kernel).
+template <bool THERMAL, bool PCONST>
+__global__ void __launch_bounds__(ST_COLS, 5)
+lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
+               const __grid_constant__ KParams<float> kp) {
+  constexpr int B = ST_COLS;
   constexpr int W = out_cols<B>();
   constexpr int NS = B - 4;
   extern __shared__ unsigned char tma_dyn_smem[];
-  float* const sF = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(tma_dyn_smem) + 127) & ~uintptr_t(127));
-  float* const sG = sF + TMA_FS * TMA_RW;                    // [TMA_GS][9][B]
-  float* const sPsi = sG + (THERMAL ? TMA_GS * TMA_RW : 0);  // [3][NS]
+  float* const sF =
+      reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(tma_dyn_smem) + 127) & ~uintptr_t(127));  // [FS][9][B]
+  float* const sG = sF + ST_FS * ST_RW;                    // [GS][9][B]
+  float* const sPsi = sG + (THERMAL ? ST_GS * ST_RW : 0);  // [3][NS]
   float* const sUx = sPsi + 3 * NS;
   float* const sUy = sUx + 3 * NS;
-  __shared__ __align__(8) unsigned long long fbar[TMA_FS];
-  __shared__ __align__(8) unsigned long long gbar[TMA_GS];
+  __shared__ __align__(8) unsigned long long fbar[ST_FS];
+  __shared__ __align__(8) unsigned long long gbar[ST_GS];
   __shared__ Inst sI;
-  __shared__ KConst<float> sC;
+  __shared__ KConst<float> sCv;
+  __shared__ float sRra;  // rho_ref - rho_avg of the previous step (buoyancy, Eq. 14)
   __shared__ double sRed[B / 32][NPART];
   __shared__ int sLast;
   __shared__ int sAbort;
 
   const int tid = threadIdx.x;
   const Tile tile = tiles[blockIdx.x];
-  {
+  if (!PCONST) {
     const int* src = reinterpret_cast<const int*>(insts + tile.inst);
     int* dst = reinterpret_cast<int*>(&sI);
     for (int k = tid; k < (int)(sizeof(Inst) / 4); k += B) dst[k] = src[k];
+    __syncthreads();
   }
-  __syncthreads();
-  InstState* st = sI.st;
+  const Inst& I = PCONST ? kp.I : sI;
+  InstState* st = I.st;
   const long long step = st->step;
   const bool local = st->local_read != 0;
   if (tid == 0) {
-    fill_consts<float>(sC, sI, st->rho_avg[(step - 1) & 1]);
+    const double rho_avg_prev = st->rho_avg[(step - 1) & 1];
+    if (!PCONST) fill_consts<float>(sCv, I, rho_avg_prev);
+    sRra = float(I.rho_ref - rho_avg_prev);
     sAbort = 0;
-    for (int j = 0; j < TMA_FS; ++j) mbar_init(&fbar[j], 1);
-    for (int j = 0; j < TMA_GS; ++j) mbar_init(&gbar[j], 1);
+    for (int j = 0; j < ST_FS; ++j) mbar_init(&fbar[j], 1);
+    for (int j = 0; j < ST_GS; ++j) mbar_init(&gbar[j], 1);
     mbar_init_fence();
   }
   __syncthreads();
+  const KConst<float>& C = PCONST ? kp.C : sCv;
 
-  const int nx = sI.nx, ny = sI.ny, pitch = sI.pitch;
-  const int plane = (int)sI.plane;
-  const bool perx = sI.geometry != GEOM_CHANNEL;
-  const bool pery = sI.geometry == GEOM_PERIODIC;
-  const bool channel = sI.geometry == GEOM_CHANNEL;
-  const bool multiphase = sI.multiphase != 0;
-  const float* __restrict__ Fin = static_cast<const float*>(sI.f[step & 1]);
-  const float* __restrict__ Gin = static_cast<const float*>(sI.g[step & 1]);
-  float* __restrict__ Fout = static_cast<float*>(sI.f[(step + 1) & 1]);
-  float* __restrict__ Gout = static_cast<float*>(sI.g[(step + 1) & 1]);
-  // tensor maps: f of buffers 0 and 1, then g of buffers 0 and 1 (128 bytes each)
-  const unsigned char* tm = static_cast<const unsigned char*>(sI.tmaps);
-  const void* fmap = tm + 128 * (step & 1);
-  const void* gmap = tm + 128 * (2 + (step & 1));
-  const float T0 = sC.T0;
+  const int nx = I.nx, ny = I.ny, pitch = I.pitch;
+  const int plane = (int)I.plane;
+  const bool perx = I.geometry != GEOM_CHANNEL;
+  const bool pery = I.geometry == GEOM_PERIODIC;
+  const bool channel = I.geometry == GEOM_CHANNEL;
+  const bool multiphase = I.multiphase != 0;
+  const float* __restrict__ Fin = static_cast<const float*>(I.f[step & 1]);
+  const float* __restrict__ Gin = static_cast<const float*>(I.g[step & 1]);
+  float* __restrict__ Fout = static_cast<float*>(I.f[(step + 1) & 1]);
+  float* __restrict__ Gout = static_cast<float*>(I.g[(step + 1) & 1]);
+  const float T0 = C.T0;
 
   const int s = tid < NS ? tid : 0;
   const int xc = tile.x0 - 2 + s;
@@ -224,30 +223,27 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) {
   const int sp = (!perx && xc == nx - 1) ? s : s + 1;
   const bool inl = channel && xn == 0;
   const bool outl = channel && xn == nx - 1;
-  // columns whose pull stays inside the box and needs no boundary condition
+  // columns whose pull stays inside the staged row and needs no boundary condition
   const bool col_plain = !local && xc >= 1 && xc <= nx - 2;
 
   const int nrow = tile.y1 - tile.y0;
   const int kend = nrow + 4;
-  const int xbox = tile.x0 - 4;  // first column of every staged box (16-byte aligned)
+  const int xbox = tile.x0 - 4;  // first column of every staged row (16-byte aligned)
 
-  // The boxes of row k (f, and g when thermal) into ring slots fsl / gsl.  Lane 0 of each of
-  // the first TMA_ISSUERS warps issues the planes i = warp (mod TMA_ISSUERS); warp 0 also
-  // posts the expected bytes (the barrier's transaction count may run ahead of or behind
-  // the copies' completions; the phase completes once both balance).
-  const int warp = tid >> 5;
-  const bool issuer = (tid & 31) == 0 && warp < TMA_ISSUERS;
+  // Row k (f, and g when thermal) into ring slots fsl / gsl (thread 0): nine boxes per
+  // population set, one barrier per set.
   auto issue_row = [&](int k, int fsl, int gsl) {
     const int r = tile.y0 - 2 + k;
-    if (warp == 0) {
-      mbar_arrive_expect_tx(&fbar[fsl], TMA_ROW_BYTES);
-      if (THERMAL) mbar_arrive_expect_tx(&gbar[gsl], TMA_ROW_BYTES);
-    }
+    const unsigned char* tm = static_cast<const unsigned char*>(I.tmaps);
+    const void* fmap = tm + 128 * (step & 1);  // f of buffers 0 and 1, then g (128 bytes each)
+    const void* gmap = tm + 128 * (2 + (step & 1));
+    mbar_arrive_expect_tx(&fbar[fsl], ST_ROW_BYTES);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      if (i % TMA_ISSUERS != warp) continue;
-      tma_load_3d(sF + fsl * TMA_RW + i * B, fmap, xbox, r - lat_cy(i), i, &fbar[fsl]);
-      if (THERMAL) tma_load_3d(sG + gsl * TMA_RW + i * B, gmap, xbox, r - lat_cy(i), i, &gbar[gsl]);
+    for (int i = 0; i < 9; ++i) tma_load_3d(sF + fsl * ST_RW + i * B, fmap, xbox, r - lat_cy(i), i, &fbar[fsl]);
+    if (THERMAL) {
+      mbar_arrive_expect_tx(&gbar[gsl], ST_ROW_BYTES);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) tma_load_3d(sG + gsl * ST_RW + i * B, gmap, xbox, r - lat_cy(i), i, &gbar[gsl]);
     }
   };
 
@@ -255,23 +251,20 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) {
   float rho_p = 1.0f, drho_p = 0.0f, ux_p = 0.0f, uy_p = 0.0f, T_p = T0, dT_p = 0.0f, coef_p = 0.0f;
   float T_p2 = T0, dT_p2 = 0.0f, coef_p2 = 0.0f;
 
-  // ring slots of row k: psi / u (mod 3), staged f (mod TMA_FS) and g (mod TMA_GS), with the
+  // ring slots of row k: psi / u (mod 3), staged f (mod ST_FS) and g (mod ST_GS), with the
   // parities of the f and g barrier phases (row k's phase of slot k mod n is (k / n) & 1)
   int p_cur = 0, f_cur = 0, g_cur = 0;
   unsigned f_par = 0u, g_par = 0u;
-  if (!local && issuer)
-    for (int j = 0; j < TMA_AHEAD && j < kend; ++j) issue_row(j, j, j);
+  if (!local && tid == 0) issue_row(0, 0, 0);
   int k = 0;
   for (; k < kend; ++k) {
     const int r = tile.y0 - 2 + k;
-    const int p_prev = (p_cur == 0) ? 2 : p_cur - 1;    // row r - 1
-    const int p_prev2 = (p_prev == 0) ? 2 : p_prev - 1; // row r - 2 (and r + 1)
-    const int f_prev = (f_cur == 0) ? TMA_FS - 1 : f_cur - 1;
-    const int g_prev2 = (g_cur >= 2) ? g_cur - 2 : g_cur + TMA_GS - 2;
-    if (!local && issuer && k + TMA_AHEAD < kend) {
-      const int fi = f_cur + TMA_AHEAD, gi = g_cur + TMA_AHEAD;
-      issue_row(k + TMA_AHEAD, fi >= TMA_FS ? fi - TMA_FS : fi, gi >= TMA_GS ? gi - TMA_GS : gi);
-    }
+    const int p_prev = (p_cur == 0) ? 2 : p_cur - 1;     // row r - 1
+    const int p_prev2 = (p_prev == 0) ? 2 : p_prev - 1;  // row r - 2 (and r + 1)
+    const int f_prev = (f_cur == 0) ? ST_FS - 1 : f_cur - 1;
+    const int g_prev2 = (g_cur >= 2) ? g_cur - 2 : g_cur + ST_GS - 2;
+    if (!local && tid == 0 && k + 1 < kend)
+      issue_row(k + 1, f_cur == ST_FS - 1 ? 0 : f_cur + 1, g_cur == ST_GS - 1 ? 0 : g_cur + 1);
     if (!local) {
       bool ok = mbar_wait(&fbar[f_cur], f_par);
       if (THERMAL) ok = mbar_wait(&gbar[g_cur], g_par) && ok;
@@ -288,8 +281,8 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) {
     ns.rho = 1.0f; ns.drho = 0.0f; ns.ux = 0.0f; ns.uy = 0.0f;
     ns.T = T0; ns.dT = 0.0f; ns.coef = 0.0f; ns.dpsi = 0.0f;
     if (col_ok && row_ok) {
-      float* const fs = sF + f_cur * TMA_RW + (s + 2);
-      float* const gs = sG + g_cur * TMA_RW + (s + 2);
+      float* const fs = sF + f_cur * ST_RW + (s + 2);
+      float* const gs = sG + g_cur * ST_RW + (s + 2);
       float fc[9], gc[9];
       const bool plain = col_plain && r >= 1 && r <= ny - 2;
       if (plain) {
@@ -302,7 +295,7 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) {
         const NodeBC nb{!pery && rn == 0, !pery && rn == ny - 1, inl, outl, false};
         pull_direct<THERMAL>(fc, gc, Fin, Gin, plane, pitch, xn, rn, nx, ny, perx, pery, local, nb);
         if (!local && (nb.wlo || nb.whi || inl || outl))
-          boundary_fill<float, THERMAL>(fc, gc, nb, sI, sC, Gin, plane, pitch, rn * pitch + xn, xn, perx, step);
+          boundary_fill<float, THERMAL>(fc, gc, nb, I, C, Gin, plane, pitch, rn * pitch + xn, xn, perx, step);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
           fs[i * B - lat_cx(i)] = fc[i];
@@ -310,7 +303,7 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) {
         }
         fence_proxy_async_smem();
       }
-      ns = node_state<float, THERMAL>(fc, gc, sC, multiphase, false);
+      ns = node_state<float, THERMAL>(fc, gc, C, multiphase, false);
       if (ns.bad) atomicOr(&st->status, STATUS_UNSTABLE);
       sPsi[p_cur * NS + s] = ns.dpsi;
       const bool out_row = r >= tile.y0 && r < tile.y1;
@@ -318,7 +311,7 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) {
         acc_m += ns.drho;
         if (THERMAL) {
           acc_e += ns.dT;
-          if (!pery && rn == 0 && xn >= sI.heater_x0 && xn < sI.heater_x0 + sI.heater_len) acc_h += ns.dT;
+          if (!pery && rn == 0 && xn >= I.heater_x0 && xn < I.heater_x0 + I.heater_len) acc_h += ns.dT;
         }
         if (channel && rn == ny / 2 && (xn == 1 || xn == nx - 2)) {
           if (xn == 1) st->p_probe[0] = (double)ns.p;
@@ -341,17 +334,17 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) {
         const float* Pp = sPsi + p_cur * NS;
         const float* Pm = sPsi + p_prev2 * NS;
         sc_force<float>(P0[s], P0[sp], P0[sm], sol_p ? 0.0f : Pp[s], sol_p ? 0.0f : Pp[sp], sol_p ? 0.0f : Pp[sm],
-                        sol_m ? 0.0f : Pm[s], sol_m ? 0.0f : Pm[sp], sol_m ? 0.0f : Pm[sm], sol_m, sol_p, sC, Fx, Fy);
+                        sol_m ? 0.0f : Pm[s], sol_m ? 0.0f : Pm[sp], sol_m ? 0.0f : Pm[sm], sol_m, sol_p, C, Fx, Fy);
       }
-      Fy -= (drho_p + sC.rho_ref_minus_avg) * sC.g_a;  // Eq. 14, gravity along -y
+      Fy -= (drho_p + sRra) * C.g_a;  // Eq. 14, gravity along -y
       const float inv_rho = fast_rcp(rho_p);
       const float dux = Fx * inv_rho, duy = Fy * inv_rho;
       const float uax = ux_p + 0.5f * dux, uay = uy_p + 0.5f * duy;  // Eq. 7
       sUx[p_prev * NS + s] = uax;
       sUy[p_prev * NS + s] = uay;
       if (out_col && q >= tile.y0 && q < tile.y1) {
-        collide_f<float>(ShiftedPops{sF + f_prev * TMA_RW + (s + 2)}, Fout + (q * pitch + xn), plane, rho_p, drho_p,
-                         ux_p, uy_p, dux, duy, sC.omega_f);
+        collide_f<float>(ShiftedPops{sF + f_prev * ST_RW + (s + 2)}, Fout + (q * pitch + xn), plane, rho_p, drho_p,
+                         ux_p, uy_p, dux, duy, C.omega_f);
         if (channel && xn == 0) acc_fi += rho_p * uax;
         if (channel && xn == nx - 1) acc_fo += rho_p * uax;
       }
@@ -372,8 +365,8 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) {
           dyu = (wall_lo && wall_hi) ? 0.0f : (wall_lo ? uyN - uyC : uyC - uyS);
         }
         const float divu = 0.5f * (uxE - uxW) + dyu;
-        collide_g<float>(ShiftedPops{sG + g_prev2 * TMA_RW + (s + 2)}, Gout + (q2 * pitch + xn), plane, T_p2, dT_p2,
-                         sUx[p_prev2 * NS + s], sUy[p_prev2 * NS + s], coef_p2 * divu, sC.omega_g);
+        collide_g<float>(ShiftedPops{sG + g_prev2 * ST_RW + (s + 2)}, Gout + (q2 * pitch + xn), plane, T_p2, dT_p2,
+                         sUx[p_prev2 * NS + s], sUy[p_prev2 * NS + s], coef_p2 * divu, C.omega_g);
       }
     }
 
@@ -388,30 +381,28 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) {
     dT_p = ns.dT;
     coef_p = ns.coef;
     p_cur = (p_cur == 2) ? 0 : p_cur + 1;
-    if (++f_cur == TMA_FS) {
+    if (++f_cur == ST_FS) {
       f_cur = 0;
       f_par ^= 1u;
     }
-    if (++g_cur == TMA_GS) {
+    if (++g_cur == ST_GS) {
       g_cur = 0;
       g_par ^= 1u;
     }
   }
-  if (k < kend && !local && tid == 0) {
-    // aborted at row k: let the copies of rows k + 1 .. k + TMA_AHEAD, possibly still in
-    // flight, land before the CTA's shared memory is released (row j: slot j mod depth,
-    // phase parity (j / depth) & 1)
-    for (int j = k + 1; j <= k + TMA_AHEAD && j < kend; ++j) {
-      mbar_wait(&fbar[j % TMA_FS], (j / TMA_FS) & 1);
-      if (THERMAL) mbar_wait(&gbar[j % TMA_GS], (j / TMA_GS) & 1);
-    }
+  if (k + 1 < kend && !local && tid == 0) {
+    // aborted at row k: let the copies of row k + 1, possibly still in flight, land before
+    // the CTA's shared memory is released (row j: slot j mod depth, parity (j / depth) & 1)
+    const int j = k + 1;
+    mbar_wait(&fbar[j % ST_FS], (j / ST_FS) & 1);
+    if (THERMAL) mbar_wait(&gbar[j % ST_GS], (j / ST_GS) & 1);
   }
 
   // ---------------- per-tile partials and the last-CTA fold ----------------
   double acc[NPART] = {(double)acc_m, (double)acc_e, (double)acc_h, (double)acc_fi, (double)acc_fo, 0.0, 0.0, 0.0, 0.0};
   block_sum<B>(acc, sRed);
   if (tid == 0) {
-    double* part = sI.partials + (long long)tile.local * NPART;
+    double* part = I.partials + (long long)tile.local * NPART;
 #pragma unroll
     for (int j = 0; j < NPART; ++j) part[j] = acc[j];
     __threadfence();
@@ -422,43 +413,55 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) {
   if (!sLast) return;
   __threadfence();
   double tot[NPART] = {};
-  fold_partials<B>(sI.partials, tile.ntiles, tot);
+  fold_partials<B>(I.partials, tile.ntiles, tot);
   __syncthreads();
   block_sum<B>(tot, sRed);
-  if (tid == 0) finish_step<THERMAL, MODE_STEP>(sI, st, tot, step);
+  if (tid == 0) finish_step<THERMAL, MODE_STEP>(I, st, tot, step);
 }
 
-template <bool THERMAL>
-cudaError_t launch_tma_t(const Inst* d_inst, const Tile* d_tiles, int ntiles, cudaStream_t s) {
+template <bool THERMAL, bool PCONST>
+cudaError_t launch_tma_t(const Inst* d_inst, const Tile* d_tiles, int ntiles, cudaStream_t s,
+                         const KParams<float>& kp) {
   constexpr size_t smem = tma_smem_bytes<THERMAL>();
+  auto fn = lbm_tma_kernel<THERMAL, PCONST>;
   static unsigned long long configured = 0ull;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(configured & bit)) {
-    e = cudaFuncSetAttribute(lbm_tma_kernel<THERMAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured |= bit;
   }
-  lbm_tma_kernel<THERMAL><<<ntiles, TMA_COLS, smem, s>>>(d_inst, d_tiles);
+  fn<<<ntiles, ST_COLS, smem, s>>>(d_inst, d_tiles, kp);
   return cudaGetLastError();
 }
 
+// h_inst: the host copy of the launch's only instance (constants as a kernel parameter),
+// or null for launches over several instances.
 inline cudaError_t launch_tma(int thermal, int cols, const Inst* d_inst, const Tile* d_tiles, int ntiles,
-                              cudaStream_t s) {
-  if (cols != TMA_COLS) return cudaErrorInvalidValue;
+                              cudaStream_t s, const Inst* h_inst) {
+  if (cols != ST_COLS) return cudaErrorInvalidValue;
   if (ntiles <= 0) return cudaSuccess;
-  return thermal ? launch_tma_t<true>(d_inst, d_tiles, ntiles, s) : launch_tma_t<false>(d_inst, d_tiles, ntiles, s);
+  KParams<float> kp{};
+  if (h_inst) {
+    kp.I = *h_inst;
+    fill_consts<float>(kp.C, *h_inst, h_inst->rho_ref);
+    return thermal ? launch_tma_t<true, true>(d_inst, d_tiles, ntiles, s, kp)
+                   : launch_tma_t<false, true>(d_inst, d_tiles, ntiles, s, kp);
+  }
+  return thermal ? launch_tma_t<true, false>(d_inst, d_tiles, ntiles, s, kp)
+                 : launch_tma_t<false, false>(d_inst, d_tiles, ntiles, s, kp);
 }
 
 template <bool THERMAL>
 int resident_tma_t() {
   constexpr size_t smem = tma_smem_bytes<THERMAL>();
+  auto fn = lbm_tma_kernel<THERMAL, true>;
   int n = 0;
-  if (cudaFuncSetAttribute(lbm_tma_kernel<THERMAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lbm_tma_kernel<THERMAL>, TMA_COLS, smem) != cudaSuccess)
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, ST_COLS, smem) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }
