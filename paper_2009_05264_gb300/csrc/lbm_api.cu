@@ -169,6 +169,31 @@ int default_band_rows(int nx, int ny, int cols, long long slots) {
   return best_rows;
 }
 
+BandPlan default_band_plan(int nx, int ny, int cols, long long slots) {
+  const int rows = default_band_rows(nx, ny, cols, slots);
+  BandPlan best{0, 0, rows};
+  const int w = cols - 8;
+  const long long strips = (nx + w - 1) / w;
+  if (slots < 1) slots = 1;
+  // the cost model of default_band_rows: row-iterations per CTA slot = the work (rows + 4 halo
+  // rows + about one row of fixed cost per tile) spread over the slots, plus half of a tile of
+  // the class dispatched last
+  const long long ubands = (ny + rows - 1) / rows;
+  double best_cost = (double)(strips * ubands) * (rows + 5) / (double)slots + 0.5 * (rows + 5);
+  const long long ks = (slots + strips - 1) / strips;  // short bands per strip: about one wave of short tiles
+  for (int h = 4; (ks + 2) * h <= ny; ++h) {
+    const int tall = (int)((ny - ks * h) / (2 * h));
+    double work = (double)strips * tall * (2 * h + 5);
+    for (int y = tall * 2 * h; y < ny; y += h) work += (double)strips * (std::min(h, ny - y) + 5);
+    const double cost = work / (double)slots + 0.5 * (h + 5);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = BandPlan{2 * h, tall, h};
+    }
+  }
+  return best;
+}
+
 long long step_wave_slots(int fp64, int thermal, int cols, int kernel) {
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -225,24 +250,29 @@ Layout make_layout(int nx, int ny, lbm_precision prec) {
 // Output columns of one tile: a CTA of `cols` threads writes cols - 8 columns.
 int tile_cols(int cols) { return cols - 8; }
 
-void build_tiles(int nx, int ny, int cols, int rows, std::vector<Tile>& out) {
+// Tiles of a band plan in dispatch order: the tall bands of every strip (band by band),
+// then the short bands.
+void build_tiles(int nx, int ny, int cols, const BandPlan& plan, std::vector<Tile>& out) {
   out.clear();
   const int w = tile_cols(cols);
   const int strips = (nx + w - 1) / w;
-  const int bands = (ny + rows - 1) / rows;
-  const int n = strips * bands;
-  int local = 0;
-  for (int b = 0; b < bands; ++b)
+  auto band = [&](int y0, int y1) {
     for (int sidx = 0; sidx < strips; ++sidx) {
       Tile t{};
       t.inst = 0;
       t.x0 = sidx * w;
-      t.y0 = b * rows;
-      t.y1 = std::min(ny, (b + 1) * rows);
-      t.local = local++;
-      t.ntiles = n;
+      t.y0 = y0;
+      t.y1 = y1;
       out.push_back(t);
     }
+  };
+  for (int b = 0; b < plan.tall_count; ++b) band(b * plan.tall_rows, (b + 1) * plan.tall_rows);
+  for (int y = plan.tall_count * plan.tall_rows; y < ny; y += plan.short_rows)
+    band(y, std::min(ny, y + plan.short_rows));
+  for (size_t k = 0; k < out.size(); ++k) {
+    out[k].local = (int)k;
+    out[k].ntiles = (int)out.size();
+  }
 }
 
 // cuTensorMapEncodeTiled, fetched from the driver at run time (the library does not
@@ -353,28 +383,28 @@ lbm_status fetch_state(lbm_ctx* c) {
   return LBM_OK;
 }
 
-lbm_status set_tiling(lbm_ctx* c, int cols, int rows) {
+lbm_status set_tiling(lbm_ctx* c, int cols, const BandPlan& plan) {
   std::vector<Tile> t;
-  build_tiles(c->nx, c->ny, cols, rows, t);
+  build_tiles(c->nx, c->ny, cols, plan, t);
   if ((int)t.size() > c->L.max_tiles) return fail(c, LBM_EINVAL, "tiling needs more tiles than reserved");
   LBM_CUDA(c, cudaMemcpyAsync(c->d_tiles_step, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
   c->cols = cols;
-  c->rows = rows;
+  c->rows = plan.short_rows;
   c->ntiles_step = (int)t.size();
   return LBM_OK;
 }
 
-// Re-choose the default band height for the current kernel, precision and thermal flag.
 int step_kernel(const lbm_ctx* c, int cols) {
   return resolve_kernel(c->kernel, c->prec == LBM_FP64, needs_full_step(c->hinst),
                         c->params.source_model == LBM_SOURCE_HAZI_MARKUS, c->have_tmaps, cols);
 }
 
+// Re-choose the default tiling for the current kernel, precision and thermal flag.
 lbm_status retile_default(lbm_ctx* c, int cols) {
   const long long slots =
       step_wave_slots(c->prec == LBM_FP64, c->have_params ? c->thermal : 1, cols, step_kernel(c, cols));
-  const lbm_status s = set_tiling(c, cols, default_band_rows(c->nx, c->ny, cols, slots));
+  const lbm_status s = set_tiling(c, cols, default_band_plan(c->nx, c->ny, cols, slots));
   if (s == LBM_OK) c->rows_default = true;
   return s;
 }
@@ -483,7 +513,7 @@ lbm_status create_impl(lbm_ctx** out, int32_t nx, int32_t ny, lbm_precision prec
     }
   }
   std::vector<Tile> t;
-  build_tiles(nx, ny, kAuxCols, std::min(kAuxRows, ny), t);
+  build_tiles(nx, ny, kAuxCols, BandPlan{0, 0, std::min(kAuxRows, ny)}, t);
   c->ntiles_aux = (int)t.size();
   if (cudaMemcpyAsync(c->d_tiles_aux, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream) !=
           cudaSuccess ||
@@ -858,7 +888,7 @@ lbm_status lbm_set_tiling(lbm_ctx* c, int32_t cols, int32_t rows) {
   if (rows == 0) return retile_default(c, cols);
   rows = std::min(rows, c->ny);
   if (rows < kMinRows && rows < c->ny) return fail(c, LBM_EINVAL, "rows must be >= 4 (or the full height)");
-  const lbm_status s = set_tiling(c, cols, rows);
+  const lbm_status s = set_tiling(c, cols, BandPlan{0, 0, rows});
   if (s == LBM_OK) c->rows_default = false;
   return s;
 }

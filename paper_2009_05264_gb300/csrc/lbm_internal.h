@@ -117,6 +117,18 @@ const char* fill_inst(Inst& I, const lbm_params* p, int nx, int ny, int pitch, l
 // halo rows (plus about one row of fixed cost) every band adds, the `slots` CTAs one
 // wave holds and half a tile of tail.  Never below 4 rows unless the lattice is lower.
 int default_band_rows(int nx, int ny, int cols, long long slots);
+// Rows of a step tiling, per strip of cols - 8 columns: tall_count bands of tall_rows from the
+// bottom, then bands of short_rows (the last one possibly lower) up to the top; every strip's
+// tall bands are dispatched before any short band (uniform tilings: tall_count = 0).
+struct BandPlan {
+  int tall_rows, tall_count, short_rows;
+};
+// The default step tiling of an nx x ny lattice for `slots` CTA slots: the uniform band height
+// of default_band_rows, or, where the same cost model finds it cheaper, tall bands of 2h rows
+// followed by about one wave of short bands of h rows, which the block scheduler dispatches
+// last, so the end of the step is filled by short tiles while most rows pay the halo of tall
+// bands only.
+BandPlan default_band_plan(int nx, int ny, int cols, long long slots);
 // CTAs of the step kernel (storage precision, thermal flag, tile columns, kernel
 // form) that one wave of the current device holds: SMs x resident CTAs per SM.
 long long step_wave_slots(int fp64, int thermal, int cols, int kernel);
