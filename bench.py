@@ -352,8 +352,9 @@ def dist_env():
     return world, rank, local
 
 
-def cpu_baseline(steps: int = 2, nx: int = 1000):
-    """The oracle as it stands on one host core: `steps` steps of a nx x 800 band of the channel."""
+def cpu_baseline(steps: int = 80, nx: int = 1000):
+    """The oracle as it stands on one host core: `steps` steps of a nx x 800 band of the channel
+    (80 steps: about 10-15 s of CPU work)."""
     import oracle
     from paper_2009_05264_gb300 import inputs as I
 
@@ -511,7 +512,7 @@ def run_ours(args):
             line["batch"] = run_batch(args.batch_steps)
             line["serve"] = run_serve(args.serve_requests, args.serve_steps,
                                       tiling=tuple(int(x) for x in line["batch"]["tiling"].split("x")))
-        if not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
     if world > 1:
