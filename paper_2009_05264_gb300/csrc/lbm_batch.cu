@@ -74,12 +74,13 @@ void drop_graph(lbm_batch* b) {
   }
 }
 
-// Default band height of a member: its share of one wave's CTA slots, in proportion
-// to its share of the batch's nodes.
-int member_rows(const lbm_batch* b, int nx, int ny, long long slots, double share) {
+// Band plan of a member: uniform bands of the batch's explicit height, or the default plan
+// for the member's share of one wave's CTA slots (in proportion to its share of the batch's
+// nodes).
+BandPlan member_plan(const lbm_batch* b, int nx, int ny, long long slots, double share) {
+  if (b->rows > 0) return BandPlan{0, 0, std::max(1, std::min(b->rows, ny))};
   const long long member_slots = std::max<long long>(1, (long long)(slots * share + 0.5));
-  const int r = b->rows > 0 ? b->rows : default_band_rows(nx, ny, b->cols, member_slots);
-  return std::max(1, std::min(r, ny));
+  return default_band_plan(nx, ny, b->cols, member_slots);
 }
 
 // Upload the descriptors and the concatenated tile table of the active members.
@@ -101,27 +102,35 @@ lbm_status rebuild(lbm_batch* b) {
   }
   const int launch_kernel = resolve_kernel(b->kernel, b->prec == LBM_FP64, any_full, any_hazi, all_tmaps, b->cols);
   const long long slots = step_wave_slots(b->prec == LBM_FP64, b->thermal, b->cols, launch_kernel);
+  // every member's tall bands first, then every member's short bands (a member's tile
+  // indices, which fix its partial-sum order, are those of the member alone)
+  std::vector<Tile> shorts;
   for (Member& m : b->slots) {
     if (!m.ctx) continue;
     const int idx = (int)insts.size();
     insts.push_back(lbm_internal_inst(m.ctx));
     m.gen = lbm_internal_params_gen(m.ctx);
-    const int rows = member_rows(b, m.nx, m.ny, slots, total > 0.0 ? (double)m.nx * m.ny / total : 1.0);
-    const int strips = (m.nx + w - 1) / w, bands = (m.ny + rows - 1) / rows;
-    const int n = strips * bands;
+    const BandPlan plan = member_plan(b, m.nx, m.ny, slots, total > 0.0 ? (double)m.nx * m.ny / total : 1.0);
+    const int strips = (m.nx + w - 1) / w;
+    const int y_short = plan.tall_count * plan.tall_rows;
+    const int n = strips * (plan.tall_count + (m.ny - y_short + plan.short_rows - 1) / plan.short_rows);
     int local = 0;
-    for (int bd = 0; bd < bands; ++bd)
+    auto band = [&](int y0, int y1, std::vector<Tile>& out) {
       for (int sx = 0; sx < strips; ++sx) {
         Tile t{};
         t.inst = idx;
         t.x0 = sx * w;
-        t.y0 = bd * rows;
-        t.y1 = std::min(m.ny, (bd + 1) * rows);
+        t.y0 = y0;
+        t.y1 = y1;
         t.local = local++;
         t.ntiles = n;
-        tiles.push_back(t);
+        out.push_back(t);
       }
+    };
+    for (int bd = 0; bd < plan.tall_count; ++bd) band(bd * plan.tall_rows, (bd + 1) * plan.tall_rows, tiles);
+    for (int y = y_short; y < m.ny; y += plan.short_rows) band(y, std::min(m.ny, y + plan.short_rows), shorts);
   }
+  tiles.insert(tiles.end(), shorts.begin(), shorts.end());
   if (insts.size() > b->cap_insts) {
     if (b->d_insts) cudaFree(b->d_insts);
     b->d_insts = nullptr;
