@@ -14,6 +14,12 @@ x_h + 2 n_h).  From those series:
   diameter over five departures and the period over four;
 * the contact-line extent L_t(t) is the wall footprint (the length of wall under
   vapour, in lattice units, in 2D); its oscillation is summarised by a fitted sine.
+
+Where a thin vapour film stays on the heater while bubbles rise from it, the heater
+footprint never returns to zero; ``detachments`` then finds departures from field
+snapshots instead: a departure is a connected vapour region that no longer touches the
+heater sites and overlaps the vapour that was attached to the heater one snapshot
+earlier (and is not the continuation of an already detached bubble).
 """
 from __future__ import annotations
 
@@ -103,3 +109,85 @@ def record(lattice, steps: int, chunk: int = 1000) -> np.ndarray:
         rows.append(lattice.diagnostics_range(first, n))
         done += n
     return np.concatenate(rows) if rows else np.empty((0, len(COLUMNS)))
+
+
+def vapour_components(rho: np.ndarray, rho_vapor: float, periodic_x: bool = False):
+    """Labels (0 = liquid) of the 4-connected vapour regions rho < rho_vapor of a (ny, nx)
+    field, joined across x = 0 / x = nx - 1 when periodic_x; returns (labels, count)."""
+    from scipy import ndimage
+
+    vap = np.asarray(rho) < rho_vapor
+    lab, n = ndimage.label(vap)
+    if periodic_x and n > 1:
+        parent = list(range(n + 1))
+
+        def find(a):
+            while parent[a] != a:
+                parent[a] = parent[parent[a]]
+                a = parent[a]
+            return a
+
+        for a, b in zip(lab[:, 0], lab[:, -1]):
+            if a and b:
+                ra, rb = find(int(a)), find(int(b))
+                if ra != rb:
+                    parent[max(ra, rb)] = min(ra, rb)
+        roots = np.array([find(k) for k in range(n + 1)])
+        uniq, lab = np.unique(roots[lab], return_inverse=True)
+        lab = lab.reshape(vap.shape)
+        n = len(uniq) - 1  # root 0 is the liquid
+    return lab, n
+
+
+def detachments(frames, steps, rho_vapor: float, heater_x0: int, heater_len: int, min_area: int = 20,
+                periodic_x: bool = False) -> list[dict]:
+    """Departure events from a sequence of density snapshots (ny, nx) taken at `steps`:
+    a vapour region of at least min_area nodes that touches none of the heater sites
+    (row 0, columns heater_x0 .. heater_x0 + heater_len - 1), overlaps the vapour attached
+    to the heater in the previous snapshot and overlaps no region that was already
+    detached there.  Each event: step, area (nodes) and diameter 2 sqrt(area / pi)."""
+    events = []
+    prev_attached = prev_detached = None
+    for rho, step in zip(frames, steps):
+        lab, n = vapour_components(rho, rho_vapor, periodic_x)
+        nx = lab.shape[1]
+        cols = np.arange(heater_x0, heater_x0 + heater_len) % nx if periodic_x else \
+            np.arange(max(heater_x0, 0), min(heater_x0 + heater_len, nx))
+        on_heater = set(int(v) for v in lab[0, cols]) - {0}
+        area = np.bincount(lab.ravel(), minlength=n + 1)
+        attached = np.isin(lab, list(on_heater)) if on_heater else np.zeros(lab.shape, dtype=bool)
+        detached = np.zeros(lab.shape, dtype=bool)
+        for c in range(1, n + 1):
+            if c in on_heater or area[c] < min_area:
+                continue
+            comp = lab == c
+            detached |= comp
+            if prev_attached is not None and (comp & prev_attached).any() and not (comp & prev_detached).any():
+                a = float(area[c])
+                events.append({"step": int(step), "area": a, "diameter": 2.0 * math.sqrt(a / math.pi)})
+        prev_attached, prev_detached = attached, detached
+    return events
+
+
+def event_statistics(events: list[dict], skip: int = 0, n_diameter: int = 5, n_period: int = 4) -> dict:
+    """Mean diameter over n_diameter departures and mean period over n_period intervals,
+    after dropping the first `skip` departures (the start-up transient); None where there
+    are too few."""
+    ev = events[skip:]
+    d = [e["diameter"] for e in ev[:n_diameter]]
+    t = [e["step"] for e in ev[: n_period + 1]]
+    return {"departures": len(events),
+            "diameter": float(np.mean(d)) if len(d) == n_diameter else None,
+            "period": float(np.mean(np.diff(t))) if len(t) == n_period + 1 else None}
+
+
+def snapshots(lattice, steps: int, every: int):
+    """Advance a lattice by `steps` steps, returning (density snapshots, their steps) taken
+    every `every` steps."""
+    frames, at = [], []
+    lattice.sync()
+    for _ in range(steps // every):
+        lattice.step(every)
+        frames.append(lattice.fields()["rho"].copy())
+        at.append(lattice.step_count)
+    return frames, at

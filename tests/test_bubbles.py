@@ -52,3 +52,74 @@ def test_sine_fit_recovers_contact_line_oscillation():
     assert fit["period"] == pytest.approx(750, rel=0.01)
     assert fit["amplitude"] == pytest.approx(12, rel=0.03)
     assert fit["offset"] == pytest.approx(40, abs=0.2)
+
+
+def _disk(mask_shape, cx, cy, r):
+    y, x = np.mgrid[0:mask_shape[0], 0:mask_shape[1]]
+    return (x - cx) ** 2 + (y - cy) ** 2 <= r * r
+
+
+def synthetic_cycles(n_cycles=5, period=10, nx=60, ny=90, rho_l=6.0, rho_v=0.6):
+    """Density snapshots of bubbles growing on a heater (columns 25-34), pinching off above a
+    vapour film that stays on the heater, and rising; returns frames, steps and the expected
+    departure events (frame step, area)."""
+    frames, steps, expected = [], [], []
+    risers = []  # (cy, r) of detached bubbles
+    film = np.zeros((ny, nx), dtype=bool)
+    film[0, 27:33] = True
+    for c in range(n_cycles):
+        for k in range(period):
+            vap = film.copy()
+            r = 3 + k if k <= 5 else 0
+            if k <= 5:
+                vap |= _disk(vap.shape, 30, r - 1, r)  # attached: reaches row 0
+            if k == 6:
+                risers.append([9.0, 6])
+            for b in risers:
+                vap |= _disk(vap.shape, 30, b[0], b[1])
+            rho = np.where(vap, rho_v, rho_l)
+            step = (c * period + k + 1) * 100
+            if k == 6:
+                lab = _disk(vap.shape, 30, 9.0, 6)
+                expected.append((step, float(lab.sum())))
+            frames.append(rho)
+            steps.append(step)
+            for b in risers:
+                b[0] += 4.0
+            risers = [b for b in risers if b[0] - b[1] < ny]
+    return frames, steps, expected
+
+
+def test_snapshot_detachments_over_a_residual_film():
+    frames, steps, expected = synthetic_cycles()
+    ev = B.detachments(frames, steps, 3.2, heater_x0=25, heater_len=10, min_area=20)
+    assert [(e["step"], e["area"]) for e in ev] == expected
+    st = B.event_statistics(ev)
+    assert st["departures"] == 5
+    assert st["period"] == pytest.approx(1000.0)
+    assert st["diameter"] == pytest.approx(2 * math.sqrt(expected[0][1] / math.pi))
+    # skipping the first departure as start-up leaves four: too few for the five-departure
+    # diameter and the four-interval period
+    late = B.event_statistics(ev, skip=1)
+    assert late["diameter"] is None and late["period"] is None
+
+
+def test_small_fragments_and_risers_are_not_departures():
+    frames, steps, expected = synthetic_cycles(n_cycles=2)
+    ev = B.detachments(frames, steps, 3.2, heater_x0=25, heater_len=10, min_area=200)
+    assert ev == []  # the 113-node bubbles are below this min_area
+    ev = B.detachments(frames[7:], steps[7:], 3.2, heater_x0=25, heater_len=10, min_area=20)
+    assert [e["step"] for e in ev] == [expected[1][0]]  # the first riser was already detached
+
+
+def test_vapour_components_join_across_a_periodic_edge():
+    rho = np.full((10, 20), 6.0)
+    rho[4:7, 0:3] = 0.5
+    rho[4:7, 17:20] = 0.5
+    rho[1, 9] = 0.5
+    lab, n = B.vapour_components(rho, 3.2, periodic_x=False)
+    assert n == 3
+    lab, n = B.vapour_components(rho, 3.2, periodic_x=True)
+    assert n == 2
+    assert lab[5, 0] == lab[5, 19] != lab[1, 9]
+    assert np.bincount(lab.ravel())[lab[5, 0]] == 18
