@@ -139,6 +139,37 @@ def vapour_components(rho: np.ndarray, rho_vapor: float, periodic_x: bool = Fals
     return lab, n
 
 
+class DepartureTracker:
+    """Online form of ``detachments``: feed snapshots in step order with update(); the
+    departure events accumulate in .events (only the previous snapshot's masks are kept)."""
+
+    def __init__(self, rho_vapor: float, heater_x0: int, heater_len: int, min_area: int = 20,
+                 periodic_x: bool = False):
+        self.rho_vapor, self.heater_x0, self.heater_len = rho_vapor, heater_x0, heater_len
+        self.min_area, self.periodic_x = min_area, periodic_x
+        self.events: list[dict] = []
+        self._att = self._det = None
+
+    def update(self, rho: np.ndarray, step: int):
+        lab, n = vapour_components(rho, self.rho_vapor, self.periodic_x)
+        nx = lab.shape[1]
+        x0, hl = self.heater_x0, self.heater_len
+        cols = np.arange(x0, x0 + hl) % nx if self.periodic_x else np.arange(max(x0, 0), min(x0 + hl, nx))
+        on_heater = set(int(v) for v in lab[0, cols]) - {0}
+        area = np.bincount(lab.ravel(), minlength=n + 1)
+        attached = np.isin(lab, sorted(on_heater)) if on_heater else np.zeros(lab.shape, dtype=bool)
+        detached = np.zeros(lab.shape, dtype=bool)
+        for c in range(1, n + 1):
+            if c in on_heater or area[c] < self.min_area:
+                continue
+            comp = lab == c
+            detached |= comp
+            if self._att is not None and (comp & self._att).any() and not (comp & self._det).any():
+                a = float(area[c])
+                self.events.append({"step": int(step), "area": a, "diameter": 2.0 * math.sqrt(a / math.pi)})
+        self._att, self._det = attached, detached
+
+
 def detachments(frames, steps, rho_vapor: float, heater_x0: int, heater_len: int, min_area: int = 20,
                 periodic_x: bool = False) -> list[dict]:
     """Departure events from a sequence of density snapshots (ny, nx) taken at `steps`:
@@ -146,27 +177,10 @@ def detachments(frames, steps, rho_vapor: float, heater_x0: int, heater_len: int
     (row 0, columns heater_x0 .. heater_x0 + heater_len - 1), overlaps the vapour attached
     to the heater in the previous snapshot and overlaps no region that was already
     detached there.  Each event: step, area (nodes) and diameter 2 sqrt(area / pi)."""
-    events = []
-    prev_attached = prev_detached = None
+    tr = DepartureTracker(rho_vapor, heater_x0, heater_len, min_area, periodic_x)
     for rho, step in zip(frames, steps):
-        lab, n = vapour_components(rho, rho_vapor, periodic_x)
-        nx = lab.shape[1]
-        cols = np.arange(heater_x0, heater_x0 + heater_len) % nx if periodic_x else \
-            np.arange(max(heater_x0, 0), min(heater_x0 + heater_len, nx))
-        on_heater = set(int(v) for v in lab[0, cols]) - {0}
-        area = np.bincount(lab.ravel(), minlength=n + 1)
-        attached = np.isin(lab, list(on_heater)) if on_heater else np.zeros(lab.shape, dtype=bool)
-        detached = np.zeros(lab.shape, dtype=bool)
-        for c in range(1, n + 1):
-            if c in on_heater or area[c] < min_area:
-                continue
-            comp = lab == c
-            detached |= comp
-            if prev_attached is not None and (comp & prev_attached).any() and not (comp & prev_detached).any():
-                a = float(area[c])
-                events.append({"step": int(step), "area": a, "diameter": 2.0 * math.sqrt(a / math.pi)})
-        prev_attached, prev_detached = attached, detached
-    return events
+        tr.update(rho, step)
+    return tr.events
 
 
 def event_statistics(events: list[dict], skip: int = 0, n_diameter: int = 5, n_period: int = 4) -> dict:
