@@ -627,8 +627,14 @@ lbm_status lbm_init_fields(lbm_ctx* c, const double* rho, const double* ux, cons
   LBM_CUDA(c, cudaMemcpyAsync(d_fields + n, ux, n * 8, cudaMemcpyHostToDevice, c->stream));
   LBM_CUDA(c, cudaMemcpyAsync(d_fields + 2 * n, uy, n * 8, cudaMemcpyHostToDevice, c->stream));
   if (T) LBM_CUDA(c, cudaMemcpyAsync(d_fields + 3 * n, T, n * 8, cudaMemcpyHostToDevice, c->stream));
-  double mass = 0.0;  // row-major FP64 mean: the buoyancy reference of step 0
-  for (size_t k = 0; k < n; ++k) mass += rho[k];
+  // FP64 mean density: the buoyancy reference of step 0 (eight interleaved partial sums, so the
+  // host adds are not one dependent chain; only the rounding order differs from a row-major sum)
+  double part[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  size_t k = 0;
+  for (; k + 8 <= n; k += 8)
+    for (int j = 0; j < 8; ++j) part[j] += rho[k + j];
+  for (; k < n; ++k) part[k & 7] += rho[k];
+  const double mass = ((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7]));
   reset_state_mirror(c, 0, 1, mass / (double)n);
   lbm_status s = upload_state(c);
   if (s != LBM_OK) return s;

@@ -270,10 +270,18 @@ class Lattice:
         return torch.cuda.ExternalStream(self.stream_handle, device=torch.device("cuda", self.device))
 
     # --- readback ---------------------------------------------------------
-    def fields(self) -> dict:
-        out = {k: np.empty((self.ny, self.nx)) for k in ("rho", "ux", "uy", "T")}
-        self._check(self._L.lbm_read_fields(self._h, *[_dptr(out[k]) for k in ("rho", "ux", "uy", "T")],
-                                            self.nx * self.ny))
+    def fields(self, out: dict | None = None) -> dict:
+        """rho, u_act (Eq. 7) and T of the current state as (ny, nx) float64 arrays.  `out`: the
+        caller's arrays to fill (C-contiguous float64 of that shape, e.g. views of pinned host
+        memory, which the device then writes directly); missing keys are not read."""
+        keys = ("rho", "ux", "uy", "T")
+        if out is None:
+            out = {k: np.empty((self.ny, self.nx)) for k in keys}
+        for k, a in out.items():
+            if k not in keys or a.dtype != np.float64 or a.shape != (self.ny, self.nx) or not a.flags.c_contiguous \
+                    or not a.flags.writeable:
+                raise ValueError(f"out[{k!r}] must be a writeable C-contiguous float64 array of shape {(self.ny, self.nx)}")
+        self._check(self._L.lbm_read_fields(self._h, *[_dptr(out.get(k)) for k in keys], self.nx * self.ny))
         return out
 
     def populations(self):

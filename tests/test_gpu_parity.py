@@ -539,3 +539,25 @@ def test_full_size_channel_against_oracle():
     got, ref = lat.fields(), orc.fields()
     for k in ("rho", "ux", "uy", "T"):
         assert rel_err(got, ref, k) < FP32_TOL, k
+
+
+def test_fields_into_caller_arrays():
+    """fields(out=...) fills the caller's arrays (here pinned host memory) with the same values
+    as a fresh read, reads only the keys given, and rejects arrays of the wrong shape or type."""
+    L = lbm()
+    nx, ny = 70, 20
+    p, fields = channel_case(nx, ny)
+    lat = L.Lattice(nx, ny, "fp32")
+    lat.set_params(p)
+    lat.init_fields(*fields)
+    lat.step(20)
+    ref = lat.fields()
+    pinned = {k: torch.empty((ny, nx), dtype=torch.float64).pin_memory().numpy() for k in ("rho", "T")}
+    got = lat.fields(out=pinned)
+    assert got is pinned and set(got) == {"rho", "T"}
+    for k in got:
+        assert np.array_equal(got[k], ref[k])
+    with pytest.raises(ValueError):
+        lat.fields(out={"rho": np.empty((nx, ny))})
+    with pytest.raises(ValueError):
+        lat.fields(out={"ux": np.empty((ny, nx), dtype=np.float32)})
