@@ -425,6 +425,9 @@ def run_ours(args):
         lat.set_tiling(c, r)
     lat.set_kernel(args.kernel)
     step_kernel = lat.step_kernel  # the form the timed launches take
+    t = lat.tiling
+    tiling_desc = (f"{t['cols']} columns; per strip {t['tall_count']} bands of {t['tall_rows']} rows, then bands of "
+                   f"{t['short_rows']}" + ("" if args.tiling else " (default plan)"))
     lat.init_fields(*fields)
     stream = lat.stream
     nodes = NX * NY
@@ -488,7 +491,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD if prec == "fp32" else WORKLOAD.replace("FP32", "FP64"),
                        "nx": NX, "ny": NY, "nodes_per_gpu": nodes, "precision": prec,
-                       "tiling": args.tiling or "default (128 columns, rows by heuristic)",
+                       "tiling": tiling_desc,
                        "kernel": f"{step_kernel} (requested {args.kernel})" if prec == "fp32" else "scalar (FP64)",
                        "l2": "inputs larger than L2: 2 x 0.92 GB population buffers vs 129 MB L2",
                        "parallelism": f"{world} independent channel replicas"},

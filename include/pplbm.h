@@ -213,8 +213,28 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* host_buf, size_t bytes);
  * cols - 8 columns, the other 8 cover halo columns; the scalar kernel runs cols
  * threads, the paired kernel cols / 2) and rows per CTA (>= 4, or the full height).
  * Results do not depend on the shape except through the summation order of the
- * domain-mean density (Eq. 14); only speed differs.  0 = default. */
+ * domain-mean density (Eq. 14); only speed differs.  0 = default: the band plan of
+ * lbm_default_band_plan for the CTA slots of the current device and kernel form. */
 lbm_status lbm_set_tiling(lbm_ctx* ctx, int32_t cols, int32_t rows);
+
+/* The context's current step tiling: CTA columns, and per strip of cols - 8 columns
+ * tall_count bands of tall_rows from the bottom followed by bands of short_rows up to the
+ * top (the last possibly lower); uniform tilings have tall_count = 0.  Any output pointer
+ * may be NULL.  LBM_EINVAL if ctx is NULL. */
+lbm_status lbm_get_tiling(const lbm_ctx* ctx, int32_t* cols, int32_t* tall_rows, int32_t* tall_count,
+                          int32_t* short_rows);
+
+/* The default step tiling of an nx x ny lattice with `cols`-column CTAs when `slots` CTAs
+ * (SMs x resident CTAs per SM) fit on the device at once: one cost model (row-iterations
+ * per CTA slot, each tile charged its rows, 4 halo rows and one row of fixed cost, plus
+ * half a tile of the class dispatched last) compares uniform bands of the balanced heights
+ * ceil(ny / bands) >= 4 rows (every band charged that height; ny itself when ny <= 4) with
+ * two-level plans: bands of 2h rows dispatched first and about one wave (ceil(slots /
+ * strips) per strip) of h-row bands dispatched last, h >= 4.
+ * Output as lbm_get_tiling.  Host-only (no device needed).  LBM_EINVAL for nx, ny < 1,
+ * cols not 64, 128 or 256, or slots < 1. */
+lbm_status lbm_default_band_plan(int32_t nx, int32_t ny, int32_t cols, int64_t slots, int32_t* tall_rows,
+                                 int32_t* tall_count, int32_t* short_rows);
 
 /* Form of the FP32 step kernel.  All forms compute the same step (Sec. 2; boundary
  * conditions of Sec. 2.C) and agree to FP32 rounding.

@@ -326,6 +326,7 @@ struct lbm_ctx {
   InstState* d_state = nullptr;
   InstState* h_state = nullptr;  // pinned mirror
   int cols = 128, rows = 16;
+  BandPlan plan{0, 0, 16};  // the step tiling's bands
   bool rows_default = true;  // band height chosen by default_band_rows (re-chosen on changes)
   int ntiles_step = 0, ntiles_aux = 0;
   Tile* d_tiles_step = nullptr;
@@ -391,6 +392,7 @@ lbm_status set_tiling(lbm_ctx* c, int cols, const BandPlan& plan) {
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
   c->cols = cols;
   c->rows = plan.short_rows;
+  c->plan = plan;
   c->ntiles_step = (int)t.size();
   return LBM_OK;
 }
@@ -883,6 +885,26 @@ lbm_status lbm_set_kernel(lbm_ctx* c, int32_t kernel) {
 }
 
 int32_t lbm_step_kernel(const lbm_ctx* c) { return c ? step_kernel(c, c->cols) : -1; }
+
+lbm_status lbm_get_tiling(const lbm_ctx* c, int32_t* cols, int32_t* tall_rows, int32_t* tall_count,
+                          int32_t* short_rows) {
+  if (!c) return LBM_EINVAL;
+  if (cols) *cols = c->cols;
+  if (tall_rows) *tall_rows = c->plan.tall_rows;
+  if (tall_count) *tall_count = c->plan.tall_count;
+  if (short_rows) *short_rows = c->plan.short_rows;
+  return LBM_OK;
+}
+
+lbm_status lbm_default_band_plan(int32_t nx, int32_t ny, int32_t cols, int64_t slots, int32_t* tall_rows,
+                                 int32_t* tall_count, int32_t* short_rows) {
+  if (nx < 1 || ny < 1 || !cols_supported(cols) || slots < 1) return LBM_EINVAL;
+  const BandPlan p = default_band_plan(nx, ny, cols, slots);
+  if (tall_rows) *tall_rows = p.tall_rows;
+  if (tall_count) *tall_count = p.tall_count;
+  if (short_rows) *short_rows = p.short_rows;
+  return LBM_OK;
+}
 
 lbm_status lbm_set_tiling(lbm_ctx* c, int32_t cols, int32_t rows) {
   if (!c) return LBM_EINVAL;

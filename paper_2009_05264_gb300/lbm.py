@@ -31,7 +31,7 @@ EXPORTS = (
     "lbm_init_fields", "lbm_step", "lbm_step_async", "lbm_sync", "lbm_read_fields", "lbm_get_populations",
     "lbm_set_populations", "lbm_read_diagnostics", "lbm_read_diagnostics_range", "lbm_state_bytes",
     "lbm_save_state", "lbm_load_state",
-    "lbm_set_tiling", "lbm_set_kernel", "lbm_step_kernel", "lbm_get_step", "lbm_launch_count", "lbm_get_stream", "lbm_critical_temperature",
+    "lbm_set_tiling", "lbm_get_tiling", "lbm_default_band_plan", "lbm_set_kernel", "lbm_step_kernel", "lbm_get_step", "lbm_launch_count", "lbm_get_stream", "lbm_critical_temperature",
     "lbm_destroy", "lbm_status_string", "lbm_last_error", "lbm_step_noalloc",
     "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_member", "lbm_batch_size",
     "lbm_batch_set_tiling", "lbm_batch_set_kernel", "lbm_batch_get_tiling", "lbm_batch_autotune", "lbm_batch_step",
@@ -104,6 +104,8 @@ def load(build_if_missing: bool = True):
         "lbm_set_tiling": (ctypes.c_int, [vp, i32, i32]),
         "lbm_set_kernel": (ctypes.c_int, [vp, i32]),
         "lbm_step_kernel": (i32, [vp]),
+        "lbm_get_tiling": (ctypes.c_int, [vp] + [ctypes.POINTER(i32)] * 4),
+        "lbm_default_band_plan": (ctypes.c_int, [i32, i32, i32, i64] + [ctypes.POINTER(i32)] * 3),
         "lbm_get_step": (i64, [vp]),
         "lbm_launch_count": (i64, [vp]),
         "lbm_get_stream": (vp, [vp]),
@@ -157,6 +159,16 @@ def make_params(p: dict, nx: int) -> LbmParams:
 
 def critical_temperature(p: dict) -> float:
     return float(load().lbm_critical_temperature(ctypes.byref(make_params(p, 8))))
+
+
+def default_band_plan(nx: int, ny: int, cols: int, slots: int) -> dict:
+    """The library's default step tiling for `slots` CTA slots (host-only): per strip,
+    tall_count bands of tall_rows, then bands of short_rows."""
+    out = [ctypes.c_int32() for _ in range(3)]
+    st = load().lbm_default_band_plan(int(nx), int(ny), int(cols), int(slots), *[ctypes.byref(o) for o in out])
+    if st != 0:
+        raise LbmError(st, "lbm_default_band_plan: invalid arguments")
+    return {"tall_rows": out[0].value, "tall_count": out[1].value, "short_rows": out[2].value}
 
 
 def _dptr(a):
@@ -239,6 +251,14 @@ class Lattice:
     def step_kernel(self) -> str:
         """The kernel form the step launches take ("scalar", "paired" or "tma")."""
         return KERNEL_NAMES[int(self._L.lbm_step_kernel(self._h))]
+
+    @property
+    def tiling(self) -> dict:
+        """The current step tiling: cols, and per strip tall_count bands of tall_rows, then
+        bands of short_rows."""
+        out = [ctypes.c_int32() for _ in range(4)]
+        self._check(self._L.lbm_get_tiling(self._h, *[ctypes.byref(o) for o in out]))
+        return dict(zip(("cols", "tall_rows", "tall_count", "short_rows"), (o.value for o in out)))
 
     # --- stepping ---------------------------------------------------------
     def step(self, n: int = 1):

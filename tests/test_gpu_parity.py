@@ -261,7 +261,10 @@ def test_step_kernel_resolution():
     assert lat.step_kernel == "tma"
     lat.set_tiling(64, 8)
     assert lat.step_kernel == "scalar"
+    assert lat.tiling == {"cols": 64, "tall_rows": 0, "tall_count": 0, "short_rows": 8}
     lat.set_tiling(128, 0)
+    t = lat.tiling
+    assert t["cols"] == 128 and t["tall_count"] * t["tall_rows"] < ny
     lat.set_params(dict(p, bubble_stats=1))  # full form
     assert lat.step_kernel == "scalar"
     lat.set_params(dict(p, source_model=1))
