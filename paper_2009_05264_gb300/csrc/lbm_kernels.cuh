@@ -349,6 +349,7 @@ __device__ __forceinline__ void boundary_fill(Real (&fc)[9], Real (&gc)[9], cons
 template <typename Real>
 struct NodeState {
   Real rho, drho, ux, uy, T, dT, coef;  // coef = T (1 - (dp/dT)_rho / (rho c_v)) of the source
+  Real inv_rho;                          // 1 / rho
   Real hmc;                              // Hazi-Markus form: T (dp/dT)_rho / (rho^2 c_v); coef is then T
   Real dpsi;                             // psi - psi_ref (psi itself in FP64)
   Real p;                                // EOS pressure (diagnostics)
@@ -370,6 +371,7 @@ __device__ __forceinline__ NodeState<Real> node_state(const Real (&fc)[9], const
   const Real jx = (fc[1] - fc[3]) + (fc[5] - fc[6]) + (fc[8] - fc[7]);
   const Real jy = (fc[2] - fc[4]) + (fc[5] + fc[6]) - (fc[7] + fc[8]);
   const Real inv_rho = fast_rcp(o.rho);
+  o.inv_rho = inv_rho;
   o.ux = jx * inv_rho;
   o.uy = jy * inv_rho;
   if (THERMAL) {
@@ -730,6 +732,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
   const bool zone_col = xn >= I.heater_x0 - I.heater_len && xn < I.heater_x0 + 2 * I.heater_len;
   // node scalars carried between iterations: row r-1 (f collision), row r-2 (g collision)
   Real rho_p = Real(1), drho_p = Real(0), ux_p = Real(0), uy_p = Real(0), T_p = T0, dT_p = Real(0), coef_p = Real(0);
+  Real inv_rho_p = Real(1);
   Real T_p2 = T0, dT_p2 = Real(0), coef_p2 = Real(0);
   Real hm_p = Real(0), hm_p2 = Real(0);  // Hazi-Markus source term of rows r-1 and r-2
 
@@ -750,7 +753,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
     const bool row_ok = pery || (r >= 0 && r < ny);
     const int rn = pery ? wrap_index(r, ny) : r;
     NodeState<Real> ns;
-    ns.rho = Real(1); ns.drho = Real(0); ns.ux = Real(0); ns.uy = Real(0);
+    ns.rho = Real(1); ns.inv_rho = Real(1); ns.drho = Real(0); ns.ux = Real(0); ns.uy = Real(0);
     ns.T = T0; ns.dT = Real(0); ns.coef = Real(0); ns.dpsi = Real(0);
     if (col_ok && row_ok) {
       Real* fs = sF + f_cur * 9 * NS + s;
@@ -837,7 +840,9 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
                        sol_m ? Real(0) : Pm[sm], sol_m, sol_p, sC, Fx, Fy);
       }
       Fy -= (drho_p + sRra) * sC.g_a;  // Eq. 14, gravity along -y
-      const Real inv_rho = fast_rcp(rho_p);
+      // FP64 reuses phase A's IEEE reciprocal (a division is several FP64 instructions); FP32
+      // recomputes its cheap approximate one rather than hold another register
+      const Real inv_rho = sizeof(Real) == 8 ? inv_rho_p : fast_rcp(rho_p);
       const Real dux = Fx * inv_rho, duy = Fy * inv_rho;
       const Real uax = ux_p + Real(0.5) * dux, uay = uy_p + Real(0.5) * duy;  // Eq. 7
       sUx[f_prev * NS + s] = uax;
@@ -893,6 +898,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
       hm_p = ns.hmc;
     }
     rho_p = ns.rho;
+    inv_rho_p = ns.inv_rho;
     drho_p = ns.drho;
     ux_p = ns.ux;
     uy_p = ns.uy;
