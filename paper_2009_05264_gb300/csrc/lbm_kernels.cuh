@@ -121,14 +121,34 @@ __device__ __forceinline__ void fold_partials(const double* __restrict__ partial
   }
 }
 
-// Reciprocal and reciprocal square root: MUFU approximations (about 2 ulp) in
-// FP32, IEEE operations in FP64 (the FP64 path matches the oracle to round-off).
+// Reciprocal and reciprocal square root.  FP32: MUFU approximations (about 2 ulp).  FP64: the
+// PTX approximations rcp.approx / rsqrt.approx (about 23 correct bits) refined by two
+// Newton-Raphson steps on f(y) = 1/y - x and f(y) = 1/y^2 - x (each step squares the relative
+// error), which ends within a few ulp of the correctly rounded result in fewer FP64
+// instructions than an IEEE division or square root on this GPU's narrow FP64 pipe; inputs are
+// positive normal numbers here (densities, temperatures, psi radicands).
 __device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ double fast_rcp(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;\n" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);  // relative error of y
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
 __device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double fast_rsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ double fast_rsqrt(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;\n" : "=d"(y) : "d"(x));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double e = fma(-x, y * y, 1.0);  // 1 - x y^2
+    y = fma(0.5 * y, e, y);
+  }
+  return y;
+}
 __device__ __forceinline__ float fast_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
-__device__ __forceinline__ double fast_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ double fast_sqrt(double x) { return x > 0.0 ? x * fast_rsqrt(x) : 0.0; }
 
 // Asynchronous global -> shared copies of one element (cp.async, Ampere and later).
 __device__ __forceinline__ void cp_async_elem(float* smem, const float* gmem) {
@@ -840,7 +860,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
                        sol_m ? Real(0) : Pm[sm], sol_m, sol_p, sC, Fx, Fy);
       }
       Fy -= (drho_p + sRra) * sC.g_a;  // Eq. 14, gravity along -y
-      // FP64 reuses phase A's IEEE reciprocal (a division is several FP64 instructions); FP32
+      // FP64 reuses phase A's reciprocal (several FP64 instructions); FP32
       // recomputes its cheap approximate one rather than hold another register
       const Real inv_rho = sizeof(Real) == 8 ? inv_rho_p : fast_rcp(rho_p);
       const Real dux = Fx * inv_rho, duy = Fy * inv_rho;
