@@ -49,3 +49,27 @@ def test_long_run_departures_match_the_oracle(precision):
     assert len(ev) >= GOLD["skip"] + 5, ev
     assert st["diameter"] == pytest.approx(GOLD["mean_diameter"], rel=TOL)
     assert st["period"] == pytest.approx(GOLD["mean_period"], rel=TOL)
+
+
+def test_per_step_counters_oscillate_with_the_departure_period():
+    """The per-step vapour counters of the same channel (bubble_stats = 1) carry the ebullition
+    cycle: the vapour around the heater and the contact-line extent L_t (wall footprint, Fig. 17)
+    oscillate with the oracle's departure period, while a vapour film keeps the heater covered
+    (so departures need the snapshot rule, not the heater footprint)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_05264_gb300 import lbm
+
+    nx, ny = GOLD["nx"], GOLD["ny"]
+    lat = lbm.Lattice(nx, ny, "fp32")
+    lat.set_params(dict(library_params(), bubble_stats=1))
+    lat.init_fields(*I.uniform(nx, ny, GOLD["rho_l"], GOLD["T"]))
+    s = B.record(lat, GOLD["steps"])
+    t = s[:, B.COLUMNS.index("step")]
+    late = t >= 12000  # after the start-up departures
+    heater = s[late, B.COLUMNS.index("heater_vapor")]
+    assert heater.min() == GOLD["params"]["heater_len"]  # the film never leaves the heater
+    zone = B.fit_sine(t[late], s[late, B.COLUMNS.index("zone_vapor")])
+    wall = B.fit_sine(t[late], s[late, B.COLUMNS.index("wall_vapor")])
+    assert zone["period"] == pytest.approx(GOLD["mean_period"], rel=TOL)
+    assert wall["period"] == pytest.approx(GOLD["mean_period"], rel=0.03) and wall["amplitude"] > 0.5
