@@ -217,6 +217,15 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* host_buf, size_t bytes);
  * lbm_default_band_plan for the CTA slots of the current device and kernel form. */
 lbm_status lbm_set_tiling(lbm_ctx* ctx, int32_t cols, int32_t rows);
 
+/* Time trial_steps steps of each candidate tiling (64, 128 and 256 columns, each with the
+ * default plan and with uniform bands of 4, 7, 10, 16, 24, 32 and 48 rows where the lattice
+ * is that high) and keep the fastest; the chosen columns and rows (0 = default plan) go to
+ * *cols and *rows (either may be NULL).  The trials advance the lattice: re-initialise it
+ * afterwards if its state matters.  Results depend on the tiling only through the summation
+ * order of the domain-mean density.  Errors: LBM_EINVAL (trial_steps < 1), LBM_ESTATE (no
+ * parameters), LBM_EUNSTABLE, LBM_ECUDA. */
+lbm_status lbm_autotune(lbm_ctx* ctx, int32_t trial_steps, int32_t* cols, int32_t* rows);
+
 /* The context's current step tiling: CTA columns, and per strip of cols - 8 columns
  * tall_count bands of tall_rows from the bottom followed by bands of short_rows up to the
  * top (the last possibly lower); uniform tilings have tall_count = 0.  Any output pointer

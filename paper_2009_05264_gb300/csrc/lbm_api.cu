@@ -886,6 +886,52 @@ lbm_status lbm_set_kernel(lbm_ctx* c, int32_t kernel) {
 
 int32_t lbm_step_kernel(const lbm_ctx* c) { return c ? step_kernel(c, c->cols) : -1; }
 
+lbm_status lbm_autotune(lbm_ctx* c, int32_t trial_steps, int32_t* cols_out, int32_t* rows_out) {
+  if (!c || trial_steps < 1) return LBM_EINVAL;
+  if (!c->have_params) return fail(c, LBM_ESTATE, "lbm_set_params first");
+  DeviceGuard g(c->device);
+  static const int kCols[] = {64, 128, 256};
+  static const int kRows[] = {0, 4, 7, 10, 16, 24, 32, 48};
+  cudaEvent_t e0, e1;
+  LBM_CUDA(c, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(c, LBM_ECUDA, "cudaEventCreate");
+  }
+  float best = -1.0f;
+  int best_c = 128, best_r = 0;
+  lbm_status s = LBM_OK;
+  for (int col : kCols) {
+    for (int r : kRows) {
+      if (r > c->ny) continue;
+      if ((s = lbm_set_tiling(c, col, r)) != LBM_OK) break;
+      if ((s = lbm_step_async(c, 2)) != LBM_OK) break;  // warm-up
+      cudaEventRecord(e0, c->stream);
+      if ((s = lbm_step_async(c, trial_steps)) != LBM_OK) break;
+      cudaEventRecord(e1, c->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        s = fail(c, LBM_ECUDA, "autotune timing");
+        break;
+      }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (best < 0.0f || ms < best) {
+        best = ms;
+        best_c = col;
+        best_r = r;
+      }
+    }
+    if (s != LBM_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != LBM_OK) return s;
+  if ((s = lbm_set_tiling(c, best_c, best_r)) != LBM_OK) return s;
+  if (cols_out) *cols_out = best_c;
+  if (rows_out) *rows_out = best_r;
+  return lbm_sync(c);
+}
+
 lbm_status lbm_get_tiling(const lbm_ctx* c, int32_t* cols, int32_t* tall_rows, int32_t* tall_count,
                           int32_t* short_rows) {
   if (!c) return LBM_EINVAL;

@@ -31,7 +31,7 @@ EXPORTS = (
     "lbm_init_fields", "lbm_step", "lbm_step_async", "lbm_sync", "lbm_read_fields", "lbm_get_populations",
     "lbm_set_populations", "lbm_read_diagnostics", "lbm_read_diagnostics_range", "lbm_state_bytes",
     "lbm_save_state", "lbm_load_state",
-    "lbm_set_tiling", "lbm_get_tiling", "lbm_default_band_plan", "lbm_set_kernel", "lbm_step_kernel", "lbm_get_step", "lbm_launch_count", "lbm_get_stream", "lbm_critical_temperature",
+    "lbm_set_tiling", "lbm_autotune", "lbm_get_tiling", "lbm_default_band_plan", "lbm_set_kernel", "lbm_step_kernel", "lbm_get_step", "lbm_launch_count", "lbm_get_stream", "lbm_critical_temperature",
     "lbm_destroy", "lbm_status_string", "lbm_last_error", "lbm_step_noalloc",
     "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_member", "lbm_batch_size",
     "lbm_batch_set_tiling", "lbm_batch_set_kernel", "lbm_batch_get_tiling", "lbm_batch_autotune", "lbm_batch_step",
@@ -105,6 +105,7 @@ def load(build_if_missing: bool = True):
         "lbm_set_kernel": (ctypes.c_int, [vp, i32]),
         "lbm_step_kernel": (i32, [vp]),
         "lbm_get_tiling": (ctypes.c_int, [vp] + [ctypes.POINTER(i32)] * 4),
+        "lbm_autotune": (ctypes.c_int, [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "lbm_default_band_plan": (ctypes.c_int, [i32, i32, i32, i64] + [ctypes.POINTER(i32)] * 3),
         "lbm_get_step": (i64, [vp]),
         "lbm_launch_count": (i64, [vp]),
@@ -251,6 +252,13 @@ class Lattice:
     def step_kernel(self) -> str:
         """The kernel form the step launches take ("scalar", "paired" or "tma")."""
         return KERNEL_NAMES[int(self._L.lbm_step_kernel(self._h))]
+
+    def autotune(self, trial_steps: int = 20) -> tuple[int, int]:
+        """Time each candidate tiling for trial_steps steps and keep the fastest; returns
+        (cols, rows), rows 0 for the default plan.  The trials advance the lattice."""
+        c, r = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._L.lbm_autotune(self._h, int(trial_steps), ctypes.byref(c), ctypes.byref(r)))
+        return c.value, r.value
 
     @property
     def tiling(self) -> dict:

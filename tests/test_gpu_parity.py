@@ -564,3 +564,26 @@ def test_fields_into_caller_arrays():
         lat.fields(out={"rho": np.empty((nx, ny))})
     with pytest.raises(ValueError):
         lat.fields(out={"ux": np.empty((ny, nx), dtype=np.float32)})
+
+
+def test_autotune_keeps_a_valid_tiling():
+    """lbm_autotune times the candidate tilings, keeps the fastest and leaves a lattice that
+    still steps in parity with the oracle after re-initialisation."""
+    L = lbm()
+    nx, ny = 150, 37
+    p, fields = channel_case(nx, ny)
+    lat = L.Lattice(nx, ny, "fp32")
+    lat.set_params(p)
+    lat.init_fields(*fields)
+    cols, rows = lat.autotune(trial_steps=3)
+    t = lat.tiling
+    assert cols in (64, 128, 256) and t["cols"] == cols
+    assert rows == 0 or (t["tall_count"] == 0 and t["short_rows"] == min(rows, ny))
+    lat.init_fields(*fields)
+    lat.step(200)
+    orc = oracle.Oracle(nx, ny, p)
+    orc.init_fields(*fields)
+    assert orc.step(200) == 0
+    got, ref = lat.fields(), orc.fields()
+    for k in ("rho", "ux", "uy", "T"):
+        assert rel_err(got, ref, k) < FP32_TOL, k
