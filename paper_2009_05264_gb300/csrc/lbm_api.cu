@@ -219,8 +219,8 @@ struct Layout {
   long long plane;
   size_t pop_bytes;  // one 9-plane buffer
   int max_tiles;
-  size_t off_f[2], off_g[2], off_rho_prev, off_tmaps, off_inst, off_state, off_part, off_ring, off_tiles_step, off_tiles_aux,
-      total;
+  size_t off_f[2], off_g[2], off_rho_prev, off_tmaps, off_inst, off_state, off_gcount, off_part, off_gpart, off_ring,
+      off_tiles_step, off_tiles_aux, total;
 };
 
 Layout make_layout(int nx, int ny, lbm_precision prec) {
@@ -239,7 +239,10 @@ Layout make_layout(int nx, int ny, lbm_precision prec) {
   L.off_tmaps = off; off += align_up(4 * sizeof(CUtensorMap));
   L.off_inst = off; off += align_up(sizeof(Inst));
   L.off_state = off; off += align_up(sizeof(InstState));
-  L.off_part = off; off += align_up((size_t)L.max_tiles * NPART * sizeof(double));
+  const size_t groups = (size_t)fold_groups(L.max_tiles);
+  L.off_gcount = off; off += align_up(groups * sizeof(unsigned));
+  L.off_part = off; off += align_up(groups * FOLD_GROUP * NPART * sizeof(double));
+  L.off_gpart = off; off += align_up(groups * NPART * sizeof(double));
   L.off_ring = off; off += align_up((size_t)RING * NDIAG * sizeof(double));
   L.off_tiles_step = off; off += align_up((size_t)L.max_tiles * sizeof(Tile));
   L.off_tiles_aux = off; off += align_up((size_t)L.max_tiles * sizeof(Tile));
@@ -437,6 +440,8 @@ lbm_status apply_params(lbm_ctx* c, const lbm_params* p) {
   I.tmaps = c->have_tmaps ? c->base + c->L.off_tmaps : nullptr;
   I.st = c->d_state;
   I.partials = reinterpret_cast<double*>(c->base + c->L.off_part);
+  I.gpartials = reinterpret_cast<double*>(c->base + c->L.off_gpart);
+  I.gcount = reinterpret_cast<unsigned*>(c->base + c->L.off_gcount);
   I.ring = reinterpret_cast<double*>(c->base + c->L.off_ring);
   LBM_CUDA(c, cudaMemcpyAsync(c->d_inst, &c->hinst, sizeof(Inst), cudaMemcpyHostToDevice, c->stream));
   c->params = *p;
@@ -519,7 +524,9 @@ lbm_status create_impl(lbm_ctx** out, int32_t nx, int32_t ny, lbm_precision prec
   c->ntiles_aux = (int)t.size();
   if (cudaMemcpyAsync(c->d_tiles_aux, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream) !=
           cudaSuccess ||
-      cudaMemsetAsync(c->base + c->L.off_state, 0, sizeof(InstState), c->stream) != cudaSuccess) {
+      cudaMemsetAsync(c->base + c->L.off_state, 0, sizeof(InstState), c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->base + c->L.off_gcount, 0, fold_groups(c->L.max_tiles) * sizeof(unsigned), c->stream) !=
+          cudaSuccess) {
     lbm_destroy(c);
     return LBM_ECUDA;
   }

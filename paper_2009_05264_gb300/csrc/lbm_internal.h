@@ -11,6 +11,11 @@ namespace pplbm {
 // Per-tile partial sums folded by the last CTA of an instance:
 // mass, energy, T summed over the heater-adjacent row, inlet flux, outlet flux.
 constexpr int NPART = 9;  // mass, energy, heater row T, inflow, outflow, vapour area, wall / heater / zone vapour
+// The tiles of an instance fold their partials in fixed groups of FOLD_GROUP consecutive
+// local indices: the tile completing a group sums it, the tile completing the last group sums
+// the group sums.
+constexpr int FOLD_GROUP = 64;
+inline long long fold_groups(long long ntiles) { return (ntiles + FOLD_GROUP - 1) / FOLD_GROUP; }
 constexpr int NDIAG = 12;  // LBM_D_COUNT
 constexpr int RING = 1024;  // diagnostics records kept per instance
 
@@ -22,7 +27,7 @@ enum : unsigned { STATUS_UNSTABLE = 1u, STATUS_TIMEOUT = 2u };
 struct InstState {
   long long step;       // steps completed
   int local_read;       // 1: buffer (step & 1) holds post-stream populations (after init/load)
-  unsigned int counter; // tiles of the current launch that have finished
+  unsigned int counter; // tile groups of the current launch that have been folded
   unsigned int status;  // sticky STATUS_* bits, cleared by the host
   int pad0;
   double rho_avg[2];    // domain-mean rho of step n in slot n & 1 (buoyancy of step n+1, Eq. 14)
@@ -55,7 +60,9 @@ struct Inst {
   void* rho_prev;                   // rho^(n-1) - rho_ref per node (storage precision, pitch layout)
   const void* tmaps;                // FP32: 4 tensor maps of 128 bytes (f of buffers 0, 1, then g); or null
   InstState* st;
-  double* partials;                 // NPART per tile of this instance
+  double* partials;                 // per tile: NPART sums, at [(g NPART + j) FOLD_GROUP + l] for local tile g FOLD_GROUP + l
+  double* gpartials;                // per tile group: NPART sums, at [g NPART + j]
+  unsigned* gcount;                 // per tile group: tiles posted in the current launch (0 between launches)
   double* ring;                     // RING records of NDIAG doubles
 };
 

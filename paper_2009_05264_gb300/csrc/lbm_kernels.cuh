@@ -97,10 +97,10 @@ __device__ __forceinline__ void block_sum(double (&v)[NPART], double (*red)[NPAR
   }
 }
 
-// Sum of the per-tile partials of one instance into tot, each thread taking tiles
-// tid, tid + BLOCK, tid + 2 BLOCK, ... in that order (the order fixes the rounding, so the
-// result is deterministic for a given tiling).  Four tiles' loads are issued before their
-// sums so the last CTA's fold is not one L2 round trip per tile.
+// Sum of n records of NPART doubles (the group sums of one instance) into tot, each thread
+// taking records tid, tid + BLOCK, tid + 2 BLOCK, ... in that order (the order fixes the
+// rounding, so the result is deterministic for a given tiling).  Four records' loads are
+// issued before their sums so a long fold is not one L2 round trip per record.
 template <int BLOCK>
 __device__ __forceinline__ void fold_partials(const double* __restrict__ partials, int ntiles, double (&tot)[NPART]) {
   int t = threadIdx.x;
@@ -638,6 +638,56 @@ __device__ __forceinline__ void finish_step(const Inst& I, InstState* st, const 
   st->counter = 0u;
 }
 
+// End of a tile of a MODE_STEP / MODE_MOMENTS launch: post its partial sums (acc, per thread)
+// and fold them in two levels.  The tile that completes a group of FOLD_GROUP tiles sums that
+// group (coalesced loads, while other tiles are still running) into a group sum;
+// the tile that completes the last group sums the group sums and finishes the step.  Both
+// levels add in a fixed order (lanes by strided passes and the block reduction's tree, groups by fold_partials),
+// so the result depends only on the tiling.  Every tile of a launch must post exactly once:
+// the group counters return to zero only when all of a group's tiles have posted.
+template <int BLOCK, bool THERMAL, int MODE>
+__device__ __forceinline__ void post_partials(const Inst& I, InstState* st, const Tile& tile, double (&acc)[NPART],
+                                              double (*red)[NPART], int* flag, long long step) {
+  const int tid = threadIdx.x;
+  const int g = tile.local / FOLD_GROUP;
+  const int gsize = min(FOLD_GROUP, tile.ntiles - g * FOLD_GROUP);
+  double* const gp = I.partials + (long long)g * NPART * FOLD_GROUP;
+  block_sum<BLOCK>(acc, red);
+  if (tid == 0) {
+    const int l = tile.local - g * FOLD_GROUP;
+#pragma unroll
+    for (int j = 0; j < NPART; ++j) gp[j * FOLD_GROUP + l] = acc[j];
+    __threadfence();
+    const unsigned ticket = atomicAdd(&I.gcount[g], 1u);
+    *flag = (ticket == (unsigned)(gsize - 1));
+  }
+  __syncthreads();
+  if (!*flag) return;
+  __threadfence();
+  double v[NPART] = {};
+  for (int l = tid; l < gsize; l += BLOCK)  // one pass when BLOCK >= FOLD_GROUP
+#pragma unroll
+    for (int j = 0; j < NPART; ++j) v[j] += __ldcg(gp + j * FOLD_GROUP + l);
+  block_sum<BLOCK>(v, red);
+  if (tid == 0) {
+    I.gcount[g] = 0u;
+    double* const out = I.gpartials + (long long)g * NPART;
+#pragma unroll
+    for (int j = 0; j < NPART; ++j) out[j] = v[j];
+    __threadfence();
+    const unsigned ticket = atomicAdd(&st->counter, 1u);
+    const int ngroups = (tile.ntiles + FOLD_GROUP - 1) / FOLD_GROUP;
+    *flag = (ticket == (unsigned)(ngroups - 1));
+  }
+  __syncthreads();
+  if (!*flag) return;
+  __threadfence();
+  double tot[NPART] = {};
+  fold_partials<BLOCK>(I.gpartials, (tile.ntiles + FOLD_GROUP - 1) / FOLD_GROUP, tot);
+  block_sum<BLOCK>(tot, red);
+  if (tid == 0) finish_step<THERMAL, MODE>(I, st, tot, step);
+}
+
 // ---------------------------------------------------------------------------
 // Block form of the fused step.  MODE_STEP advances one step; MODE_FIELDS writes
 // rho, u_act and T (FP64) of the current state to the spare f buffer; MODE_POPS
@@ -931,26 +981,10 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
 
   if (MODE != MODE_STEP && MODE != MODE_MOMENTS) return;
 
-  // ---------------- per-tile partials and the last-CTA fold ----------------
+  // ---------------- per-tile partials and their two-level fold ----------------
   double acc[NPART] = {(double)acc_m,  (double)acc_e,  (double)acc_h,  (double)acc_fi, (double)acc_fo,
                        (double)acc_va, (double)acc_wv, (double)acc_hv, (double)acc_zv};
-  block_sum<BLOCK>(acc, sRed);
-  if (tid == 0) {
-    double* part = I.partials + (long long)tile.local * NPART;
-#pragma unroll
-    for (int j = 0; j < NPART; ++j) part[j] = acc[j];
-    __threadfence();
-    const unsigned ticket = atomicAdd(&st->counter, 1u);
-    sLast = (ticket == (unsigned)(tile.ntiles - 1));
-  }
-  __syncthreads();
-  if (!sLast) return;
-  __threadfence();
-  double tot[NPART] = {};
-  fold_partials<BLOCK>(I.partials, tile.ntiles, tot);
-  __syncthreads();
-  block_sum<BLOCK>(tot, sRed);
-  if (tid == 0) finish_step<THERMAL, MODE>(I, st, tot, step);
+  post_partials<BLOCK, THERMAL, MODE>(I, st, tile, acc, sRed, &sLast, step);
 }
 
 // ---------------------------------------------------------------------------

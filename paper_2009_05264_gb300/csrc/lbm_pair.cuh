@@ -528,27 +528,11 @@ lbm_pair_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) 
     g_cur = g_next;
   }
 
-  // ---------------- per-tile partials and the last-CTA fold ----------------
+  // ---------------- per-tile partials and their two-level fold ----------------
   double acc[NPART] = {(double)acc_m.x + (double)acc_m.y, (double)acc_e.x + (double)acc_e.y, (double)acc_h,
                        (double)acc_fi, (double)acc_fo, (double)acc_va, (double)acc_wv, (double)acc_hv,
                        (double)acc_zv};
-  block_sum<B>(acc, sRed);
-  if (tid == 0) {
-    double* part = sI.partials + (long long)tile.local * NPART;
-#pragma unroll
-    for (int j = 0; j < NPART; ++j) part[j] = acc[j];
-    __threadfence();
-    const unsigned ticket = atomicAdd(&st->counter, 1u);
-    sLast = (ticket == (unsigned)(tile.ntiles - 1));
-  }
-  __syncthreads();
-  if (!sLast) return;
-  __threadfence();
-  double tot[NPART] = {};
-  fold_partials<B>(sI.partials, tile.ntiles, tot);
-  __syncthreads();
-  block_sum<B>(tot, sRed);
-  if (tid == 0) finish_step<THERMAL, MODE_STEP>(sI, st, tot, step);
+  post_partials<B, THERMAL, MODE_STEP>(sI, st, tile, acc, sRed, &sLast, step);
 }
 
 template <bool THERMAL, int B>

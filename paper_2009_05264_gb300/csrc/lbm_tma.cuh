@@ -398,25 +398,9 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
     if (THERMAL) mbar_wait(&gbar[j % ST_GS], (j / ST_GS) & 1);
   }
 
-  // ---------------- per-tile partials and the last-CTA fold ----------------
+  // ---------------- per-tile partials and their two-level fold ----------------
   double acc[NPART] = {(double)acc_m, (double)acc_e, (double)acc_h, (double)acc_fi, (double)acc_fo, 0.0, 0.0, 0.0, 0.0};
-  block_sum<B>(acc, sRed);
-  if (tid == 0) {
-    double* part = I.partials + (long long)tile.local * NPART;
-#pragma unroll
-    for (int j = 0; j < NPART; ++j) part[j] = acc[j];
-    __threadfence();
-    const unsigned ticket = atomicAdd(&st->counter, 1u);
-    sLast = (ticket == (unsigned)(tile.ntiles - 1));
-  }
-  __syncthreads();
-  if (!sLast) return;
-  __threadfence();
-  double tot[NPART] = {};
-  fold_partials<B>(I.partials, tile.ntiles, tot);
-  __syncthreads();
-  block_sum<B>(tot, sRed);
-  if (tid == 0) finish_step<THERMAL, MODE_STEP>(I, st, tot, step);
+  post_partials<B, THERMAL, MODE_STEP>(I, st, tile, acc, sRed, &sLast, step);
 }
 
 template <bool THERMAL, bool PCONST>
