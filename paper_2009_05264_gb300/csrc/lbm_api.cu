@@ -84,6 +84,14 @@ const char* fill_inst(Inst& I, const lbm_params* p, int nx, int ny, int pitch, l
   I.pitch = pitch;
   I.geometry = p->geometry;
   I.plane = plane;
+  for (int j = 0; j < NPART; ++j) {
+    // nodes feeding total j: the heater row (2), the inlet and outlet columns (3, 4), else all
+    const long long m = j == 2 ? nx : (j == 3 || j == 4) ? ny : (long long)nx * ny;
+    int e = 0;  // ceil(log2(m))
+    while ((1ll << e) < m) ++e;
+    I.fix_scale[j] = std::ldexp(1.0, FIX_BITS - e);
+    I.fix_unscale[j] = std::ldexp(1.0, e - FIX_BITS);
+  }
   I.multiphase = p->multiphase;
   I.omega_f = 1.0 / p->tau_f;
   I.omega_g = 1.0 / p->tau_g;
@@ -219,8 +227,8 @@ struct Layout {
   long long plane;
   size_t pop_bytes;  // one 9-plane buffer
   int max_tiles;
-  size_t off_f[2], off_g[2], off_rho_prev, off_tmaps, off_inst, off_state, off_gcount, off_part, off_gpart, off_ring,
-      off_tiles_step, off_tiles_aux, total;
+  size_t off_f[2], off_g[2], off_rho_prev, off_tmaps, off_inst, off_state, off_sums, off_ring, off_tiles_step,
+      off_tiles_aux, total;
 };
 
 Layout make_layout(int nx, int ny, lbm_precision prec) {
@@ -239,10 +247,7 @@ Layout make_layout(int nx, int ny, lbm_precision prec) {
   L.off_tmaps = off; off += align_up(4 * sizeof(CUtensorMap));
   L.off_inst = off; off += align_up(sizeof(Inst));
   L.off_state = off; off += align_up(sizeof(InstState));
-  const size_t groups = (size_t)fold_groups(L.max_tiles);
-  L.off_gcount = off; off += align_up(groups * sizeof(unsigned));
-  L.off_part = off; off += align_up(groups * FOLD_GROUP * NPART * sizeof(double));
-  L.off_gpart = off; off += align_up(groups * NPART * sizeof(double));
+  L.off_sums = off; off += align_up(NPART * sizeof(unsigned long long));
   L.off_ring = off; off += align_up((size_t)RING * NDIAG * sizeof(double));
   L.off_tiles_step = off; off += align_up((size_t)L.max_tiles * sizeof(Tile));
   L.off_tiles_aux = off; off += align_up((size_t)L.max_tiles * sizeof(Tile));
@@ -439,9 +444,7 @@ lbm_status apply_params(lbm_ctx* c, const lbm_params* p) {
   I.rho_prev = c->base + c->L.off_rho_prev;
   I.tmaps = c->have_tmaps ? c->base + c->L.off_tmaps : nullptr;
   I.st = c->d_state;
-  I.partials = reinterpret_cast<double*>(c->base + c->L.off_part);
-  I.gpartials = reinterpret_cast<double*>(c->base + c->L.off_gpart);
-  I.gcount = reinterpret_cast<unsigned*>(c->base + c->L.off_gcount);
+  I.sums = reinterpret_cast<unsigned long long*>(c->base + c->L.off_sums);
   I.ring = reinterpret_cast<double*>(c->base + c->L.off_ring);
   LBM_CUDA(c, cudaMemcpyAsync(c->d_inst, &c->hinst, sizeof(Inst), cudaMemcpyHostToDevice, c->stream));
   c->params = *p;
@@ -525,8 +528,7 @@ lbm_status create_impl(lbm_ctx** out, int32_t nx, int32_t ny, lbm_precision prec
   if (cudaMemcpyAsync(c->d_tiles_aux, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream) !=
           cudaSuccess ||
       cudaMemsetAsync(c->base + c->L.off_state, 0, sizeof(InstState), c->stream) != cudaSuccess ||
-      cudaMemsetAsync(c->base + c->L.off_gcount, 0, fold_groups(c->L.max_tiles) * sizeof(unsigned), c->stream) !=
-          cudaSuccess) {
+      cudaMemsetAsync(c->base + c->L.off_sums, 0, NPART * sizeof(unsigned long long), c->stream) != cudaSuccess) {
     lbm_destroy(c);
     return LBM_ECUDA;
   }

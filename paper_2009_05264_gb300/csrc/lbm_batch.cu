@@ -4,9 +4,9 @@
 // partial sums and diagnostics ring, created on the batch's stream) and a
 // concatenated tile table over all members; one launch of the fused kernel per
 // step covers every member's tiles, so lattices of uneven size and parameters
-// share the GPU in one grid.  Each member's partials are folded by that member's
-// last tile, so per-member results are those of the member run alone with the same
-// tiling.  Runs of steps are captured once into a CUDA graph and replayed.
+// share the GPU in one grid.  Each member's partials go into that member's own
+// totals, taken by its last tile, so per-member results are those of the member run
+// alone with the same tiling.  Runs of steps are captured once into a CUDA graph and replayed.
 #include <cuda_runtime.h>
 
 #include <algorithm>

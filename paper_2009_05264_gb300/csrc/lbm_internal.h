@@ -11,11 +11,13 @@ namespace pplbm {
 // Per-tile partial sums folded by the last CTA of an instance:
 // mass, energy, T summed over the heater-adjacent row, inlet flux, outlet flux.
 constexpr int NPART = 9;  // mass, energy, heater row T, inflow, outflow, vapour area, wall / heater / zone vapour
-// The tiles of an instance fold their partials in fixed groups of FOLD_GROUP consecutive
-// local indices: the tile completing a group sums it, the tile completing the last group sums
-// the group sums.
-constexpr int FOLD_GROUP = 64;
-inline long long fold_groups(long long ntiles) { return (ntiles + FOLD_GROUP - 1) / FOLD_GROUP; }
+// The tiles of a launch add their partial sums into NPART signed 64-bit fixed-point totals;
+// total j has 52 - ceil(log2(m_j)) fraction bits, m_j the most nodes that feed it (nx ny for
+// mass, energy and the vapour counts, nx for the heater row, ny for the inlet and outlet
+// columns).  Every per-node term is at most 1024 in magnitude, so a total stays below 2^62,
+// and integer addition is exact and commutative, so the totals do not depend on the order in
+// which tiles finish.
+constexpr int FIX_BITS = 52;
 constexpr int NDIAG = 12;  // LBM_D_COUNT
 constexpr int RING = 1024;  // diagnostics records kept per instance
 
@@ -27,7 +29,7 @@ enum : unsigned { STATUS_UNSTABLE = 1u, STATUS_TIMEOUT = 2u };
 struct InstState {
   long long step;       // steps completed
   int local_read;       // 1: buffer (step & 1) holds post-stream populations (after init/load)
-  unsigned int counter; // tile groups of the current launch that have been folded
+  unsigned int counter; // tiles of the current launch that have posted their partials
   unsigned int status;  // sticky STATUS_* bits, cleared by the host
   int pad0;
   double rho_avg[2];    // domain-mean rho of step n in slot n & 1 (buoyancy of step n+1, Eq. 14)
@@ -60,9 +62,9 @@ struct Inst {
   void* rho_prev;                   // rho^(n-1) - rho_ref per node (storage precision, pitch layout)
   const void* tmaps;                // FP32: 4 tensor maps of 128 bytes (f of buffers 0, 1, then g); or null
   InstState* st;
-  double* partials;                 // per tile: NPART sums, at [(g NPART + j) FOLD_GROUP + l] for local tile g FOLD_GROUP + l
-  double* gpartials;                // per tile group: NPART sums, at [g NPART + j]
-  unsigned* gcount;                 // per tile group: tiles posted in the current launch (0 between launches)
+  unsigned long long* sums;         // NPART fixed-point totals of the current launch (zero between launches)
+  double fix_scale[NPART];          // 2^f_j, f_j the fraction bits of total j
+  double fix_unscale[NPART];        // 2^-f_j
   double* ring;                     // RING records of NDIAG doubles
 };
 

@@ -76,51 +76,6 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
 __device__ __forceinline__ float ld_ro(const float* p) { return __ldg(p); }
 __device__ __forceinline__ double ld_ro(const double* p) { return __ldg(p); }
 
-template <int BLOCK>
-__device__ __forceinline__ void block_sum(double (&v)[NPART], double (*red)[NPART]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int j = 0; j < NPART; ++j) {
-    double x = v[j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) red[warp][j] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int j = 0; j < NPART; ++j) {
-      double s = 0.0;
-      for (int w = 0; w < BLOCK / 32; ++w) s += red[w][j];
-      v[j] = s;
-    }
-  }
-}
-
-// Sum of n records of NPART doubles (the group sums of one instance) into tot, each thread
-// taking records tid, tid + BLOCK, tid + 2 BLOCK, ... in that order (the order fixes the
-// rounding, so the result is deterministic for a given tiling).  Four records' loads are
-// issued before their sums so a long fold is not one L2 round trip per record.
-template <int BLOCK>
-__device__ __forceinline__ void fold_partials(const double* __restrict__ partials, int ntiles, double (&tot)[NPART]) {
-  int t = threadIdx.x;
-  for (; t + 3 * BLOCK < ntiles; t += 4 * BLOCK) {
-    double v[4][NPART];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int j = 0; j < NPART; ++j) v[u][j] = __ldcg(partials + (long long)(t + u * BLOCK) * NPART + j);
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int j = 0; j < NPART; ++j) tot[j] += v[u][j];
-  }
-  for (; t < ntiles; t += BLOCK) {
-#pragma unroll
-    for (int j = 0; j < NPART; ++j) tot[j] += __ldcg(partials + (long long)t * NPART + j);
-  }
-}
-
 // Reciprocal and reciprocal square root.  FP32: MUFU approximations (about 2 ulp).  FP64: the
 // PTX approximations rcp.approx / rsqrt.approx (about 23 correct bits) refined by two
 // Newton-Raphson steps on f(y) = 1/y - x and f(y) = 1/y^2 - x (each step squares the relative
@@ -595,9 +550,9 @@ __device__ __forceinline__ void pull_node(Real* f_dst, Real* g_dst, int dstride,
   }
 }
 
-// Fold of the per-tile partials by the last tile of a launch: the diagnostics
-// record of the step, the domain-mean density for the next step's buoyancy, and the
-// step counter (tot: sums of deviations from the storage references).
+// Completion of a launch by the tile drawing its last ticket: the diagnostics record
+// of the step, the domain-mean density for the next step's buoyancy, and the step
+// counter (tot: the launch's totals of deviations from the storage references).
 template <bool THERMAL, int MODE>
 __device__ __forceinline__ void finish_step(const Inst& I, InstState* st, const double (&tot)[NPART],
                                             long long step) {
@@ -638,54 +593,50 @@ __device__ __forceinline__ void finish_step(const Inst& I, InstState* st, const 
   st->counter = 0u;
 }
 
-// End of a tile of a MODE_STEP / MODE_MOMENTS launch: post its partial sums (acc, per thread)
-// and fold them in two levels.  The tile that completes a group of FOLD_GROUP tiles sums that
-// group (coalesced loads, while other tiles are still running) into a group sum;
-// the tile that completes the last group sums the group sums and finishes the step.  Both
-// levels add in a fixed order (lanes by strided passes and the block reduction's tree, groups by fold_partials),
-// so the result depends only on the tiling.  Every tile of a launch must post exactly once:
-// the group counters return to zero only when all of a group's tiles have posted.
+// End of a tile of a MODE_STEP / MODE_MOMENTS launch: post its partial sums (acc, per thread).
+// The tile's FP64 sums (warp shuffles, then warps in order) are rounded to the fixed-point
+// totals' grid and added to them by NPART integer atomics; then a ticket counts the tile.  The
+// tile drawing the last ticket takes the totals (and leaves zeros for the next launch) by one
+// atomic exchange each and finishes the step.  A sum outside the totals' range (only a diverged
+// run, or a NaN) marks the instance unstable.  Every tile of a launch must post exactly once.
 template <int BLOCK, bool THERMAL, int MODE>
-__device__ __forceinline__ void post_partials(const Inst& I, InstState* st, const Tile& tile, double (&acc)[NPART],
+__device__ __forceinline__ void post_partials(const Inst& I, InstState* st, const Tile& tile, const double (&acc)[NPART],
                                               double (*red)[NPART], int* flag, long long step) {
-  const int tid = threadIdx.x;
-  const int g = tile.local / FOLD_GROUP;
-  const int gsize = min(FOLD_GROUP, tile.ntiles - g * FOLD_GROUP);
-  double* const gp = I.partials + (long long)g * NPART * FOLD_GROUP;
-  block_sum<BLOCK>(acc, red);
-  if (tid == 0) {
-    const int l = tile.local - g * FOLD_GROUP;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 #pragma unroll
-    for (int j = 0; j < NPART; ++j) gp[j * FOLD_GROUP + l] = acc[j];
-    __threadfence();
-    const unsigned ticket = atomicAdd(&I.gcount[g], 1u);
-    *flag = (ticket == (unsigned)(gsize - 1));
+  for (int j = 0; j < NPART; ++j) {
+    double x = acc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) red[warp][j] = x;
   }
   __syncthreads();
-  if (!*flag) return;
-  __threadfence();
-  double v[NPART] = {};
-  for (int l = tid; l < gsize; l += BLOCK)  // one pass when BLOCK >= FOLD_GROUP
-#pragma unroll
-    for (int j = 0; j < NPART; ++j) v[j] += __ldcg(gp + j * FOLD_GROUP + l);
-  block_sum<BLOCK>(v, red);
+  if (tid < NPART) {
+    double sum = 0.0;
+    for (int w = 0; w < BLOCK / 32; ++w) sum += red[w][tid];
+    const double x = sum * I.fix_scale[tid];  // a power of two: exact
+    long long q = 0;
+    if (fabs(x) < 0x1p62) q = __double2ll_rn(x);
+    else atomicOr(&st->status, STATUS_UNSTABLE);
+    atomicAdd(I.sums + tid, (unsigned long long)q);
+  }
+  __syncthreads();
   if (tid == 0) {
-    I.gcount[g] = 0u;
-    double* const out = I.gpartials + (long long)g * NPART;
-#pragma unroll
-    for (int j = 0; j < NPART; ++j) out[j] = v[j];
-    __threadfence();
+    __threadfence();  // the block's additions are performed before its ticket
     const unsigned ticket = atomicAdd(&st->counter, 1u);
-    const int ngroups = (tile.ntiles + FOLD_GROUP - 1) / FOLD_GROUP;
-    *flag = (ticket == (unsigned)(ngroups - 1));
+    *flag = (ticket == (unsigned)(tile.ntiles - 1));
   }
   __syncthreads();
   if (!*flag) return;
   __threadfence();
-  double tot[NPART] = {};
-  fold_partials<BLOCK>(I.gpartials, (tile.ntiles + FOLD_GROUP - 1) / FOLD_GROUP, tot);
-  block_sum<BLOCK>(tot, red);
-  if (tid == 0) finish_step<THERMAL, MODE>(I, st, tot, step);
+  if (tid < NPART) red[0][tid] = (double)(long long)atomicExch(I.sums + tid, 0ull) * I.fix_unscale[tid];
+  __syncthreads();
+  if (tid == 0) {
+    double tot[NPART];
+#pragma unroll
+    for (int j = 0; j < NPART; ++j) tot[j] = red[0][j];
+    finish_step<THERMAL, MODE>(I, st, tot, step);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -981,7 +932,7 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
 
   if (MODE != MODE_STEP && MODE != MODE_MOMENTS) return;
 
-  // ---------------- per-tile partials and their two-level fold ----------------
+  // ---------------- per-tile partials into the launch's totals ----------------
   double acc[NPART] = {(double)acc_m,  (double)acc_e,  (double)acc_h,  (double)acc_fi, (double)acc_fo,
                        (double)acc_va, (double)acc_wv, (double)acc_hv, (double)acc_zv};
   post_partials<BLOCK, THERMAL, MODE>(I, st, tile, acc, sRed, &sLast, step);

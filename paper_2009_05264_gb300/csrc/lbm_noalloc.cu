@@ -3,9 +3,9 @@
 // host that has handed its whole device budget to another allocator, or a
 // plug-in inside someone else's memory-managed process).  The caller owns the
 // population buffers; the step's scratch -- instance descriptor, step state, tile
-// table, per-tile and per-group partial sums, group counters and the diagnostics
-// record -- lives in the fixed-size file-scope device array below, which every GPU
-// that loads the library holds until the process exits.
+// table, fixed-point totals of the partial sums and the diagnostics record -- lives
+// in the fixed-size file-scope device array below, which every GPU that loads the
+// library holds until the process exits.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,11 +27,8 @@ constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 constexpr size_t kOffInst = 0;
 constexpr size_t kOffState = align256(kOffInst + sizeof(Inst));
 constexpr size_t kOffRing = align256(kOffState + sizeof(InstState));
-constexpr int kNoAllocGroups = (kNoAllocMaxTiles + FOLD_GROUP - 1) / FOLD_GROUP;
-constexpr size_t kOffGcount = align256(kOffRing + sizeof(double) * RING * NDIAG);
-constexpr size_t kOffPart = align256(kOffGcount + sizeof(unsigned) * kNoAllocGroups);
-constexpr size_t kOffGpart = align256(kOffPart + sizeof(double) * NPART * FOLD_GROUP * kNoAllocGroups);
-constexpr size_t kOffTiles = align256(kOffGpart + sizeof(double) * NPART * kNoAllocGroups);
+constexpr size_t kOffSums = align256(kOffRing + sizeof(double) * RING * NDIAG);
+constexpr size_t kOffTiles = align256(kOffSums + sizeof(unsigned long long) * NPART);
 constexpr size_t kScratchBytes = align256(kOffTiles + sizeof(Tile) * kNoAllocMaxTiles);
 
 }  // namespace
@@ -119,9 +116,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, int32_t nx, int32_t 
   I.g[(step + 1) & 1] = g_out;
   I.st = reinterpret_cast<InstState*>(base + kOffState);
   I.ring = reinterpret_cast<double*>(base + kOffRing);
-  I.partials = reinterpret_cast<double*>(base + kOffPart);
-  I.gpartials = reinterpret_cast<double*>(base + kOffGpart);
-  I.gcount = reinterpret_cast<unsigned*>(base + kOffGcount);
+  I.sums = reinterpret_cast<unsigned long long*>(base + kOffSums);
   InstState S;
   std::memset(&S, 0, sizeof(S));  // counter and status start at zero on every call
   S.step = step;
@@ -131,7 +126,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, int32_t nx, int32_t 
   // both copies read host stack memory, staged by the runtime before the calls return
   if (cudaMemcpyAsync(base + kOffInst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(base + kOffState, &S, sizeof(InstState), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemsetAsync(base + kOffGcount, 0, sizeof(unsigned) * kNoAllocGroups, s) != cudaSuccess)
+      cudaMemsetAsync(base + kOffSums, 0, sizeof(unsigned long long) * NPART, s) != cudaSuccess)
     return LBM_ECUDA;
   Tile* tiles = reinterpret_cast<Tile*>(base + kOffTiles);
   fill_tiles_kernel<<<(ntiles + 255) / 256, 256, 0, s>>>(tiles, nx, ny, w, rows, strips, ntiles);

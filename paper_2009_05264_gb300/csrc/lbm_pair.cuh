@@ -528,7 +528,7 @@ lbm_pair_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) 
     g_cur = g_next;
   }
 
-  // ---------------- per-tile partials and their two-level fold ----------------
+  // ---------------- per-tile partials into the launch's totals ----------------
   double acc[NPART] = {(double)acc_m.x + (double)acc_m.y, (double)acc_e.x + (double)acc_e.y, (double)acc_h,
                        (double)acc_fi, (double)acc_fo, (double)acc_va, (double)acc_wv, (double)acc_hv,
                        (double)acc_zv};

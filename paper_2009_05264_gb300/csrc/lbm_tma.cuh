@@ -398,7 +398,7 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
     if (THERMAL) mbar_wait(&gbar[j % ST_GS], (j / ST_GS) & 1);
   }
 
-  // ---------------- per-tile partials and their two-level fold ----------------
+  // ---------------- per-tile partials into the launch's totals ----------------
   double acc[NPART] = {(double)acc_m, (double)acc_e, (double)acc_h, (double)acc_fi, (double)acc_fo, 0.0, 0.0, 0.0, 0.0};
   post_partials<B, THERMAL, MODE_STEP>(I, st, tile, acc, sRed, &sLast, step);
 }
