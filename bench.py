@@ -174,6 +174,13 @@ def run_fp64(steps: int):
                            "frac": tf / FP64_NOMINAL_TFLOPS, "flops_per_node": fpn,
                            "peak_source": "nominal GB300 FP64 (non-tensor) rate",
                            "flops_source": f"ncu DADD + DMUL + 2 DFMA per node ({FP64_PROFILE})"}
+        ipn = profiled_fp64_flops_per_node("fp64-pipe-inst-per-node")
+        if ipn:  # DADD and DMUL take an issue slot of the FP64 pipe as a DFMA does, for half its flops
+            ti = ipn * nodes * steps / (ms * 1e-3) / 1e12
+            slots = FP64_NOMINAL_TFLOPS / 2.0
+            out["roofline"]["pipe"] = {"achieved": ti, "peak": slots, "unit": "T FP64 thread-instructions/s",
+                                       "frac": ti / slots, "inst_per_node": ipn,
+                                       "peak_source": "nominal FP64 rate / 2 flops per DFMA"}
     else:
         out["roofline"] = dict(out["hbm"], bound="hbm")
     lat.close()
@@ -340,15 +347,16 @@ FP64_PROFILE = "profiles/lbm_fused_step_fp64_channel.md"
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate; no measured figure on this machine
 
 
-def profiled_fp64_flops_per_node():
+def profiled_fp64_flops_per_node(key: str = "fp64-flops-per-node"):
     """FP64 floating-point operations per node update of the step kernel (DADD + DMUL + 2 DFMA,
-    counted by ncu), or None when the summary was taken on other kernel sources."""
+    counted by ncu; key "fp64-pipe-inst-per-node": DADD + DMUL + DFMA thread instructions), or
+    None when the summary was taken on other kernel sources."""
     import re
 
     path = os.path.join(ROOT, FP64_PROFILE)
     if not os.path.exists(path):
         return None
-    m = re.search(r"fp64-flops-per-node:\s*([0-9.]+)\s*\(source digest ([0-9a-f]+)", open(path).read())
+    m = re.search(re.escape(key) + r":\s*([0-9.]+)\s*\(source digest ([0-9a-f]+)", open(path).read())
     if not m or m.group(2) != step_source_digest():
         return None
     return float(m.group(1))

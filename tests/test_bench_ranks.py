@@ -56,3 +56,16 @@ def test_single_rank_needs_no_process_group():
 
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert bench.whole_job_mlups(6_400_000, 300, 1, 0.08) == pytest.approx(24000.0)
+
+
+def test_fp64_pipe_figure_is_consistent_with_the_flop_figure():
+    """DADD + DMUL + DFMA instructions per node lie between half the flops (all DFMA) and the flops
+    (no DFMA); both figures come from the same committed summary, or neither does."""
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+
+    flops = bench.profiled_fp64_flops_per_node()
+    inst = bench.profiled_fp64_flops_per_node("fp64-pipe-inst-per-node")
+    assert (flops is None) == (inst is None)
+    if flops is not None:
+        assert flops / 2 <= inst <= flops
