@@ -587,3 +587,37 @@ def test_autotune_keeps_a_valid_tiling():
     got, ref = lat.fields(), orc.fields()
     for k in ("rho", "ux", "uy", "T"):
         assert rel_err(got, ref, k) < FP32_TOL, k
+
+
+def test_fixed_point_totals_at_full_width():
+    """The step's totals are 64-bit fixed point with 52 - ceil(log2 m) fraction bits, m the nodes
+    feeding a total (nx ny for mass and energy, ny for the inlet and outlet fluxes).  On a
+    4000 x 800 FP64 channel (30 and 42 fraction bits) the record of step n equals the exact sums
+    over the fields the step starts from, within one grid step per tile plus FP64 rounding."""
+    import math
+
+    L = lbm()
+    nx, ny = 4000, 800
+    p, fields = channel_case(nx, ny)
+    lat = L.Lattice(nx, ny, "fp64")
+    lat.set_params(p)
+    lat.init_fields(*fields)
+    lat.step(5)
+    f = lat.fields()
+    lat.step(1)
+    d = lat.diagnostics()
+    assert d["step"] == 5
+    ntiles_max = -(-nx // 56) * -(-ny // 4)  # the narrowest, shortest tiling
+
+    def bound(m, size):
+        frac_bits = 52 - math.ceil(math.log2(m))
+        return ntiles_max * 2.0 ** -(frac_bits + 1) + 1e-14 * size
+
+    mass, energy = math.fsum(f["rho"].ravel()), math.fsum(f["T"].ravel())
+    assert abs(d["mass"] - mass) <= bound(nx * ny, mass)
+    assert abs(d["energy"] - energy) <= bound(nx * ny, energy)
+    for key, col in (("flux_in", 0), ("flux_out", nx - 1)):
+        q = f["rho"][:, col] * f["ux"][:, col]
+        want = math.fsum(q)
+        assert abs(d[key] - want) <= bound(ny, float(np.abs(q).sum())), key
+    lat.close()
