@@ -62,7 +62,13 @@ enum {
 
 enum { LBM_INIT_UNIFORM = 0, LBM_INIT_DISK = 1 };
 
-/* Diagnostics record of one step, computed in FP64 from that step's moments. */
+/* Diagnostics record of one step, computed from that step's moments: each CTA sums its nodes in
+ * FP64, and the CTA sums are added as signed 64-bit fixed-point totals with 52 - ceil(log2 m)
+ * fraction bits (m = nx*ny for mass, energy and the vapour counts, nx for the heater row, ny for
+ * the inlet and outlet columns).  Integer addition makes a record independent of the order in
+ * which CTAs finish; rounding adds at most 2^-(53 - ceil(log2 m)) per CTA.  A CTA sum outside the
+ * totals' range (per-node terms above 1024 in magnitude: a diverged run) or a NaN sets the
+ * unstable status. */
 enum {
   LBM_D_STEP = 0,    /* step index n */
   LBM_D_MASS,        /* sum of rho over fluid nodes (Eq. 4) */
@@ -212,8 +218,8 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* host_buf, size_t bytes);
 /* Tile shape of the fused kernel: columns per CTA (64, 128 or 256; a CTA writes
  * cols - 8 columns, the other 8 cover halo columns; the scalar kernel runs cols
  * threads, the paired kernel cols / 2) and rows per CTA (>= 4, or the full height).
- * Results do not depend on the shape except through the summation order of the
- * domain-mean density (Eq. 14); only speed differs.  0 = default: the band plan of
+ * Results do not depend on the shape except through the per-CTA sums of the
+ * domain-mean density (Eq. 14) and their rounding to the fixed-point totals; only speed differs.  0 = default: the band plan of
  * lbm_default_band_plan for the CTA slots of the current device and kernel form. */
 lbm_status lbm_set_tiling(lbm_ctx* ctx, int32_t cols, int32_t rows);
 
@@ -221,8 +227,8 @@ lbm_status lbm_set_tiling(lbm_ctx* ctx, int32_t cols, int32_t rows);
  * default plan and with uniform bands of 4, 7, 10, 16, 24, 32 and 48 rows where the lattice
  * is that high) and keep the fastest; the chosen columns and rows (0 = default plan) go to
  * *cols and *rows (either may be NULL).  The trials advance the lattice: re-initialise it
- * afterwards if its state matters.  Results depend on the tiling only through the summation
- * order of the domain-mean density.  Errors: LBM_EINVAL (trial_steps < 1), LBM_ESTATE (no
+ * afterwards if its state matters.  Results depend on the tiling only through the per-CTA
+ * sums of the domain-mean density.  Errors: LBM_EINVAL (trial_steps < 1), LBM_ESTATE (no
  * parameters), LBM_EUNSTABLE, LBM_ECUDA. */
 lbm_status lbm_autotune(lbm_ctx* ctx, int32_t trial_steps, int32_t* cols, int32_t* rows);
 
@@ -260,7 +266,7 @@ lbm_status lbm_default_band_plan(int32_t nx, int32_t ny, int32_t cols, int64_t s
  *     128-column tiles and the step's lean form (no pool geometry, Hazi-Markus source
  *     or bubble statistics); other lattices take the scalar form.  A bulk copy that does
  *     not complete within a bounded wait makes lbm_sync return LBM_ETIMEOUT.  Its results
- *     are bit-identical to the scalar form's; on GB300 it runs about 6 % slower (its
+ *     are bit-identical to the scalar form's; on GB300 it runs about 9 % slower (its
  *     warps wait on rows that arrive later than the per-thread copies do).
  * FP64 lattices, and lbm_step_noalloc on caller-laid-out buffers, always use the scalar
  * form.  LBM_EINVAL for other values. */
