@@ -352,7 +352,7 @@ lbm_status lbm_batch_destroy(lbm_batch* b);
  * whose LBM_D_RHO_AVG is the rho_avg_prev of the next call.  The call waits for
  * the step on cuda_stream (a cudaStream_t; NULL = the default stream).
  *
- * Scratch: a fixed 0.96 MB device array inside the library, which every GPU that
+ * Scratch: a fixed 0.36 MB device array inside the library, which every GPU that
  * loads the library holds until the process exits.  The first call on a device
  * looks up that array's device address (once per device, with the device
  * current); make that first call before capturing any CUDA graph.  Every call

@@ -34,7 +34,7 @@ constexpr size_t kScratchBytes = align256(kOffTiles + sizeof(Tile) * kNoAllocMax
 }  // namespace
 }  // namespace pplbm
 
-// The scratch of lbm_step_noalloc (about 0.96 MB).  In host code this name is only
+// The scratch of lbm_step_noalloc (about 0.36 MB).  In host code this name is only
 // a stand-in for the device array: its device address comes from
 // cudaGetSymbolAddress (scratch_on_device below), never from taking it directly.
 static __device__ __align__(256) unsigned char g_lbm_noalloc_scratch[pplbm::kScratchBytes];
