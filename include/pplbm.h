@@ -169,7 +169,9 @@ lbm_status lbm_set_params(lbm_ctx* ctx, const lbm_params* p);
 /* Start from host fields (n = nx*ny each, row-major): f = f^eq(rho, u) (Eq. 3),
  * g = g^eq(T, u) (Eq. 18); T is the absolute lattice temperature (T_R * Tc) and
  * may be NULL (T0 everywhere).  Sets step 0; the buoyancy mean of the previous
- * step (Eq. 14) is the row-major FP64 mean of rho.  Requires lbm_set_params. */
+ * step (Eq. 14) is the mean density of the initialised populations, summed on the
+ * device (FP64: the mean of rho up to rounding; FP32: of rho as stored).  Returns
+ * once the populations are in place.  Requires lbm_set_params. */
 lbm_status lbm_init_fields(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy,
                            const double* T, size_t n);
 

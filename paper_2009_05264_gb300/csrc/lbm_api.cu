@@ -638,23 +638,18 @@ lbm_status lbm_init_fields(lbm_ctx* c, const double* rho, const double* ux, cons
   LBM_CUDA(c, cudaMemcpyAsync(d_fields + n, ux, n * 8, cudaMemcpyHostToDevice, c->stream));
   LBM_CUDA(c, cudaMemcpyAsync(d_fields + 2 * n, uy, n * 8, cudaMemcpyHostToDevice, c->stream));
   if (T) LBM_CUDA(c, cudaMemcpyAsync(d_fields + 3 * n, T, n * 8, cudaMemcpyHostToDevice, c->stream));
-  // FP64 mean density: the buoyancy reference of step 0 (eight interleaved partial sums, so the
-  // host adds are not one dependent chain; only the rounding order differs from a row-major sum)
-  double part[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  size_t k = 0;
-  for (; k + 8 <= n; k += 8)
-    for (int j = 0; j < 8; ++j) part[j] += rho[k + j];
-  for (; k < n; ++k) part[k & 7] += rho[k];
-  const double mass = ((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7]));
-  reset_state_mirror(c, 0, 1, mass / (double)n);
+  reset_state_mirror(c, 0, 1, 0.0);
   lbm_status s = upload_state(c);
   if (s != LBM_OK) return s;
   cudaError_t e = launch_init_from_fields(c->prec == LBM_FP64, c->d_inst, c->nx, c->ny, d_fields, T ? 1 : 0, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
   ++c->launches;
-  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  // the buoyancy reference of step 0 (Eq. 14): the mean density of the initialised populations,
+  // summed on the device (a host sum of the input field would hold the caller's thread for
+  // milliseconds on large lattices)
+  if ((s = launch(c, MODE_MOMENTS)) != LBM_OK) return s;
   c->step_host = 0;
-  return LBM_OK;
+  return fetch_state(c);
 }
 
 lbm_status lbm_step_async(lbm_ctx* c, int64_t nsteps) {
