@@ -511,3 +511,68 @@ def test_contact_angle_decreases_with_wall_density():
         height = liquid.any(axis=1).sum()
         thetas.append(PP.contact_angle_from_cap(height, base))
     assert thetas[0] > thetas[1] > thetas[2]
+
+
+def test_centreline_pressure_drop():
+    """Delta p (Sec. 3.B, Fig. 12b): the pressure at (1, ny/2) minus that at (nx-2, ny/2), taken from
+    the moments the step starts from.  Without the pseudopotential the fluid is the lattice ideal
+    gas p = c_s^2 rho = rho/3 (Sec. 2.A), so a density varying in x and y gives the two probes'
+    density difference over 3 (a wrong probe row or column, or a flipped sign, misses it); a liquid
+    and a vapour at Maxwell coexistence (Sec. 2.D) have equal pressures and unequal densities, so
+    Delta p vanishes there while a density difference would not."""
+    nx, ny = 24, 9
+    xs, ys = np.arange(nx)[None, :], np.arange(ny)[:, None]
+    zero = np.zeros((ny, nx))
+    p = prm(nx, geometry="channel", thermal=0, multiphase=0, g_a=0.0, u_in=0.0, rho_out=1.0)
+    rho = 1.0 + 0.01 * xs * (1.0 + 0.05 * ys ** 2)  # the x-difference depends on the row
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(rho, zero, zero)
+    assert O.step(1) == 0
+    d = O.last_diag()
+    assert d["step"] == 0
+    assert d["dp"] == pytest.approx((rho[ny // 2, 1] - rho[ny // 2, nx - 2]) / 3.0, rel=1e-13)
+
+    p2 = prm(nx, geometry="channel", thermal=0, g_a=0.0, u_in=0.0)
+    T = p2["T0_R"] * oracle.Tc(p2)
+    rv, rl, ps = oracle.maxwell(p2, T)
+    assert rl - rv > 1.0
+    two = np.where(xs < nx // 2, rl, rv) + 0.0 * zero
+    O2 = oracle.Oracle(nx, ny, dict(p2, rho_out=rv))
+    O2.init_fields(two, zero, zero)
+    O2.step(1)
+    d2 = O2.last_diag()
+    assert abs(d2["dp"]) < 1e-9 * ps
+
+
+def test_heater_temperature_contrast():
+    """delta T* (Sec. 3.B, Fig. 12c) = (T_w - T_nb) / (T_w - T_bulk): T_nb the mean temperature over
+    the heater columns of the row next to the heater, T_bulk the domain mean, T_w the heater
+    temperature once it is on.  A uniform field away from T_w gives exactly 1 (bulk and
+    heater-adjacent row agree; a bulk taken from T_in instead would not); the heater-adjacent
+    nodes at T_w give exactly 0 (a neighbouring row or column in T_nb would not); with the heater
+    off it is 0 by definition."""
+    nx, ny = 20, 8
+    x0, nh = 6, 5
+    zero = np.zeros((ny, nx))
+    base = dict(geometry="channel", thermal=1, multiphase=0, g_a=0.0, u_in=0.0, rho_out=1.0, heater_x0=x0,
+                heater_len=nh, dTheat_R=0.3)
+    p = prm(nx, heat_on_step=0, **base)
+    Tc = oracle.Tc(p)
+    Tw = (p["Tin_R"] + p["dTheat_R"]) * Tc
+    T1 = (p["Tin_R"] + 0.05) * Tc
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(1.0 + zero, zero, zero, T1 + zero)
+    O.step(1)
+    assert O.last_diag()["dtstar"] == pytest.approx(1.0, abs=1e-13)
+
+    T = T1 + zero
+    T[0, x0:x0 + nh] = Tw
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(1.0 + zero, zero, zero, T)
+    O.step(1)
+    assert abs(O.last_diag()["dtstar"]) < 1e-13
+
+    O = oracle.Oracle(nx, ny, prm(nx, heat_on_step=10, **base))
+    O.init_fields(1.0 + zero, zero, zero, T)
+    O.step(1)
+    assert O.last_diag()["dtstar"] == 0.0
