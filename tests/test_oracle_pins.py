@@ -576,3 +576,25 @@ def test_heater_temperature_contrast():
     O.init_fields(1.0 + zero, zero, zero, T)
     O.step(1)
     assert O.last_diag()["dtstar"] == 0.0
+
+
+def test_inlet_and_outlet_flux_diagnostics():
+    """The flux records are sums over the rows of rho u_x at x = 0 and x = nx - 1.  From a fluid at
+    rest (rho = 1, no force) the first step starts from the initialised populations (no boundary
+    fill yet): both are 0.  The next step's inlet and outlet nodes pull rest populations, so Zou-He
+    gives closed forms per row: rho u_x = u_in / (1 - u_in) at the velocity inlet and 1 - rho_out at
+    the pressure outlet, while the neighbouring columns are still at rest."""
+    nx, ny = 16, 7
+    u_in, rho_out = 0.02, 1.01
+    p = prm(nx, geometry="channel", thermal=0, multiphase=0, g_a=0.0, u_in=u_in, rho_out=rho_out)
+    zero = np.zeros((ny, nx))
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(1.0 + zero, zero, zero)
+    O.step(1)
+    d = O.last_diag()
+    assert d["flux_in"] == 0.0 and d["flux_out"] == 0.0
+    O.step(1)
+    d = O.last_diag()
+    assert d["step"] == 1
+    assert d["flux_in"] == pytest.approx(ny * u_in / (1.0 - u_in), rel=1e-13)
+    assert d["flux_out"] == pytest.approx(ny * (1.0 - rho_out), rel=1e-12)
