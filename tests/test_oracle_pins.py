@@ -598,3 +598,40 @@ def test_inlet_and_outlet_flux_diagnostics():
     assert d["step"] == 1
     assert d["flux_in"] == pytest.approx(ny * u_in / (1.0 - u_in), rel=1e-13)
     assert d["flux_out"] == pytest.approx(ny * (1.0 - rho_out), rel=1e-12)
+
+
+def test_inlet_temperature_is_a_fixed_point_at_rest():
+    """The inlet's anti-bounce-back (Sec. 2.C) imposes T_in on the links that streaming leaves
+    unknown; with the fluid at rest and uniformly at T_in the incoming populations are exactly
+    g^eq(T_in, 0), so the field stays at T_in to rounding.  T_in differs from the initial-state T0
+    here, so an inlet that imposed T0 (or anything else) would move the inlet column."""
+    nx, ny = 20, 9
+    p = prm(nx, geometry="channel", thermal=1, multiphase=0, g_a=0.0, u_in=0.0, rho_out=1.0, Tin_R=0.95,
+            T0_R=0.9, heater_len=0)
+    Tin = p["Tin_R"] * oracle.Tc(p)
+    zero = np.zeros((ny, nx))
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(1.0 + zero, zero, zero, Tin + zero)
+    assert O.step(20) == 0
+    assert np.abs(O.fields()["T"] - Tin).max() < 1e-14
+
+
+def test_zou_he_non_equilibrium_bounce_back():
+    """Zou-He (Sec. 2.C) closes the open boundaries by bouncing back the non-equilibrium part normal
+    to them, f_1 - f_1^eq = f_3 - f_3^eq; the odd part of the equilibrium (Eq. 3) then gives
+    f_1 - f_3 = (2/3) rho u_x on every inlet and outlet node off the corners.  Imposing only the
+    moments (an equilibrium f_1, say) would keep rho and u right and break this."""
+    nx, ny = 20, 9
+    p = prm(nx, geometry="channel", thermal=1, u_in=0.03, rho_out=5.9)
+    T = p["T0_R"] * oracle.Tc(p)
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(*I.smooth_random(nx, ny, 5.9, T, seed=12, drho=0.01, du=0.01, dT=0.01))
+    for _ in range(3):
+        assert O.step(1) == 0
+        f, _ = O.populations()
+        rho = f.sum(axis=0)
+        jx = (f * CX[:, None, None]).sum(axis=0)
+        for x in (0, nx - 1):
+            lhs = f[1, 1:-1, x] - f[3, 1:-1, x]
+            np.testing.assert_allclose(lhs, (2.0 / 3.0) * jx[1:-1, x], rtol=0, atol=1e-13)
+        assert np.abs(jx[1:-1, -1]).max() > 1e-4  # the outlet carries flow: the check has teeth
