@@ -635,3 +635,22 @@ def test_zou_he_non_equilibrium_bounce_back():
             lhs = f[1, 1:-1, x] - f[3, 1:-1, x]
             np.testing.assert_allclose(lhs, (2.0 / 3.0) * jx[1:-1, x], rtol=0, atol=1e-13)
         assert np.abs(jx[1:-1, -1]).max() > 1e-4  # the outlet carries flow: the check has teeth
+
+
+def test_buoyancy_uses_the_previous_steps_mean():
+    """Eq. 14 with its one-step lag: F_y = -(rho - rho_avg) g_a, rho_avg the mean density of the
+    previous step's state, so summed over the nodes the buoyancy is -g_a (M_n - M_(n-1)), the mass
+    change over the last step.  A closed box keeps its mass and cannot tell; a channel whose outlet
+    density exceeds the fluid's gains mass every step, so a mean of the current step (sum zero) or
+    a stale one (the sum since the start) misses it."""
+    nx, ny, ga = 20, 9, 1e-3
+    p = prm(nx, geometry="channel", thermal=0, multiphase=0, g_a=ga, u_in=0.01, rho_out=1.02)
+    zero = np.zeros((ny, nx))
+    O = oracle.Oracle(nx, ny, p)
+    O.init_fields(1.0 + zero, zero, zero)
+    for _ in range(4):
+        assert O.step(1) == 0
+        F = O.fields()
+        m_now, m_prev = math.fsum(F["rho"].ravel()), O.last_diag()["mass"]
+        assert m_now - m_prev > 0.1
+        assert math.fsum(F["Fy"].ravel()) == pytest.approx(-ga * (m_now - m_prev), rel=1e-9)
