@@ -380,6 +380,33 @@ def profiled_traffic_per_node(kernel: str):
     return float(m.group(1)), f"ncu dram__bytes_read+write per node ({PROFILES[kernel]})"
 
 
+def profiled_inst_per_node(kernel: str):
+    """Warp-instructions per node update of a step kernel form from its committed ncu summary
+    (smsp__inst_executed.sum over the output nodes, halo work included), or None when there is
+    none or it was taken on other kernel sources."""
+    import re
+
+    if kernel not in PROFILES:
+        return None
+    path = os.path.join(ROOT, PROFILES[kernel])
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"inst-per-node:\s*([0-9.]+)\s*\(source digest ([0-9a-f]+)", open(path).read())
+    if not m or m.group(2) != step_source_digest(kernel):
+        return None
+    return float(m.group(1))
+
+
+def issue_roofline(inst_per_node: float, nodes: int, launch_s: float, sms: int, sm_mhz: float) -> dict:
+    """Instruction issue of a step launch against the issue peak: every SM issues at most one
+    warp-instruction per clock from each of its four schedulers."""
+    achieved = inst_per_node * nodes / launch_s / 1e9
+    peak = sms * 4 * sm_mhz * 1e6 / 1e9
+    return {"achieved": achieved, "peak": peak, "unit": "G warp-instructions/s", "frac": achieved / peak,
+            "inst_per_node": inst_per_node,
+            "peak_source": f"{sms} SMs x 4 schedulers x the sampled {sm_mhz:.0f} MHz SM clock"}
+
+
 def max_over_ranks(value: float, world: int, device=None) -> float:
     """The largest of every rank's value (the slowest rank's time); the value itself on one rank."""
     if world <= 1:
@@ -559,6 +586,13 @@ def run_ours(args):
             "gpu_launches": gpu_launches,
             "clocks": clocks,
         }
+        ipn = profiled_inst_per_node(step_kernel) if prec == "fp32" else None
+        if ipn and clocks and clocks.get("sm_mhz"):  # the step is issue-bound: its fraction of the issue peak
+            try:
+                sms = torch.cuda.get_device_properties(dev).multi_processor_count
+                line["roofline"]["issue"] = issue_roofline(ipn, nodes, avg_launch_ms * 1e-3, sms, clocks["sm_mhz"])
+            except Exception as exc:  # reporting only: never lose the line over it
+                line["roofline"]["issue"] = {"unavailable": repr(exc)}
         if world == 1 and not args.no_extras:
             lat.close()
             line["fp64"] = run_fp64(max(10, args.steps // 10))

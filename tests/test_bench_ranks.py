@@ -69,3 +69,22 @@ def test_fp64_pipe_figure_is_consistent_with_the_flop_figure():
     assert (flops is None) == (inst is None)
     if flops is not None:
         assert flops / 2 <= inst <= flops
+
+
+def test_issue_roofline_arithmetic_and_profile_figures():
+    """The issue figure is warp-instructions per node x nodes / launch time against 4 per SM per
+    clock; the committed per-node counts come from the same summaries as the traffic figures."""
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+
+    r = bench.issue_roofline(30.0, 1_000_000, 1e-3, 100, 2000.0)
+    assert r["achieved"] == pytest.approx(30.0)      # 3e7 warp-instructions in 1 ms
+    assert r["peak"] == pytest.approx(800.0)         # 100 SMs x 4 x 2 GHz
+    assert r["frac"] == pytest.approx(30.0 / 800.0)
+    for kernel in ("scalar", "tma"):
+        ipn = bench.profiled_inst_per_node(kernel)
+        tpn, _ = bench.profiled_traffic_per_node(kernel)
+        assert (ipn is None) == (tpn is None)
+        if ipn is not None:
+            assert 10.0 < ipn < 60.0
+    assert bench.profiled_inst_per_node("paired") is None
