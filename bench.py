@@ -174,7 +174,7 @@ def run_fp64(steps: int):
                            "frac": tf / FP64_NOMINAL_TFLOPS, "flops_per_node": fpn,
                            "peak_source": "nominal GB300 FP64 (non-tensor) rate",
                            "flops_source": f"ncu DADD + DMUL + 2 DFMA per node ({FP64_PROFILE})"}
-        ipn = profiled_fp64_flops_per_node("fp64-pipe-inst-per-node")
+        ipn = profiled_fp64_figure("fp64-pipe-inst-per-node")
         if ipn:  # DADD and DMUL take an issue slot of the FP64 pipe as a DFMA does, for half its flops
             ti = ipn * nodes * steps / (ms * 1e-3) / 1e12
             slots = FP64_NOMINAL_TFLOPS / 2.0
@@ -347,10 +347,16 @@ FP64_PROFILE = "profiles/lbm_fused_step_fp64_channel.md"
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate; no measured figure on this machine
 
 
-def profiled_fp64_flops_per_node(key: str = "fp64-flops-per-node"):
+def profiled_fp64_flops_per_node():
     """FP64 floating-point operations per node update of the step kernel (DADD + DMUL + 2 DFMA,
-    counted by ncu; key "fp64-pipe-inst-per-node": DADD + DMUL + DFMA thread instructions), or
-    None when the summary was taken on other kernel sources."""
+    counted by ncu), or None when the summary was taken on other kernel sources."""
+    return profiled_fp64_figure("fp64-flops-per-node")
+
+
+def profiled_fp64_figure(key: str):
+    """A per-node figure of the FP64 step kernel's committed ncu summary ("fp64-flops-per-node",
+    "fp64-pipe-inst-per-node": DADD + DMUL + DFMA thread instructions), or None when the summary
+    was taken on other kernel sources."""
     import re
 
     path = os.path.join(ROOT, FP64_PROFILE)

@@ -65,7 +65,7 @@ def test_fp64_pipe_figure_is_consistent_with_the_flop_figure():
     import bench
 
     flops = bench.profiled_fp64_flops_per_node()
-    inst = bench.profiled_fp64_flops_per_node("fp64-pipe-inst-per-node")
+    inst = bench.profiled_fp64_figure("fp64-pipe-inst-per-node")
     assert (flops is None) == (inst is None)
     if flops is not None:
         assert flops / 2 <= inst <= flops
