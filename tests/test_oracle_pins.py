@@ -339,13 +339,15 @@ def test_vapour_diagnostics_count_the_bubble():
     p = prm(nx, geometry="walls", thermal=1, g_a=0.0, heater_x0=25, heater_len=7, heat_on_step=0)
     T = 0.9 * oracle.Tc(p)
     rv, rl, _ = oracle.maxwell(p, T)
-    fields = I.sessile(nx, ny, R, rv, rl, T)  # a vapour half-disk on the bottom wall
+    fields = list(I.sessile(nx, ny, R, rv, rl, T))  # a vapour half-disk on the bottom wall
+    fields[0] = fields[0].copy()
+    fields[0][1, 2:5] = rv  # vapour on the second row only, away from the heater: wall rows differ
     O = oracle.Oracle(nx, ny, p)
     O.init_fields(*fields)
     assert O.step(1) == 0
     d = O.last_diag()
     vap = fields[0] < p["rho_vapor"]
-    assert d["vapor_area"] == vap.sum() and d["wall_vapor"] == vap[0].sum()
+    assert d["vapor_area"] == vap.sum() and d["wall_vapor"] == vap[0].sum() != vap[1].sum()
     assert d["heater_vapor"] == vap[0, 25:32].sum()
     assert d["zone_vapor"] == vap[:, 18:39].sum()
     assert 0.4 * np.pi * R * R < d["vapor_area"] < 0.6 * np.pi * R * R and d["heater_vapor"] == 7
