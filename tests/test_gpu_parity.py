@@ -621,3 +621,26 @@ def test_fixed_point_totals_at_full_width():
         want = math.fsum(q)
         assert abs(d[key] - want) <= bound(ny, float(np.abs(q).sum())), key
     lat.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_repeated_runs_are_bit_identical(precision):
+    """The per-tile sums enter integer fixed-point totals, so the order in which the tiles of a
+    launch finish (which varies from run to run) cannot change a record or, through the buoyancy
+    mean, a population: two runs of the same lattice with the same tiling agree bit for bit."""
+    L = lbm()
+    nx, ny = 1000, 200
+    p, fields = channel_case(nx, ny, heat_on_step=10)
+    runs = []
+    for _ in range(2):
+        lat = L.Lattice(nx, ny, precision)
+        lat.set_params(p)
+        lat.set_tiling(64, 4)  # many small tiles: 18 strips x 50 bands = 900 per launch
+        lat.init_fields(*fields)
+        lat.step(60)
+        f, g = lat.populations()
+        runs.append((f, g, lat.diagnostics_range(0, 60)))
+        lat.close()
+    (f0, g0, r0), (f1, g1, r1) = runs
+    assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+    assert np.array_equal(r0, r1)
