@@ -123,3 +123,34 @@ def test_vapour_components_join_across_a_periodic_edge():
     assert n == 2
     assert lab[5, 0] == lab[5, 19] != lab[1, 9]
     assert np.bincount(lab.ravel())[lab[5, 0]] == 18
+
+
+def test_detachment_rule_edge_cases():
+    """The departure rule's clauses one at a time, on hand-made frames (60 x 40, heater columns
+    25-34): a bubble lifted one row off the heater departs (row 0 decides what is attached); a
+    rising bubble that grows into where the previous frame's attached vapour was is not counted
+    again (it overlaps a region already detached); a blob that appears away from the heater is
+    not a departure (it overlaps no attached vapour); and 4-connectivity keeps regions that touch
+    only at a corner apart."""
+    ny, nx, rho_l, rho_v = 40, 60, 6.0, 0.6
+
+    def frame(*disks):
+        vap = np.zeros((ny, nx), dtype=bool)
+        for cx, cy, r in disks:
+            vap |= _disk(vap.shape, cx, cy, r)
+        return np.where(vap, rho_v, rho_l)
+
+    det = lambda fr: B.detachments(fr, [100 * (k + 1) for k in range(len(fr))], 3.2, heater_x0=25,  # noqa: E731
+                                   heater_len=10, min_area=20)
+    lifted = [frame((30, 5, 5)), frame((30, 6, 5))]  # rows 0-10, then rows 1-11
+    assert [e["step"] for e in det(lifted)] == [200]
+    grow = [frame((30, 5, 6)),                    # attached, rows 0-11
+            frame((30, 3, 4), (30, 14, 5)),       # new attached bubble rows 0-7; riser rows 9-19 departs
+            frame((30, 2, 2), (30, 15, 8))]       # the riser grows into rows 7-23: overlaps both
+    assert [e["step"] for e in det(grow)] == [200]
+    appear = [frame((30, 5, 6)), frame((30, 5, 6), (8, 25, 5))]
+    assert det(appear) == []
+    rho = np.full((10, 10), rho_l)
+    rho[2:5, 2:5] = rho_v
+    rho[5:8, 5:8] = rho_v  # touches the first block only at the corner (4, 4)-(5, 5)
+    assert B.vapour_components(rho, 3.2)[1] == 2
