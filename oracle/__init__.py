@@ -54,12 +54,24 @@ class OrcParams(ctypes.Structure):
     ]
 
 
+CFLAGS = ["-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off"]
+
+
+def compile_oracle(src: str, out: str) -> None:
+    """gcc, plain -O2, no fast-math, no contraction; with OpenMP for the optional threaded
+    loops where the compiler has it, else without (the pragmas are then ignored)."""
+    try:
+        subprocess.check_call(["gcc"] + CFLAGS + ["-fopenmp", "-o", out, src, "-lm"],
+                              stderr=subprocess.DEVNULL)
+    except subprocess.CalledProcessError:
+        subprocess.check_call(["gcc"] + CFLAGS + ["-o", out, src, "-lm"])
+
+
 def build(force: bool = False) -> str:
-    """Compile liboracle.so from the C source (gcc, plain -O2, no fast-math)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
-             "-o", _LIB, _SRC, "-lm"])
+    """Compile liboracle.so from the C source."""
+    hdr = os.path.join(_HERE, "lbm_oracle.h")
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(hdr)):
+        compile_oracle(_SRC, _LIB)
     return _LIB
 
 
@@ -75,6 +87,7 @@ def lib():
         L.orc_create.restype = ctypes.c_void_p
         L.orc_create.argtypes = [ctypes.c_int32, ctypes.c_int32]
         L.orc_destroy.argtypes = [ctypes.c_void_p]
+        L.orc_set_threads.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_init_fields.argtypes = [ctypes.c_void_p, P, dp, dp, dp, dp]
         L.orc_set_populations.argtypes = [ctypes.c_void_p, dp, dp, ctypes.c_int64, ctypes.c_double]
         L.orc_get_populations.argtypes = [ctypes.c_void_p, dp, dp]
@@ -114,12 +127,14 @@ def _ptr(a):
 class Oracle:
     """One lattice of the oracle: post-stream populations f^n, g^n, shape (9, ny, nx)."""
 
-    def __init__(self, nx: int, ny: int, params: dict):
+    def __init__(self, nx: int, ny: int, params: dict, threads: int = 1):
         self.nx, self.ny = int(nx), int(ny)
         self.params = make_params(params)
         self._h = lib().orc_create(self.nx, self.ny)
         if not self._h:
             raise MemoryError("orc_create failed")
+        if threads != 1 and lib().orc_set_threads(self._h, int(threads)) != 0:
+            raise ValueError("threads must be >= 1")
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -44,6 +44,14 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* The per-node loops over rows may run on several threads (orc_set_threads, in a build with
+ * OpenMP; without it the pragmas are ignored).  Every node's arithmetic is the same either
+ * way and every sum over nodes stays serial in row-major order, so the results do not depend
+ * on the thread count.  The default is one thread (no thread pool is started). */
+#define ORC_ROWS _Pragma("omp parallel for if(L->threads > 1) num_threads(L->threads > 1 ? L->threads : 1)")
+#define ORC_ROWS_STATUS \
+  _Pragma("omp parallel for reduction(max : status) if(L->threads > 1) num_threads(L->threads > 1 ? L->threads : 1)")
+
 /* D2Q9 velocity set (Fig. 1) with the standard weights 4/9, 1/9, 1/36. */
 static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
@@ -64,6 +72,7 @@ struct orc_lattice {
   double *rho, *ux, *uy, *T, *psi, *dpdT, *Fx, *Fy, *uax, *uay, *phi;
   double *fpost, *gpost, *fnew, *gnew;
   unsigned char* unknown;
+  int threads; /* threads of the per-node loops (<= 1: serial) */
 };
 
 static size_t nodes(const orc_lattice* L) { return (size_t)L->nx * (size_t)L->ny; }
@@ -99,6 +108,12 @@ orc_lattice* orc_create(int32_t nx, int32_t ny) {
     return NULL;
   }
   return L;
+}
+
+int orc_set_threads(orc_lattice* L, int threads) {
+  if (!L || threads < 1) return ORC_BAD_ARG;
+  L->threads = threads;
+  return ORC_OK;
 }
 
 void orc_destroy(orc_lattice* L) {
@@ -288,6 +303,7 @@ static int macroscopic(orc_lattice* L, const orc_params* P) {
   int status = ORC_OK;
 
   /* Moments, Eqs. 4, 6, 17 */
+  ORC_ROWS_STATUS
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       size_t k = nid(L, x, y);
@@ -313,6 +329,7 @@ static int macroscopic(orc_lattice* L, const orc_params* P) {
   if (status != ORC_OK) return status;
 
   /* Pseudopotential (Eqs. 11-12) and (dp/dT)_rho */
+  ORC_ROWS_STATUS
   for (size_t k = 0; k < n; ++k) {
     if (P->multiphase) {
       L->psi[k] = orc_psi(P, L->rho[k], L->T[k]);
@@ -324,6 +341,7 @@ static int macroscopic(orc_lattice* L, const orc_params* P) {
   const double psi_w = P->multiphase ? orc_psi(P, P->rho_w, T0) : 0.0;
 
   /* Body force: Shan-Chen (Eqs. 9-10), wetting (Eq. 15), buoyancy (Eq. 14) */
+  ORC_ROWS
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       size_t k = nid(L, x, y);
@@ -518,6 +536,7 @@ static int one_step(orc_lattice* L, const orc_params* P) {
   if (status != ORC_OK) return status;
 
   /* f collision: Eqs. 1-3 with the exact-difference force term of Eq. 5 */
+  ORC_ROWS
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       size_t k = nid(L, x, y);
@@ -534,6 +553,7 @@ static int one_step(orc_lattice* L, const orc_params* P) {
   /* g collision: Eq. 16 with g^eq of Eq. 18 and the source of the second Eq. 19 */
   double source_total = 0.0;
   if (P->thermal) {
+    ORC_ROWS
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
         size_t k = nid(L, x, y);
@@ -634,7 +654,8 @@ static int one_step(orc_lattice* L, const orc_params* P) {
 
   /* Streaming (Eqs. 1, 16) with the wall rules; open-end unknowns marked */
   memset(L->unknown, 0, 9 * n);
-  for (int i = 0; i < 9; ++i)
+  for (int i = 0; i < 9; ++i) {
+    ORC_ROWS
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
         int sx = x - CX[i], sy = y - CY[i];
@@ -660,6 +681,7 @@ static int one_step(orc_lattice* L, const orc_params* P) {
         L->fnew[dst] = L->fpost[pid(L, i, sx, sy)];
         if (P->thermal) L->gnew[dst] = L->gpost[pid(L, i, sx, sy)];
       }
+  }
   if (P->geometry == ORC_CHANNEL) {
     for (int y = 0; y < ny; ++y) inlet_node(L, P, y);
     for (int y = 0; y < ny; ++y) outlet_node(L, P, y);

@@ -62,6 +62,10 @@ typedef struct orc_lattice orc_lattice;
 
 orc_lattice* orc_create(int32_t nx, int32_t ny);
 void orc_destroy(orc_lattice* L);
+/* Threads for the per-node loops (a build with OpenMP; otherwise ignored).  Results do not
+ * depend on it: node arithmetic is unchanged and every sum over nodes stays serial.
+ * Default 1.  ORC_BAD_ARG for threads < 1. */
+int orc_set_threads(orc_lattice* L, int threads);
 
 /* f = f^eq(rho, u) (Eq. 3), g = g^eq(T, u) (Eq. 18); step = 0; rho_avg of the
  * previous step is taken as the mean of the initial rho.  Arrays: ny*nx row-major. */
