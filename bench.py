@@ -168,23 +168,36 @@ def run_fp64(steps: int):
            "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                    "peak_source": f"{kind} HBM copy bandwidth", "algorithmic_bytes_per_node": bytes_per_node("fp64")}}
     fpn = profiled_fp64_flops_per_node()
+    peak_tf, peak_src = fp64_peak_tflops()
+    out["fp64_fma_peak"] = {"value": peak_tf, "unit": "TFLOP/s", "source": peak_src}
     if fpn:  # FP64 arithmetic, not HBM, bounds this form on GB300
         tf = fpn * nodes * steps / (ms * 1e-3) / 1e12
-        out["roofline"] = {"bound": "alu", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                           "frac": tf / FP64_NOMINAL_TFLOPS, "flops_per_node": fpn,
-                           "peak_source": "nominal GB300 FP64 (non-tensor) rate",
+        out["roofline"] = {"bound": "alu", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
+                           "frac": tf / peak_tf, "flops_per_node": fpn, "peak_source": peak_src,
                            "flops_source": f"ncu DADD + DMUL + 2 DFMA per node ({FP64_PROFILE})"}
         ipn = profiled_fp64_figure("fp64-pipe-inst-per-node")
         if ipn:  # DADD and DMUL take an issue slot of the FP64 pipe as a DFMA does, for half its flops
             ti = ipn * nodes * steps / (ms * 1e-3) / 1e12
-            slots = FP64_NOMINAL_TFLOPS / 2.0
+            slots = peak_tf / 2.0
             out["roofline"]["pipe"] = {"achieved": ti, "peak": slots, "unit": "T FP64 thread-instructions/s",
                                        "frac": ti / slots, "inst_per_node": ipn,
-                                       "peak_source": "nominal FP64 rate / 2 flops per DFMA"}
+                                       "peak_source": peak_src + " / 2 flops per DFMA"}
     else:
         out["roofline"] = dict(out["hbm"], bound="hbm")
     lat.close()
     return out
+
+
+def fp64_peak_tflops():
+    """FP64 FMA rate of this GPU, measured by the library's probe (independent DFMA chains, CUDA
+    events), with the nominal datasheet figure only as a fallback."""
+    try:
+        from paper_2009_05264_gb300 import lbm
+
+        best = max(lbm.probe_fma_rate("fp64", 1 << 16) for _ in range(3))
+        return best / 1e12, "measured: FP64 FMA probe (independent DFMA chains, best of 3, CUDA events)"
+    except Exception as exc:  # reporting only
+        return FP64_NOMINAL_TFLOPS, f"nominal GB300 FP64 (non-tensor) rate; probe failed: {exc!r}"
 
 
 def run_c2(steps: int = 2000, nx: int = 1000, ny: int = 100):
@@ -263,7 +276,8 @@ def run_batch(steps: int, trial_steps: int = 4, n: int = 64, seed: int = SEED + 
     for m in members:
         m.sync()
     ms_s = e0.elapsed_time(e1)
-    ok = all(np.isfinite(m.fields()["rho"]).all() for m in members[:4])
+    member_ok = [bool(np.isfinite(m.fields()["rho"]).all()) for m in members]
+    ok = all(member_ok)
     b.close()
     batched = nodes * steps / (ms_b * 1e-3) / 1e6
     seq = nodes * steps / (ms_s * 1e-3) / 1e6
@@ -275,6 +289,7 @@ def run_batch(steps: int, trial_steps: int = 4, n: int = 64, seed: int = SEED + 
                            "how": "each lattice alone through lbm_step_async, one after another"},
             "speedup_vs_sequential": batched / seq, "tiling": f"{cols}x{rows}", "autotune_s": tune_s,
             "gpu_launches": launches, "launches_sequential": n * steps, "finite": bool(ok),
+            "members_finite": sum(member_ok), "members": len(member_ok),
             "solves_per_hour_50k_steps": n * 3600.0 / (50000 * ms_b * 1e-3 / steps),
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                          "peak_source": f"{kind} HBM copy bandwidth"}}
@@ -324,9 +339,11 @@ def run_serve(n_requests: int, steps: int, rate: float = 2.0, seed: int = SEED +
 _CSRC = "paper_2009_05264_gb300/csrc/"
 # sources of each step-kernel form (scalar: also the FP64 step) and its ncu summary
 STEP_SOURCES = {"scalar": (_CSRC + "lbm_kernels.cuh", _CSRC + "lbm_internal.h"),
+                "interior": (_CSRC + "lbm_kernels.cuh", _CSRC + "lbm_internal.h"),
                 "tma": (_CSRC + "lbm_kernels.cuh", _CSRC + "lbm_internal.h", _CSRC + "lbm_tma.cuh")}
-PROFILES = {"scalar": "profiles/lbm_fused_step_fp32_channel.md", "tma": "profiles/lbm_tma_step_fp32_channel.md"}
+PROFILES = {"interior": "profiles/lbm_fused_step_fp32_channel.md", "tma": "profiles/lbm_tma_step_fp32_channel.md"}
 KERNEL_LABELS = {"scalar": "lbm_fused_kernel (MODE_STEP)",
+                 "interior": "lbm_fused_kernel (MODE_STEP, interior path on tiles away from the open ends)",
                  "paired": "lbm_pair_kernel (two columns per thread, packed FP32)",
                  "tma": "lbm_tma_kernel (MODE_STEP, rows staged by bulk tensor copies)"}
 
@@ -344,7 +361,7 @@ def step_source_digest(kernel: str = "scalar") -> str:
 
 
 FP64_PROFILE = "profiles/lbm_fused_step_fp64_channel.md"
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate; no measured figure on this machine
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate: the fallback when the probe cannot run
 
 
 def profiled_fp64_flops_per_node():
@@ -437,25 +454,56 @@ def dist_env():
     return world, rank, local
 
 
-def cpu_baseline(steps: int = 80, nx: int = 1000):
-    """The oracle as it stands on one host core: `steps` steps of a nx x 800 band of the channel
-    (80 steps: about 10-15 s of CPU work)."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_rate(steps: int, nx: int, threads: int):
+    """MLUPS of the oracle as it stands on `threads` host threads: `steps` steps of a nx x NY band
+    of the benchmark channel (its rows spread over the threads; same results at any count)."""
     import oracle
     from paper_2009_05264_gb300 import inputs as I
 
     p = workload_params("fp64")
     Tc = oracle.Tc(p)
     fields = I.smooth_random(nx, NY, 5.95, 0.9 * Tc, seed=SEED, drho=0.002, du=0.005, dT=0.002)
-    orc = oracle.Oracle(nx, NY, p)
+    orc = oracle.Oracle(nx, NY, p, threads=threads)
     orc.init_fields(*fields)
     t0 = time.perf_counter()
     st = orc.step(steps)
     dt = time.perf_counter() - t0
     if st != 0:
         raise RuntimeError("oracle unstable on the baseline sample")
-    return {"value": nx * NY * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} steps of a {nx}x{NY} band of the channel (same physics), FP64, single thread",
-            "seconds": dt}
+    return nx * NY * steps / dt / 1e6, dt
+
+
+def cpu_baseline(steps: int = 60, nx: int = 1000):
+    """The oracle as it stands on the host: all cores (OpenMP over rows, serial fixed-order sums)
+    on `steps` steps of a nx x 800 band of the channel, and one core on a third of them
+    (about 10-20 s of CPU work in all)."""
+    cores = os.cpu_count() or 1
+    v_all, dt_all = oracle_rate(steps, nx, cores)
+    s1 = max(steps // 3, 5)
+    v_one, dt_one = oracle_rate(s1, nx, 1)
+    return {"value": v_all, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{steps} steps of a {nx}x{NY} band of the channel (same physics), FP64, "
+                      f"{cores} threads (OpenMP over rows)", "seconds": dt_all, "cpu_model": cpu_model(),
+            "single_core": {"value": v_one, "unit": "MLUPS", "cores": 1, "seconds": dt_one,
+                            "sample": f"{s1} steps of the same band, one thread"}}
 
 
 def run_reference(args):
@@ -464,22 +512,23 @@ def run_reference(args):
         return 0
     import oracle  # noqa: F401
 
+    cores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        cpu_baseline(steps=1, nx=200)
+        oracle_rate(1, 200, cores)
     t0 = time.perf_counter()
     per = []
     for _ in range(args.steps):
-        r = cpu_baseline(steps=1, nx=1000)
-        per.append(r["seconds"])
+        per.append(oracle_rate(1, 2000, cores)[1])
     total = time.perf_counter() - t0
-    value = 1000 * NY * args.steps / sum(per) / 1e6
+    value = 2000 * NY * args.steps / sum(per) / 1e6
     line = {"impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "nx": NX, "ny": NY,
-                       "sample": f"each step: one oracle step on a 1000x{NY} band"},
-            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": f"one step of a 1000x{NY} band per timed step"},
+                       "sample": f"each step: one oracle step on a 2000x{NY} band"},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"one step of a 2000x{NY} band per timed step, {cores} threads (OpenMP "
+                                       f"over rows)", "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -577,7 +626,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD if prec == "fp32" else WORKLOAD.replace("FP32", "FP64"),
                        "nx": NX, "ny": NY, "nodes_per_gpu": nodes, "precision": prec,
                        "tiling": tiling_desc,
-                       "kernel": f"{step_kernel} (requested {args.kernel})" if prec == "fp32" else "scalar (FP64)",
+                       "kernel": f"{step_kernel} (requested {args.kernel})",
                        "l2": "inputs larger than L2: 2 x 0.92 GB population buffers vs 129 MB L2",
                        "parallelism": f"{world} independent channel replicas"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -623,7 +672,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--tiling", default=None, help="COLSxROWS, e.g. 128x32")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "scalar", "paired", "tma"], help="FP32 step kernel form")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "scalar", "paired", "tma", "interior"],
+                    help="step kernel form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the fp64, batch and serve measurements")
     ap.add_argument("--batch-steps", type=int, default=300)

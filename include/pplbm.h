@@ -272,11 +272,37 @@ lbm_status lbm_default_band_plan(int32_t nx, int32_t ny, int32_t cols, int64_t s
  *     warps wait on rows that arrive later than the per-thread copies do).
  * FP64 lattices, and lbm_step_noalloc on caller-laid-out buffers, always use the scalar
  * form.  LBM_EINVAL for other values. */
-enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_SCALAR = 1, LBM_KERNEL_PAIRED = 2, LBM_KERNEL_TMA = 3 };
+enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_SCALAR = 1, LBM_KERNEL_PAIRED = 2, LBM_KERNEL_TMA = 3, LBM_KERNEL_INTERIOR = 4 };
 lbm_status lbm_set_kernel(lbm_ctx* ctx, int32_t kernel);
 /* The form (LBM_KERNEL_SCALAR, _PAIRED or _TMA) the context's step launches take
  * with its current kernel request, precision, parameters and tiling; -1 if ctx is NULL. */
 int32_t lbm_step_kernel(const lbm_ctx* ctx);
+
+/* How lbm_step / lbm_step_async advance the lattice (a calling convention of the library;
+ * the paper's time loop, Sec. 2 and Fig. 2, is the same either way).
+ *   LBM_LOOP_LAUNCHES: one step-kernel launch per step.
+ *   LBM_LOOP_PERSISTENT: one cooperative launch per call advances all nsteps steps (nsteps >= 2;
+ *     a single step is one launch); its CTAs draw the tiles of each step from a counter and
+ *     meet at a grid-wide barrier between steps.  Every barrier wait is bounded: a CTA that
+ *     waits longer than 5 s (or than the poll limit of lbm_set_wait_limit) gives up, the
+ *     launch ends, and the next lbm_sync returns LBM_ETIMEOUT; the lattice state is then
+ *     undefined until it is initialised again (lbm_set_params, lbm_init_fields,
+ *     lbm_set_populations or lbm_load_state), and the CUDA context stays usable.  Only the
+ *     one-column step forms (LBM_KERNEL_SCALAR, LBM_KERNEL_INTERIOR) have a persistent form.
+ *   LBM_LOOP_AUTO (default): persistent where the step tiling fits in one wave of the
+ *     persistent kernel (small lattices, whose steps are short enough for the launch gap and
+ *     the kernel boundary to count), else one launch per step.
+ * Results are the same either way up to the rounding of separately compiled kernels.
+ * LBM_EINVAL for other values. */
+enum { LBM_LOOP_AUTO = 0, LBM_LOOP_LAUNCHES = 1, LBM_LOOP_PERSISTENT = 2 };
+lbm_status lbm_set_step_loop(lbm_ctx* ctx, int32_t loop);
+/* The loop (LBM_LOOP_LAUNCHES or _PERSISTENT) a multi-step call takes now; -1 if ctx is NULL. */
+int32_t lbm_step_loop(lbm_ctx* ctx);
+/* Poll limit of the persistent launch's barrier waits: a CTA gives up after max_polls polls
+ * (0, the default: after 5 s of polling only).  A test sets 1 to make a wait run out while
+ * the other CTAs are still working, and checks that lbm_sync reports LBM_ETIMEOUT and that the
+ * context recovers.  LBM_EINVAL for max_polls < 0 or >= 2^32. */
+lbm_status lbm_set_wait_limit(lbm_ctx* ctx, int64_t max_polls);
 
 int64_t lbm_get_step(const lbm_ctx* ctx);
 /* Kernel launches enqueued by this context since creation (all kinds). */
@@ -325,6 +351,16 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps);
  * status and its slot in *unstable_slot (-1 if none; may be NULL). */
 lbm_status lbm_batch_step_async(lbm_batch* b, int64_t nsteps);
 lbm_status lbm_batch_sync(lbm_batch* b, int32_t* unstable_slot);
+/* The step loop of the batch's multi-step calls (LBM_LOOP_* as lbm_set_step_loop: one
+ * cooperative launch per call over every member's tiles with bounded grid barriers between
+ * steps, or one launch per step replayed from CUDA graphs; auto: persistent when the batch's
+ * tiles fit in one wave).  A barrier wait that gives up sets LBM_ETIMEOUT on the members of
+ * the CTAs that gave up; lbm_batch_sync reports it. */
+lbm_status lbm_batch_set_step_loop(lbm_batch* b, int32_t loop);
+/* The loop a multi-step call takes now (LBM_LOOP_LAUNCHES or _PERSISTENT); -1 on error. */
+int32_t lbm_batch_step_loop(lbm_batch* b);
+/* As lbm_set_wait_limit, for the batch's persistent launches. */
+lbm_status lbm_batch_set_wait_limit(lbm_batch* b, int64_t max_polls);
 /* lbm_read_fields of one member. */
 lbm_status lbm_batch_read_fields(lbm_batch* b, int32_t slot, double* rho, double* ux, double* uy, double* T,
                                  size_t n);
@@ -355,12 +391,14 @@ lbm_status lbm_batch_destroy(lbm_batch* b);
  * the step on cuda_stream (a cudaStream_t; NULL = the default stream).
  *
  * Scratch: a fixed 0.36 MB device array inside the library, which every GPU that
- * loads the library holds until the process exits.  The first call on a device
- * looks up that array's device address (once per device, with the device
- * current); make that first call before capturing any CUDA graph.  Every call
- * reuses the same array and overwrites the previous call's contents, so calls that
- * overlap on the GPU (other streams, other host threads) race and must be
- * serialised by the caller.  Sizes beyond the array's capacity are rejected:
+ * loads the library holds until the process exits.  Every call looks up that array's
+ * device address on the current device (cudaGetSymbolAddress), so a device reset or a
+ * recreated context between calls is safe.  Every call reuses the same array and
+ * overwrites the previous call's contents (the parts that must start at zero are
+ * cleared by each call), so calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  The call allocates nothing:
+ * no cudaMalloc, cudaFree or allocating library routine; it copies two small
+ * descriptors from host memory, launches, reads the step's state back and waits.  Sizes beyond the array's capacity are rejected:
  * the lattice is cut into ceil(nx / 120) column strips and at most 8192 tiles,
  * so nx > 983040, or 9 * nx * ny >= 2^31, returns LBM_EINVAL.
  * Errors: LBM_EINVAL (invalid parameters, sizes, NULL or aliased buffers),
@@ -368,6 +406,15 @@ lbm_status lbm_batch_destroy(lbm_batch* b);
 lbm_status lbm_step_noalloc(const lbm_params* p, int32_t nx, int32_t ny, lbm_precision prec, const void* f_in,
                             const void* g_in, void* f_out, void* g_out, int32_t in_post_stream, int64_t step,
                             double rho_avg_prev, double* diag_out, void* cuda_stream);
+
+/* Measurement helper, not part of the paper's method: the fused multiply-add rate
+ * (floating-point operations per second, two per FMA) that a plain kernel of independent
+ * FMA chains reaches on the current device, in FP64 (fp64 = 1) or FP32 (fp64 = 0), over
+ * iters FMAs per chain (1 <= iters <= 2^30; 2^16 runs for milliseconds).  The FP64 step is
+ * bounded by this rate, which the benchmark reports its FP64 roofline against.  Allocates
+ * a small output buffer on cuda_stream (a cudaStream_t; NULL = the default stream) and waits
+ * for the probe.  LBM_EINVAL for bad arguments, LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_probe_fma_rate(int32_t fp64, int64_t iters, void* cuda_stream, double* flops_per_s);
 
 /* Free the context and its device memory (not caller-provided memory).  NULL-safe. */
 lbm_status lbm_destroy(lbm_ctx* ctx);

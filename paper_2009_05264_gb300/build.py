@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libpplbm.so")
-SOURCES = ["lbm_api.cu", "lbm_batch.cu", "lbm_f32.cu", "lbm_f64.cu", "lbm_noalloc.cu"]
+SOURCES = ["lbm_api.cu", "lbm_batch.cu", "lbm_f32.cu", "lbm_f64.cu", "lbm_noalloc.cu", "lbm_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -17,15 +17,39 @@
 
 namespace pplbm {
 cudaError_t launch_lbm_f32(int, int, int, int, bool, const Inst*, const Tile*, int, cudaStream_t, const Inst*);
-cudaError_t launch_lbm_f64(int, int, int, bool, const Inst*, const Tile*, int, cudaStream_t, const Inst*);
+cudaError_t launch_lbm_f64(int, int, int, int, bool, const Inst*, const Tile*, int, cudaStream_t, const Inst*);
 cudaError_t launch_init_from_fields_f32(const Inst*, int, int, const double*, int, cudaStream_t);
 cudaError_t launch_init_from_fields_f64(const Inst*, int, int, const double*, int, cudaStream_t);
 cudaError_t launch_init_builtin_f32(const Inst*, int, int, InitSpec, cudaStream_t);
 cudaError_t launch_init_builtin_f64(const Inst*, int, int, InitSpec, cudaStream_t);
 
+cudaError_t launch_persistent_f32(int, int, int, bool, const Inst*, const Tile*, int, int, GridBar*, unsigned,
+                                  cudaStream_t, const Inst*);
+cudaError_t launch_persistent_f64(int, int, int, bool, const Inst*, const Tile*, int, int, GridBar*, unsigned,
+                                  cudaStream_t, const Inst*);
+int persistent_resident_f32(int, int, int, bool, bool);
+int persistent_resident_f64(int, int, int, bool, bool);
+
+cudaError_t launch_persistent(int fp64, int thermal, int cols, int kernel, bool full, const Inst* d_inst,
+                              const Tile* d_tiles, int ntiles, int nsteps, GridBar* bar, unsigned max_polls,
+                              cudaStream_t s, const Inst* h_inst) {
+  return fp64 ? launch_persistent_f64(thermal, cols, kernel, full, d_inst, d_tiles, ntiles, nsteps, bar, max_polls, s,
+                                      h_inst)
+              : launch_persistent_f32(thermal, cols, kernel, full, d_inst, d_tiles, ntiles, nsteps, bar, max_polls, s,
+                                      h_inst);
+}
+
+long long persistent_slots(int fp64, int thermal, int cols, int kernel, bool full, bool single) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = fp64 ? persistent_resident_f64(thermal, cols, kernel, full, single)
+                          : persistent_resident_f32(thermal, cols, kernel, full, single);
+  return (long long)sms * per_sm;
+}
+
 cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, int kernel, bool full, const Inst* d_inst,
                        const Tile* d_tiles, int ntiles, cudaStream_t s, const Inst* h_inst) {
-  return fp64 ? launch_lbm_f64(thermal, cols, mode, full, d_inst, d_tiles, ntiles, s, h_inst)
+  return fp64 ? launch_lbm_f64(thermal, cols, mode, kernel, full, d_inst, d_tiles, ntiles, s, h_inst)
               : launch_lbm_f32(thermal, cols, mode, kernel, full, d_inst, d_tiles, ntiles, s, h_inst);
 }
 cudaError_t launch_init_from_fields(int fp64, const Inst* d_inst, int nx, int ny, const double* d_fields,
@@ -144,6 +168,21 @@ const char* fill_inst(Inst& I, const lbm_params* p, int nx, int ny, int pitch, l
     I.sqrtT_r = std::sqrt(Tr);
     I.rr2_Dr = rr * rr / Dr;
   }
+  for (int i = 0; i < 9; ++i) {
+    static const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1}, cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    I.poff[i] = (int)(i * plane);
+    I.loff[i] = (int)(i * plane - cy[i] * (long long)pitch - cx[i]);
+  }
+  I.mix = 0.5 * (1.0 - I.beta);
+  I.drho_out = I.rho_out - I.rho_ref;
+  I.dT_in = I.T_in - I.T_ref;
+  I.dT_heat = I.T_heat - I.T_ref;
+  I.drho_vapor = p->rho_vapor - I.rho_ref;
+  {
+    const double G3 = 1.5 * I.G2, pr = I.psi_ref;
+    I.wall0 = -G3 * (I.beta + I.mix) * pr * pr + I.Gwet_psiw * pr / 6.0;
+    I.wall1 = -G3 * I.beta * pr + I.Gwet_psiw / 6.0;
+  }
   I.heater_x0 = p->heater_x0 < 0 ? nx / 5 : p->heater_x0;
   I.heater_len = p->heater_len;
   I.heat_on_step = p->heat_on_step;
@@ -205,7 +244,7 @@ BandPlan default_band_plan(int nx, int ny, int cols, long long slots) {
 long long step_wave_slots(int fp64, int thermal, int cols, int kernel) {
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int per_sm = fp64 ? resident_ctas_f64(thermal, cols) : resident_ctas_f32(thermal, cols, kernel);
+  const int per_sm = fp64 ? resident_ctas_f64(thermal, cols, kernel) : resident_ctas_f32(thermal, cols, kernel);
   return (long long)sms * (per_sm > 0 ? per_sm : 1);
 }
 }  // namespace pplbm
@@ -227,8 +266,8 @@ struct Layout {
   long long plane;
   size_t pop_bytes;  // one 9-plane buffer
   int max_tiles;
-  size_t off_f[2], off_g[2], off_rho_prev, off_tmaps, off_inst, off_state, off_sums, off_ring, off_tiles_step,
-      off_tiles_aux, total;
+  size_t off_f[2], off_g[2], off_rho_prev, off_tmaps, off_inst, off_state, off_sums, off_bar, off_ring,
+      off_tiles_step, off_tiles_aux, total;
 };
 
 Layout make_layout(int nx, int ny, lbm_precision prec) {
@@ -248,6 +287,7 @@ Layout make_layout(int nx, int ny, lbm_precision prec) {
   L.off_inst = off; off += align_up(sizeof(Inst));
   L.off_state = off; off += align_up(sizeof(InstState));
   L.off_sums = off; off += align_up(NPART * sizeof(unsigned long long));
+  L.off_bar = off; off += align_up(sizeof(GridBar));
   L.off_ring = off; off += align_up((size_t)RING * NDIAG * sizeof(double));
   L.off_tiles_step = off; off += align_up((size_t)L.max_tiles * sizeof(Tile));
   L.off_tiles_aux = off; off += align_up((size_t)L.max_tiles * sizeof(Tile));
@@ -260,7 +300,7 @@ int tile_cols(int cols) { return cols - 8; }
 
 // Tiles of a band plan in dispatch order: the tall bands of every strip (band by band),
 // then the short bands.
-void build_tiles(int nx, int ny, int cols, const BandPlan& plan, std::vector<Tile>& out) {
+void build_tiles(int nx, int ny, int cols, const BandPlan& plan, std::vector<Tile>& out, int geometry) {
   out.clear();
   const int w = tile_cols(cols);
   const int strips = (nx + w - 1) / w;
@@ -271,6 +311,7 @@ void build_tiles(int nx, int ny, int cols, const BandPlan& plan, std::vector<Til
       t.x0 = sidx * w;
       t.y0 = y0;
       t.y1 = y1;
+      t.interior = tile_is_interior(geometry, nx, cols, t.x0);
       out.push_back(t);
     }
   };
@@ -346,6 +387,8 @@ struct lbm_ctx {
   long long step_host = 0;  // step count as last synchronised
   unsigned long long params_gen = 0;  // bumped whenever the descriptor changes
   int kernel = LBM_KERNEL_AUTO;        // requested step kernel form (resolve_kernel picks the one launched)
+  int loop = LBM_LOOP_AUTO;            // requested step loop (one launch per step or persistent)
+  unsigned max_polls = 0;              // barrier polls before a persistent launch gives up (0: time limit only)
   bool have_tmaps = false;             // FP32: the tensor maps of the population buffers are on the device
   std::string err;
 };
@@ -380,8 +423,11 @@ struct DeviceGuard {
 
 size_t elt_size(const lbm_ctx* c) { return c->prec == LBM_FP64 ? 8 : 4; }
 
+// A new state (initialisation, injected populations, a loaded checkpoint): the step state,
+// and zero totals of the partial sums (a launch that gave up waiting may have left some).
 lbm_status upload_state(lbm_ctx* c) {
   LBM_CUDA(c, cudaMemcpyAsync(c->d_state, c->h_state, sizeof(InstState), cudaMemcpyHostToDevice, c->stream));
+  LBM_CUDA(c, cudaMemsetAsync(c->base + c->L.off_sums, 0, NPART * sizeof(unsigned long long), c->stream));
   return LBM_OK;
 }
 
@@ -394,7 +440,8 @@ lbm_status fetch_state(lbm_ctx* c) {
 
 lbm_status set_tiling(lbm_ctx* c, int cols, const BandPlan& plan) {
   std::vector<Tile> t;
-  build_tiles(c->nx, c->ny, cols, plan, t);
+  // the interior flags depend on the geometry: set_params and load_state rebuild the table
+  build_tiles(c->nx, c->ny, cols, plan, t, c->have_params ? c->params.geometry : LBM_GEOM_PERIODIC);
   if ((int)t.size() > c->L.max_tiles) return fail(c, LBM_EINVAL, "tiling needs more tiles than reserved");
   LBM_CUDA(c, cudaMemcpyAsync(c->d_tiles_step, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -417,6 +464,20 @@ lbm_status retile_default(lbm_ctx* c, int cols) {
   const lbm_status s = set_tiling(c, cols, default_band_plan(c->nx, c->ny, cols, slots));
   if (s == LBM_OK) c->rows_default = true;
   return s;
+}
+
+// Whether lbm_step_async takes the persistent launch: requested, or (LBM_LOOP_AUTO) when the
+// step tiling is one wave of the persistent kernel, where a step's launch gap and kernel
+// boundary are a large part of it.  Only the one-column kernel (general or interior path)
+// has a persistent form.
+bool use_persistent(lbm_ctx* c) {
+  if (c->loop == LBM_LOOP_LAUNCHES) return false;
+  const int kernel = step_kernel(c, c->cols);
+  if (kernel != LBM_KERNEL_SCALAR && kernel != LBM_KERNEL_INTERIOR) return false;
+  if (c->loop == LBM_LOOP_PERSISTENT) return true;
+  const long long slots = persistent_slots(c->prec == LBM_FP64, c->thermal, c->cols, kernel,
+                                           needs_full_step(c->hinst), true);
+  return c->ntiles_step <= slots;
 }
 
 lbm_status launch(lbm_ctx* c, int mode) {
@@ -523,7 +584,7 @@ lbm_status create_impl(lbm_ctx** out, int32_t nx, int32_t ny, lbm_precision prec
     }
   }
   std::vector<Tile> t;
-  build_tiles(nx, ny, kAuxCols, BandPlan{0, 0, std::min(kAuxRows, ny)}, t);
+  build_tiles(nx, ny, kAuxCols, BandPlan{0, 0, std::min(kAuxRows, ny)}, t, LBM_GEOM_PERIODIC);
   c->ntiles_aux = (int)t.size();
   if (cudaMemcpyAsync(c->d_tiles_aux, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream) !=
           cudaSuccess ||
@@ -606,7 +667,7 @@ lbm_status lbm_set_params(lbm_ctx* c, const lbm_params* p) {
   DeviceGuard g(c->device);
   lbm_status s = apply_params(c, p);
   if (s != LBM_OK) return s;
-  if (c->rows_default && (s = retile_default(c, c->cols)) != LBM_OK) return s;
+  if ((s = c->rows_default ? retile_default(c, c->cols) : set_tiling(c, c->cols, c->plan)) != LBM_OK) return s;
   InitSpec spec{};
   spec.kind = p->init_kind;
   spec.rho_in = p->init_rho_in;
@@ -657,6 +718,21 @@ lbm_status lbm_step_async(lbm_ctx* c, int64_t nsteps) {
   if (nsteps < 0) return fail(c, LBM_EINVAL, "nsteps < 0");
   if (!c->have_params) return fail(c, LBM_ESTATE, "lbm_set_params first");
   DeviceGuard g(c->device);
+  if (nsteps >= 2 && use_persistent(c)) {
+    const int kernel = step_kernel(c, c->cols);
+    GridBar* bar = reinterpret_cast<GridBar*>(c->base + c->L.off_bar);
+    for (int64_t done = 0; done < nsteps;) {
+      const int n = (int)std::min<int64_t>(nsteps - done, 1 << 30);
+      LBM_CUDA(c, cudaMemsetAsync(bar, 0, sizeof(GridBar), c->stream));
+      cudaError_t e = launch_persistent(c->prec == LBM_FP64, c->thermal, c->cols, kernel, needs_full_step(c->hinst),
+                                        c->d_inst, c->d_tiles_step, c->ntiles_step, n, bar, c->max_polls, c->stream,
+                                        &c->hinst);
+      if (e != cudaSuccess) return cuda_fail(c, e, "persistent kernel launch");
+      ++c->launches;
+      done += n;
+    }
+    return LBM_OK;
+  }
   for (int64_t k = 0; k < nsteps; ++k) {
     lbm_status s = launch(c, MODE_STEP);
     if (s != LBM_OK) return s;
@@ -670,7 +746,9 @@ lbm_status lbm_sync(lbm_ctx* c) {
   lbm_status s = fetch_state(c);
   if (s != LBM_OK) return s;
   if (c->h_state->status & STATUS_TIMEOUT)
-    return fail(c, LBM_ETIMEOUT, "a bulk tensor copy of the step did not complete within its bounded wait");
+    return fail(c, LBM_ETIMEOUT,
+                "a bounded device wait gave up (a bulk tensor copy of the TMA step, or the grid barrier between the "
+                "steps of a persistent launch); the lattice state is undefined until it is initialised again");
   if (c->h_state->status & STATUS_UNSTABLE)
     return fail(c, LBM_EUNSTABLE, "lattice left the EOS domain (rho <= 0, rho >= 1/b, NaN or psi radicand < 0)");
   return LBM_OK;
@@ -858,6 +936,7 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t bytes) {
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
   lbm_status s = apply_params(c, &h.params);
   if (s != LBM_OK) return s;
+  if ((s = c->rows_default ? retile_default(c, c->cols) : set_tiling(c, c->cols, c->plan)) != LBM_OK) return s;
   *c->h_state = h.state;
   c->h_state->counter = 0;
   if ((s = upload_state(c)) != LBM_OK) return s;
@@ -879,8 +958,8 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t bytes) {
 
 lbm_status lbm_set_kernel(lbm_ctx* c, int32_t kernel) {
   if (!c) return LBM_EINVAL;
-  if (kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_TMA)
-    return fail(c, LBM_EINVAL, "kernel must be LBM_KERNEL_AUTO, _SCALAR, _PAIRED or _TMA");
+  if (kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_INTERIOR)
+    return fail(c, LBM_EINVAL, "kernel must be LBM_KERNEL_AUTO, _SCALAR, _PAIRED, _TMA or _INTERIOR");
   c->kernel = kernel;
   if (!c->rows_default) return LBM_OK;
   DeviceGuard g(c->device);
@@ -889,6 +968,28 @@ lbm_status lbm_set_kernel(lbm_ctx* c, int32_t kernel) {
 }
 
 int32_t lbm_step_kernel(const lbm_ctx* c) { return c ? step_kernel(c, c->cols) : -1; }
+
+lbm_status lbm_set_step_loop(lbm_ctx* c, int32_t loop) {
+  if (!c) return LBM_EINVAL;
+  if (loop < LBM_LOOP_AUTO || loop > LBM_LOOP_PERSISTENT)
+    return fail(c, LBM_EINVAL, "loop must be LBM_LOOP_AUTO, _LAUNCHES or _PERSISTENT");
+  c->loop = loop;
+  return LBM_OK;
+}
+
+int32_t lbm_step_loop(lbm_ctx* c) {
+  if (!c) return -1;
+  if (!c->have_params) return c->loop == LBM_LOOP_PERSISTENT ? LBM_LOOP_PERSISTENT : LBM_LOOP_LAUNCHES;
+  DeviceGuard g(c->device);
+  return use_persistent(c) ? LBM_LOOP_PERSISTENT : LBM_LOOP_LAUNCHES;
+}
+
+lbm_status lbm_set_wait_limit(lbm_ctx* c, int64_t max_polls) {
+  if (!c) return LBM_EINVAL;
+  if (max_polls < 0 || max_polls > 0xffffffffll) return fail(c, LBM_EINVAL, "max_polls out of range");
+  c->max_polls = (unsigned)max_polls;
+  return LBM_OK;
+}
 
 lbm_status lbm_autotune(lbm_ctx* c, int32_t trial_steps, int32_t* cols_out, int32_t* rows_out) {
   if (!c || trial_steps < 1) return LBM_EINVAL;

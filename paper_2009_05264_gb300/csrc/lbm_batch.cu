@@ -51,6 +51,9 @@ struct lbm_batch {
   bool dirty = true;
   cudaGraphExec_t graph = nullptr;
   long long launches = 0;
+  int loop = LBM_LOOP_AUTO;     // requested step loop
+  unsigned max_polls = 0;        // barrier polls before a persistent launch gives up (0: time limit only)
+  GridBar* d_bar = nullptr;      // grid barrier of the persistent launches (allocated on first use)
   std::string err;
 };
 
@@ -124,6 +127,7 @@ lbm_status rebuild(lbm_batch* b) {
         t.y1 = y1;
         t.local = local++;
         t.ntiles = n;
+        t.interior = tile_is_interior(insts[idx].geometry, m.nx, b->cols, t.x0);
         out.push_back(t);
       }
     };
@@ -169,6 +173,31 @@ lbm_status launch_steps(lbm_batch* b, int64_t n) {
     LBM_BCUDA(b, launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->launch_kernel, b->any_full, b->d_insts, b->d_tiles, b->ntiles,
                             b->stream));
     ++b->launches;
+  }
+  return LBM_OK;
+}
+
+// Whether a multi-step call takes the persistent launch (the rule of lbm_step_async: requested,
+// or the batch's tiles fit in one wave of the persistent kernel).
+bool batch_persistent(lbm_batch* b) {
+  if (b->loop == LBM_LOOP_LAUNCHES) return false;
+  if (b->launch_kernel != LBM_KERNEL_SCALAR && b->launch_kernel != LBM_KERNEL_INTERIOR) return false;
+  if (b->loop == LBM_LOOP_PERSISTENT) return true;
+  return b->ntiles <= persistent_slots(b->prec == LBM_FP64, b->thermal, b->cols, b->launch_kernel, b->any_full, false);
+}
+
+lbm_status launch_persistent_steps(lbm_batch* b, int64_t nsteps) {
+  if (!b->d_bar && cudaMalloc(&b->d_bar, sizeof(GridBar)) != cudaSuccess) {
+    b->d_bar = nullptr;
+    return bfail(b, LBM_ENOMEM, "grid barrier of the persistent launch");
+  }
+  for (int64_t done = 0; done < nsteps;) {
+    const int n = (int)std::min<int64_t>(nsteps - done, 1 << 30);
+    LBM_BCUDA(b, cudaMemsetAsync(b->d_bar, 0, sizeof(GridBar), b->stream));
+    LBM_BCUDA(b, launch_persistent(b->prec == LBM_FP64, b->thermal, b->cols, b->launch_kernel, b->any_full, b->d_insts,
+                                   b->d_tiles, b->ntiles, n, b->d_bar, b->max_polls, b->stream, nullptr));
+    ++b->launches;
+    done += n;
   }
   return LBM_OK;
 }
@@ -295,8 +324,8 @@ lbm_status lbm_batch_set_tiling(lbm_batch* b, int32_t cols, int32_t rows) {
 
 lbm_status lbm_batch_set_kernel(lbm_batch* b, int32_t kernel) {
   if (!b) return LBM_EINVAL;
-  if (kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_TMA)
-    return bfail(b, LBM_EINVAL, "kernel must be LBM_KERNEL_AUTO, _SCALAR, _PAIRED or _TMA");
+  if (kernel < LBM_KERNEL_AUTO || kernel > LBM_KERNEL_INTERIOR)
+    return bfail(b, LBM_EINVAL, "kernel must be LBM_KERNEL_AUTO, _SCALAR, _PAIRED, _TMA or _INTERIOR");
   b->kernel = kernel;
   b->dirty = true;  // default band heights depend on the kernel's occupancy; the graph names the kernel
   return LBM_OK;
@@ -318,7 +347,9 @@ lbm_status lbm_batch_step_async(lbm_batch* b, int64_t nsteps) {
   for (const Member& m : b->slots)  // a member's parameters or state were replaced directly
     if (m.ctx && m.gen != lbm_internal_params_gen(m.ctx)) b->dirty = true;
   if (b->dirty) s = rebuild(b);
-  if (s == LBM_OK && b->ntiles > 0) {
+  if (s == LBM_OK && b->ntiles > 0 && nsteps >= 2 && batch_persistent(b)) {
+    s = launch_persistent_steps(b, nsteps);
+  } else if (s == LBM_OK && b->ntiles > 0) {
     int64_t left = nsteps;
     if (left >= kGraphChunk && !b->graph) s = capture_graph(b);
     while (s == LBM_OK && left >= kGraphChunk) {
@@ -331,6 +362,32 @@ lbm_status lbm_batch_step_async(lbm_batch* b, int64_t nsteps) {
   }
   if (prev >= 0) cudaSetDevice(prev);
   return s;
+}
+
+lbm_status lbm_batch_set_step_loop(lbm_batch* b, int32_t loop) {
+  if (!b) return LBM_EINVAL;
+  if (loop < LBM_LOOP_AUTO || loop > LBM_LOOP_PERSISTENT)
+    return bfail(b, LBM_EINVAL, "loop must be LBM_LOOP_AUTO, _LAUNCHES or _PERSISTENT");
+  b->loop = loop;
+  return LBM_OK;
+}
+
+int32_t lbm_batch_step_loop(lbm_batch* b) {
+  if (!b) return -1;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->device);
+  int32_t out = -1;
+  if (!b->dirty || rebuild(b) == LBM_OK) out = batch_persistent(b) ? LBM_LOOP_PERSISTENT : LBM_LOOP_LAUNCHES;
+  if (prev >= 0) cudaSetDevice(prev);
+  return out;
+}
+
+lbm_status lbm_batch_set_wait_limit(lbm_batch* b, int64_t max_polls) {
+  if (!b) return LBM_EINVAL;
+  if (max_polls < 0 || max_polls > 0xffffffffll) return bfail(b, LBM_EINVAL, "max_polls out of range");
+  b->max_polls = (unsigned)max_polls;
+  return LBM_OK;
 }
 
 lbm_status lbm_batch_sync(lbm_batch* b, int32_t* unstable_slot) {
@@ -419,6 +476,7 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
     if (m.ctx) lbm_destroy(m.ctx);
   if (b->d_insts) cudaFree(b->d_insts);
   if (b->d_tiles) cudaFree(b->d_tiles);
+  if (b->d_bar) cudaFree(b->d_bar);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   if (prev >= 0) cudaSetDevice(prev);
   delete b;

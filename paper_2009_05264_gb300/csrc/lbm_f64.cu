@@ -3,12 +3,26 @@
 
 namespace pplbm {
 
-cudaError_t launch_lbm_f64(int thermal, int cols, int mode, bool full, const Inst* d_inst, const Tile* d_tiles,
-                          int ntiles, cudaStream_t s, const Inst* h_inst) {
-  return launch_precision<double>(thermal, cols, mode, full, d_inst, d_tiles, ntiles, s, h_inst);
+cudaError_t launch_lbm_f64(int thermal, int cols, int mode, int kernel, bool full, const Inst* d_inst,
+                          const Tile* d_tiles, int ntiles, cudaStream_t s, const Inst* h_inst) {
+  return launch_precision<double>(thermal, cols, mode, full, mode == MODE_STEP && kernel == LBM_KERNEL_INTERIOR, d_inst,
+                                  d_tiles, ntiles, s, h_inst);
 }
 
-int resident_ctas_f64(int thermal, int cols) { return resident_precision<double>(thermal, cols); }
+cudaError_t launch_persistent_f64(int thermal, int cols, int kernel, bool full, const Inst* d_inst,
+                                  const Tile* d_tiles, int ntiles, int nsteps, GridBar* bar, unsigned max_polls,
+                                  cudaStream_t s, const Inst* h_inst) {
+  return launch_persistent_precision<double>(thermal, cols, full, kernel == LBM_KERNEL_INTERIOR, d_inst, d_tiles,
+                                             ntiles, nsteps, bar, max_polls, s, h_inst);
+}
+
+int persistent_resident_f64(int thermal, int cols, int kernel, bool full, bool single) {
+  return persistent_resident_precision<double>(thermal, cols, full, kernel == LBM_KERNEL_INTERIOR, single);
+}
+
+int resident_ctas_f64(int thermal, int cols, int kernel) {
+  return resident_precision<double>(thermal, cols, kernel == LBM_KERNEL_INTERIOR);
+}
 
 cudaError_t launch_init_from_fields_f64(const Inst* d_inst, int nx, int ny, const double* d_fields, int has_T,
                                        cudaStream_t s) {

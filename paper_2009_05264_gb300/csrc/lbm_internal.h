@@ -66,35 +66,79 @@ struct Inst {
   double fix_scale[NPART];          // 2^f_j, f_j the fraction bits of total j
   double fix_unscale[NPART];        // 2^-f_j
   double* ring;                     // RING records of NDIAG doubles
+  // Element offsets within a population buffer: population i of node n sits at n + poff[i]
+  // (poff[i] = i * plane), and on a node with no wall or open-end link it is pulled from
+  // n + loff[i] (the node n - c_i, in plane i: loff[i] = poff[i] - c_iy pitch - c_ix).
+  int loff[9], poff[9];
+  // Derived constants of the step, formed on the host only (so that every kernel converts the
+  // same doubles): (1 - beta)/2 of Eq. 8; the outlet density, inlet and heater temperatures as
+  // deviations from the storage references; the vapour threshold as a density deviation; and
+  // the reference parts of Eqs. 9 and 15 on a row next to the bottom wall, wall0 + d wall1 with
+  // d = psi - psi_ref (its fluid neighbours have sum G_i c_iy = 3G and its solid neighbours
+  // sum w_i c_iy = -1/6; the two parts cancel exactly for a balanced wall, which keeps the FP32
+  // force free of the cancellation).
+  double mix, drho_out, dT_in, dT_heat, drho_vapor, wall0, wall1;
 };
+
+// State of the grid-wide barrier between the steps of a persistent launch (device memory,
+// zeroed by the host before every persistent launch).  count: CTAs arrived at the current
+// barrier; gen: barriers completed; status: 1 once a CTA gave up waiting; next[2]: the
+// dynamic tile counters of even and odd steps.
+struct GridBar {
+  unsigned int count, gen, status, pad;
+  unsigned int next[2];
+  unsigned int pad2[2];
+};
+// Bounded waits of the persistent launch: a CTA stops waiting at a barrier after wait_ns
+// nanoseconds of polling, or after max_polls polls when max_polls > 0 (a test lowers it to
+// make the wait run out while the other CTAs are still busy).
+constexpr unsigned long long BARRIER_WAIT_NS = 5000000000ull;
 
 // One CTA's work: output columns [x0, x0 + W) of instance `inst`, rows [y0, y1).
 struct Tile {
   int inst, x0, y0, y1;
   int local;   // index of this tile among its instance's tiles (partials slot)
   int ntiles;  // tiles of this instance in the launch
-  int pad0, pad1;
+  int interior;  // 1: every column the tile pulls, [x0 - 2, x0 + cols - 6), lies in [1, nx - 2] of a
+                 // channel or walls lattice (no open end, no wrap): the interior path may take it
+  int pad1;
 };
+// Whether a tile of a cols-thread step tiling starting at column x0 may take the interior path.
+inline int tile_is_interior(int geometry, int nx, int cols, int x0) {
+  return (geometry == GEOM_CHANNEL || geometry == GEOM_WALLS) && x0 - 2 >= 1 && x0 + (cols - 8) + 1 <= nx - 2;
+}
 
 // Launchers (defined per precision).  Tiles must have been built for `cols`.
-// kernel: a resolved form (resolve_kernel): LBM_KERNEL_SCALAR, _PAIRED or _TMA.
+// kernel: a resolved form (resolve_kernel): LBM_KERNEL_SCALAR, _INTERIOR, _PAIRED or _TMA.
 // full: the instances use the pool geometry, the Hazi-Markus source or bubble statistics, which
 // only the step's full form handles (the lean form leaves them out of the hot loop).
 // h_inst: host copy of the launch's only instance (the lean scalar step then takes its
 // constants as a kernel parameter), or null for launches over several instances.
 cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, int kernel, bool full, const Inst* d_inst,
                        const Tile* d_tiles, int ntiles, cudaStream_t s, const Inst* h_inst = nullptr);
+// nsteps steps of the step kernel in one cooperative launch (tiles drawn dynamically from a
+// counter, a bounded grid barrier between steps; MODE_STEP only).  grid <= resident CTAs of
+// the device; bar: zeroed GridBar in device memory.
+cudaError_t launch_persistent(int fp64, int thermal, int cols, int kernel, bool full, const Inst* d_inst,
+                              const Tile* d_tiles, int ntiles, int nsteps, GridBar* bar, unsigned max_polls,
+                              cudaStream_t s, const Inst* h_inst);
+// CTAs one persistent launch may hold on the current device (SMs x resident CTAs per SM).
+long long persistent_slots(int fp64, int thermal, int cols, int kernel, bool full, bool single);
 // Whether an instance needs the step's full form.
 inline bool needs_full_step(const Inst& I) {
   return I.geometry == GEOM_POOL || I.source_model != 0 || I.bubble_stats != 0;
 }
-// The step-kernel form a launch takes for a requested LBM_KERNEL_* value: FP64 has only
-// the scalar kernel; the paired kernel has no Hazi-Markus source; the TMA kernel needs
-// 128-column tiles, the step's lean form and the instances' tensor maps (tmaps: all
-// instances of the launch have them).  LBM_KERNEL_AUTO takes the scalar kernel, the
-// fastest form on GB300.
+// The step-kernel form a launch takes for a requested LBM_KERNEL_* value.  LBM_KERNEL_AUTO
+// and LBM_KERNEL_INTERIOR take the one-column kernel with its interior path (tiles away from
+// open ends and wraps run a loop without any per-node boundary logic; the others run the
+// general loop), the fastest form on GB300, whenever the step's lean form applies, else the
+// plain one-column kernel.  FP64 has no other forms; the paired kernel has no Hazi-Markus
+// source; the TMA kernel needs 128-column tiles, the step's lean form and the instances'
+// tensor maps (tmaps: all instances of the launch have them).
 constexpr int TMA_TILE_COLS = 128;
 inline int resolve_kernel(int requested, int fp64, bool full, bool hazi, bool tmaps, int cols) {
+  if (requested == LBM_KERNEL_AUTO || requested == LBM_KERNEL_INTERIOR)
+    return full ? LBM_KERNEL_SCALAR : LBM_KERNEL_INTERIOR;
   if (fp64) return LBM_KERNEL_SCALAR;
   if (requested == LBM_KERNEL_PAIRED) return hazi ? LBM_KERNEL_SCALAR : LBM_KERNEL_PAIRED;
   if (requested == LBM_KERNEL_TMA && !full && tmaps && cols == TMA_TILE_COLS) return LBM_KERNEL_TMA;
@@ -142,7 +186,7 @@ BandPlan default_band_plan(int nx, int ny, int cols, long long slots);
 // form) that one wave of the current device holds: SMs x resident CTAs per SM.
 long long step_wave_slots(int fp64, int thermal, int cols, int kernel);
 int resident_ctas_f32(int thermal, int cols, int kernel);
-int resident_ctas_f64(int thermal, int cols);
+int resident_ctas_f64(int thermal, int cols, int kernel);
 // The instance descriptor of a context (device pointers included), for batching.
 Inst lbm_internal_inst(const lbm_ctx* c);
 // Changes whenever the context's descriptor is rewritten (parameters or a loaded state).

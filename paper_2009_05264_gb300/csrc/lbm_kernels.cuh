@@ -116,6 +116,11 @@ __device__ __forceinline__ void cp_async_elem(double* smem, const double* gmem) 
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+// Wait until at most N of this thread's most recent copy groups are still in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait_lookahead() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // Ring depths of the staged populations: f of rows r+1 (in flight), r (pulled
 // now) and r-1 (collided now); g additionally keeps row r-2 (collided now).
@@ -131,6 +136,25 @@ __host__ __device__ constexpr int out_cols() { return B - 8; }
 template <typename Real, bool THERMAL, int B>
 constexpr size_t fused_smem_bytes() {
   return sizeof(Real) * (size_t)(B - 4) * (9 * F_SLOTS + (THERMAL ? 9 * G_SLOTS : 0) + 9);
+}
+
+// Rows the interior path stages ahead of the row it computes (its rings hold f of rows
+// r + LOOKAHEAD .. r - 1 and g of rows r + LOOKAHEAD .. r - 2).  One row: the copies of row r + 1
+// are in flight during the arithmetic of row r (deeper staging measured slower on GB300: the
+// larger rings leave less room for L1).
+constexpr int LOOKAHEAD = 1;
+constexpr int FI_SLOTS = 2 + LOOKAHEAD;
+constexpr int GI_SLOTS = 3 + LOOKAHEAD;
+template <typename Real, bool THERMAL, int B>
+constexpr size_t interior_smem_bytes() {
+  return sizeof(Real) * (size_t)(B - 4) * (9 * FI_SLOTS + (THERMAL ? 9 * GI_SLOTS : 0) + 9);
+}
+// Dynamic shared memory of a step-kernel instantiation (the interior path's layout is larger).
+template <typename Real, bool THERMAL, int B, bool INTERIOR>
+constexpr size_t step_smem_bytes() {
+  return INTERIOR && interior_smem_bytes<Real, THERMAL, B>() > fused_smem_bytes<Real, THERMAL, B>()
+             ? interior_smem_bytes<Real, THERMAL, B>()
+             : fused_smem_bytes<Real, THERMAL, B>();
 }
 
 // ---------------------------------------------------------------------------
@@ -149,6 +173,9 @@ struct KConst {
   Real drho_vapor;         // rho_vapor - rho_ref: vapour when drho < drho_vapor
 };
 
+// Every member is a conversion of a descriptor value (derived values are formed once, on the
+// host, in fill_inst), so the host's copy (kernel parameter) and a CTA's copy (shared memory)
+// are bit-identical.
 template <typename Real>
 __host__ __device__ inline void fill_consts(KConst<Real>& c, const Inst& I, double rho_avg_prev) {
   c.omega_f = Real(I.omega_f);
@@ -162,7 +189,7 @@ __host__ __device__ inline void fill_consts(KConst<Real>& c, const Inst& I, doub
   c.beta = Real(I.beta);
   c.G2 = Real(I.G2);
   c.Gh = Real(I.Ghalf);
-  c.mix = Real(0.5 * (1.0 - I.beta));
+  c.mix = Real(I.mix);
   c.g_a = Real(I.g_a);
   c.inv_cv = Real(I.inv_cv);
   c.T0 = Real(I.T0);
@@ -170,9 +197,9 @@ __host__ __device__ inline void fill_consts(KConst<Real>& c, const Inst& I, doub
   c.T_ref = Real(I.T_ref);
   c.alpha0 = Real(I.alpha0);
   c.u_in = Real(I.u_in);
-  c.drho_out = Real(I.rho_out - I.rho_ref);
-  c.dT_in = Real(I.T_in - I.T_ref);
-  c.dT_heat = Real(I.T_heat - I.T_ref);
+  c.drho_out = Real(I.drho_out);
+  c.dT_in = Real(I.dT_in);
+  c.dT_heat = Real(I.dT_heat);
   c.inv_u1r = Real(I.inv_u1r);
   c.inv_Dr = Real(I.inv_Dr);
   c.sqrtT_r = Real(I.sqrtT_r);
@@ -181,15 +208,10 @@ __host__ __device__ inline void fill_consts(KConst<Real>& c, const Inst& I, doub
   c.rad_ref = Real(I.rad_ref);
   c.psi_ref = Real(I.psi_ref);
   c.p_ref = Real(I.p_ref);
-  // Wall rows: the fluid neighbours of a row above the bottom wall have sum G_i c_iy = 3G
-  // and its solid neighbours sum w_i c_iy = -1/6, so with psi = psi_ref + d the reference
-  // parts of Eqs. 9 and 15 combine to wall0 + d wall1 (FP64 here: they cancel exactly for a
-  // balanced wall, which keeps the FP32 force free of the cancellation).
-  const double G3 = 1.5 * I.G2, pr = I.psi_ref, mixd = 0.5 * (1.0 - I.beta);
-  c.wall0 = Real(-G3 * (I.beta + mixd) * pr * pr + I.Gwet_psiw * pr / 6.0);
-  c.wall1 = Real(-G3 * I.beta * pr + I.Gwet_psiw / 6.0);
+  c.wall0 = Real(I.wall0);
+  c.wall1 = Real(I.wall1);
   c.rho_ref_minus_avg = Real(I.rho_ref - rho_avg_prev);
-  c.drho_vapor = Real(I.rho_vapor - I.rho_ref);
+  c.drho_vapor = Real(I.drho_vapor);
 }
 
 // Kernel parameter of a launch over one instance: its descriptor and converted constants.
@@ -445,14 +467,31 @@ struct StridedPops {
   __device__ __forceinline__ Real operator()(int i) const { return p[i * stride]; }
 };
 
+// Population i of one node in an output buffer: p[i * plane] (p at the node in plane 0).
+template <typename Real>
+struct PlaneOut {
+  Real* p;
+  int plane;
+  __device__ __forceinline__ Real& operator()(int i) const { return p[i * plane]; }
+};
+// The same through the descriptor's plane offsets: base[m + poff[i]], m the node's element
+// index (one add per population, the offsets read from the descriptor).
+template <typename Real>
+struct OffsetOut {
+  Real* base;
+  int m;
+  const Inst& I;
+  __device__ __forceinline__ Real& operator()(int i) const { return base[m + I.poff[i]]; }
+};
+
 // BGK toward f^eq(rho, u_eq) (Eqs. 2-3) plus the exact-difference term (Eq. 5),
 // written pairwise over opposite directions i, i': with cu = c_i.u, cd = c_i.du and
 // cs = c_i.(2u + du), omega f^eq_i + F_i = w_i (K + 4.5 rho (omega cu^2 + cd cs))
 // + 3 w_i rho (omega cu + cd), K = omega (drho - 1.5 rho u.u) - 1.5 rho du.(2u + du);
 // the direction i' flips the sign of the second term only.  fs(i): the pulled
-// population i of the node; fo: the node in the output buffer, planes `plane` apart.
-template <typename Real, typename Pops>
-__device__ __forceinline__ void collide_f(const Pops& fs, Real* __restrict__ fo, int plane, Real rho,
+// population i of the node; fo(i): population i of the node in the output buffer.
+template <typename Real, typename Pops, typename Out>
+__device__ __forceinline__ void collide_f(const Pops& fs, const Out& fo, Real rho,
                                           Real drho, Real ux, Real uy, Real dux, Real duy, Real omega_f) {
   const Real sx = Real(2) * ux + dux, sy = Real(2) * uy + duy;
   const Real usq = ux * ux + uy * uy;
@@ -461,10 +500,10 @@ __device__ __forceinline__ void collide_f(const Pops& fs, Real* __restrict__ fo,
   auto pair = [&](int i, int j, Real cu, Real cd, Real cs, Real w) {
     const Real sym = w * (K + r45 * (omega_f * cu * cu + cd * cs));
     const Real anti = w * r3 * (omega_f * cu + cd);
-    fo[i * plane] = keep * fs(i) + sym + anti;
-    fo[j * plane] = keep * fs(j) + sym - anti;
+    fo(i) = keep * fs(i) + sym + anti;
+    fo(j) = keep * fs(j) + sym - anti;
   };
-  fo[0] = keep * fs(0) + lat_w<Real>(0) * K;
+  fo(0) = keep * fs(0) + lat_w<Real>(0) * K;
   pair(1, 3, ux, dux, sx, lat_w<Real>(1));
   pair(2, 4, uy, duy, sy, lat_w<Real>(2));
   pair(5, 7, ux + uy, dux + duy, sx + sy, lat_w<Real>(5));
@@ -473,8 +512,8 @@ __device__ __forceinline__ void collide_f(const Pops& fs, Real* __restrict__ fo,
 
 // Eq. 16 with g^eq of Eq. 18 and the source phi (second Eq. 19), pairwise as for f:
 // omega g^eq_i + w_i phi = w_i (Kg + 4.5 omega T cu^2) + 3 w_i omega T cu.
-template <typename Real, typename Pops>
-__device__ __forceinline__ void collide_g(const Pops& gs, Real* __restrict__ go, int plane, Real T,
+template <typename Real, typename Pops, typename Out>
+__device__ __forceinline__ void collide_g(const Pops& gs, const Out& go, Real T,
                                           Real dT, Real uax, Real uay, Real phi, Real omega_g) {
   const Real usq = uax * uax + uay * uay;
   const Real Kg = omega_g * (dT - Real(1.5) * T * usq) + phi;
@@ -482,10 +521,10 @@ __device__ __forceinline__ void collide_g(const Pops& gs, Real* __restrict__ go,
   auto pair = [&](int i, int j, Real cu, Real w) {
     const Real sym = w * (Kg + t45 * cu * cu);
     const Real anti = w * t3 * cu;
-    go[i * plane] = keep * gs(i) + sym + anti;
-    go[j * plane] = keep * gs(j) + sym - anti;
+    go(i) = keep * gs(i) + sym + anti;
+    go(j) = keep * gs(j) + sym - anti;
   };
-  go[0] = keep * gs(0) + lat_w<Real>(0) * Kg;
+  go(0) = keep * gs(0) + lat_w<Real>(0) * Kg;
   pair(1, 3, uax, lat_w<Real>(1));
   pair(2, 4, uay, lat_w<Real>(2));
   pair(5, 7, uax + uay, lat_w<Real>(5));
@@ -640,6 +679,293 @@ __device__ __forceinline__ void post_partials(const Inst& I, InstState* st, cons
 }
 
 // ---------------------------------------------------------------------------
+// Interior path of the step (MODE_STEP, lean form).  A tile whose pulled columns
+// [x0 - 2, x0 + B - 6) all lie in [1, nx - 2] of a channel or walls lattice meets no open
+// end and no wrap in x, so its nodes need none of the general loop's per-node boundary
+// logic: a pull is one add per link (the descriptor's link offsets), the stencil
+// neighbours are the adjacent lanes, and only the wall rows 0 and ny - 1 take the wall
+// branches (bounce-back links, anti-bounce-back temperature, solid neighbours of the force,
+// one-sided wall divergence), decided once per row for the whole CTA.  The arithmetic is the
+// general loop's, expression for expression, so the results are bit-identical to it.
+// ---------------------------------------------------------------------------
+
+// Anti-bounce-back of g on the links of a wall row (the wall part of boundary_fill): the
+// links with c_y = +1 come from the bottom wall (lo), those with c_y = -1 from the top (hi).
+template <typename Real>
+__device__ __forceinline__ void wall_temperature(Real (&gc)[9], bool lo, bool hi, int xn, const Inst& I,
+                                                 const KConst<Real>& C, long long step) {
+  const bool heat_bc = I.heater_len > 0 && (step - 1) >= I.heat_on_step;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int cxi = lat_cx(i), cyi = lat_cy(i);
+    if ((cyi == 1 && lo) || (cyi == -1 && hi)) {
+      Real dTw = C.dT_in;
+      if (cyi == 1 && heat_bc) {
+        const int sx = xn - cxi;
+        if (sx >= I.heater_x0 && sx < I.heater_x0 + I.heater_len) dTw = C.dT_heat;
+      }
+      gc[i] = -gc[i] + Real(2) * lat_w<Real>(i) * dTw;
+    }
+  }
+}
+
+// Shared memory (smem, interior_smem_bytes): per-thread rings of the staged f (FI_SLOTS rows)
+// and g (GI_SLOTS rows), then three-row rings of psi, u_act,x and u_act,y.  Each row's pull is
+// issued LOOKAHEAD iterations before it is used.
+template <typename Real, bool THERMAL, int B>
+__device__ __forceinline__ void interior_rows(const Inst& I, const KConst<Real>& C, Real rra, const Tile& tile,
+                                              long long step, bool local, unsigned char* smem, Real& acc_m,
+                                              Real& acc_e, Real& acc_h, bool& bad_any) {
+  constexpr int W = out_cols<B>();
+  constexpr int NS = B - 4;
+  Real* const sF = reinterpret_cast<Real*>(smem);           // [FI_SLOTS][9][NS]
+  Real* const sG = sF + FI_SLOTS * 9 * NS;                   // [GI_SLOTS][9][NS]
+  Real* const sPsi = sG + (THERMAL ? GI_SLOTS * 9 * NS : 0);  // [3][NS]
+  Real* const sUx = sPsi + 3 * NS;                           // [3][NS]
+  Real* const sUy = sUx + 3 * NS;                            // [3][NS]
+  const int tid = threadIdx.x;
+  const bool act = tid < NS;
+  const int s = act ? tid : 0;
+  const int xn = tile.x0 - 2 + s;
+  const bool out_col = act && s >= 2 && s < W + 2;
+  const bool f_col = act && s >= 1 && s <= W + 2;
+  const int ny = I.ny, pitch = I.pitch;
+  const int y0 = tile.y0, y1 = tile.y1;
+  const int kend = y1 - y0 + 4;
+  const bool multiphase = I.multiphase != 0;
+  const bool heat_col = xn >= I.heater_x0 && xn < I.heater_x0 + I.heater_len;
+  const Real* __restrict__ Fin = static_cast<const Real*>(I.f[step & 1]);
+  const Real* __restrict__ Gin = static_cast<const Real*>(I.g[step & 1]);
+  Real* __restrict__ Fout = static_cast<Real*>(I.f[(step + 1) & 1]);
+  Real* __restrict__ Gout = static_cast<Real*>(I.g[(step + 1) & 1]);
+
+  // pull of row y0 - 2 + k into ring slots (fslot, gslot): interior rows take each link from
+  // node + loff[i]; a wall row takes its wall links from the node's own opposite population
+  // (halfway bounce-back); right after an initialisation every node copies its own populations
+  auto issue_row = [&](int k, int fslot, int gslot) {
+    const int rr = y0 - 2 + k;
+    if (act && k < kend && rr >= 0 && rr < ny) {
+      Real* fd = sF + fslot * 9 * NS + s;
+      Real* gd = sG + gslot * 9 * NS + s;
+      const int node = rr * pitch + xn;
+      if (local) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          const int src = node + I.poff[i];
+          cp_async_elem(fd + i * NS, Fin + src);
+          if (THERMAL) cp_async_elem(gd + i * NS, Gin + src);
+        }
+      } else if (rr > 0 && rr < ny - 1) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          const int src = node + I.loff[i];
+          cp_async_elem(fd + i * NS, Fin + src);
+          if (THERMAL) cp_async_elem(gd + i * NS, Gin + src);
+        }
+      } else {
+        const bool lo = rr == 0, hi = rr == ny - 1;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          const int cyi = lat_cy(i);
+          const bool wall = (cyi == 1 && lo) || (cyi == -1 && hi);
+          const int src = wall ? node + I.poff[lat_opp(i)] : node + I.loff[i];
+          cp_async_elem(fd + i * NS, Fin + src);
+          if (THERMAL) cp_async_elem(gd + i * NS, Gin + src);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
+  Real rho_p = Real(1), drho_p = Real(0), ux_p = Real(0), uy_p = Real(0), T_p = C.T0, dT_p = Real(0), coef_p = Real(0);
+  Real inv_rho_p = Real(1);
+  Real T_p2 = C.T0, dT_p2 = Real(0), coef_p2 = Real(0);
+  // Iterations whose rows r + 1 (pulled), r (moments), r - 1 (force, f collision) and r - 2
+  // (g collision) are all interior rows of the lattice, and r, r - 1, r - 2 output rows of the
+  // band, take the steady body, with no row tests at all: k in [k_lo, k_hi) (r = y0 - 2 + k:
+  // r - 2 >= max(y0, 1), r + 1 <= ny - 2, r < y1), unless the input is post-stream (the first
+  // step after an initialisation).
+  const int k_lo = local ? kend : (y0 >= 1 ? 4 : 5 - y0);
+  const int k_hi = min(kend - 2, ny - y0);
+  // ring slots of row r = y0 - 2 + k: f (k mod FI_SLOTS), g (k mod GI_SLOTS), psi and u_act (k mod 3)
+  int f_cur = 0, g_cur = 0, p_cur = 0;
+#pragma unroll
+  for (int a = 0; a < LOOKAHEAD; ++a) issue_row(a, a, a);
+  for (int k = 0; k < kend; ++k) {
+    const int r = y0 - 2 + k;
+    const int f_prev = f_cur == 0 ? FI_SLOTS - 1 : f_cur - 1;                      // row r-1
+    const int f_issue = f_cur >= 2 ? f_cur - 2 : f_cur + (FI_SLOTS - 2);            // row r+LOOKAHEAD
+    const int g_issue = g_cur >= 3 ? g_cur - 3 : g_cur + (GI_SLOTS - 3);            // row r+LOOKAHEAD
+    const int g_prev2 = g_cur >= 2 ? g_cur - 2 : g_cur + (GI_SLOTS - 2);            // row r-2
+    const int p_prev = p_cur == 0 ? 2 : p_cur - 1;                 // row r-1
+    const int p_prev2 = p_cur == 2 ? 0 : p_cur + 1;                // row r-2 (= r+1 = r-3)
+    NodeState<Real> ns;
+    ns.rho = Real(1); ns.inv_rho = Real(1); ns.drho = Real(0); ns.ux = Real(0); ns.uy = Real(0);
+    ns.T = C.T0; ns.dT = Real(0); ns.coef = Real(0); ns.dpsi = Real(0);
+    if (k >= k_lo && k < k_hi) {
+      // ---------------- steady body: interior rows only ----------------
+      if (act) {
+        Real* fd = sF + f_issue * 9 * NS + s;
+        Real* gd = sG + g_issue * 9 * NS + s;
+        const int node = (r + 1) * pitch + xn;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          const int src = node + I.loff[i];
+          cp_async_elem(fd + i * NS, Fin + src);
+          if (THERMAL) cp_async_elem(gd + i * NS, Gin + src);
+        }
+      }
+      cp_async_commit();
+      cp_async_wait_lookahead<LOOKAHEAD>();
+      if (act) {  // phase A: row r
+        const Real* fs = sF + f_cur * 9 * NS + s;
+        const Real* gs = sG + g_cur * 9 * NS + s;
+        Real fc[9], gc[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          fc[i] = fs[i * NS];
+          gc[i] = THERMAL ? gs[i * NS] : Real(0);
+        }
+        ns = node_state<Real, THERMAL>(fc, gc, C, multiphase, false);
+        bad_any = bad_any || ns.bad;
+        sPsi[p_cur * NS + s] = ns.dpsi;
+        if (out_col) {
+          acc_m += ns.drho;
+          if (THERMAL) acc_e += ns.dT;
+        }
+      }
+      __syncthreads();
+      if (f_col) {  // phase B: row r - 1
+        Real Fx = Real(0), Fy = Real(0);
+        if (multiphase) {
+          const Real* P0 = sPsi + p_prev * NS + s;
+          const Real* Pp = sPsi + p_cur * NS + s;
+          const Real* Pm = sPsi + p_prev2 * NS + s;
+          sc_force<Real>(P0[0], P0[1], P0[-1], Pp[0], Pp[1], Pp[-1], Pm[0], Pm[1], Pm[-1], false, false, C, Fx, Fy);
+        }
+        Fy -= (drho_p + rra) * C.g_a;  // Eq. 14, gravity along -y
+        const Real inv_rho = sizeof(Real) == 8 ? inv_rho_p : fast_rcp(rho_p);
+        const Real dux = Fx * inv_rho, duy = Fy * inv_rho;
+        const Real uax = ux_p + Real(0.5) * dux, uay = uy_p + Real(0.5) * duy;  // Eq. 7
+        sUx[p_prev * NS + s] = uax;
+        sUy[p_prev * NS + s] = uay;
+        if (out_col)
+          collide_f<Real>(StridedPops<Real>{sF + f_prev * 9 * NS + s, NS},
+                          OffsetOut<Real>{Fout, (r - 1) * pitch + xn, I}, rho_p, drho_p, ux_p, uy_p, dux, duy,
+                          C.omega_f);
+      }
+      __syncthreads();
+      if (THERMAL && out_col) {  // phase C: row r - 2
+        const Real* U2x = sUx + p_prev2 * NS + s;
+        const Real* U2y = sUy + p_prev2 * NS + s;
+        const Real divu = Real(0.5) * (U2x[1] - U2x[-1]) + Real(0.5) * (sUy[p_prev * NS + s] - sUy[p_cur * NS + s]);
+        const Real phi = coef_p2 * divu;
+        collide_g<Real>(StridedPops<Real>{sG + g_prev2 * 9 * NS + s, NS},
+                        OffsetOut<Real>{Gout, (r - 2) * pitch + xn, I}, T_p2, dT_p2, U2x[0], U2y[0], phi, C.omega_g);
+      }
+    } else {
+      // ---------------- general body: band ends, wall rows, post-stream input ----------------
+      issue_row(k + LOOKAHEAD, f_issue, g_issue);
+      cp_async_wait_lookahead<LOOKAHEAD>();  // this thread's copies of row r have landed
+
+      // ===================== phase A: row r =====================
+      if (act && r >= 0 && r < ny) {
+        const Real* fs = sF + f_cur * 9 * NS + s;
+        Real* gs = sG + g_cur * 9 * NS + s;
+        Real fc[9], gc[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          fc[i] = fs[i * NS];
+          gc[i] = THERMAL ? gs[i * NS] : Real(0);
+        }
+        if (THERMAL && !local && (r == 0 || r == ny - 1)) {
+          wall_temperature<Real>(gc, r == 0, r == ny - 1, xn, I, C, step);
+#pragma unroll
+          for (int i = 0; i < 9; ++i) gs[i * NS] = gc[i];
+        }
+        ns = node_state<Real, THERMAL>(fc, gc, C, multiphase, false);
+        bad_any = bad_any || ns.bad;
+        sPsi[p_cur * NS + s] = ns.dpsi;
+        if (out_col && r >= y0 && r < y1) {
+          acc_m += ns.drho;
+          if (THERMAL) {
+            acc_e += ns.dT;
+            if (r == 0 && heat_col) acc_h += ns.dT;
+          }
+        }
+      }
+      __syncthreads();
+
+      // ===================== phase B: row q = r - 1 =====================
+      const int q = r - 1;
+      if (f_col && q >= y0 - 1 && q >= 0 && q < ny) {
+        Real Fx = Real(0), Fy = Real(0);
+        if (multiphase) {
+          const Real* P0 = sPsi + p_prev * NS + s;
+          const Real* Pp = sPsi + p_cur * NS + s;
+          const Real* Pm = sPsi + p_prev2 * NS + s;
+          if (q > 0 && q < ny - 1) {
+            sc_force<Real>(P0[0], P0[1], P0[-1], Pp[0], Pp[1], Pp[-1], Pm[0], Pm[1], Pm[-1], false, false, C, Fx, Fy);
+          } else {
+            const bool sol_m = q == 0, sol_p = q == ny - 1;  // row q-1 / q+1 is a wall
+            sc_force<Real>(P0[0], P0[1], P0[-1], sol_p ? Real(0) : Pp[0], sol_p ? Real(0) : Pp[1],
+                           sol_p ? Real(0) : Pp[-1], sol_m ? Real(0) : Pm[0], sol_m ? Real(0) : Pm[1],
+                           sol_m ? Real(0) : Pm[-1], sol_m, sol_p, C, Fx, Fy);
+          }
+        }
+        Fy -= (drho_p + rra) * C.g_a;  // Eq. 14, gravity along -y
+        const Real inv_rho = sizeof(Real) == 8 ? inv_rho_p : fast_rcp(rho_p);
+        const Real dux = Fx * inv_rho, duy = Fy * inv_rho;
+        const Real uax = ux_p + Real(0.5) * dux, uay = uy_p + Real(0.5) * duy;  // Eq. 7
+        sUx[p_prev * NS + s] = uax;
+        sUy[p_prev * NS + s] = uay;
+        if (out_col && q >= y0 && q < y1)
+          collide_f<Real>(StridedPops<Real>{sF + f_prev * 9 * NS + s, NS}, OffsetOut<Real>{Fout, q * pitch + xn, I},
+                          rho_p, drho_p, ux_p, uy_p, dux, duy, C.omega_f);
+      }
+      __syncthreads();
+
+      // ===================== phase C: row q2 = r - 2 =====================
+      if (THERMAL) {
+        const int q2 = r - 2;
+        if (out_col && q2 >= y0 && q2 < y1) {
+          const Real* U2x = sUx + p_prev2 * NS + s;
+          const Real* U2y = sUy + p_prev2 * NS + s;
+          const Real uxE = U2x[1], uxW = U2x[-1];
+          const Real uyN = sUy[p_prev * NS + s];
+          const Real uyS = sUy[p_cur * NS + s];  // slot of row r-3
+          Real dyu = Real(0.5) * (uyN - uyS);
+          if (q2 == 0 || q2 == ny - 1) {  // one-sided wall-normal difference over the fluid rows
+            const bool wall_lo = q2 == 0, wall_hi = q2 == ny - 1;
+            const Real uyC = U2y[0];
+            dyu = (wall_lo && wall_hi) ? Real(0) : (wall_lo ? uyN - uyC : uyC - uyS);
+          }
+          const Real divu = Real(0.5) * (uxE - uxW) + dyu;
+          const Real phi = coef_p2 * divu;
+          collide_g<Real>(StridedPops<Real>{sG + g_prev2 * 9 * NS + s, NS}, OffsetOut<Real>{Gout, q2 * pitch + xn, I},
+                          T_p2, dT_p2, U2x[0], U2y[0], phi, C.omega_g);
+        }
+      }
+    }
+
+    T_p2 = T_p;
+    dT_p2 = dT_p;
+    coef_p2 = coef_p;
+    rho_p = ns.rho;
+    inv_rho_p = ns.inv_rho;
+    drho_p = ns.drho;
+    ux_p = ns.ux;
+    uy_p = ns.uy;
+    T_p = ns.T;
+    dT_p = ns.dT;
+    coef_p = ns.coef;
+    f_cur = f_cur == FI_SLOTS - 1 ? 0 : f_cur + 1;
+    g_cur = g_cur == GI_SLOTS - 1 ? 0 : g_cur + 1;
+    p_cur = p_cur == 2 ? 0 : p_cur + 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Block form of the fused step.  MODE_STEP advances one step; MODE_FIELDS writes
 // rho, u_act and T (FP64) of the current state to the spare f buffer; MODE_POPS
 // writes the post-stream populations to the spare buffers; MODE_MOMENTS only
@@ -657,48 +983,83 @@ __device__ __forceinline__ void post_partials(const Inst& I, InstState* st, cons
 // rematerialised from there instead of held in registers); the buoyancy reference
 // rho_ref - rho_avg, which depends on the previous step, is still formed on the device.
 // Otherwise every CTA copies its instance's descriptor and constants into shared memory.
-template <typename Real, bool THERMAL, int B, int MODE, bool FULL = true, bool PCONST = false>
-__global__ void __launch_bounds__(B, (sizeof(Real) == 4 ? (B <= 64 ? 10 : (B <= 128 ? 5 : 2))
-                                                        : (B <= 64 ? 4 : (B <= 128 ? 2 : 1))))
-lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
-                 const __grid_constant__ KParams<Real> kp) {
+// INTERIOR: tiles flagged interior take the interior path (MODE_STEP, lean form only).
+//
+// Per-CTA shared state of the step kernels besides the dynamic rings.  Launches over several
+// instances also keep the tile's instance descriptor and its converted constants there;
+// single-instance launches (PCONST) read both from the kernel parameter.
+template <typename Real, int B>
+struct StepSharedCommon {
+  Real sRra;  // rho_ref - rho_avg of the previous step (buoyancy, Eq. 14)
+  double sRed[B / 32][NPART];
+  int sLast;
+};
+template <typename Real, int B, bool PCONST>
+struct StepShared : StepSharedCommon<Real, B> {
+  Inst sI;
+  KConst<Real> sCv;
+};
+template <typename Real, int B>
+struct StepShared<Real, B, true> : StepSharedCommon<Real, B> {};
+
+// The tile's descriptor and constants: the kernel parameter's (PCONST) or the CTA's copies.
+template <typename Real, int B, bool PCONST>
+__device__ __forceinline__ const Inst& tile_inst(const KParams<Real>& kp, StepShared<Real, B, PCONST>& sh) {
+  if constexpr (PCONST) return kp.I;
+  else return sh.sI;
+}
+template <typename Real, int B, bool PCONST>
+__device__ __forceinline__ const KConst<Real>& tile_consts(const KParams<Real>& kp, StepShared<Real, B, PCONST>& sh) {
+  if constexpr (PCONST) return kp.C;
+  else return sh.sCv;
+}
+
+// One tile of the fused step (the body of lbm_fused_kernel and of the persistent kernel).
+template <typename Real, bool THERMAL, int B, int MODE, bool FULL, bool PCONST, bool INTERIOR>
+__device__ __forceinline__ void fused_tile(const Inst* __restrict__ insts, const Tile tile, const KParams<Real>& kp,
+                                           unsigned char* dyn_smem, StepShared<Real, B, PCONST>& sh) {
   constexpr int BLOCK = B;
   constexpr int W = out_cols<B>();
   constexpr int NS = B - 4;
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
   Real* const sF = reinterpret_cast<Real*>(dyn_smem);               // [F_SLOTS][9][NS]
   Real* const sG = sF + F_SLOTS * 9 * NS;                           // [G_SLOTS][9][NS]
   Real* const sPsi = sG + (THERMAL ? G_SLOTS * 9 * NS : 0);         // [3][NS]
   Real* const sUx = sPsi + 3 * NS;                                  // [3][NS]
   Real* const sUy = sUx + 3 * NS;                                   // [3][NS]
-  __shared__ Inst sI;
-  __shared__ KConst<Real> sCv;
-  __shared__ Real sRra;  // rho_ref - rho_avg of the previous step (buoyancy, Eq. 14)
-  __shared__ double sRed[BLOCK / 32][NPART];
-  __shared__ int sLast;
+  Real& sRra = sh.sRra;
+  double (*sRed)[NPART] = sh.sRed;
+  int& sLast = sh.sLast;
 
   const int tid = threadIdx.x;
-  const Tile tile = tiles[blockIdx.x];
-  if (!PCONST) {
+  if constexpr (!PCONST) {
     const int* src = reinterpret_cast<const int*>(insts + tile.inst);
-    int* dst = reinterpret_cast<int*>(&sI);
+    int* dst = reinterpret_cast<int*>(&sh.sI);
     for (int k = tid; k < (int)(sizeof(Inst) / 4); k += BLOCK) dst[k] = src[k];
     __syncthreads();
   }
-  const Inst& I = PCONST ? kp.I : sI;
+  const Inst& I = tile_inst<Real, B, PCONST>(kp, sh);
   InstState* st = I.st;
   const long long step = st->step;
   if (tid == 0) {
     const double rho_avg_prev = st->rho_avg[(step - 1) & 1];
-    if (!PCONST) fill_consts<Real>(sCv, I, rho_avg_prev);
+    if constexpr (!PCONST) fill_consts<Real>(sh.sCv, I, rho_avg_prev);
     sRra = Real(I.rho_ref - rho_avg_prev);
   }
   __syncthreads();
-  const KConst<Real>& sC = PCONST ? kp.C : sCv;
+  const KConst<Real>& sC = tile_consts<Real, B, PCONST>(kp, sh);
 
   const int nx = I.nx, ny = I.ny, pitch = I.pitch;
   const int plane = (int)I.plane;  // the host guarantees 9 * plane < 2^31
   const bool local = st->local_read != 0;
+  if (INTERIOR && MODE == MODE_STEP && !FULL && tile.interior) {
+    Real am = Real(0), ae = Real(0), ah = Real(0);
+    bool bad_any = false;
+    interior_rows<Real, THERMAL, B>(I, sC, sRra, tile, step, local, dyn_smem, am, ae, ah, bad_any);
+    if (bad_any) atomicOr(&st->status, STATUS_UNSTABLE);
+    const double acc[NPART] = {(double)am, (double)ae, (double)ah, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    post_partials<BLOCK, THERMAL, MODE>(I, st, tile, acc, sRed, &sLast, step);
+    return;
+  }
   const bool perx = I.geometry != GEOM_CHANNEL;
   const bool pery = I.geometry == GEOM_PERIODIC;
   const bool channel = I.geometry == GEOM_CHANNEL;
@@ -870,8 +1231,8 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
       sUy[f_prev * NS + s] = uay;
       const bool out_q = out_col && q >= tile.y0 && q < tile.y1;
       if (MODE == MODE_STEP && out_q) {
-        collide_f<Real>(StridedPops<Real>{sF + f_prev * 9 * NS + s, NS}, Fout + (q * pitch + xn), plane, rho_p, drho_p, ux_p, uy_p,
-                        dux, duy, sC.omega_f);
+        collide_f<Real>(StridedPops<Real>{sF + f_prev * 9 * NS + s, NS}, PlaneOut<Real>{Fout + (q * pitch + xn), plane},
+                        rho_p, drho_p, ux_p, uy_p, dux, duy, sC.omega_f);
         if (channel && xn == 0) acc_fi += rho_p * uax;
         if (channel && xn == nx - 1) acc_fo += rho_p * uax;
       }
@@ -906,8 +1267,8 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
         const Real divu = Real(0.5) * (uxE - uxW) + dyu;
         Real phi = coef_p2 * divu;
         if (hazi) phi += hm_p2;
-        collide_g<Real>(StridedPops<Real>{sG + g_prev2 * 9 * NS + s, NS}, Gout + (q2 * pitch + xn), plane, T_p2, dT_p2,
-                        sUx[f_prev2 * NS + s], sUy[f_prev2 * NS + s], phi, sC.omega_g);
+        collide_g<Real>(StridedPops<Real>{sG + g_prev2 * 9 * NS + s, NS}, PlaneOut<Real>{Gout + (q2 * pitch + xn), plane},
+                        T_p2, dT_p2, sUx[f_prev2 * NS + s], sUy[f_prev2 * NS + s], phi, sC.omega_g);
       }
     }
 
@@ -936,6 +1297,223 @@ lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
   double acc[NPART] = {(double)acc_m,  (double)acc_e,  (double)acc_h,  (double)acc_fi, (double)acc_fo,
                        (double)acc_va, (double)acc_wv, (double)acc_hv, (double)acc_zv};
   post_partials<BLOCK, THERMAL, MODE>(I, st, tile, acc, sRed, &sLast, step);
+}
+
+// Resident CTAs per SM the step kernels are compiled for (register budget).  The FP32 kernel
+// with the interior path is compiled for 4 CTAs of 128 threads per SM (up to 128 registers):
+// measured faster than 5 at 96 registers or 6 at 80, both of which also leave less L1 beside
+// the shared-memory rings.
+template <typename Real, int B, bool INTERIOR>
+constexpr int step_min_blocks() {
+  return sizeof(Real) == 4 ? (B <= 64 ? 10 : (B <= 128 ? (INTERIOR ? 4 : 5) : 2)) : (B <= 64 ? 4 : (B <= 128 ? 2 : 1));
+}
+
+template <typename Real, bool THERMAL, int B, int MODE, bool FULL = true, bool PCONST = false, bool INTERIOR = false>
+__global__ void __launch_bounds__(B, (step_min_blocks<Real, B, INTERIOR>()))
+lbm_fused_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
+                 const __grid_constant__ KParams<Real> kp) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  __shared__ StepShared<Real, B, PCONST> sh;
+  fused_tile<Real, THERMAL, B, MODE, FULL, PCONST, INTERIOR>(insts, tiles[blockIdx.x], kp, dyn_smem, sh);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent form of the step: one cooperative launch advances the instances nsteps steps.
+// Every CTA draws tiles from a per-step counter and runs them with the same tile body as
+// lbm_fused_kernel; the tile that completes a step still finishes it (totals, record, mean
+// density for the next step's buoyancy), and a grid-wide barrier separates the steps.  The
+// launch is cooperative, so every CTA is resident and the barrier cannot wait on a CTA that
+// has not started; each wait is still bounded (BARRIER_WAIT_NS of polling, or max_polls
+// polls), after which the CTA marks the barrier, sets STATUS_TIMEOUT on its instance and
+// returns, and the others stop at their next poll.  Between steps no launch is needed, which
+// takes the launch gap and the kernel boundary off lattices whose step is a single wave.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier: false if this CTA gave up waiting (or another one did).
+__device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned nblocks, unsigned max_polls, int* s_ok) {
+  __syncthreads();  // the CTA's work of this step is done
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &bar->gen;
+    volatile unsigned* vstatus = &bar->status;
+    const unsigned gen = *vgen;  // read before arriving: it cannot advance before this CTA arrives
+    __threadfence();             // this CTA's writes are visible before its arrival
+    int ok = 1;
+    if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
+      atomicExch(&bar->count, 0u);  // nobody touches count again before gen advances
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      unsigned polls = 0;
+      while (*vgen == gen) {
+        ++polls;
+        if ((max_polls != 0 && polls >= max_polls) || *vstatus != 0 || global_ns() - t0 > BARRIER_WAIT_NS) {
+          ok = *vgen != gen;  // released at the last moment
+          break;
+        }
+      }
+    }
+    if (!ok) atomicOr(&bar->status, 1u);
+    __threadfence();  // the other CTAs' writes of this step are visible after the barrier
+    *s_ok = ok && *vstatus == 0;  // a CTA that gave up ends the launch for all
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+template <typename Real, bool THERMAL, int B, bool FULL, bool PCONST, bool INTERIOR>
+__global__ void __launch_bounds__(B, (step_min_blocks<Real, B, INTERIOR>()))
+lbm_persistent_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, int ntiles, int nsteps,
+                      GridBar* bar, unsigned max_polls, const __grid_constant__ KParams<Real> kp) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  __shared__ StepShared<Real, B, PCONST> sh;
+  __shared__ int s_tile, s_ok;
+  int first_inst = -1;
+  // With a CTA per tile (one wave) every CTA runs tile blockIdx.x; otherwise the CTAs draw tiles
+  // from the step's counter, so that the tall bands dispatched first are shared out as they end.
+  const bool one_wave = ntiles <= (int)gridDim.x;
+  for (int n = 0; n < nsteps; ++n) {
+    if (one_wave) {
+      const Tile tile = tiles[blockIdx.x];
+      first_inst = tile.inst;
+      fused_tile<Real, THERMAL, B, MODE_STEP, FULL, PCONST, INTERIOR>(insts, tile, kp, dyn_smem, sh);
+    } else {
+      if (blockIdx.x == 0 && threadIdx.x == 0) bar->next[(n + 1) & 1] = 0u;  // last drawn from in step n - 1
+      for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(&bar->next[n & 1], 1u);
+        __syncthreads();
+        const int t = s_tile;
+        __syncthreads();
+        if (t >= ntiles) break;
+        const Tile tile = tiles[t];
+        if (first_inst < 0) first_inst = tile.inst;
+        fused_tile<Real, THERMAL, B, MODE_STEP, FULL, PCONST, INTERIOR>(insts, tile, kp, dyn_smem, sh);
+        __syncthreads();
+      }
+    }
+    if (n + 1 < nsteps && !grid_barrier(bar, gridDim.x, max_polls, &s_ok)) {
+      if (threadIdx.x == 0 && first_inst >= 0) atomicOr(&insts[first_inst].st->status, STATUS_TIMEOUT);
+      if (threadIdx.x == 0 && PCONST) atomicOr(&kp.I.st->status, STATUS_TIMEOUT);
+      return;
+    }
+  }
+}
+
+template <typename Real, bool THERMAL, int B, bool FULL, bool PCONST, bool INTERIOR>
+cudaError_t launch_persistent_one(const Inst* d_inst, const Tile* d_tiles, int ntiles, int nsteps, GridBar* bar,
+                                  unsigned max_polls, cudaStream_t s, const KParams<Real>& kp) {
+  constexpr size_t smem = step_smem_bytes<Real, THERMAL, B, INTERIOR>();
+  auto fn = lbm_persistent_kernel<Real, THERMAL, B, FULL, PCONST, INTERIOR>;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, B, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int grid = ntiles < sms * per_sm ? ntiles : sms * per_sm;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(B);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, d_inst, d_tiles, ntiles, nsteps, bar, max_polls, kp);
+}
+
+template <typename Real, bool THERMAL, int B, bool FULL, bool PCONST, bool INTERIOR>
+int persistent_resident() {
+  constexpr size_t smem = step_smem_bytes<Real, THERMAL, B, INTERIOR>();
+  auto fn = lbm_persistent_kernel<Real, THERMAL, B, FULL, PCONST, INTERIOR>;
+  int n = 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, B, smem) != cudaSuccess)
+    return 0;
+  return n;
+}
+
+// Persistent launch for one precision: the lean form with the interior path (single instance:
+// constants as the kernel parameter), or the full form.
+template <typename Real, bool THERMAL, int B>
+cudaError_t launch_persistent_cols(bool full, bool interior, const Inst* d_inst, const Tile* d_tiles, int ntiles,
+                                   int nsteps, GridBar* bar, unsigned max_polls, cudaStream_t s, const Inst* h_inst) {
+  KParams<Real> kp{};
+  if (full) return launch_persistent_one<Real, THERMAL, B, true, false, false>(d_inst, d_tiles, ntiles, nsteps, bar,
+                                                                               max_polls, s, kp);
+  if (h_inst) {
+    kp.I = *h_inst;
+    fill_consts<Real>(kp.C, *h_inst, h_inst->rho_ref);
+    if (interior)
+      return launch_persistent_one<Real, THERMAL, B, false, true, true>(d_inst, d_tiles, ntiles, nsteps, bar,
+                                                                        max_polls, s, kp);
+    return launch_persistent_one<Real, THERMAL, B, false, true, false>(d_inst, d_tiles, ntiles, nsteps, bar,
+                                                                       max_polls, s, kp);
+  }
+  if (interior)
+    return launch_persistent_one<Real, THERMAL, B, false, false, true>(d_inst, d_tiles, ntiles, nsteps, bar,
+                                                                       max_polls, s, kp);
+  return launch_persistent_one<Real, THERMAL, B, false, false, false>(d_inst, d_tiles, ntiles, nsteps, bar, max_polls,
+                                                                      s, kp);
+}
+
+template <typename Real, bool THERMAL, int B>
+int persistent_resident_cols(bool full, bool interior, bool single) {
+  if (full) return persistent_resident<Real, THERMAL, B, true, false, false>();
+  if (single) return interior ? persistent_resident<Real, THERMAL, B, false, true, true>()
+                              : persistent_resident<Real, THERMAL, B, false, true, false>();
+  return interior ? persistent_resident<Real, THERMAL, B, false, false, true>()
+                  : persistent_resident<Real, THERMAL, B, false, false, false>();
+}
+
+template <typename Real>
+cudaError_t launch_persistent_precision(int thermal, int cols, bool full, bool interior, const Inst* d_inst,
+                                        const Tile* d_tiles, int ntiles, int nsteps, GridBar* bar, unsigned max_polls,
+                                        cudaStream_t s, const Inst* h_inst) {
+  if (ntiles <= 0 || nsteps <= 0) return cudaSuccess;
+#define PPLBM_PERSIST(TH, COLS) \
+  launch_persistent_cols<Real, TH, COLS>(full, interior, d_inst, d_tiles, ntiles, nsteps, bar, max_polls, s, h_inst)
+  if (thermal) {
+    switch (cols) {
+      case 64: return PPLBM_PERSIST(true, 64);
+      case 128: return PPLBM_PERSIST(true, 128);
+      case 256: return PPLBM_PERSIST(true, 256);
+    }
+  } else {
+    switch (cols) {
+      case 64: return PPLBM_PERSIST(false, 64);
+      case 128: return PPLBM_PERSIST(false, 128);
+      case 256: return PPLBM_PERSIST(false, 256);
+    }
+  }
+#undef PPLBM_PERSIST
+  return cudaErrorInvalidValue;
+}
+
+template <typename Real>
+int persistent_resident_precision(int thermal, int cols, bool full, bool interior, bool single) {
+  if (thermal) {
+    switch (cols) {
+      case 64: return persistent_resident_cols<Real, true, 64>(full, interior, single);
+      case 128: return persistent_resident_cols<Real, true, 128>(full, interior, single);
+      case 256: return persistent_resident_cols<Real, true, 256>(full, interior, single);
+    }
+  } else {
+    switch (cols) {
+      case 64: return persistent_resident_cols<Real, false, 64>(full, interior, single);
+      case 128: return persistent_resident_cols<Real, false, 128>(full, interior, single);
+      case 256: return persistent_resident_cols<Real, false, 256>(full, interior, single);
+    }
+  }
+  return 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1008,10 +1586,10 @@ __global__ void lbm_init_builtin_kernel(const Inst* __restrict__ insts, InitSpec
 // ---------------------------------------------------------------------------
 // Host launchers for one storage precision.
 // ---------------------------------------------------------------------------
-template <typename Real, bool THERMAL, int B, int MODE, bool FULL, bool PCONST = false>
+template <typename Real, bool THERMAL, int B, int MODE, bool FULL, bool PCONST = false, bool INTERIOR = false>
 cudaError_t launch_one(const Inst* d_inst, const Tile* d_tiles, int ntiles, cudaStream_t s,
                        const KParams<Real>& kp = KParams<Real>{}) {
-  constexpr size_t smem = fused_smem_bytes<Real, THERMAL, B>();
+  constexpr size_t smem = step_smem_bytes<Real, THERMAL, B, INTERIOR>();
   // the dynamic shared-memory opt-in is per device; remember which devices have it
   static unsigned long long configured = 0ull;
   int dev = 0;
@@ -1019,20 +1597,20 @@ cudaError_t launch_one(const Inst* d_inst, const Tile* d_tiles, int ntiles, cuda
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(configured & bit)) {
-    e = cudaFuncSetAttribute(lbm_fused_kernel<Real, THERMAL, B, MODE, FULL, PCONST>,
+    e = cudaFuncSetAttribute(lbm_fused_kernel<Real, THERMAL, B, MODE, FULL, PCONST, INTERIOR>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured |= bit;
   }
-  lbm_fused_kernel<Real, THERMAL, B, MODE, FULL, PCONST><<<ntiles, B, smem, s>>>(d_inst, d_tiles, kp);
+  lbm_fused_kernel<Real, THERMAL, B, MODE, FULL, PCONST, INTERIOR><<<ntiles, B, smem, s>>>(d_inst, d_tiles, kp);
   return cudaGetLastError();
 }
 
 // Step-kernel CTAs resident per SM on the current device (at least 1).
-template <typename Real, bool THERMAL, int B>
+template <typename Real, bool THERMAL, int B, bool INTERIOR>
 int resident_one() {
-  constexpr size_t smem = fused_smem_bytes<Real, THERMAL, B>();
-  auto fn = lbm_fused_kernel<Real, THERMAL, B, MODE_STEP, false>;
+  constexpr size_t smem = step_smem_bytes<Real, THERMAL, B, INTERIOR>();
+  auto fn = lbm_fused_kernel<Real, THERMAL, B, MODE_STEP, false, INTERIOR, INTERIOR>;
   int n = 0;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, B, smem) != cudaSuccess)
@@ -1040,29 +1618,34 @@ int resident_one() {
   return n > 0 ? n : 1;
 }
 
-template <typename Real>
-int resident_precision(int thermal, int cols) {
+template <typename Real, bool INTERIOR>
+int resident_form(int thermal, int cols) {
   if (thermal) {
     switch (cols) {
-      case 64: return resident_one<Real, true, 64>();
-      case 128: return resident_one<Real, true, 128>();
-      case 256: return resident_one<Real, true, 256>();
+      case 64: return resident_one<Real, true, 64, INTERIOR>();
+      case 128: return resident_one<Real, true, 128, INTERIOR>();
+      case 256: return resident_one<Real, true, 256, INTERIOR>();
     }
   } else {
     switch (cols) {
-      case 64: return resident_one<Real, false, 64>();
-      case 128: return resident_one<Real, false, 128>();
-      case 256: return resident_one<Real, false, 256>();
+      case 64: return resident_one<Real, false, 64, INTERIOR>();
+      case 128: return resident_one<Real, false, 128, INTERIOR>();
+      case 256: return resident_one<Real, false, 256, INTERIOR>();
     }
   }
   return 1;
 }
 
+template <typename Real>
+int resident_precision(int thermal, int cols, bool interior) {
+  return interior ? resident_form<Real, true>(thermal, cols) : resident_form<Real, false>(thermal, cols);
+}
+
 // h_inst: the host copy of the launch's only instance (its constants then travel as a kernel
 // parameter to the lean step), or null for launches over several instances.
 template <typename Real, bool THERMAL, int B>
-cudaError_t launch_cols(int mode, bool full, const Inst* d_inst, const Tile* d_tiles, int ntiles, cudaStream_t s,
-                        const Inst* h_inst) {
+cudaError_t launch_cols(int mode, bool full, bool interior, const Inst* d_inst, const Tile* d_tiles, int ntiles,
+                        cudaStream_t s, const Inst* h_inst) {
   switch (mode) {
     case MODE_STEP:
       if (full) return launch_one<Real, THERMAL, B, MODE_STEP, true>(d_inst, d_tiles, ntiles, s);
@@ -1070,8 +1653,10 @@ cudaError_t launch_cols(int mode, bool full, const Inst* d_inst, const Tile* d_t
         KParams<Real> kp;
         kp.I = *h_inst;
         fill_consts<Real>(kp.C, *h_inst, h_inst->rho_ref);
+        if (interior) return launch_one<Real, THERMAL, B, MODE_STEP, false, true, true>(d_inst, d_tiles, ntiles, s, kp);
         return launch_one<Real, THERMAL, B, MODE_STEP, false, true>(d_inst, d_tiles, ntiles, s, kp);
       }
+      if (interior) return launch_one<Real, THERMAL, B, MODE_STEP, false, false, true>(d_inst, d_tiles, ntiles, s);
       return launch_one<Real, THERMAL, B, MODE_STEP, false>(d_inst, d_tiles, ntiles, s);
     case MODE_FIELDS: return launch_one<Real, THERMAL, B, MODE_FIELDS, true>(d_inst, d_tiles, ntiles, s);
     case MODE_POPS: return launch_one<Real, THERMAL, B, MODE_POPS, true>(d_inst, d_tiles, ntiles, s);
@@ -1080,21 +1665,22 @@ cudaError_t launch_cols(int mode, bool full, const Inst* d_inst, const Tile* d_t
   return cudaErrorInvalidValue;
 }
 
+// interior: the step takes the kernel with its interior path (LBM_KERNEL_INTERIOR).
 template <typename Real>
-cudaError_t launch_precision(int thermal, int cols, int mode, bool full, const Inst* d_inst, const Tile* d_tiles,
-                             int ntiles, cudaStream_t s, const Inst* h_inst) {
+cudaError_t launch_precision(int thermal, int cols, int mode, bool full, bool interior, const Inst* d_inst,
+                             const Tile* d_tiles, int ntiles, cudaStream_t s, const Inst* h_inst) {
   if (ntiles <= 0) return cudaSuccess;
   if (thermal) {
     switch (cols) {
-      case 64: return launch_cols<Real, true, 64>(mode, full, d_inst, d_tiles, ntiles, s, h_inst);
-      case 128: return launch_cols<Real, true, 128>(mode, full, d_inst, d_tiles, ntiles, s, h_inst);
-      case 256: return launch_cols<Real, true, 256>(mode, full, d_inst, d_tiles, ntiles, s, h_inst);
+      case 64: return launch_cols<Real, true, 64>(mode, full, interior, d_inst, d_tiles, ntiles, s, h_inst);
+      case 128: return launch_cols<Real, true, 128>(mode, full, interior, d_inst, d_tiles, ntiles, s, h_inst);
+      case 256: return launch_cols<Real, true, 256>(mode, full, interior, d_inst, d_tiles, ntiles, s, h_inst);
     }
   } else {
     switch (cols) {
-      case 64: return launch_cols<Real, false, 64>(mode, full, d_inst, d_tiles, ntiles, s, h_inst);
-      case 128: return launch_cols<Real, false, 128>(mode, full, d_inst, d_tiles, ntiles, s, h_inst);
-      case 256: return launch_cols<Real, false, 256>(mode, full, d_inst, d_tiles, ntiles, s, h_inst);
+      case 64: return launch_cols<Real, false, 64>(mode, full, interior, d_inst, d_tiles, ntiles, s, h_inst);
+      case 128: return launch_cols<Real, false, 128>(mode, full, interior, d_inst, d_tiles, ntiles, s, h_inst);
+      case 256: return launch_cols<Real, false, 256>(mode, full, interior, d_inst, d_tiles, ntiles, s, h_inst);
     }
   }
   return cudaErrorInvalidValue;

@@ -10,7 +10,6 @@
 
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 
 #include "lbm_internal.h"
 #include "pplbm.h"
@@ -20,7 +19,6 @@ namespace {
 
 constexpr int kNoAllocMaxTiles = 8192;
 constexpr int kNoAllocCols = 128;  // threads per CTA of the fused kernel on this path
-constexpr int kMaxDevices = 64;
 
 // Byte layout of the scratch array (offsets 256-byte aligned).
 constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -36,7 +34,8 @@ constexpr size_t kScratchBytes = align256(kOffTiles + sizeof(Tile) * kNoAllocMax
 
 // The scratch of lbm_step_noalloc (about 0.36 MB).  In host code this name is only
 // a stand-in for the device array: its device address comes from
-// cudaGetSymbolAddress (scratch_on_device below), never from taking it directly.
+// cudaGetSymbolAddress on the current device, at every call, never from taking it
+// directly.
 static __device__ __align__(256) unsigned char g_lbm_noalloc_scratch[pplbm::kScratchBytes];
 
 namespace pplbm {
@@ -57,20 +56,14 @@ __global__ void fill_tiles_kernel(Tile* tiles, int nx, int ny, int w, int rows, 
   }
 }
 
-std::mutex g_setup_mutex;
-char* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up once per device.
-cudaError_t scratch_on_device(int dev, char** out) {
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_lbm_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<char*>(ptr);
-  }
-  *out = g_scratch_ptr[dev];
+// Device address of the scratch array on the current device.  Looked up at every call and
+// never kept: a caller's host may reset the device or recreate its primary context between
+// calls, which loads the module again at another address.
+cudaError_t scratch_on_device(char** out) {
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_lbm_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<char*>(ptr);
   return cudaSuccess;
 }
 
@@ -100,10 +93,8 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, int32_t nx, int32_t 
   rows = std::min(rows, ny);
   const int ntiles = strips * ((ny + rows - 1) / rows);
 
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ECUDA;
   char* base = nullptr;
-  if (scratch_on_device(dev, &base) != cudaSuccess) return LBM_ECUDA;
+  if (scratch_on_device(&base) != cudaSuccess) return LBM_ECUDA;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
 
   Inst I;

@@ -343,8 +343,8 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
       sUx[p_prev * NS + s] = uax;
       sUy[p_prev * NS + s] = uay;
       if (out_col && q >= tile.y0 && q < tile.y1) {
-        collide_f<float>(ShiftedPops{sF + f_prev * ST_RW + (s + 2)}, Fout + (q * pitch + xn), plane, rho_p, drho_p,
-                         ux_p, uy_p, dux, duy, C.omega_f);
+        collide_f<float>(ShiftedPops{sF + f_prev * ST_RW + (s + 2)}, PlaneOut<float>{Fout + (q * pitch + xn), plane},
+                         rho_p, drho_p, ux_p, uy_p, dux, duy, C.omega_f);
         if (channel && xn == 0) acc_fi += rho_p * uax;
         if (channel && xn == nx - 1) acc_fo += rho_p * uax;
       }
@@ -365,8 +365,8 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
           dyu = (wall_lo && wall_hi) ? 0.0f : (wall_lo ? uyN - uyC : uyC - uyS);
         }
         const float divu = 0.5f * (uxE - uxW) + dyu;
-        collide_g<float>(ShiftedPops{sG + g_prev2 * ST_RW + (s + 2)}, Gout + (q2 * pitch + xn), plane, T_p2, dT_p2,
-                         sUx[p_prev2 * NS + s], sUy[p_prev2 * NS + s], coef_p2 * divu, C.omega_g);
+        collide_g<float>(ShiftedPops{sG + g_prev2 * ST_RW + (s + 2)}, PlaneOut<float>{Gout + (q2 * pitch + xn), plane},
+                         T_p2, dT_p2, sUx[p_prev2 * NS + s], sUy[p_prev2 * NS + s], coef_p2 * divu, C.omega_g);
       }
     }
 

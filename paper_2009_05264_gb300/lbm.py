@@ -31,17 +31,22 @@ EXPORTS = (
     "lbm_init_fields", "lbm_step", "lbm_step_async", "lbm_sync", "lbm_read_fields", "lbm_get_populations",
     "lbm_set_populations", "lbm_read_diagnostics", "lbm_read_diagnostics_range", "lbm_state_bytes",
     "lbm_save_state", "lbm_load_state",
-    "lbm_set_tiling", "lbm_autotune", "lbm_get_tiling", "lbm_default_band_plan", "lbm_set_kernel", "lbm_step_kernel", "lbm_get_step", "lbm_launch_count", "lbm_get_stream", "lbm_critical_temperature",
-    "lbm_destroy", "lbm_status_string", "lbm_last_error", "lbm_step_noalloc",
+    "lbm_set_tiling", "lbm_autotune", "lbm_get_tiling", "lbm_default_band_plan", "lbm_set_kernel", "lbm_step_kernel",
+    "lbm_set_step_loop", "lbm_step_loop", "lbm_set_wait_limit", "lbm_get_step", "lbm_launch_count", "lbm_get_stream",
+    "lbm_critical_temperature",
+    "lbm_destroy", "lbm_status_string", "lbm_last_error", "lbm_step_noalloc", "lbm_probe_fma_rate",
     "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_member", "lbm_batch_size",
     "lbm_batch_set_tiling", "lbm_batch_set_kernel", "lbm_batch_get_tiling", "lbm_batch_autotune", "lbm_batch_step",
-    "lbm_batch_step_async", "lbm_batch_sync", "lbm_batch_read_fields", "lbm_batch_launch_count",
+    "lbm_batch_step_async", "lbm_batch_sync", "lbm_batch_set_step_loop", "lbm_batch_step_loop",
+    "lbm_batch_set_wait_limit", "lbm_batch_read_fields", "lbm_batch_launch_count",
     "lbm_batch_get_stream", "lbm_batch_last_error", "lbm_batch_destroy",
 )
 
 
-KERNELS = {"auto": 0, "scalar": 1, "paired": 2, "tma": 3}
+KERNELS = {"auto": 0, "scalar": 1, "paired": 2, "tma": 3, "interior": 4}
 KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
+LOOPS = {"auto": 0, "launches": 1, "persistent": 2}
+LOOP_NAMES = {v: k for k, v in LOOPS.items()}
 
 
 class LbmParams(ctypes.Structure):
@@ -104,6 +109,9 @@ def load(build_if_missing: bool = True):
         "lbm_set_tiling": (ctypes.c_int, [vp, i32, i32]),
         "lbm_set_kernel": (ctypes.c_int, [vp, i32]),
         "lbm_step_kernel": (i32, [vp]),
+        "lbm_set_step_loop": (ctypes.c_int, [vp, i32]),
+        "lbm_step_loop": (i32, [vp]),
+        "lbm_set_wait_limit": (ctypes.c_int, [vp, i64]),
         "lbm_get_tiling": (ctypes.c_int, [vp] + [ctypes.POINTER(i32)] * 4),
         "lbm_autotune": (ctypes.c_int, [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "lbm_default_band_plan": (ctypes.c_int, [i32, i32, i32, i64] + [ctypes.POINTER(i32)] * 3),
@@ -116,6 +124,7 @@ def load(build_if_missing: bool = True):
         "lbm_last_error": (ctypes.c_char_p, [vp]),
         "lbm_step_noalloc": (ctypes.c_int, [P, i32, i32, ctypes.c_int, vp, vp, vp, vp, i32, i64, ctypes.c_double,
                                             dp, vp]),
+        "lbm_probe_fma_rate": (ctypes.c_int, [i32, i64, vp, dp]),
         "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, i32, i32, vp]),
         "lbm_batch_add": (ctypes.c_int, [vp, i32, i32, P, ctypes.POINTER(i32)]),
         "lbm_batch_remove": (ctypes.c_int, [vp, i32]),
@@ -127,6 +136,9 @@ def load(build_if_missing: bool = True):
         "lbm_batch_autotune": (ctypes.c_int, [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "lbm_batch_step": (ctypes.c_int, [vp, i64]),
         "lbm_batch_step_async": (ctypes.c_int, [vp, i64]),
+        "lbm_batch_set_step_loop": (ctypes.c_int, [vp, i32]),
+        "lbm_batch_step_loop": (i32, [vp]),
+        "lbm_batch_set_wait_limit": (ctypes.c_int, [vp, i64]),
         "lbm_batch_sync": (ctypes.c_int, [vp, ctypes.POINTER(i32)]),
         "lbm_batch_read_fields": (ctypes.c_int, [vp, i32, dp, dp, dp, dp, sz]),
         "lbm_batch_launch_count": (i64, [vp]),
@@ -245,13 +257,27 @@ class Lattice:
         self._check(self._L.lbm_set_tiling(self._h, int(cols), int(rows)))
 
     def set_kernel(self, kernel: str):
-        """FP32 step kernel form: "auto", "scalar", "paired" or "tma"."""
+        """Step kernel form: "auto", "scalar", "interior", "paired" or "tma"."""
         self._check(self._L.lbm_set_kernel(self._h, KERNELS[kernel]))
 
     @property
     def step_kernel(self) -> str:
-        """The kernel form the step launches take ("scalar", "paired" or "tma")."""
+        """The kernel form the step launches take ("scalar", "interior", "paired" or "tma")."""
         return KERNEL_NAMES[int(self._L.lbm_step_kernel(self._h))]
+
+    def set_step_loop(self, loop: str):
+        """How multi-step calls run: "auto", "launches" (one launch per step) or "persistent"
+        (one cooperative launch per call, bounded grid barriers between steps)."""
+        self._check(self._L.lbm_set_step_loop(self._h, LOOPS[loop]))
+
+    @property
+    def step_loop(self) -> str:
+        """The loop a multi-step call takes now ("launches" or "persistent")."""
+        return LOOP_NAMES[int(self._L.lbm_step_loop(self._h))]
+
+    def set_wait_limit(self, max_polls: int):
+        """Polls before a persistent launch's barrier wait gives up (0: its 5 s time limit only)."""
+        self._check(self._L.lbm_set_wait_limit(self._h, int(max_polls)))
 
     def autotune(self, trial_steps: int = 20) -> tuple[int, int]:
         """Time each candidate tiling for trial_steps steps and keep the fastest; returns
@@ -428,6 +454,17 @@ class Batch:
     def set_kernel(self, kernel: str):
         self._check(self._L.lbm_batch_set_kernel(self._h, KERNELS[kernel]))
 
+    def set_step_loop(self, loop: str):
+        """"auto", "launches" (graph-replayed launches, one per step) or "persistent"."""
+        self._check(self._L.lbm_batch_set_step_loop(self._h, LOOPS[loop]))
+
+    @property
+    def step_loop(self) -> str:
+        return LOOP_NAMES[int(self._L.lbm_batch_step_loop(self._h))]
+
+    def set_wait_limit(self, max_polls: int):
+        self._check(self._L.lbm_batch_set_wait_limit(self._h, int(max_polls)))
+
     @property
     def tiling(self):
         c, r = ctypes.c_int32(), ctypes.c_int32()
@@ -462,3 +499,14 @@ class Batch:
 
         return torch.cuda.ExternalStream(int(self._L.lbm_batch_get_stream(self._h) or 0),
                                          device=torch.device("cuda", self.device))
+
+
+def probe_fma_rate(precision: str = "fp64", iters: int = 1 << 16, stream=None) -> float:
+    """Fused multiply-add rate (flop/s, two per FMA) of independent FMA chains on the current
+    device in "fp64" or "fp32" (the FP64 step's arithmetic roofline)."""
+    L = load()
+    out = ctypes.c_double(0.0)
+    st = L.lbm_probe_fma_rate(1 if precision == "fp64" else 0, int(iters), stream, ctypes.byref(out))
+    if st != 0:
+        raise LbmError(st, "lbm_probe_fma_rate failed")
+    return out.value

@@ -142,7 +142,7 @@ def test_fp64_single_phase_poiseuille():
         assert rel_err(got, ref, k) < FP64_TOL, k
 
 
-@pytest.mark.parametrize("kernel", ["paired", "scalar", "tma"])
+@pytest.mark.parametrize("kernel", ["paired", "scalar", "tma", "interior"])
 @pytest.mark.parametrize("tiling", [(128, 16), (64, 4), (256, 37)])
 def test_fp32_channel_thermal_1000_steps(tiling, kernel):
     nx, ny = 300, 37
@@ -226,14 +226,15 @@ def test_fp32_kernel_odd_and_periodic_edges(nx, ny, geometry, tiling, kernel):
 
 def test_fp32_step_kernel_forms_agree():
     """The FP32 step forms compute the same update.  The TMA form does the scalar form's
-    arithmetic in the same order (only the staging of the pulled populations differs), so
-    their populations agree bit for bit; the paired form orders a few roundings
-    differently, so after 200 steps it agrees to ~1e-6."""
+    arithmetic in the same order within the same code (only the staging of the pulled
+    populations differs), so their populations agree bit for bit; the paired form orders a
+    few roundings differently and the interior path is compiled separately (the compiler
+    may fuse a few multiply-adds differently), so after 200 steps they agree to ~1e-6."""
     L = lbm()
     nx, ny = 260, 41
     p, fields = channel_case(nx, ny, heat_on_step=10)
     pops = {}
-    for kernel in ("paired", "scalar", "tma"):
+    for kernel in ("paired", "scalar", "tma", "interior"):
         lat = L.Lattice(nx, ny, "fp32")
         lat.set_params(p)
         lat.set_kernel(kernel)
@@ -245,17 +246,26 @@ def test_fp32_step_kernel_forms_agree():
         assert np.abs(a - b).max() < 1e-5 * np.abs(b).max()
     for a, b in zip(pops["tma"], pops["scalar"]):
         assert np.array_equal(a, b)
+    for a, b in zip(pops["interior"], pops["scalar"]):
+        assert np.abs(a - b).max() < 1e-5 * np.abs(b).max()
     assert L.load().lbm_set_kernel(lat._h, 7) == 1  # LBM_EINVAL
 
 
 def test_step_kernel_resolution():
-    """LBM_KERNEL_AUTO takes the scalar form; a TMA request takes the TMA form for a lean
-    FP32 lattice on 128-column tiles and the scalar form where the TMA form does not apply."""
+    """LBM_KERNEL_AUTO takes the interior form (the one-column kernel with its interior path)
+    for the step's lean form and the scalar form for the full form; a TMA request takes the
+    TMA form for a lean FP32 lattice on 128-column tiles and the scalar form where the TMA
+    form does not apply."""
     L = lbm()
     nx, ny = 130, 20
     p, _ = channel_case(nx, ny)
     lat = L.Lattice(nx, ny, "fp32")
     lat.set_params(p)
+    assert lat.step_kernel == "interior"
+    lat.set_params(dict(p, bubble_stats=1))
+    assert lat.step_kernel == "scalar"
+    lat.set_params(p)
+    lat.set_kernel("scalar")
     assert lat.step_kernel == "scalar"
     lat.set_kernel("tma")
     assert lat.step_kernel == "tma"
@@ -275,6 +285,7 @@ def test_step_kernel_resolution():
     assert lat.step_kernel == "paired"
     lat64 = L.Lattice(nx, ny, "fp64")
     lat64.set_params(p)
+    assert lat64.step_kernel == "interior"
     lat64.set_kernel("tma")
     assert lat64.step_kernel == "scalar"
 

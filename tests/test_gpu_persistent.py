@@ -1,0 +1,150 @@
+"""The persistent step loop: one cooperative launch per call, a bounded grid barrier between
+steps, tiles drawn from a per-step counter.
+
+It runs the step kernel's tile body, so it must agree with one launch per step to rounding
+(the two are compiled separately) and with the oracle at the parity tolerances, both where
+every CTA holds one tile per step (a small channel, the case it is chosen for) and where the
+CTAs draw several tiles per step.  Its barrier waits are bounded: with the poll limit set to
+one poll, the first CTA to reach a barrier gives up while the others still work, the call
+reports LBM_ETIMEOUT, nothing faults, and the context is usable again after a fresh
+initialisation.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_05264_gb300 import inputs as I
+from paper_2009_05264_gb300 import params as PP
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+ROUNDING = {"fp64": 1e-12, "fp32": 1e-6}
+
+
+def lbm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_05264_gb300 import lbm as L
+
+    return L
+
+
+def channel(nx, ny, **kw):
+    base = dict(geometry="channel", u_in=0.03, dTheat_R=0.08, heater_x0=nx // 5, heater_len=max(5, nx // 25),
+                heat_on_step=20, g_a=5e-5)
+    base.update(kw)
+    p = PP.resolve(PP.default_params(**base), nx)
+    fields = I.smooth_random(nx, ny, 5.95, 0.9 * oracle.Tc(p), seed=nx + ny, drho=0.002, du=0.005, dT=0.002)
+    return p, fields
+
+
+def run(L, nx, ny, p, fields, precision, loop, steps, tiling=None, calls=1):
+    lat = L.Lattice(nx, ny, precision)
+    lat.set_params(p)
+    lat.set_step_loop(loop)
+    if tiling:
+        lat.set_tiling(*tiling)
+    lat.init_fields(*fields)
+    launches0 = lat.launches
+    for _ in range(calls):
+        lat.step(steps // calls)
+    return lat, lat.launches - launches0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("nx,ny,tiling", [(400, 60, None), (1000, 100, (64, 4)), (2000, 160, (64, 4))])
+def test_persistent_loop_agrees_with_one_launch_per_step(precision, nx, ny, tiling):
+    L = lbm()
+    p, fields = channel(nx, ny)
+    steps = 120
+    per, n_per = run(L, nx, ny, p, fields, precision, "persistent", steps, tiling, calls=3)
+    ref, n_ref = run(L, nx, ny, p, fields, precision, "launches", steps, tiling)
+    assert n_per == 3 and n_ref == steps  # one launch per call against one per step
+    assert per.step_count == ref.step_count == steps
+    f_p, g_p = per.populations()
+    f_r, g_r = ref.populations()
+    tol = ROUNDING[precision]
+    assert np.abs(f_p - f_r).max() <= tol * np.abs(f_r).max()
+    assert np.abs(g_p - g_r).max() <= tol * np.abs(g_r).max()
+    rec_p, rec_r = per.diagnostics_range(0, steps), ref.diagnostics_range(0, steps)
+    assert np.array_equal(rec_p[:, 0], rec_r[:, 0])
+    for j in (1, 2, 3, 5, 6, 7):
+        scale = max(np.abs(rec_r[:, j]).max(), 1e-300)
+        assert np.abs(rec_p[:, j] - rec_r[:, j]).max() <= 100 * tol * scale, j
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_persistent_loop_matches_oracle(precision):
+    L = lbm()
+    nx, ny, steps = 300, 50, 1000
+    p, fields = channel(nx, ny)
+    lat = L.Lattice(nx, ny, precision)
+    lat.set_params(p)
+    lat.init_fields(*fields)
+    assert lat.step_loop == "persistent"  # a small lattice: one wave of the persistent kernel
+    lat.step(steps)
+    orc = oracle.Oracle(nx, ny, p)
+    orc.init_fields(*fields)
+    assert orc.step(steps) == 0
+    got, ref = lat.fields(), orc.fields()
+    scale_u = max(np.abs(ref["ux"]).max(), np.abs(ref["uy"]).max())
+    for k in ("rho", "ux", "uy", "T"):
+        scale = scale_u if k in ("ux", "uy") else np.abs(ref[k]).max()
+        assert np.abs(got[k] - ref[k]).max() < TOL[precision] * scale, k
+    d, od = lat.diagnostics(), orc.last_diag()
+    for k in ("mass", "energy", "flux_in", "flux_out"):
+        assert d[k] == pytest.approx(od[k], rel=TOL[precision]), k
+
+
+def test_barrier_timeout_is_reported_and_the_context_recovers():
+    L = lbm()
+    nx, ny = 1000, 100
+    p, fields = channel(nx, ny)
+    lat = L.Lattice(nx, ny, "fp32")
+    lat.set_params(p)
+    lat.set_step_loop("persistent")
+    lat.set_tiling(64, 4)  # hundreds of CTAs: the first at a barrier cannot find all the others there
+    lat.init_fields(*fields)
+    lat.set_wait_limit(1)
+    with pytest.raises(L.LbmError) as err:
+        lat.step(20)
+    assert err.value.status == 4  # LBM_ETIMEOUT
+    # the device is still usable: the same context, initialised again, reproduces a fresh run
+    lat.set_wait_limit(0)
+    lat.init_fields(*fields)
+    lat.step(30)
+    fresh, _ = run(L, nx, ny, p, fields, "fp32", "persistent", 30, (64, 4))
+    for a, b in zip(lat.populations(), fresh.populations()):
+        assert np.array_equal(a, b)
+    assert lat.diagnostics()["mass"] == fresh.diagnostics()["mass"]
+    with pytest.raises(L.LbmError):
+        lat.set_wait_limit(-1)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_persistent_batch_agrees_with_graph_replayed_launches(precision):
+    """A batch of uneven channels advanced by one cooperative launch per call agrees with the
+    same batch advanced by graph-replayed launches, member by member, to rounding."""
+    L = lbm()
+    sizes = [(300, 40), (170, 64), (520, 33)]
+    runs = {}
+    for loop in ("persistent", "launches"):
+        b = L.Batch(precision, thermal=True)
+        b.set_step_loop(loop)
+        members = []
+        for k, (nx, ny) in enumerate(sizes):
+            p, fields = channel(nx, ny, u_in=0.01 + 0.01 * k)
+            m = b.add(nx, ny, p)
+            m.init_fields(*fields)
+            members.append(m)
+        assert b.step_loop == loop
+        b.step(40)
+        runs[loop] = [m.populations() for m in members]
+        assert all(m.step_count == 40 for m in members)
+        b.close()
+    tol = ROUNDING[precision]
+    for (fp, gp), (fr, gr) in zip(runs["persistent"], runs["launches"]):
+        assert np.abs(fp - fr).max() <= tol * np.abs(fr).max()
+        assert np.abs(gp - gr).max() <= tol * np.abs(gr).max()
