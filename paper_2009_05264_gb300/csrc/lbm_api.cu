@@ -689,6 +689,7 @@ lbm_status lbm_set_params(lbm_ctx* c, const lbm_params* p) {
 
 lbm_status lbm_init_fields(lbm_ctx* c, const double* rho, const double* ux, const double* uy, const double* T,
                            size_t n) {
+  NvtxRange nvtx("pplbm init_fields");
   if (!c || !rho || !ux || !uy) return fail(c, LBM_EINVAL, "NULL field");
   if (n != (size_t)c->nx * c->ny) return fail(c, LBM_EINVAL, "n != nx*ny");
   if (!c->have_params) return fail(c, LBM_ESTATE, "lbm_set_params first");
@@ -714,6 +715,7 @@ lbm_status lbm_init_fields(lbm_ctx* c, const double* rho, const double* ux, cons
 }
 
 lbm_status lbm_step_async(lbm_ctx* c, int64_t nsteps) {
+  NvtxRange nvtx("pplbm step");
   if (!c) return LBM_EINVAL;
   if (nsteps < 0) return fail(c, LBM_EINVAL, "nsteps < 0");
   if (!c->have_params) return fail(c, LBM_ESTATE, "lbm_set_params first");
@@ -741,6 +743,7 @@ lbm_status lbm_step_async(lbm_ctx* c, int64_t nsteps) {
 }
 
 lbm_status lbm_sync(lbm_ctx* c) {
+  NvtxRange nvtx("pplbm sync");
   if (!c) return LBM_EINVAL;
   DeviceGuard g(c->device);
   lbm_status s = fetch_state(c);
@@ -761,6 +764,7 @@ lbm_status lbm_step(lbm_ctx* c, int64_t nsteps) {
 }
 
 lbm_status lbm_read_fields(lbm_ctx* c, double* rho, double* ux, double* uy, double* T, size_t n) {
+  NvtxRange nvtx("pplbm read_fields");
   if (!c) return LBM_EINVAL;
   if (n != (size_t)c->nx * c->ny) return fail(c, LBM_EINVAL, "n != nx*ny");
   if (!c->have_params) return fail(c, LBM_ESTATE, "lbm_set_params first");

@@ -187,6 +187,7 @@ bool batch_persistent(lbm_batch* b) {
 }
 
 lbm_status launch_persistent_steps(lbm_batch* b, int64_t nsteps) {
+  NvtxRange nvtx("pplbm batch persistent launch");
   if (!b->d_bar && cudaMalloc(&b->d_bar, sizeof(GridBar)) != cudaSuccess) {
     b->d_bar = nullptr;
     return bfail(b, LBM_ENOMEM, "grid barrier of the persistent launch");
@@ -339,6 +340,7 @@ lbm_status lbm_batch_get_tiling(const lbm_batch* b, int32_t* cols, int32_t* rows
 }
 
 lbm_status lbm_batch_step_async(lbm_batch* b, int64_t nsteps) {
+  NvtxRange nvtx("pplbm batch chunk");
   if (!b || nsteps < 0) return LBM_EINVAL;
   int prev = -1;
   cudaGetDevice(&prev);

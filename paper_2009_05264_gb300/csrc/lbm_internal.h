@@ -2,11 +2,20 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>  // header-only: ranges cost nothing unless a profiler is attached
 #include <stdint.h>
 
 #include "pplbm.h"
 
 namespace pplbm {
+
+// An NVTX range around a host call (step, chunk, readback), named for the profiler's timeline.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Per-tile partial sums folded by the last CTA of an instance:
 // mass, energy, T summed over the heater-adjacent row, inlet flux, outlet flux.

@@ -780,13 +780,6 @@ __device__ __forceinline__ void interior_rows(const Inst& I, const KConst<Real>&
   Real rho_p = Real(1), drho_p = Real(0), ux_p = Real(0), uy_p = Real(0), T_p = C.T0, dT_p = Real(0), coef_p = Real(0);
   Real inv_rho_p = Real(1);
   Real T_p2 = C.T0, dT_p2 = Real(0), coef_p2 = Real(0);
-  // Iterations whose rows r + 1 (pulled), r (moments), r - 1 (force, f collision) and r - 2
-  // (g collision) are all interior rows of the lattice, and r, r - 1, r - 2 output rows of the
-  // band, take the steady body, with no row tests at all: k in [k_lo, k_hi) (r = y0 - 2 + k:
-  // r - 2 >= max(y0, 1), r + 1 <= ny - 2, r < y1), unless the input is post-stream (the first
-  // step after an initialisation).
-  const int k_lo = local ? kend : (y0 >= 1 ? 4 : 5 - y0);
-  const int k_hi = min(kend - 2, ny - y0);
   // ring slots of row r = y0 - 2 + k: f (k mod FI_SLOTS), g (k mod GI_SLOTS), psi and u_act (k mod 3)
   int f_cur = 0, g_cur = 0, p_cur = 0;
 #pragma unroll
@@ -802,149 +795,85 @@ __device__ __forceinline__ void interior_rows(const Inst& I, const KConst<Real>&
     NodeState<Real> ns;
     ns.rho = Real(1); ns.inv_rho = Real(1); ns.drho = Real(0); ns.ux = Real(0); ns.uy = Real(0);
     ns.T = C.T0; ns.dT = Real(0); ns.coef = Real(0); ns.dpsi = Real(0);
-    if (k >= k_lo && k < k_hi) {
-      // ---------------- steady body: interior rows only ----------------
-      if (act) {
-        Real* fd = sF + f_issue * 9 * NS + s;
-        Real* gd = sG + g_issue * 9 * NS + s;
-        const int node = (r + 1) * pitch + xn;
+    issue_row(k + LOOKAHEAD, f_issue, g_issue);
+    cp_async_wait_lookahead<LOOKAHEAD>();  // this thread's copies of row r have landed
+
+    // ===================== phase A: row r =====================
+    if (act && r >= 0 && r < ny) {
+      const Real* fs = sF + f_cur * 9 * NS + s;
+      Real* gs = sG + g_cur * 9 * NS + s;
+      Real fc[9], gc[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          const int src = node + I.loff[i];
-          cp_async_elem(fd + i * NS, Fin + src);
-          if (THERMAL) cp_async_elem(gd + i * NS, Gin + src);
+      for (int i = 0; i < 9; ++i) {
+        fc[i] = fs[i * NS];
+        gc[i] = THERMAL ? gs[i * NS] : Real(0);
+      }
+      if (THERMAL && !local && (r == 0 || r == ny - 1)) {
+        wall_temperature<Real>(gc, r == 0, r == ny - 1, xn, I, C, step);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) gs[i * NS] = gc[i];
+      }
+      ns = node_state<Real, THERMAL>(fc, gc, C, multiphase, false);
+      bad_any = bad_any || ns.bad;
+      sPsi[p_cur * NS + s] = ns.dpsi;
+      if (out_col && r >= y0 && r < y1) {
+        acc_m += ns.drho;
+        if (THERMAL) {
+          acc_e += ns.dT;
+          if (r == 0 && heat_col) acc_h += ns.dT;
         }
       }
-      cp_async_commit();
-      cp_async_wait_lookahead<LOOKAHEAD>();
-      if (act) {  // phase A: row r
-        const Real* fs = sF + f_cur * 9 * NS + s;
-        const Real* gs = sG + g_cur * 9 * NS + s;
-        Real fc[9], gc[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          fc[i] = fs[i * NS];
-          gc[i] = THERMAL ? gs[i * NS] : Real(0);
-        }
-        ns = node_state<Real, THERMAL>(fc, gc, C, multiphase, false);
-        bad_any = bad_any || ns.bad;
-        sPsi[p_cur * NS + s] = ns.dpsi;
-        if (out_col) {
-          acc_m += ns.drho;
-          if (THERMAL) acc_e += ns.dT;
-        }
-      }
-      __syncthreads();
-      if (f_col) {  // phase B: row r - 1
-        Real Fx = Real(0), Fy = Real(0);
-        if (multiphase) {
-          const Real* P0 = sPsi + p_prev * NS + s;
-          const Real* Pp = sPsi + p_cur * NS + s;
-          const Real* Pm = sPsi + p_prev2 * NS + s;
+    }
+    __syncthreads();
+
+    // ===================== phase B: row q = r - 1 =====================
+    const int q = r - 1;
+    if (f_col && q >= y0 - 1 && q >= 0 && q < ny) {
+      Real Fx = Real(0), Fy = Real(0);
+      if (multiphase) {
+        const Real* P0 = sPsi + p_prev * NS + s;
+        const Real* Pp = sPsi + p_cur * NS + s;
+        const Real* Pm = sPsi + p_prev2 * NS + s;
+        if (q > 0 && q < ny - 1) {
           sc_force<Real>(P0[0], P0[1], P0[-1], Pp[0], Pp[1], Pp[-1], Pm[0], Pm[1], Pm[-1], false, false, C, Fx, Fy);
+        } else {
+          const bool sol_m = q == 0, sol_p = q == ny - 1;  // row q-1 / q+1 is a wall
+          sc_force<Real>(P0[0], P0[1], P0[-1], sol_p ? Real(0) : Pp[0], sol_p ? Real(0) : Pp[1],
+                         sol_p ? Real(0) : Pp[-1], sol_m ? Real(0) : Pm[0], sol_m ? Real(0) : Pm[1],
+                         sol_m ? Real(0) : Pm[-1], sol_m, sol_p, C, Fx, Fy);
         }
-        Fy -= (drho_p + rra) * C.g_a;  // Eq. 14, gravity along -y
-        const Real inv_rho = sizeof(Real) == 8 ? inv_rho_p : fast_rcp(rho_p);
-        const Real dux = Fx * inv_rho, duy = Fy * inv_rho;
-        const Real uax = ux_p + Real(0.5) * dux, uay = uy_p + Real(0.5) * duy;  // Eq. 7
-        sUx[p_prev * NS + s] = uax;
-        sUy[p_prev * NS + s] = uay;
-        if (out_col)
-          collide_f<Real>(StridedPops<Real>{sF + f_prev * 9 * NS + s, NS},
-                          OffsetOut<Real>{Fout, (r - 1) * pitch + xn, I}, rho_p, drho_p, ux_p, uy_p, dux, duy,
-                          C.omega_f);
       }
-      __syncthreads();
-      if (THERMAL && out_col) {  // phase C: row r - 2
+      Fy -= (drho_p + rra) * C.g_a;  // Eq. 14, gravity along -y
+      const Real inv_rho = sizeof(Real) == 8 ? inv_rho_p : fast_rcp(rho_p);
+      const Real dux = Fx * inv_rho, duy = Fy * inv_rho;
+      const Real uax = ux_p + Real(0.5) * dux, uay = uy_p + Real(0.5) * duy;  // Eq. 7
+      sUx[p_prev * NS + s] = uax;
+      sUy[p_prev * NS + s] = uay;
+      if (out_col && q >= y0 && q < y1)
+        collide_f<Real>(StridedPops<Real>{sF + f_prev * 9 * NS + s, NS}, OffsetOut<Real>{Fout, q * pitch + xn, I},
+                        rho_p, drho_p, ux_p, uy_p, dux, duy, C.omega_f);
+    }
+    __syncthreads();
+
+    // ===================== phase C: row q2 = r - 2 =====================
+    if (THERMAL) {
+      const int q2 = r - 2;
+      if (out_col && q2 >= y0 && q2 < y1) {
         const Real* U2x = sUx + p_prev2 * NS + s;
         const Real* U2y = sUy + p_prev2 * NS + s;
-        const Real divu = Real(0.5) * (U2x[1] - U2x[-1]) + Real(0.5) * (sUy[p_prev * NS + s] - sUy[p_cur * NS + s]);
+        const Real uxE = U2x[1], uxW = U2x[-1];
+        const Real uyN = sUy[p_prev * NS + s];
+        const Real uyS = sUy[p_cur * NS + s];  // slot of row r-3
+        Real dyu = Real(0.5) * (uyN - uyS);
+        if (q2 == 0 || q2 == ny - 1) {  // one-sided wall-normal difference over the fluid rows
+          const bool wall_lo = q2 == 0, wall_hi = q2 == ny - 1;
+          const Real uyC = U2y[0];
+          dyu = (wall_lo && wall_hi) ? Real(0) : (wall_lo ? uyN - uyC : uyC - uyS);
+        }
+        const Real divu = Real(0.5) * (uxE - uxW) + dyu;
         const Real phi = coef_p2 * divu;
-        collide_g<Real>(StridedPops<Real>{sG + g_prev2 * 9 * NS + s, NS},
-                        OffsetOut<Real>{Gout, (r - 2) * pitch + xn, I}, T_p2, dT_p2, U2x[0], U2y[0], phi, C.omega_g);
-      }
-    } else {
-      // ---------------- general body: band ends, wall rows, post-stream input ----------------
-      issue_row(k + LOOKAHEAD, f_issue, g_issue);
-      cp_async_wait_lookahead<LOOKAHEAD>();  // this thread's copies of row r have landed
-
-      // ===================== phase A: row r =====================
-      if (act && r >= 0 && r < ny) {
-        const Real* fs = sF + f_cur * 9 * NS + s;
-        Real* gs = sG + g_cur * 9 * NS + s;
-        Real fc[9], gc[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          fc[i] = fs[i * NS];
-          gc[i] = THERMAL ? gs[i * NS] : Real(0);
-        }
-        if (THERMAL && !local && (r == 0 || r == ny - 1)) {
-          wall_temperature<Real>(gc, r == 0, r == ny - 1, xn, I, C, step);
-#pragma unroll
-          for (int i = 0; i < 9; ++i) gs[i * NS] = gc[i];
-        }
-        ns = node_state<Real, THERMAL>(fc, gc, C, multiphase, false);
-        bad_any = bad_any || ns.bad;
-        sPsi[p_cur * NS + s] = ns.dpsi;
-        if (out_col && r >= y0 && r < y1) {
-          acc_m += ns.drho;
-          if (THERMAL) {
-            acc_e += ns.dT;
-            if (r == 0 && heat_col) acc_h += ns.dT;
-          }
-        }
-      }
-      __syncthreads();
-
-      // ===================== phase B: row q = r - 1 =====================
-      const int q = r - 1;
-      if (f_col && q >= y0 - 1 && q >= 0 && q < ny) {
-        Real Fx = Real(0), Fy = Real(0);
-        if (multiphase) {
-          const Real* P0 = sPsi + p_prev * NS + s;
-          const Real* Pp = sPsi + p_cur * NS + s;
-          const Real* Pm = sPsi + p_prev2 * NS + s;
-          if (q > 0 && q < ny - 1) {
-            sc_force<Real>(P0[0], P0[1], P0[-1], Pp[0], Pp[1], Pp[-1], Pm[0], Pm[1], Pm[-1], false, false, C, Fx, Fy);
-          } else {
-            const bool sol_m = q == 0, sol_p = q == ny - 1;  // row q-1 / q+1 is a wall
-            sc_force<Real>(P0[0], P0[1], P0[-1], sol_p ? Real(0) : Pp[0], sol_p ? Real(0) : Pp[1],
-                           sol_p ? Real(0) : Pp[-1], sol_m ? Real(0) : Pm[0], sol_m ? Real(0) : Pm[1],
-                           sol_m ? Real(0) : Pm[-1], sol_m, sol_p, C, Fx, Fy);
-          }
-        }
-        Fy -= (drho_p + rra) * C.g_a;  // Eq. 14, gravity along -y
-        const Real inv_rho = sizeof(Real) == 8 ? inv_rho_p : fast_rcp(rho_p);
-        const Real dux = Fx * inv_rho, duy = Fy * inv_rho;
-        const Real uax = ux_p + Real(0.5) * dux, uay = uy_p + Real(0.5) * duy;  // Eq. 7
-        sUx[p_prev * NS + s] = uax;
-        sUy[p_prev * NS + s] = uay;
-        if (out_col && q >= y0 && q < y1)
-          collide_f<Real>(StridedPops<Real>{sF + f_prev * 9 * NS + s, NS}, OffsetOut<Real>{Fout, q * pitch + xn, I},
-                          rho_p, drho_p, ux_p, uy_p, dux, duy, C.omega_f);
-      }
-      __syncthreads();
-
-      // ===================== phase C: row q2 = r - 2 =====================
-      if (THERMAL) {
-        const int q2 = r - 2;
-        if (out_col && q2 >= y0 && q2 < y1) {
-          const Real* U2x = sUx + p_prev2 * NS + s;
-          const Real* U2y = sUy + p_prev2 * NS + s;
-          const Real uxE = U2x[1], uxW = U2x[-1];
-          const Real uyN = sUy[p_prev * NS + s];
-          const Real uyS = sUy[p_cur * NS + s];  // slot of row r-3
-          Real dyu = Real(0.5) * (uyN - uyS);
-          if (q2 == 0 || q2 == ny - 1) {  // one-sided wall-normal difference over the fluid rows
-            const bool wall_lo = q2 == 0, wall_hi = q2 == ny - 1;
-            const Real uyC = U2y[0];
-            dyu = (wall_lo && wall_hi) ? Real(0) : (wall_lo ? uyN - uyC : uyC - uyS);
-          }
-          const Real divu = Real(0.5) * (uxE - uxW) + dyu;
-          const Real phi = coef_p2 * divu;
-          collide_g<Real>(StridedPops<Real>{sG + g_prev2 * 9 * NS + s, NS}, OffsetOut<Real>{Gout, q2 * pitch + xn, I},
-                          T_p2, dT_p2, U2x[0], U2y[0], phi, C.omega_g);
-        }
+        collide_g<Real>(StridedPops<Real>{sG + g_prev2 * 9 * NS + s, NS}, OffsetOut<Real>{Gout, q2 * pitch + xn, I},
+                        T_p2, dT_p2, U2x[0], U2y[0], phi, C.omega_g);
       }
     }
 

@@ -4,10 +4,11 @@ A batch advances lattices of uneven size and parameters with one fused launch pe
 step (replayed from a CUDA graph); each member's partial sums are folded by its
 own last tile, so with the same tiling and the same compiled tile code a member's
 populations are bit-identical to a single-lattice run.  That holds for the general
-loop (LBM_KERNEL_SCALAR), whose batch and single-lattice instantiations compile the
-update alike.  The default form's interior path is instantiated once with its constants
-in shared memory (batches) and once as kernel parameters (single lattices), and the
-compiler may fuse a few FP32 multiply-adds differently in the two: there a member agrees
+loop (LBM_KERNEL_SCALAR) launched once per step, whose batch and single-lattice
+instantiations compile the update alike.  The default form's interior path is instantiated once with its constants
+in shared memory (batches) and once as kernel parameters (single lattices), as is the
+persistent loop, and the compiler may fuse a few FP32 multiply-adds differently in each:
+there a member agrees
 with the lattice alone to FP32 rounding (1e-6 of the population scale after 37 steps,
 far inside the 1e-5 parity tolerance).
 """
@@ -43,10 +44,11 @@ def member_case(k, nx, ny):
 ROUNDING = {"fp64": 1e-12, "fp32": 1e-6}
 
 
-def single_run(L, nx, ny, p, fields, prec, steps, tiling, kernel="auto"):
+def single_run(L, nx, ny, p, fields, prec, steps, tiling, kernel="auto", loop="auto"):
     lat = L.Lattice(nx, ny, prec)
     lat.set_params(p)
     lat.set_kernel(kernel)
+    lat.set_step_loop(loop)
     lat.set_tiling(*tiling)
     lat.init_fields(*fields)
     lat.step(steps)
@@ -59,26 +61,27 @@ def agree(a, b, prec, bitwise):
     return np.abs(a - b).max() <= ROUNDING[prec] * np.abs(b).max()
 
 
-@pytest.mark.parametrize("kernel", ["scalar", "auto"])
+@pytest.mark.parametrize("kernel,loop", [("scalar", "launches"), ("auto", "launches"), ("auto", "auto")])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_batch_members_match_single_runs(prec, kernel):
+def test_batch_members_match_single_runs(prec, kernel, loop):
     L = lbm()
     sizes = [(403, 57), (250, 121), (129, 50), (777, 64)]
     b = L.Batch(prec, thermal=True)
     b.set_kernel(kernel)
+    b.set_step_loop(loop)
     cases = []
     for k, (nx, ny) in enumerate(sizes):
         p, fields = member_case(k, nx, ny)
         m = b.add(nx, ny, p)
         m.init_fields(*fields)
         cases.append((m, nx, ny, p, fields))
-    steps = 37  # two captured 16-step graphs plus single launches
+    steps = 37  # two captured 16-step graphs plus single launches (or one persistent launch)
     b.set_tiling(128, 16)  # bitwise equality needs the same band heights as the single runs
     b.step(steps)
-    assert b.launches == steps
-    bitwise = kernel == "scalar"
+    assert b.launches == (steps if b.step_loop == "launches" else 1)
+    bitwise = kernel == "scalar" and loop == "launches"  # the same compiled tile code on both sides
     for m, nx, ny, p, fields in cases:
-        f_ref, g_ref = single_run(L, nx, ny, p, fields, prec, steps, (128, 16), kernel)
+        f_ref, g_ref = single_run(L, nx, ny, p, fields, prec, steps, (128, 16), kernel, loop)
         f, g = m.populations()
         assert agree(f, f_ref, prec, bitwise) and agree(g, g_ref, prec, bitwise)
         assert m.step_count == steps
