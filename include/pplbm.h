@@ -267,7 +267,8 @@ lbm_status lbm_default_band_plan(int32_t nx, int32_t ny, int32_t cols, int64_t s
  *     on mbarriers), which removes the per-thread copy work from the step.  Needs
  *     128-column tiles and the step's lean form (no pool geometry, Hazi-Markus source
  *     or bubble statistics); other lattices take the scalar form.  A bulk copy that does
- *     not complete within a bounded wait makes lbm_sync return LBM_ETIMEOUT.  Its results
+ *     not complete within a bounded wait (lbm_set_wait_limit) makes lbm_sync return
+ *     LBM_ETIMEOUT.  Its results
  *     are bit-identical to the scalar form's; on GB300 it runs about 9 % slower (its
  *     warps wait on rows that arrive later than the per-thread copies do).
  * FP64 lattices, and lbm_step_noalloc on caller-laid-out buffers, always use the scalar
@@ -298,10 +299,13 @@ enum { LBM_LOOP_AUTO = 0, LBM_LOOP_LAUNCHES = 1, LBM_LOOP_PERSISTENT = 2 };
 lbm_status lbm_set_step_loop(lbm_ctx* ctx, int32_t loop);
 /* The loop (LBM_LOOP_LAUNCHES or _PERSISTENT) a multi-step call takes now; -1 if ctx is NULL. */
 int32_t lbm_step_loop(lbm_ctx* ctx);
-/* Poll limit of the persistent launch's barrier waits: a CTA gives up after max_polls polls
- * (0, the default: after 5 s of polling only).  A test sets 1 to make a wait run out while
- * the other CTAs are still working, and checks that lbm_sync reports LBM_ETIMEOUT and that the
- * context recovers.  LBM_EINVAL for max_polls < 0 or >= 2^32. */
+/* Poll limit of the step's bounded device waits: the persistent launch's grid-barrier waits
+ * (default: 5 s of polling) and the TMA form's waits for its staged rows (default: 2^22
+ * polls); a wait gives up after max_polls polls (0 restores the defaults).  A test sets 1 to
+ * make a wait run out while the work it waits for is still under way, and checks that
+ * lbm_sync reports LBM_ETIMEOUT, that nothing faults, and that the context recovers after a
+ * new initialisation (a TMA wait that gives up still lets its row's copies land before the
+ * CTA ends).  LBM_EINVAL for max_polls < 0 or >= 2^32. */
 lbm_status lbm_set_wait_limit(lbm_ctx* ctx, int64_t max_polls);
 
 int64_t lbm_get_step(const lbm_ctx* ctx);
@@ -359,7 +363,7 @@ lbm_status lbm_batch_sync(lbm_batch* b, int32_t* unstable_slot);
 lbm_status lbm_batch_set_step_loop(lbm_batch* b, int32_t loop);
 /* The loop a multi-step call takes now (LBM_LOOP_LAUNCHES or _PERSISTENT); -1 on error. */
 int32_t lbm_batch_step_loop(lbm_batch* b);
-/* As lbm_set_wait_limit, for the batch's persistent launches. */
+/* As lbm_set_wait_limit, for the batch's persistent and TMA launches. */
 lbm_status lbm_batch_set_wait_limit(lbm_batch* b, int64_t max_polls);
 /* lbm_read_fields of one member. */
 lbm_status lbm_batch_read_fields(lbm_batch* b, int32_t slot, double* rho, double* ux, double* uy, double* T,

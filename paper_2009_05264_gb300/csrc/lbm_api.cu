@@ -16,7 +16,8 @@
 #include "pplbm.h"
 
 namespace pplbm {
-cudaError_t launch_lbm_f32(int, int, int, int, bool, const Inst*, const Tile*, int, cudaStream_t, const Inst*);
+cudaError_t launch_lbm_f32(int, int, int, int, bool, const Inst*, const Tile*, int, cudaStream_t, const Inst*,
+                          unsigned);
 cudaError_t launch_lbm_f64(int, int, int, int, bool, const Inst*, const Tile*, int, cudaStream_t, const Inst*);
 cudaError_t launch_init_from_fields_f32(const Inst*, int, int, const double*, int, cudaStream_t);
 cudaError_t launch_init_from_fields_f64(const Inst*, int, int, const double*, int, cudaStream_t);
@@ -48,9 +49,9 @@ long long persistent_slots(int fp64, int thermal, int cols, int kernel, bool ful
 }
 
 cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, int kernel, bool full, const Inst* d_inst,
-                       const Tile* d_tiles, int ntiles, cudaStream_t s, const Inst* h_inst) {
+                       const Tile* d_tiles, int ntiles, cudaStream_t s, const Inst* h_inst, unsigned max_polls) {
   return fp64 ? launch_lbm_f64(thermal, cols, mode, kernel, full, d_inst, d_tiles, ntiles, s, h_inst)
-              : launch_lbm_f32(thermal, cols, mode, kernel, full, d_inst, d_tiles, ntiles, s, h_inst);
+              : launch_lbm_f32(thermal, cols, mode, kernel, full, d_inst, d_tiles, ntiles, s, h_inst, max_polls);
 }
 cudaError_t launch_init_from_fields(int fp64, const Inst* d_inst, int nx, int ny, const double* d_fields,
                                     int has_T, cudaStream_t s) {
@@ -486,7 +487,7 @@ lbm_status launch(lbm_ctx* c, int mode) {
   cudaError_t e = launch_lbm(c->prec == LBM_FP64, c->thermal, step_tiles ? c->cols : kAuxCols, mode, kernel,
                              needs_full_step(c->hinst), c->d_inst,
                              step_tiles ? c->d_tiles_step : c->d_tiles_aux,
-                             step_tiles ? c->ntiles_step : c->ntiles_aux, c->stream, &c->hinst);
+                             step_tiles ? c->ntiles_step : c->ntiles_aux, c->stream, &c->hinst, c->max_polls);
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
   ++c->launches;
   return LBM_OK;

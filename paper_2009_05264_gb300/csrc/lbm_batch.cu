@@ -170,8 +170,8 @@ lbm_status rebuild(lbm_batch* b) {
 
 lbm_status launch_steps(lbm_batch* b, int64_t n) {
   for (int64_t k = 0; k < n; ++k) {
-    LBM_BCUDA(b, launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->launch_kernel, b->any_full, b->d_insts, b->d_tiles, b->ntiles,
-                            b->stream));
+    LBM_BCUDA(b, launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->launch_kernel, b->any_full,
+                            b->d_insts, b->d_tiles, b->ntiles, b->stream, nullptr, b->max_polls));
     ++b->launches;
   }
   return LBM_OK;
@@ -208,8 +208,8 @@ lbm_status capture_graph(lbm_batch* b) {
   LBM_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   lbm_status s = LBM_OK;
   for (int k = 0; k < kGraphChunk && s == LBM_OK; ++k) {
-    if (launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->launch_kernel, b->any_full, b->d_insts, b->d_tiles, b->ntiles,
-                   b->stream) != cudaSuccess)
+    if (launch_lbm(b->prec == LBM_FP64, b->thermal, b->cols, MODE_STEP, b->launch_kernel, b->any_full, b->d_insts,
+                   b->d_tiles, b->ntiles, b->stream, nullptr, b->max_polls) != cudaSuccess)
       s = bfail(b, LBM_ECUDA, "launch during graph capture");
   }
   const cudaError_t e = cudaStreamEndCapture(b->stream, &g);

@@ -6,9 +6,10 @@
 namespace pplbm {
 
 cudaError_t launch_lbm_f32(int thermal, int cols, int mode, int kernel, bool full, const Inst* d_inst,
-                          const Tile* d_tiles, int ntiles, cudaStream_t s, const Inst* h_inst) {
+                          const Tile* d_tiles, int ntiles, cudaStream_t s, const Inst* h_inst, unsigned max_polls) {
   if (mode == MODE_STEP && kernel == LBM_KERNEL_PAIRED) return launch_pair(thermal, cols, d_inst, d_tiles, ntiles, s);
-  if (mode == MODE_STEP && kernel == LBM_KERNEL_TMA) return launch_tma(thermal, cols, d_inst, d_tiles, ntiles, s, h_inst);
+  if (mode == MODE_STEP && kernel == LBM_KERNEL_TMA)
+    return launch_tma(thermal, cols, d_inst, d_tiles, ntiles, s, h_inst, max_polls);
   return launch_precision<float>(thermal, cols, mode, full, mode == MODE_STEP && kernel == LBM_KERNEL_INTERIOR, d_inst,
                                  d_tiles, ntiles, s, h_inst);
 }

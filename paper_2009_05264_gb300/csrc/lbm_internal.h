@@ -123,8 +123,10 @@ inline int tile_is_interior(int geometry, int nx, int cols, int x0) {
 // only the step's full form handles (the lean form leaves them out of the hot loop).
 // h_inst: host copy of the launch's only instance (the lean scalar step then takes its
 // constants as a kernel parameter), or null for launches over several instances.
+// max_polls: poll cap of the TMA form's row waits (0: its full limit; lbm_set_wait_limit).
 cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, int kernel, bool full, const Inst* d_inst,
-                       const Tile* d_tiles, int ntiles, cudaStream_t s, const Inst* h_inst = nullptr);
+                       const Tile* d_tiles, int ntiles, cudaStream_t s, const Inst* h_inst = nullptr,
+                       unsigned max_polls = 0);
 // nsteps steps of the step kernel in one cooperative launch (tiles drawn dynamically from a
 // counter, a bounded grid barrier between steps; MODE_STEP only).  grid <= resident CTAs of
 // the device; bar: zeroed GridBar in device memory.

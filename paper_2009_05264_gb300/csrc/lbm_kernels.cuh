@@ -531,6 +531,73 @@ __device__ __forceinline__ void collide_g(const Pops& gs, const Out& go, Real T,
   pair(6, 8, uay - uax, lat_w<Real>(6));
 }
 
+// FP32 forms of the two collisions for the interior path, with paired FP32 arithmetic
+// (FADD2 / FMUL2 / FFMA2: two independent operations per instruction).  The pairs of
+// opposite directions that share a weight are computed two at a time: the axis pairs
+// (1,3) and (2,4) in the two lanes of one register pair, the diagonal pairs (5,7) and (6,8)
+// in another.  Same formulas as collide_f / collide_g; only the grouping of the roundings
+// differs (paired instructions round each lane exactly as the scalar instruction would).
+__device__ __forceinline__ float2 f2bc(float a) { return make_float2(a, a); }
+
+template <typename Pops, typename Out>
+__device__ __forceinline__ void collide_f_paired(const Pops& fs, const Out& fo, float rho, float drho, float ux,
+                                                 float uy, float dux, float duy, float omega_f) {
+  constexpr float w0 = LatWeights<float>::w0(), w1 = LatWeights<float>::w1(), w5 = LatWeights<float>::w5();
+  const float2 U = make_float2(ux, uy), D = make_float2(dux, duy);
+  const float2 S = __ffma2_rn(f2bc(2.0f), U, D);  // (2u + du) per axis
+  const float2 UU = __fmul2_rn(U, U);
+  const float2 DS = __fmul2_rn(D, S);
+  const float r15 = 1.5f * rho;
+  const float K = omega_f * (drho - r15 * (UU.x + UU.y)) - r15 * (DS.x + DS.y);
+  const float r45 = 4.5f * rho, r3 = 3.0f * rho, keep = 1.0f - omega_f;
+  fo(0) = keep * fs(0) + w0 * K;
+  const float2 KEEP = f2bc(keep), R45 = f2bc(r45), KK = f2bc(K), WF = f2bc(omega_f), NEG = f2bc(-1.0f);
+  auto pairs = [&](float2 cu, float2 cd, float2 cs, float w, int i, int j, int ib, int jb) {
+    const float2 wcu = __fmul2_rn(WF, cu);                                     // omega c.u
+    const float2 X = __ffma2_rn(wcu, cu, __fmul2_rn(cd, cs));                  // omega cu^2 + cd cs
+    const float2 sym = __fmul2_rn(f2bc(w), __ffma2_rn(R45, X, KK));           // w (K + 4.5 rho X)
+    const float2 anti = __fmul2_rn(f2bc(w * r3), __fadd2_rn(wcu, cd));        // 3 w rho (omega cu + cd)
+    const float2 plus = __fadd2_rn(sym, anti), minus = __ffma2_rn(anti, NEG, sym);
+    const float2 a = __ffma2_rn(KEEP, make_float2(fs(i), fs(j)), plus);
+    const float2 b = __ffma2_rn(KEEP, make_float2(fs(ib), fs(jb)), minus);
+    fo(i) = a.x;
+    fo(j) = a.y;
+    fo(ib) = b.x;
+    fo(jb) = b.y;
+  };
+  pairs(U, D, S, w1, 1, 2, 3, 4);  // lanes: (1,3) with c.u = ux, (2,4) with c.u = uy
+  const float2 PM = make_float2(1.0f, -1.0f);
+  const float2 Ud = __ffma2_rn(f2bc(ux), PM, f2bc(uy));    // (ux + uy, uy - ux)
+  const float2 Dd = __ffma2_rn(f2bc(dux), PM, f2bc(duy));
+  const float2 Sd = __ffma2_rn(f2bc(S.x), PM, f2bc(S.y));
+  pairs(Ud, Dd, Sd, w5, 5, 6, 7, 8);  // lanes: (5,7) with c.u = ux + uy, (6,8) with c.u = uy - ux
+}
+
+template <typename Pops, typename Out>
+__device__ __forceinline__ void collide_g_paired(const Pops& gs, const Out& go, float T, float dT, float uax,
+                                                 float uay, float phi, float omega_g) {
+  constexpr float w0 = LatWeights<float>::w0(), w1 = LatWeights<float>::w1(), w5 = LatWeights<float>::w5();
+  const float2 U = make_float2(uax, uay);
+  const float2 UU = __fmul2_rn(U, U);
+  const float Kg = omega_g * (dT - 1.5f * T * (UU.x + UU.y)) + phi;
+  const float t45 = 4.5f * omega_g * T, t3 = 3.0f * omega_g * T, keep = 1.0f - omega_g;
+  go(0) = keep * gs(0) + w0 * Kg;
+  const float2 KEEP = f2bc(keep), NEG = f2bc(-1.0f);
+  auto pairs = [&](float2 cu, float w, int i, int j, int ib, int jb) {
+    const float2 sym = __ffma2_rn(f2bc(w * t45), __fmul2_rn(cu, cu), f2bc(w * Kg));  // w (Kg + 4.5 omega T cu^2)
+    const float2 anti = __fmul2_rn(f2bc(w * t3), cu);                                 // 3 w omega T cu
+    const float2 plus = __fadd2_rn(sym, anti), minus = __ffma2_rn(anti, NEG, sym);
+    const float2 a = __ffma2_rn(KEEP, make_float2(gs(i), gs(j)), plus);
+    const float2 b = __ffma2_rn(KEEP, make_float2(gs(ib), gs(jb)), minus);
+    go(i) = a.x;
+    go(j) = a.y;
+    go(ib) = b.x;
+    go(jb) = b.y;
+  };
+  pairs(U, w1, 1, 2, 3, 4);
+  pairs(__ffma2_rn(f2bc(uax), make_float2(1.0f, -1.0f), f2bc(uay)), w5, 5, 6, 7, 8);
+}
+
 // Issue the asynchronous pull of one node's populations into f_dst/g_dst (stride
 // dstride).  Interior links copy f*_i(x - c_i); links from a wall row copy
 // f*_opp(x) (halfway bounce-back; boundary_fill applies the g sign flip and wall
@@ -849,9 +916,14 @@ __device__ __forceinline__ void interior_rows(const Inst& I, const KConst<Real>&
       const Real uax = ux_p + Real(0.5) * dux, uay = uy_p + Real(0.5) * duy;  // Eq. 7
       sUx[p_prev * NS + s] = uax;
       sUy[p_prev * NS + s] = uay;
-      if (out_col && q >= y0 && q < y1)
-        collide_f<Real>(StridedPops<Real>{sF + f_prev * 9 * NS + s, NS}, OffsetOut<Real>{Fout, q * pitch + xn, I},
-                        rho_p, drho_p, ux_p, uy_p, dux, duy, C.omega_f);
+      if (out_col && q >= y0 && q < y1) {
+        if constexpr (sizeof(Real) == 4)
+          collide_f_paired(StridedPops<Real>{sF + f_prev * 9 * NS + s, NS}, OffsetOut<Real>{Fout, q * pitch + xn, I},
+                           rho_p, drho_p, ux_p, uy_p, dux, duy, C.omega_f);
+        else
+          collide_f<Real>(StridedPops<Real>{sF + f_prev * 9 * NS + s, NS}, OffsetOut<Real>{Fout, q * pitch + xn, I},
+                          rho_p, drho_p, ux_p, uy_p, dux, duy, C.omega_f);
+      }
     }
     __syncthreads();
 
@@ -872,8 +944,12 @@ __device__ __forceinline__ void interior_rows(const Inst& I, const KConst<Real>&
         }
         const Real divu = Real(0.5) * (uxE - uxW) + dyu;
         const Real phi = coef_p2 * divu;
-        collide_g<Real>(StridedPops<Real>{sG + g_prev2 * 9 * NS + s, NS}, OffsetOut<Real>{Gout, q2 * pitch + xn, I},
-                        T_p2, dT_p2, U2x[0], U2y[0], phi, C.omega_g);
+        if constexpr (sizeof(Real) == 4)
+          collide_g_paired(StridedPops<Real>{sG + g_prev2 * 9 * NS + s, NS}, OffsetOut<Real>{Gout, q2 * pitch + xn, I},
+                           T_p2, dT_p2, U2x[0], U2y[0], phi, C.omega_g);
+        else
+          collide_g<Real>(StridedPops<Real>{sG + g_prev2 * 9 * NS + s, NS}, OffsetOut<Real>{Gout, q2 * pitch + xn, I},
+                          T_p2, dT_p2, U2x[0], U2y[0], phi, C.omega_g);
       }
     }
 

@@ -58,11 +58,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, u
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
-// Wait for the phase of the given parity to complete; false if it has not after
-// TMA_WAIT_LIMIT polls.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+// Wait for the phase of the given parity to complete; false if it has not after `limit`
+// polls (TMA_WAIT_LIMIT, or a test's lower cap for the row waits).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit = TMA_WAIT_LIMIT) {
   const unsigned a = smem_u32(bar);
-  for (long long it = 0; it < TMA_WAIT_LIMIT; ++it) {
+  for (long long it = 0; it < limit; ++it) {
     unsigned done;
     asm volatile(
         "{\n"
@@ -151,9 +151,10 @@ __device__ __forceinline__ void pull_direct(float (&fc)[9], float (&gc)[9], cons
 // parameter kp (as in lbm_fused_kernel).
 template <bool THERMAL, bool PCONST>
 __global__ void __launch_bounds__(ST_COLS, 5)
-lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
+lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, unsigned max_polls,
                const __grid_constant__ KParams<float> kp) {
   constexpr int B = ST_COLS;
+  const long long row_wait_limit = max_polls != 0 ? (long long)max_polls : TMA_WAIT_LIMIT;
   constexpr int W = out_cols<B>();
   constexpr int NS = B - 4;
   extern __shared__ unsigned char tma_dyn_smem[];
@@ -266,8 +267,8 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
     if (!local && tid == 0 && k + 1 < kend)
       issue_row(k + 1, f_cur == ST_FS - 1 ? 0 : f_cur + 1, g_cur == ST_GS - 1 ? 0 : g_cur + 1);
     if (!local) {
-      bool ok = mbar_wait(&fbar[f_cur], f_par);
-      if (THERMAL) ok = mbar_wait(&gbar[g_cur], g_par) && ok;
+      bool ok = mbar_wait(&fbar[f_cur], f_par, row_wait_limit);
+      if (THERMAL) ok = mbar_wait(&gbar[g_cur], g_par, row_wait_limit) && ok;
       if (!ok) {
         atomicOr(&st->status, STATUS_TIMEOUT);
         sAbort = 1;
@@ -390,12 +391,14 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
       g_par ^= 1u;
     }
   }
-  if (k + 1 < kend && !local && tid == 0) {
-    // aborted at row k: let the copies of row k + 1, possibly still in flight, land before
-    // the CTA's shared memory is released (row j: slot j mod depth, parity (j / depth) & 1)
-    const int j = k + 1;
-    mbar_wait(&fbar[j % ST_FS], (j / ST_FS) & 1);
-    if (THERMAL) mbar_wait(&gbar[j % ST_GS], (j / ST_GS) & 1);
+  if (k < kend && !local && tid == 0) {
+    // aborted at row k: let the copies of row k (whose waits gave up, possibly before they
+    // landed) and of row k + 1 (issued before them) land before the CTA's shared memory is
+    // released (row j: slot j mod depth, parity (j / depth) & 1); each wait has the full limit
+    for (int j = k; j <= k + 1 && j < kend; ++j) {
+      mbar_wait(&fbar[j % ST_FS], (j / ST_FS) & 1);
+      if (THERMAL) mbar_wait(&gbar[j % ST_GS], (j / ST_GS) & 1);
+    }
   }
 
   // ---------------- per-tile partials into the launch's totals ----------------
@@ -404,7 +407,7 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
 }
 
 template <bool THERMAL, bool PCONST>
-cudaError_t launch_tma_t(const Inst* d_inst, const Tile* d_tiles, int ntiles, cudaStream_t s,
+cudaError_t launch_tma_t(const Inst* d_inst, const Tile* d_tiles, int ntiles, unsigned max_polls, cudaStream_t s,
                          const KParams<float>& kp) {
   constexpr size_t smem = tma_smem_bytes<THERMAL>();
   auto fn = lbm_tma_kernel<THERMAL, PCONST>;
@@ -418,25 +421,26 @@ cudaError_t launch_tma_t(const Inst* d_inst, const Tile* d_tiles, int ntiles, cu
     if (e != cudaSuccess) return e;
     configured |= bit;
   }
-  fn<<<ntiles, ST_COLS, smem, s>>>(d_inst, d_tiles, kp);
+  fn<<<ntiles, ST_COLS, smem, s>>>(d_inst, d_tiles, max_polls, kp);
   return cudaGetLastError();
 }
 
 // h_inst: the host copy of the launch's only instance (constants as a kernel parameter),
-// or null for launches over several instances.
+// or null for launches over several instances.  max_polls: poll cap of the row waits (0: the
+// full TMA_WAIT_LIMIT; a test lowers it to make a wait give up while the copies still land).
 inline cudaError_t launch_tma(int thermal, int cols, const Inst* d_inst, const Tile* d_tiles, int ntiles,
-                              cudaStream_t s, const Inst* h_inst) {
+                              cudaStream_t s, const Inst* h_inst, unsigned max_polls) {
   if (cols != ST_COLS) return cudaErrorInvalidValue;
   if (ntiles <= 0) return cudaSuccess;
   KParams<float> kp{};
   if (h_inst) {
     kp.I = *h_inst;
     fill_consts<float>(kp.C, *h_inst, h_inst->rho_ref);
-    return thermal ? launch_tma_t<true, true>(d_inst, d_tiles, ntiles, s, kp)
-                   : launch_tma_t<false, true>(d_inst, d_tiles, ntiles, s, kp);
+    return thermal ? launch_tma_t<true, true>(d_inst, d_tiles, ntiles, max_polls, s, kp)
+                   : launch_tma_t<false, true>(d_inst, d_tiles, ntiles, max_polls, s, kp);
   }
-  return thermal ? launch_tma_t<true, false>(d_inst, d_tiles, ntiles, s, kp)
-                 : launch_tma_t<false, false>(d_inst, d_tiles, ntiles, s, kp);
+  return thermal ? launch_tma_t<true, false>(d_inst, d_tiles, ntiles, max_polls, s, kp)
+                 : launch_tma_t<false, false>(d_inst, d_tiles, ntiles, max_polls, s, kp);
 }
 
 template <bool THERMAL>

@@ -153,21 +153,48 @@ def test_fp32_channel_thermal_1000_steps(tiling, kernel):
         assert rel_err(got, ref, k) < FP32_TOL, k
 
 
-def two_phase_fp32_checks(got, ref, lat_mass, orc_mass):
-    """FP32 criteria where an interface is present: rounding noise moves an interface by a
-    fraction of a lattice unit, and a pointwise difference there is that displacement times
-    the density gradient; so bulk nodes keep the 1e-5 bound, interface nodes bound the
-    displacement, and the whole field is compared in the relative L2 norm."""
+def two_phase_errors(got, ref):
+    """Pointwise errors of an FP32 two-phase field against the oracle, split into bulk nodes
+    (density gradient below 1 % of its maximum) and interface nodes: density relative to its
+    maximum, the interface displacement in lattice units (the density difference over the
+    local gradient, regularised at the bulk edge), the relative L2 norms, and the velocity in
+    lattice units (relative to the lattice speed dx/dt = 1) and relative to its own maximum."""
     gy, gx = np.gradient(ref["rho"])
     grad = np.hypot(gx, gy)
     bulk = grad < 0.01 * grad.max()
     diff = np.abs(got["rho"] - ref["rho"])
-    assert diff[bulk].max() < FP32_TOL * np.abs(ref["rho"]).max()
-    # interface displacement in lattice units (gradient regularised at the bulk edge)
-    assert (diff[~bulk] / (grad[~bulk] + 0.1 * grad.max())).max() < 1e-3
-    for k in ("rho", "T"):
-        assert np.linalg.norm(got[k] - ref[k]) < FP32_TOL * np.linalg.norm(ref[k]), k
+    du = np.maximum(np.abs(got["ux"] - ref["ux"]), np.abs(got["uy"] - ref["uy"]))
+    u_max = max(np.abs(ref["ux"]).max(), np.abs(ref["uy"]).max())
+    e = {"rho_bulk": diff[bulk].max() / np.abs(ref["rho"]).max(),
+         "rho_interface": diff[~bulk].max() / np.abs(ref["rho"]).max(),
+         "displacement": (diff[~bulk] / (grad[~bulk] + 0.1 * grad.max())).max(),
+         "rho_L2": np.linalg.norm(got["rho"] - ref["rho"]) / np.linalg.norm(ref["rho"]),
+         "rho_L2_shift": np.linalg.norm(got["rho"] - ref["rho"]) / np.linalg.norm(grad),
+         "T": np.abs(got["T"] - ref["T"]).max() / np.abs(ref["T"]).max(),
+         "T_L2": np.linalg.norm(got["T"] - ref["T"]) / np.linalg.norm(ref["T"]),
+         "u_lattice": du.max(), "u_rel_max": du.max() / u_max, "u_max": u_max}
+    print("FP32 two-phase errors: " + ", ".join(f"{k} {v:.2e}" for k, v in e.items()))
+    return e
+
+
+def two_phase_fp32_checks(got, ref, lat_mass, orc_mass):
+    """FP32 criteria where an interface is present: rounding noise moves an interface by a
+    fraction of a lattice unit, and a pointwise difference there is that displacement times
+    the density gradient; so bulk nodes keep the 1e-5 bound, interface nodes bound the
+    displacement to 1e-3 lattice units, the density field differs in the L2 norm by no more
+    than a rigid shift of the whole field by 1e-3 lattice units plus 1e-5 of the field, the
+    temperature within 1e-5 in the relative L2 norm, and the velocity (in a drop only the
+    spurious current) within 1e-5 in lattice units, i.e. relative to the lattice speed."""
+    e = two_phase_errors(got, ref)
+    assert e["rho_bulk"] < FP32_TOL
+    assert e["displacement"] < 1e-3
+    gy, gx = np.gradient(ref["rho"])
+    assert (np.linalg.norm(got["rho"] - ref["rho"]) <
+            1e-3 * np.linalg.norm(np.hypot(gx, gy)) + FP32_TOL * np.linalg.norm(ref["rho"]))
+    assert e["T_L2"] < FP32_TOL
+    assert e["u_lattice"] < FP32_TOL
     assert abs(lat_mass - orc_mass) < FP32_TOL * orc_mass
+    return e
 
 
 @pytest.mark.parametrize("kernel", ["paired", "scalar", "tma"])

@@ -1,5 +1,6 @@
-"""The persistent step loop: one cooperative launch per call, a bounded grid barrier between
-steps, tiles drawn from a per-step counter.
+"""Bounded device waits.  The persistent step loop: one cooperative launch per call, a
+bounded grid barrier between steps, tiles drawn from a per-step counter; and the TMA step
+form's bounded waits on its bulk-copied rows.
 
 It runs the step kernel's tile body, so it must agree with one launch per step to rounding
 (the two are compiled separately) and with the oracle at the parity tolerances, both where
@@ -148,3 +149,37 @@ def test_persistent_batch_agrees_with_graph_replayed_launches(precision):
     for (fp, gp), (fr, gr) in zip(runs["persistent"], runs["launches"]):
         assert np.abs(fp - fr).max() <= tol * np.abs(fr).max()
         assert np.abs(gp - gr).max() <= tol * np.abs(gr).max()
+
+
+def test_tma_row_wait_timeout_is_reported_and_the_context_recovers():
+    """The TMA step form waits on mbarriers for its bulk-copied rows, each wait bounded.  With
+    the poll limit at one poll a wait gives up while its row's copies are still in flight; the
+    CTA lets them (and the next row's) land before it ends, the call reports LBM_ETIMEOUT, and
+    the context, initialised again, reproduces a fresh run bit for bit."""
+    L = lbm()
+    nx, ny = 1000, 100
+    p, fields = channel(nx, ny)
+
+    def tma_lattice():
+        lat = L.Lattice(nx, ny, "fp32")
+        lat.set_params(p)
+        lat.set_kernel("tma")
+        lat.set_step_loop("launches")
+        lat.set_tiling(128, 0)
+        lat.init_fields(*fields)
+        assert lat.step_kernel == "tma"
+        return lat
+
+    lat = tma_lattice()
+    lat.step(1)  # the first step after an initialisation reads its own populations: no bulk copies
+    lat.set_wait_limit(1)
+    with pytest.raises(L.LbmError) as err:
+        lat.step(5)
+    assert err.value.status == 4  # LBM_ETIMEOUT
+    lat.set_wait_limit(0)
+    lat.init_fields(*fields)
+    lat.step(20)
+    fresh = tma_lattice()
+    fresh.step(20)
+    for a, b in zip(lat.populations(), fresh.populations()):
+        assert np.array_equal(a, b)
