@@ -653,8 +653,9 @@ def run_ours(args):
             line["fp64"] = run_fp64(max(10, args.steps // 10))
             line["c2"] = run_c2()
             line["batch"] = run_batch(args.batch_steps)
-            line["serve"] = run_serve(args.serve_requests, args.serve_steps,
-                                      tiling=tuple(int(x) for x in line["batch"]["tiling"].split("x")))
+            # the server keeps each member's default band plan: a fixed band height tuned for the
+            # 64-channel sweep leaves the served mix (a few lattices, some 4000 x 400) slower
+            line["serve"] = run_serve(args.serve_requests, args.serve_steps, tiling=None)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

@@ -357,9 +357,9 @@ lbm_status lbm_batch_step_async(lbm_batch* b, int64_t nsteps);
 lbm_status lbm_batch_sync(lbm_batch* b, int32_t* unstable_slot);
 /* The step loop of the batch's multi-step calls (LBM_LOOP_* as lbm_set_step_loop: one
  * cooperative launch per call over every member's tiles with bounded grid barriers between
- * steps, or one launch per step replayed from CUDA graphs; auto: persistent when the batch's
- * tiles fit in one wave).  A barrier wait that gives up sets LBM_ETIMEOUT on the members of
- * the CTAs that gave up; lbm_batch_sync reports it. */
+ * steps, or one launch per step replayed from CUDA graphs; LBM_LOOP_AUTO takes the graph-
+ * replayed launches, measured faster for batches).  A barrier wait that gives up sets
+ * LBM_ETIMEOUT on the members of the CTAs that gave up; lbm_batch_sync reports it. */
 lbm_status lbm_batch_set_step_loop(lbm_batch* b, int32_t loop);
 /* The loop a multi-step call takes now (LBM_LOOP_LAUNCHES or _PERSISTENT); -1 on error. */
 int32_t lbm_batch_step_loop(lbm_batch* b);

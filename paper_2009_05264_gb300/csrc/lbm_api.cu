@@ -184,6 +184,11 @@ const char* fill_inst(Inst& I, const lbm_params* p, int nx, int ny, int pitch, l
     I.wall0 = -G3 * (I.beta + I.mix) * pr * pr + I.Gwet_psiw * pr / 6.0;
     I.wall1 = -G3 * I.beta * pr + I.Gwet_psiw / 6.0;
   }
+  I.R_u1r = I.R * I.inv_u1r;
+  I.a_Dr = I.a * I.inv_Dr;
+  I.twob_rr = 2.0 * I.b * I.rho_ref;
+  I.nk_sTc = -I.kappa * I.inv_sqrtTc;
+  I.a_rr2_Dr = I.a * I.rr2_Dr;
   I.heater_x0 = p->heater_x0 < 0 ? nx / 5 : p->heater_x0;
   I.heater_len = p->heater_len;
   I.heat_on_step = p->heat_on_step;

@@ -87,6 +87,10 @@ struct Inst {
   // sum w_i c_iy = -1/6; the two parts cancel exactly for a balanced wall, which keeps the FP32
   // force free of the cancellation).
   double mix, drho_out, dT_in, dT_heat, drho_vapor, wall0, wall1;
+  // products of constants of the FP32 equation of state, formed on the host: R / (1 - b rho_ref),
+  // a / D(rho_ref) with D(rho) = 1 + 2 b rho - (b rho)^2, 2 b rho_ref, -kappa / sqrt(Tc),
+  // a rho_ref^2 / D(rho_ref)
+  double R_u1r, a_Dr, twob_rr, nk_sTc, a_rr2_Dr;
 };
 
 // State of the grid-wide barrier between the steps of a persistent launch (device memory,

@@ -171,6 +171,9 @@ struct KConst {
   Real wall0, wall1;
   Real rho_ref_minus_avg;  // rho_ref - rho_avg of the previous step (buoyancy, Eq. 14)
   Real drho_vapor;         // rho_vapor - rho_ref: vapour when drho < drho_vapor
+  // products of the constants above, formed once (host doubles): R / (1 - b rho_ref),
+  // a / D(rho_ref), 2 b rho_ref, -kappa / sqrt(Tc), a rho_ref^2 / D(rho_ref)
+  Real R_u1r, a_Dr, twob_rr, nk_sTc, a_rr2_Dr;
 };
 
 // Every member is a conversion of a descriptor value (derived values are formed once, on the
@@ -212,6 +215,11 @@ __host__ __device__ inline void fill_consts(KConst<Real>& c, const Inst& I, doub
   c.wall1 = Real(I.wall1);
   c.rho_ref_minus_avg = Real(I.rho_ref - rho_avg_prev);
   c.drho_vapor = Real(I.drho_vapor);
+  c.R_u1r = Real(I.R_u1r);
+  c.a_Dr = Real(I.a_Dr);
+  c.twob_rr = Real(I.twob_rr);
+  c.nk_sTc = Real(I.nk_sTc);
+  c.a_rr2_Dr = Real(I.a_rr2_Dr);
 }
 
 // Kernel parameter of a launch over one instance: its descriptor and converted constants.
@@ -357,13 +365,28 @@ struct NodeState {
 // (dp/dT)_rho of one node.  In FP32 psi is evaluated as psi - psi_ref from exact
 // difference forms of Eq. 12 in rho - rho_ref and T - T_ref, so that neighbour
 // differences in the force keep their low-order bits.
-template <typename Real, bool THERMAL>
+// PAIRED (FP32 thermal, interior path): the two sums of Eqs. 4 and 17 in the two lanes of
+// paired FP32 additions (same association, each lane rounded as before).
+template <typename Real, bool THERMAL, bool PAIRED = false>
 __device__ __forceinline__ NodeState<Real> node_state(const Real (&fc)[9], const Real (&gc)[9],
                                                       const KConst<Real>& C, bool multiphase, bool hazi = false) {
   NodeState<Real> o;
   o.hmc = Real(0);
   const Real rho_ref = C.rho_ref;
-  o.drho = ((fc[0] + fc[1]) + (fc[2] + fc[3])) + ((fc[4] + fc[5]) + (fc[6] + fc[7])) + fc[8];
+  Real sum_g = Real(0);
+  if constexpr (PAIRED && THERMAL && sizeof(Real) == 4) {
+    float2 q[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) q[i] = make_float2(fc[i], gc[i]);
+    const float2 sum = __fadd2_rn(__fadd2_rn(__fadd2_rn(__fadd2_rn(q[0], q[1]), __fadd2_rn(q[2], q[3])),
+                                             __fadd2_rn(__fadd2_rn(q[4], q[5]), __fadd2_rn(q[6], q[7]))),
+                                  q[8]);
+    o.drho = sum.x;
+    sum_g = sum.y;
+  } else {
+    o.drho = ((fc[0] + fc[1]) + (fc[2] + fc[3])) + ((fc[4] + fc[5]) + (fc[6] + fc[7])) + fc[8];
+    if (THERMAL) sum_g = ((gc[0] + gc[1]) + (gc[2] + gc[3])) + ((gc[4] + gc[5]) + (gc[6] + gc[7])) + gc[8];
+  }
   o.rho = rho_ref + o.drho;
   const Real jx = (fc[1] - fc[3]) + (fc[5] - fc[6]) + (fc[8] - fc[7]);
   const Real jy = (fc[2] - fc[4]) + (fc[5] + fc[6]) - (fc[7] + fc[8]);
@@ -372,7 +395,7 @@ __device__ __forceinline__ NodeState<Real> node_state(const Real (&fc)[9], const
   o.ux = jx * inv_rho;
   o.uy = jy * inv_rho;
   if (THERMAL) {
-    o.dT = ((gc[0] + gc[1]) + (gc[2] + gc[3])) + ((gc[4] + gc[5]) + (gc[6] + gc[7])) + gc[8];
+    o.dT = sum_g;
     o.T = C.T_ref + o.dT;
   } else {
     o.dT = Real(0);
@@ -401,12 +424,14 @@ __device__ __forceinline__ NodeState<Real> node_state(const Real (&fc)[9], const
     }
     Real rad;
     if (sizeof(Real) == 4) {
-      const Real rr = rho_ref, inv_u1r = C.inv_u1r;
-      const Real dA = pR * (drho_c * T_c * inv1 * inv_u1r + (THERMAL ? rr * dT_c * inv_u1r : Real(0)));
-      Real dB = pa * alpha * drho_c * (rho_c + rr + Real(2) * pb * rho_c * rr) * invD * C.inv_Dr;
+      const Real rr = rho_ref;
+      // R (rho T / (1 - b rho) - rho_ref T_ref / (1 - b rho_ref)) and the attraction term's
+      // difference, as exact difference forms in drho = rho - rho_ref and dT = T - T_ref
+      const Real dA = C.R_u1r * (drho_c * T_c * inv1 + (THERMAL ? rr * dT_c : Real(0)));
+      Real dB = C.a_Dr * alpha * drho_c * (rho_c + rr + C.twob_rr * rho_c) * invD;
       if (THERMAL) {
-        const Real dsa = -kappa * inv_sqrtTc * dT_c * fast_rcp(sT + C.sqrtT_r);
-        dB += pa * dsa * (sa + C.sa_r) * C.rr2_Dr;
+        const Real dsa = C.nk_sTc * dT_c * fast_rcp(sT + C.sqrtT_r);
+        dB += C.a_rr2_Dr * dsa * (sa + C.sa_r);
       }
       const Real dp = dA - dB;
       const Real drad = (dp - drho_c * Real(1.0 / 3.0)) * C.psi_scale;
@@ -422,7 +447,7 @@ __device__ __forceinline__ NodeState<Real> node_state(const Real (&fc)[9], const
     }
     bad = bad || !(br < Real(1)) || !(rad >= Real(0));
     if (THERMAL) {
-      const Real dalpha = -kappa * sa * inv_sT * inv_sqrtTc;
+      const Real dalpha = C.nk_sTc * sa * inv_sT;  // d alpha / dT = -kappa sqrt(alpha) / sqrt(T Tc)
       dpdT = rho_c * pR * inv1 - pa * dalpha * rr_den;
     }
   }
@@ -455,6 +480,33 @@ __device__ __forceinline__ void sc_force(Real dc, Real dE, Real dW, Real dN, Rea
   const Real lead = C.psi_ref + C.beta * dc;
   Fx = -lead * t1x - C.mix * t2x;
   Fy = -lead * t1y - C.mix * t2y;
+  if (sol_m) Fy += C.wall0 + dc * C.wall1;
+  if (sol_p) Fy -= C.wall0 + dc * C.wall1;
+}
+
+// FP32 form of sc_force for the interior path, with paired FP32 instructions: the x and y
+// components in the two lanes of a register pair, and the diagonal neighbours' sums and
+// differences formed two at a time.  The same expressions as sc_force (the products keep its
+// difference-of-squares form (a - b)(a + b)); only the grouping of the roundings differs.
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+
+__device__ __forceinline__ void sc_force_paired(float dc, float dE, float dW, float dN, float dNE, float dNW, float dS,
+                                                float dSE, float dSW, bool sol_m, bool sol_p, const KConst<float>& C,
+                                                float& Fx, float& Fy) {
+  const float2 P = make_float2(dE, dN), Q = make_float2(dW, dS);
+  const float2 A = f2sub(P, Q), S = __fadd2_rn(P, Q);        // (dE - dW, dN - dS), (dE + dW, dN + dS)
+  const float2 U = make_float2(dNE, dSE), V = make_float2(dNW, dSW);
+  const float2 m = f2sub(U, V), p = __fadd2_rn(U, V);        // (dNE - dNW, dSE - dSW), (dNE + dNW, dSE + dSW)
+  const float2 U2 = make_float2(dNE, dNW), V2 = make_float2(dSE, dSW);
+  const float2 b = f2sub(U2, V2), a = __fadd2_rn(U2, V2);    // (dNE - dSE, dNW - dSW), (dNE + dSE, dNW + dSW)
+  const float2 mp = __fmul2_rn(m, p), ab = __fmul2_rn(b, a);
+  const float2 G2 = make_float2(C.G2, C.G2), Gh = make_float2(C.Gh, C.Gh);
+  const float2 t1 = __ffma2_rn(G2, A, __fmul2_rn(Gh, make_float2(m.x + m.y, p.x - p.y)));
+  const float2 t2 = __ffma2_rn(__fmul2_rn(G2, A), S, __fmul2_rn(Gh, make_float2(mp.x + mp.y, ab.x + ab.y)));
+  const float nlead = -(C.psi_ref + C.beta * dc);
+  const float2 F = __ffma2_rn(make_float2(nlead, nlead), t1, __fmul2_rn(make_float2(-C.mix, -C.mix), t2));
+  Fx = F.x;
+  Fy = F.y;
   if (sol_m) Fy += C.wall0 + dc * C.wall1;
   if (sol_p) Fy -= C.wall0 + dc * C.wall1;
 }
@@ -880,7 +932,7 @@ __device__ __forceinline__ void interior_rows(const Inst& I, const KConst<Real>&
 #pragma unroll
         for (int i = 0; i < 9; ++i) gs[i * NS] = gc[i];
       }
-      ns = node_state<Real, THERMAL>(fc, gc, C, multiphase, false);
+      ns = node_state<Real, THERMAL, true>(fc, gc, C, multiphase, false);
       bad_any = bad_any || ns.bad;
       sPsi[p_cur * NS + s] = ns.dpsi;
       if (out_col && r >= y0 && r < y1) {
@@ -901,13 +953,18 @@ __device__ __forceinline__ void interior_rows(const Inst& I, const KConst<Real>&
         const Real* P0 = sPsi + p_prev * NS + s;
         const Real* Pp = sPsi + p_cur * NS + s;
         const Real* Pm = sPsi + p_prev2 * NS + s;
+        auto force = [&](Real dN, Real dNE, Real dNW, Real dS, Real dSE, Real dSW, bool sol_m, bool sol_p) {
+          if constexpr (sizeof(Real) == 4)
+            sc_force_paired(P0[0], P0[1], P0[-1], dN, dNE, dNW, dS, dSE, dSW, sol_m, sol_p, C, Fx, Fy);
+          else
+            sc_force<Real>(P0[0], P0[1], P0[-1], dN, dNE, dNW, dS, dSE, dSW, sol_m, sol_p, C, Fx, Fy);
+        };
         if (q > 0 && q < ny - 1) {
-          sc_force<Real>(P0[0], P0[1], P0[-1], Pp[0], Pp[1], Pp[-1], Pm[0], Pm[1], Pm[-1], false, false, C, Fx, Fy);
+          force(Pp[0], Pp[1], Pp[-1], Pm[0], Pm[1], Pm[-1], false, false);
         } else {
           const bool sol_m = q == 0, sol_p = q == ny - 1;  // row q-1 / q+1 is a wall
-          sc_force<Real>(P0[0], P0[1], P0[-1], sol_p ? Real(0) : Pp[0], sol_p ? Real(0) : Pp[1],
-                         sol_p ? Real(0) : Pp[-1], sol_m ? Real(0) : Pm[0], sol_m ? Real(0) : Pm[1],
-                         sol_m ? Real(0) : Pm[-1], sol_m, sol_p, C, Fx, Fy);
+          force(sol_p ? Real(0) : Pp[0], sol_p ? Real(0) : Pp[1], sol_p ? Real(0) : Pp[-1], sol_m ? Real(0) : Pm[0],
+                sol_m ? Real(0) : Pm[1], sol_m ? Real(0) : Pm[-1], sol_m, sol_p);
         }
       }
       Fy -= (drho_p + rra) * C.g_a;  // Eq. 14, gravity along -y

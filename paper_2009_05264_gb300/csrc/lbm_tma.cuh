@@ -58,8 +58,29 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, u
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
+// Test, without waiting, whether the phase of the given parity has completed.
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// The row waits under a test's poll cap: at most `polls` non-blocking tests (a blocking try_wait
+// may suspend the thread until the copies land, so one poll of it rarely gives up).
+__device__ __forceinline__ bool mbar_poll(unsigned long long* bar, unsigned parity, unsigned polls) {
+  for (unsigned it = 0; it < polls; ++it)
+    if (mbar_test(bar, parity)) return true;
+  return false;
+}
 // Wait for the phase of the given parity to complete; false if it has not after `limit`
-// polls (TMA_WAIT_LIMIT, or a test's lower cap for the row waits).
+// polls of the (potentially blocking) try_wait.
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit = TMA_WAIT_LIMIT) {
   const unsigned a = smem_u32(bar);
   for (long long it = 0; it < limit; ++it) {
@@ -154,7 +175,6 @@ __global__ void __launch_bounds__(ST_COLS, 5)
 lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, unsigned max_polls,
                const __grid_constant__ KParams<float> kp) {
   constexpr int B = ST_COLS;
-  const long long row_wait_limit = max_polls != 0 ? (long long)max_polls : TMA_WAIT_LIMIT;
   constexpr int W = out_cols<B>();
   constexpr int NS = B - 4;
   extern __shared__ unsigned char tma_dyn_smem[];
@@ -267,8 +287,8 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, u
     if (!local && tid == 0 && k + 1 < kend)
       issue_row(k + 1, f_cur == ST_FS - 1 ? 0 : f_cur + 1, g_cur == ST_GS - 1 ? 0 : g_cur + 1);
     if (!local) {
-      bool ok = mbar_wait(&fbar[f_cur], f_par, row_wait_limit);
-      if (THERMAL) ok = mbar_wait(&gbar[g_cur], g_par, row_wait_limit) && ok;
+      bool ok = max_polls ? mbar_poll(&fbar[f_cur], f_par, max_polls) : mbar_wait(&fbar[f_cur], f_par);
+      if (THERMAL) ok = (max_polls ? mbar_poll(&gbar[g_cur], g_par, max_polls) : mbar_wait(&gbar[g_cur], g_par)) && ok;
       if (!ok) {
         atomicOr(&st->status, STATUS_TIMEOUT);
         sAbort = 1;

@@ -146,3 +146,30 @@ def test_unstable_member_is_reported_with_its_slot():
         b.step(2)
     assert e.value.status == 3 and f"member {bad.slot}" in str(e.value)
     b.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_batch_member_matches_oracle(prec, tol):
+    """A member of a batch of uneven channels (default tiling, default step loop), compared
+    directly with the oracle after 300 steps."""
+    import os
+
+    L = lbm()
+    b = L.Batch(prec, thermal=True)
+    members = []
+    for k, (nx, ny) in enumerate([(403, 57), (250, 121), (129, 50)]):
+        p, fields = member_case(k, nx, ny)
+        m = b.add(nx, ny, p)
+        m.init_fields(*fields)
+        members.append((m, nx, ny, p, fields))
+    b.step(300)
+    m, nx, ny, p, fields = members[1]
+    orc = oracle.Oracle(nx, ny, p, threads=os.cpu_count() or 1)
+    orc.init_fields(*fields)
+    assert orc.step(300) == 0
+    got, ref = m.fields(), orc.fields()
+    for key in ("rho", "ux", "uy", "T"):
+        scale = (max(np.abs(ref["ux"]).max(), np.abs(ref["uy"]).max()) if key in ("ux", "uy")
+                 else np.abs(ref[key]).max())
+        assert np.abs(got[key] - ref[key]).max() < tol * scale, key
+    b.close()

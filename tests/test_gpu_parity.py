@@ -561,25 +561,41 @@ def test_bad_arguments_are_rejected():
         small.set_params(prm(2, geometry="channel"))
 
 
-def test_full_size_channel_against_oracle():
-    """8000 x 800 thermal channel in the benchmark's FP32 launch configuration:
-    two fused steps compared with the oracle over every node."""
+@pytest.mark.parametrize("precision,steps,tol", [("fp32", 20, FP32_TOL), ("fp64", 10, FP64_TOL)])
+def test_full_size_channel_against_oracle(precision, steps, tol):
+    """8000 x 800 thermal channel in the benchmark's launch configuration (the default
+    two-level band plan, the interior path on every tile away from the open ends, one launch
+    per step): 20 FP32 or 10 FP64 fused steps compared with the oracle over every node, and
+    every step's diagnostics record (the 1742 tiles' fixed-point totals) against the
+    oracle's."""
+    import os
+
     L = lbm()
     nx, ny = 8000, 800
     p = prm(nx, geometry="channel", u_in=0.03, dTheat_R=0.08, heater_x0=1600, heater_len=40, heat_on_step=1,
             rho_out=5.95)
     Tc = oracle.Tc(p)
     fields = I.smooth_random(nx, ny, 5.95, 0.9 * Tc, seed=2009052643, drho=0.002, du=0.005, dT=0.002)
-    lat = L.Lattice(nx, ny, "fp32")
+    lat = L.Lattice(nx, ny, precision)
     lat.set_params(p)
+    t = lat.tiling
+    assert t["cols"] == 128 and t["tall_count"] > 0  # the two-level plan
+    assert lat.step_kernel == "interior" and lat.step_loop == "launches"
     lat.init_fields(*fields)
-    lat.step(2)
-    orc = oracle.Oracle(nx, ny, p)
+    orc = oracle.Oracle(nx, ny, p, threads=os.cpu_count() or 1)
     orc.init_fields(*fields)
-    assert orc.step(2) == 0
+    flux_scale = p["rho_out"] * p["u_in"] * ny  # the inflow once developed; early records are small sums
+    for _ in range(steps):
+        lat.step(1)
+        assert orc.step(1) == 0
+        d, od = lat.diagnostics(), orc.last_diag()
+        for k in ("mass", "energy"):
+            assert d[k] == pytest.approx(od[k], rel=tol), k
+        for k in ("flux_in", "flux_out"):
+            assert abs(d[k] - od[k]) < tol * flux_scale, k
     got, ref = lat.fields(), orc.fields()
     for k in ("rho", "ux", "uy", "T"):
-        assert rel_err(got, ref, k) < FP32_TOL, k
+        assert rel_err(got, ref, k) < tol, k
 
 
 def test_fields_into_caller_arrays():
