@@ -322,8 +322,14 @@ void build_tiles(int nx, int ny, int cols, const BandPlan& plan, std::vector<Til
     }
   };
   for (int b = 0; b < plan.tall_count; ++b) band(b * plan.tall_rows, (b + 1) * plan.tall_rows);
+  const size_t ntall = out.size();
   for (int y = plan.tall_count * plan.tall_rows; y < ny; y += plan.short_rows)
     band(y, std::min(ny, y + plan.short_rows));
+  // Longest tiles first: within each band class the tiles that take the general loop (the
+  // strips at the open ends or at a wrap, slower per row than the interior path) go before
+  // the interior ones, so that none of them is among the last tiles the launch dispatches.
+  std::stable_partition(out.begin(), out.begin() + ntall, general_tile);
+  std::stable_partition(out.begin() + ntall, out.end(), general_tile);
   for (size_t k = 0; k < out.size(); ++k) {
     out[k].local = (int)k;
     out[k].ntiles = (int)out.size();

@@ -134,6 +134,9 @@ lbm_status rebuild(lbm_batch* b) {
     for (int bd = 0; bd < plan.tall_count; ++bd) band(bd * plan.tall_rows, (bd + 1) * plan.tall_rows, tiles);
     for (int y = y_short; y < m.ny; y += plan.short_rows) band(y, std::min(m.ny, y + plan.short_rows), shorts);
   }
+  // longest tiles first within each class: the general-loop tiles before the interior ones
+  std::stable_partition(tiles.begin(), tiles.end(), general_tile);
+  std::stable_partition(shorts.begin(), shorts.end(), general_tile);
   tiles.insert(tiles.end(), shorts.begin(), shorts.end());
   if (insts.size() > b->cap_insts) {
     if (b->d_insts) cudaFree(b->d_insts);

@@ -120,6 +120,8 @@ struct Tile {
 inline int tile_is_interior(int geometry, int nx, int cols, int x0) {
   return (geometry == GEOM_CHANNEL || geometry == GEOM_WALLS) && x0 - 2 >= 1 && x0 + (cols - 8) + 1 <= nx - 2;
 }
+// Tiles that take the general loop (dispatched before the interior tiles of their class).
+inline bool general_tile(const Tile& t) { return !t.interior; }
 
 // Launchers (defined per precision).  Tiles must have been built for `cols`.
 // kernel: a resolved form (resolve_kernel): LBM_KERNEL_SCALAR, _INTERIOR, _PAIRED or _TMA.
