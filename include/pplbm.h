@@ -46,7 +46,10 @@ typedef enum {
   LBM_ETIMEOUT = 4,  /* a bounded device wait gave up */
   LBM_ECUDA = 5,     /* a CUDA runtime call failed (text in lbm_last_error) */
   LBM_EBUDGET = 6,   /* admission refused: device memory budget exceeded */
-  LBM_ESTATE = 7     /* call out of order (e.g. lbm_step before lbm_set_params) */
+  LBM_ESTATE = 7,    /* call out of order (e.g. lbm_step before lbm_set_params) */
+  LBM_EBOUNDS = 8    /* only from a library compiled with -DLBM_BOUNDS_CHECK (a test build): a
+                        kernel formed an element index outside the buffer it addresses; the
+                        access was skipped, so the lattice state is undefined */
 } lbm_status;
 
 typedef enum { LBM_FP32 = 0, LBM_FP64 = 1 } lbm_precision;

@@ -2,6 +2,9 @@
 
 The translation units are compiled in parallel and linked into
 ``paper_2009_05264_gb300/_lib/libpplbm.so`` (static CUDA runtime, C ABI only).
+``build(bounds_check=True)`` makes the test build with -DLBM_BOUNDS_CHECK in
+``paper_2009_05264_gb300/_lib_bounds/libpplbm.so``: every global access of the kernels
+checks its index against its buffer and a rejected access becomes LBM_EBOUNDS.
 """
 from __future__ import annotations
 
@@ -15,6 +18,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libpplbm.so")
+BOUNDS_DIR = os.path.join(PKG, "_lib_bounds")
+BOUNDS_LIB = os.path.join(BOUNDS_DIR, "libpplbm.so")
 SOURCES = ["lbm_api.cu", "lbm_batch.cu", "lbm_f32.cu", "lbm_f64.cu", "lbm_noalloc.cu", "lbm_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -33,26 +38,30 @@ def _inputs():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str | None = None) -> bool:
+    lib = lib or LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, bounds_check: bool = False) -> str:
+    out_dir, lib = (BOUNDS_DIR, BOUNDS_LIB) if bounds_check else (OUT_DIR, LIB)
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                     "-I", os.path.join(ROOT, "include"), "-I", CSRC]
     if ptxas_info:
         flags += ["-Xptxas", "-v"]
+    if bounds_check:
+        flags += ["-DLBM_BOUNDS_CHECK"]
     procs = []
     objs = []
     for src in SOURCES:
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
         objs.append(obj)
         cmd = [cc, "-c", os.path.join(CSRC, src), "-o", obj] + flags
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
@@ -65,12 +74,12 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             failed.append(src)
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     subprocess.check_call([cc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                bounds_check="--bounds-check" in sys.argv))

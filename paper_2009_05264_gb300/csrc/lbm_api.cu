@@ -760,6 +760,9 @@ lbm_status lbm_sync(lbm_ctx* c) {
   DeviceGuard g(c->device);
   lbm_status s = fetch_state(c);
   if (s != LBM_OK) return s;
+  if (c->h_state->status & STATUS_BOUNDS)
+    return fail(c, LBM_EBOUNDS, std::to_string(c->h_state->bounds_hits) +
+                                    " accesses outside their buffers were skipped (bounds-checked build)");
   if (c->h_state->status & STATUS_TIMEOUT)
     return fail(c, LBM_ETIMEOUT,
                 "a bounded device wait gave up (a bulk tensor copy of the TMA step, or the grid barrier between the "
@@ -1143,6 +1146,7 @@ const char* lbm_status_string(lbm_status s) {
     case LBM_ECUDA: return "CUDA error";
     case LBM_EBUDGET: return "memory budget exceeded";
     case LBM_ESTATE: return "call out of order";
+    case LBM_EBOUNDS: return "index outside its buffer (bounds-checked build)";
   }
   return "unknown status";
 }

@@ -32,7 +32,7 @@ constexpr int RING = 1024;  // diagnostics records kept per instance
 
 enum : int { GEOM_PERIODIC = 0, GEOM_CHANNEL = 1, GEOM_WALLS = 2, GEOM_POOL = 3 };
 enum : int { MODE_STEP = 0, MODE_FIELDS = 1, MODE_POPS = 2, MODE_MOMENTS = 3 };
-enum : unsigned { STATUS_UNSTABLE = 1u, STATUS_TIMEOUT = 2u };
+enum : unsigned { STATUS_UNSTABLE = 1u, STATUS_TIMEOUT = 2u, STATUS_BOUNDS = 4u };
 
 // Device-resident mutable state of one lattice instance.
 struct InstState {
@@ -40,7 +40,7 @@ struct InstState {
   int local_read;       // 1: buffer (step & 1) holds post-stream populations (after init/load)
   unsigned int counter; // tiles of the current launch that have posted their partials
   unsigned int status;  // sticky STATUS_* bits, cleared by the host
-  int pad0;
+  unsigned int bounds_hits;  // accesses a bounds-checked build rejected (STATUS_BOUNDS), else 0
   double rho_avg[2];    // domain-mean rho of step n in slot n & 1 (buoyancy of step n+1, Eq. 14)
   double p_probe[2];    // EOS pressure at (1, ny/2) and (nx-2, ny/2) of the current step
 };

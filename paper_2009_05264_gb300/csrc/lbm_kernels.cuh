@@ -76,6 +76,28 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
 __device__ __forceinline__ float ld_ro(const float* p) { return __ldg(p); }
 __device__ __forceinline__ double ld_ro(const double* p) { return __ldg(p); }
 
+// Bounds-checked build (compiled with -DLBM_BOUNDS_CHECK, for tests): before each global access
+// of the step and initialisation kernels, idx_ok checks the element index k against the n
+// elements of the buffer it addresses.  An index outside [0, n) sets STATUS_BOUNDS in the
+// instance's status word and counts the access in bounds_hits, and the caller skips the
+// access (a load reads 0, a store goes to a scratch word), so nothing faults or traps.  In the
+// default build idx_ok is the constant true and every check compiles away.
+#ifdef LBM_BOUNDS_CHECK
+__device__ inline bool idx_ok(InstState* st, long long k, long long n) {
+  if (k >= 0 && k < n) return true;
+  atomicOr(&st->status, STATUS_BOUNDS);
+  atomicAdd(&st->bounds_hits, 1u);
+  return false;
+}
+template <typename Real>
+__device__ inline Real& bounds_sink() {
+  __shared__ Real sink;  // where a rejected store goes
+  return sink;
+}
+#else
+__device__ __forceinline__ constexpr bool idx_ok(InstState*, long long, long long) { return true; }
+#endif
+
 // Reciprocal and reciprocal square root.  FP32: MUFU approximations (about 2 ulp).  FP64: the
 // PTX approximations rcp.approx / rsqrt.approx (about 23 correct bits) refined by two
 // Newton-Raphson steps on f(y) = 1/y - x and f(y) = 1/y^2 - x (each step squares the relative
@@ -250,6 +272,8 @@ __device__ __forceinline__ void boundary_fill(Real (&fc)[9], Real (&gc)[9], cons
                                               int pitch, int node, int xn, bool perx, long long step) {
   const Real rho_ref = C.rho_ref;
   const Real dT_in = C.dT_in;
+  // element k of the g buffer (0 outside it, in a bounds-checked build)
+  auto gload = [&](int k) { return idx_ok(I.st, k, 9LL * plane) ? ld_ro(Gin + k) : Real(0); };
   if (THERMAL && (nb.wlo || nb.whi)) {
     // anti-bounce-back at the wall temperature (the heater heats the bottom wall
     // once the boundary condition of step heat_on_step has been applied)
@@ -288,9 +312,9 @@ __device__ __forceinline__ void boundary_fill(Real (&fc)[9], Real (&gc)[9], cons
     }
     if (THERMAL) {
       // anti-bounce-back at the inlet temperature
-      if (!nb.wlo) gc[5] = -ld_ro(Gin + 7 * plane + node) + Real(2) * lat_w<Real>(5) * dT_in;
-      if (!nb.whi) gc[8] = -ld_ro(Gin + 6 * plane + node) + Real(2) * lat_w<Real>(8) * dT_in;
-      gc[1] = -ld_ro(Gin + 3 * plane + node) + Real(2) * lat_w<Real>(1) * dT_in;
+      if (!nb.wlo) gc[5] = -gload(7 * plane + node) + Real(2) * lat_w<Real>(5) * dT_in;
+      if (!nb.whi) gc[8] = -gload(6 * plane + node) + Real(2) * lat_w<Real>(8) * dT_in;
+      gc[1] = -gload(3 * plane + node) + Real(2) * lat_w<Real>(1) * dT_in;
     }
   }
   if (nb.outl) {
@@ -322,9 +346,9 @@ __device__ __forceinline__ void boundary_fill(Real (&fc)[9], Real (&gc)[9], cons
           const int sx = xu - cxi;
           const Real dTw = (cyi == 1 && heat_bc && sx >= I.heater_x0 && sx < I.heater_x0 + I.heater_len)
                                ? C.dT_heat : dT_in;
-          gc[i] = -ld_ro(Gin + lat_opp(i) * plane + node - 1) + Real(2) * lat_w<Real>(i) * dTw;
+          gc[i] = -gload(lat_opp(i) * plane + node - 1) + Real(2) * lat_w<Real>(i) * dTw;
         } else {
-          gc[i] = ld_ro(Gin + i * plane + node - 1 - cyi * pitch - cxi);
+          gc[i] = gload(i * plane + node - 1 - cyi * pitch - cxi);
         }
       }
     }
@@ -344,7 +368,7 @@ __device__ __forceinline__ void boundary_fill(Real (&fc)[9], Real (&gc)[9], cons
       for (int i = 0; i < 9; ++i) {
         int sx = xn - lat_cx(i);
         if (perx) sx = wrap_index(sx, I.nx);
-        gc[i] = ld_ro(Gin + i * plane + (node - pitch) - xn + sx - lat_cy(i) * pitch);
+        gc[i] = gload(i * plane + (node - pitch) - xn + sx - lat_cy(i) * pitch);
       }
     }
   }
@@ -526,6 +550,31 @@ struct PlaneOut {
   int plane;
   __device__ __forceinline__ Real& operator()(int i) const { return p[i * plane]; }
 };
+#ifdef LBM_BOUNDS_CHECK
+// PlaneOut of the bounds-checked build: element m + i * plane of a buffer of n elements.
+template <typename Real>
+struct CheckedPlaneOut {
+  Real* base;
+  int m, plane;
+  InstState* st;
+  long long n;
+  __device__ __forceinline__ Real& operator()(int i) const {
+    const long long k = (long long)m + (long long)i * plane;
+    return idx_ok(st, k, n) ? base[k] : bounds_sink<Real>();
+  }
+};
+#endif
+// Output view of node m (element index in plane 0) of a 9-plane buffer `base` of n elements.
+template <typename Real>
+__device__ __forceinline__ auto plane_out(Real* base, int m, int plane, InstState* st, long long n) {
+#ifdef LBM_BOUNDS_CHECK
+  return CheckedPlaneOut<Real>{base, m, plane, st, n};
+#else
+  (void)st;
+  (void)n;
+  return PlaneOut<Real>{base + m, plane};
+#endif
+}
 // The same through the descriptor's plane offsets: base[m + poff[i]], m the node's element
 // index (one add per population, the offsets read from the descriptor).
 template <typename Real>
@@ -533,7 +582,14 @@ struct OffsetOut {
   Real* base;
   int m;
   const Inst& I;
-  __device__ __forceinline__ Real& operator()(int i) const { return base[m + I.poff[i]]; }
+  __device__ __forceinline__ Real& operator()(int i) const {
+#ifdef LBM_BOUNDS_CHECK
+    const int k = m + I.poff[i];
+    return idx_ok(I.st, k, 9 * I.plane) ? base[k] : bounds_sink<Real>();
+#else
+    return base[m + I.poff[i]];
+#endif
+  }
 };
 
 // BGK toward f^eq(rho, u_eq) (Eqs. 2-3) plus the exact-difference term (Eq. 5),
@@ -657,11 +713,14 @@ __device__ __forceinline__ void collide_g_paired(const Pops& gs, const Out& go, 
 template <typename Real, bool THERMAL>
 __device__ __forceinline__ void pull_node(Real* f_dst, Real* g_dst, int dstride, const Real* __restrict__ Fin,
                                           const Real* __restrict__ Gin, int plane, int pitch, int xn, int rn,
-                                          int nx, int ny, bool perx, bool pery, bool local, const NodeBC& nb) {
+                                          int nx, int ny, bool perx, bool pery, bool local, const NodeBC& nb,
+                                          InstState* bst) {
   const int node = rn * pitch + xn;
+  const long long nbuf = 9LL * plane;  // elements of one population buffer (bounds checks)
   if (local) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
+      if (!idx_ok(bst, node + i * plane, nbuf)) continue;
       cp_async_elem(f_dst + i * dstride, Fin + node + i * plane);
       if (THERMAL) cp_async_elem(g_dst + i * dstride, Gin + node + i * plane);
     }
@@ -674,6 +733,7 @@ __device__ __forceinline__ void pull_node(Real* f_dst, Real* g_dst, int dstride,
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const int off = i * plane - lat_cy(i) * pitch - lat_cx(i);
+      if (!idx_ok(bst, node + off, nbuf)) continue;
       cp_async_elem(f_dst + i * dstride, fn + off);
       if (THERMAL) cp_async_elem(g_dst + i * dstride, gn + off);
     }
@@ -703,6 +763,7 @@ __device__ __forceinline__ void pull_node(Real* f_dst, Real* g_dst, int dstride,
     } else {
       continue;
     }
+    if (!idx_ok(bst, pl * plane + src, nbuf)) continue;
     cp_async_elem(f_dst + i * dstride, Fin + pl * plane + src);
     if (THERMAL) cp_async_elem(g_dst + i * dstride, Gin + pl * plane + src);
   }
@@ -867,10 +928,12 @@ __device__ __forceinline__ void interior_rows(const Inst& I, const KConst<Real>&
       Real* fd = sF + fslot * 9 * NS + s;
       Real* gd = sG + gslot * 9 * NS + s;
       const int node = rr * pitch + xn;
+      const long long nbuf = 9LL * I.plane;  // elements of one population buffer (bounds checks)
       if (local) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
           const int src = node + I.poff[i];
+          if (!idx_ok(I.st, src, nbuf)) continue;
           cp_async_elem(fd + i * NS, Fin + src);
           if (THERMAL) cp_async_elem(gd + i * NS, Gin + src);
         }
@@ -878,6 +941,7 @@ __device__ __forceinline__ void interior_rows(const Inst& I, const KConst<Real>&
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
           const int src = node + I.loff[i];
+          if (!idx_ok(I.st, src, nbuf)) continue;
           cp_async_elem(fd + i * NS, Fin + src);
           if (THERMAL) cp_async_elem(gd + i * NS, Gin + src);
         }
@@ -888,6 +952,7 @@ __device__ __forceinline__ void interior_rows(const Inst& I, const KConst<Real>&
           const int cyi = lat_cy(i);
           const bool wall = (cyi == 1 && lo) || (cyi == -1 && hi);
           const int src = wall ? node + I.poff[lat_opp(i)] : node + I.loff[i];
+          if (!idx_ok(I.st, src, nbuf)) continue;
           cp_async_elem(fd + i * NS, Fin + src);
           if (THERMAL) cp_async_elem(gd + i * NS, Gin + src);
         }
@@ -1165,7 +1230,7 @@ __device__ __forceinline__ void fused_tile(const Inst* __restrict__ insts, const
         const int rn = pery ? wrap_index(r, ny) : r;
         const NodeBC nb{!pery && rn == 0, !pery && !pool && rn == ny - 1, inl, outl, pool && rn == ny - 1};
         pull_node<Real, THERMAL>(sF + fslot * 9 * NS + s, sG + gslot * 9 * NS + s, NS, Fin, Gin, plane, pitch, xn,
-                                 rn, nx, ny, perx, pery, local, nb);
+                                 rn, nx, ny, perx, pery, local, nb, I.st);
       }
     }
     cp_async_commit();
@@ -1226,9 +1291,12 @@ __device__ __forceinline__ void fused_tile(const Inst* __restrict__ insts, const
       if (hazi && out_col && out_row) {
         // temporal density gradient rho^n - rho^(n-1), both as deviations from rho_ref; this
         // thread owns the node's history (read, then overwritten with rho^n)
-        Real* rp = rho_prev + (rn * pitch + xn);
-        if (MODE == MODE_STEP) ns.hmc = hmc * (ns.drho - *rp);
-        if (MODE == MODE_STEP || MODE == MODE_MOMENTS) *rp = ns.drho;
+        const int kp = rn * pitch + xn;
+        if (idx_ok(I.st, kp, I.plane)) {
+          Real* rp = rho_prev + kp;
+          if (MODE == MODE_STEP) ns.hmc = hmc * (ns.drho - *rp);
+          if (MODE == MODE_STEP || MODE == MODE_MOMENTS) *rp = ns.drho;
+        }
       }
       if ((MODE == MODE_STEP || MODE == MODE_MOMENTS) && out_col && out_row) {
         acc_m += ns.drho;
@@ -1254,6 +1322,7 @@ __device__ __forceinline__ void fused_tile(const Inst* __restrict__ insts, const
         const int oo = rn * pitch + xn;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
+          if (!idx_ok(I.st, i * plane + oo, 9LL * plane)) continue;
           Fout[i * plane + oo] = fc[i];
           if (THERMAL) Gout[i * plane + oo] = gc[i];
         }
@@ -1293,7 +1362,7 @@ __device__ __forceinline__ void fused_tile(const Inst* __restrict__ insts, const
       sUy[f_prev * NS + s] = uay;
       const bool out_q = out_col && q >= tile.y0 && q < tile.y1;
       if (MODE == MODE_STEP && out_q) {
-        collide_f<Real>(StridedPops<Real>{sF + f_prev * 9 * NS + s, NS}, PlaneOut<Real>{Fout + (q * pitch + xn), plane},
+        collide_f<Real>(StridedPops<Real>{sF + f_prev * 9 * NS + s, NS}, plane_out(Fout, q * pitch + xn, plane, I.st, 9LL * plane),
                         rho_p, drho_p, ux_p, uy_p, dux, duy, sC.omega_f);
         if (channel && xn == 0) acc_fi += rho_p * uax;
         if (channel && xn == nx - 1) acc_fo += rho_p * uax;
@@ -1302,10 +1371,12 @@ __device__ __forceinline__ void fused_tile(const Inst* __restrict__ insts, const
         double* out = static_cast<double*>(I.f[(step + 1) & 1]);
         const long long n = (long long)nx * ny;
         const long long oo = (long long)q * nx + xn;
-        out[oo] = (double)rho_p;
-        out[n + oo] = (double)uax;
-        out[2 * n + oo] = (double)uay;
-        out[3 * n + oo] = (double)T_p;
+        if (idx_ok(I.st, oo, n) && idx_ok(I.st, 3 * n + oo, 9LL * plane * (long long)sizeof(Real) / 8)) {
+          out[oo] = (double)rho_p;
+          out[n + oo] = (double)uax;
+          out[2 * n + oo] = (double)uay;
+          out[3 * n + oo] = (double)T_p;
+        }
       }
     }
     __syncthreads();
@@ -1329,7 +1400,7 @@ __device__ __forceinline__ void fused_tile(const Inst* __restrict__ insts, const
         const Real divu = Real(0.5) * (uxE - uxW) + dyu;
         Real phi = coef_p2 * divu;
         if (hazi) phi += hm_p2;
-        collide_g<Real>(StridedPops<Real>{sG + g_prev2 * 9 * NS + s, NS}, PlaneOut<Real>{Gout + (q2 * pitch + xn), plane},
+        collide_g<Real>(StridedPops<Real>{sG + g_prev2 * 9 * NS + s, NS}, plane_out(Gout, q2 * pitch + xn, plane, I.st, 9LL * plane),
                         T_p2, dT_p2, sUx[f_prev2 * NS + s], sUy[f_prev2 * NS + s], phi, sC.omega_g);
       }
     }
@@ -1588,6 +1659,7 @@ __device__ __forceinline__ void write_equilibrium(const Inst& I, long long node,
   // The reference parts are taken off in FP64; the rest is computed in the storage
   // precision (FP32 storage keeps FP32 rounding of the deviations either way, and FP64
   // arithmetic is scarce on this GPU).
+  if (!idx_ok(I.st, node, I.plane)) return;  // node of plane 0: every plane's element is then in its buffer
   Real* F = static_cast<Real*>(I.f[0]);
   Real* Gb = static_cast<Real*>(I.g[0]);
   const Real drho = Real(rho - I.rho_ref), dT = Real(T - I.T_ref);

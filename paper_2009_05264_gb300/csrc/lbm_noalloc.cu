@@ -135,5 +135,6 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, int32_t nx, int32_t 
       cudaStreamSynchronize(s) != cudaSuccess)
     return LBM_ECUDA;
   if (diag_out) std::memcpy(diag_out, rec, sizeof(rec));
+  if (out.status & STATUS_BOUNDS) return LBM_EBOUNDS;
   return (out.status & STATUS_UNSTABLE) ? LBM_EUNSTABLE : LBM_OK;
 }

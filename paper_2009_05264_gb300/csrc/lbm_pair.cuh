@@ -210,13 +210,16 @@ __device__ __forceinline__ void cp_async_pair(float2* smem, const float* gmem) {
 template <bool THERMAL>
 __device__ __forceinline__ void pair_pull(float2* f_dst, float2* g_dst, int stride, const float* __restrict__ Fin,
                                           const float* __restrict__ Gin, int plane, int pitch, int x, int rn, int nx,
-                                          int ny, bool perx, bool pery, bool local, bool wlo, bool whi, bool top) {
+                                          int ny, bool perx, bool pery, bool local, bool wlo, bool whi, bool top,
+                                          InstState* bst) {
+  const long long nbuf = 9LL * plane;  // elements of one population buffer (bounds checks)
   const bool interior = !local && x >= 1 && x + 2 <= nx - 1 && rn >= 1 && rn <= ny - 2;
   if (interior) {
     const int node = rn * pitch + x;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const int off = node + i * plane - lat_cy(i) * pitch - lat_cx(i);
+      if (!idx_ok(bst, off, nbuf) || !idx_ok(bst, off + 1, nbuf)) continue;
       if (lat_cx(i) == 0) {
         cp_async_pair(f_dst + i * stride, Fin + off);
         if (THERMAL) cp_async_pair(g_dst + i * stride, Gin + off);
@@ -253,6 +256,7 @@ __device__ __forceinline__ void pair_pull(float2* f_dst, float2* g_dst, int stri
         if (sx < 0 || sx >= nx || (top && cyi == -1)) continue;  // unknown link at an open end
         src = sy * pitch + sx;
       }
+      if (!idx_ok(bst, pl * plane + src, nbuf)) continue;
       cp_async_elem(reinterpret_cast<float*>(f_dst + i * stride) + lane, Fin + pl * plane + src);
       if (THERMAL) cp_async_elem(reinterpret_cast<float*>(g_dst + i * stride) + lane, Gin + pl * plane + src);
     }
@@ -338,7 +342,7 @@ lbm_pair_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) 
         const int rn = pery ? wrap_index(r, ny) : r;
         pair_pull<THERMAL>(sF + fslot * 9 * B + t, sG + gslot * 9 * B + t, B, Fin, Gin, plane, pitch, xa, rn, nx, ny,
                            perx, pery, local, !pery && rn == 0, !pery && !pool && rn == ny - 1,
-                           pool && rn == ny - 1);
+                           pool && rn == ny - 1, st);
       }
     }
     cp_async_commit();
@@ -481,7 +485,10 @@ lbm_pair_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) 
         float2 fsv[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) fsv[i] = fsp[i * B];
-        pair_collide_f(fsv, Fout + (q * pitch + xa), plane, out1, rho_p, drho_p, ux_p, uy_p, dux, duy, sC.omega_f);
+        // the nine stores go to q * pitch + xa + i * plane (+ 1 for the second node): checking the
+        // first and the last covers them all in a bounds-checked build
+        if (idx_ok(st, q * pitch + xa, 9LL * plane) && idx_ok(st, q * pitch + xa + 8LL * plane + out1, 9LL * plane))
+          pair_collide_f(fsv, Fout + (q * pitch + xa), plane, out1, rho_p, drho_p, ux_p, uy_p, dux, duy, sC.omega_f);
         if (edge) {
           if (xn0 == 0) acc_fi += rho_p.x * uax.x;
           if (xn0 == nx - 1) acc_fo += rho_p.x * uax.x;
@@ -509,8 +516,9 @@ lbm_pair_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) 
 #pragma unroll
         for (int i = 0; i < 9; ++i) gsv[i] = gsp[i * B];
         const float2 uax = *reinterpret_cast<const float2*>(Ux + c0);
-        pair_collide_g(gsv, Gout + (q2 * pitch + xa), plane, out1, T_p2, dT_p2, uax, uyC, p_mul(coef_p2, divu),
-                       sC.omega_g);
+        if (idx_ok(st, q2 * pitch + xa, 9LL * plane) && idx_ok(st, q2 * pitch + xa + 8LL * plane + out1, 9LL * plane))
+          pair_collide_g(gsv, Gout + (q2 * pitch + xa), plane, out1, T_p2, dT_p2, uax, uyC, p_mul(coef_p2, divu),
+                         sC.omega_g);
       }
     }
 

@@ -127,13 +127,16 @@ struct ShiftedPops {
 template <bool THERMAL>
 __device__ __forceinline__ void pull_direct(float (&fc)[9], float (&gc)[9], const float* __restrict__ Fin,
                                             const float* __restrict__ Gin, int plane, int pitch, int xn, int rn,
-                                            int nx, int ny, bool perx, bool pery, bool local, const NodeBC& nb) {
+                                            int nx, int ny, bool perx, bool pery, bool local, const NodeBC& nb,
+                                            InstState* bst) {
   const int node = rn * pitch + xn;
+  const long long nbuf = 9LL * plane;  // elements of one population buffer (bounds checks)
   if (local) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      fc[i] = ld_ro(Fin + i * plane + node);
-      gc[i] = THERMAL ? ld_ro(Gin + i * plane + node) : 0.0f;
+      const bool ok = idx_ok(bst, i * plane + node, nbuf);
+      fc[i] = ok ? ld_ro(Fin + i * plane + node) : 0.0f;
+      gc[i] = THERMAL && ok ? ld_ro(Gin + i * plane + node) : 0.0f;
     }
     return;
   }
@@ -160,6 +163,7 @@ __device__ __forceinline__ void pull_direct(float (&fc)[9], float (&gc)[9], cons
       src = (cyi == 1 ? rm : (cyi == -1 ? rp : rn)) * pitch + (cxi == 1 ? xm : (cxi == -1 ? xp : xn));
       pl = i;
     }
+    if (!idx_ok(bst, pl * plane + src, nbuf)) continue;
     fc[i] = ld_ro(Fin + pl * plane + src);
     if (THERMAL) gc[i] = ld_ro(Gin + pl * plane + src);
   }
@@ -314,7 +318,7 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, u
         }
       } else {
         const NodeBC nb{!pery && rn == 0, !pery && rn == ny - 1, inl, outl, false};
-        pull_direct<THERMAL>(fc, gc, Fin, Gin, plane, pitch, xn, rn, nx, ny, perx, pery, local, nb);
+        pull_direct<THERMAL>(fc, gc, Fin, Gin, plane, pitch, xn, rn, nx, ny, perx, pery, local, nb, I.st);
         if (!local && (nb.wlo || nb.whi || inl || outl))
           boundary_fill<float, THERMAL>(fc, gc, nb, I, C, Gin, plane, pitch, rn * pitch + xn, xn, perx, step);
 #pragma unroll
@@ -364,7 +368,7 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, u
       sUx[p_prev * NS + s] = uax;
       sUy[p_prev * NS + s] = uay;
       if (out_col && q >= tile.y0 && q < tile.y1) {
-        collide_f<float>(ShiftedPops{sF + f_prev * ST_RW + (s + 2)}, PlaneOut<float>{Fout + (q * pitch + xn), plane},
+        collide_f<float>(ShiftedPops{sF + f_prev * ST_RW + (s + 2)}, plane_out(Fout, q * pitch + xn, plane, I.st, 9LL * plane),
                          rho_p, drho_p, ux_p, uy_p, dux, duy, C.omega_f);
         if (channel && xn == 0) acc_fi += rho_p * uax;
         if (channel && xn == nx - 1) acc_fo += rho_p * uax;
@@ -386,7 +390,7 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, u
           dyu = (wall_lo && wall_hi) ? 0.0f : (wall_lo ? uyN - uyC : uyC - uyS);
         }
         const float divu = 0.5f * (uxE - uxW) + dyu;
-        collide_g<float>(ShiftedPops{sG + g_prev2 * ST_RW + (s + 2)}, PlaneOut<float>{Gout + (q2 * pitch + xn), plane},
+        collide_g<float>(ShiftedPops{sG + g_prev2 * ST_RW + (s + 2)}, plane_out(Gout, q2 * pitch + xn, plane, I.st, 9LL * plane),
                          T_p2, dT_p2, sUx[p_prev2 * NS + s], sUy[p_prev2 * NS + s], coef_p2 * divu, C.omega_g);
       }
     }

@@ -20,7 +20,7 @@ from .params import GEOMETRY, resolve
 _lib = None
 
 STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_EUNSTABLE", 4: "LBM_ETIMEOUT",
-          5: "LBM_ECUDA", 6: "LBM_EBUDGET", 7: "LBM_ESTATE"}
+          5: "LBM_ECUDA", 6: "LBM_EBUDGET", 7: "LBM_ESTATE", 8: "LBM_EBOUNDS"}
 FP32, FP64 = 0, 1
 DIAG_NAMES = ("step", "mass", "energy", "rho_avg", "dp", "dtstar", "flux_in", "flux_out", "vapor_area",
               "wall_vapor", "heater_vapor", "zone_vapor")
@@ -76,16 +76,19 @@ def library_path() -> str:
     return _build.LIB
 
 
-def load(build_if_missing: bool = True):
-    """Load libpplbm.so (building it with nvcc first if needed)."""
+def load(build_if_missing: bool = True, path: str | None = None):
+    """Load libpplbm.so (building it with nvcc first if needed).  `path` loads another build
+    of the same library instead (the bounds-checked test build); the first load of a process
+    fixes the library for the rest of it."""
     global _lib
     if _lib is not None:
         return _lib
-    if build_if_missing:
+    lib = path or _build.LIB
+    if build_if_missing and path is None:
         _build.build()
-    if not os.path.exists(_build.LIB):
-        raise RuntimeError(f"CUDA library not built: {_build.LIB}")
-    L = ctypes.CDLL(_build.LIB)
+    if not os.path.exists(lib):
+        raise RuntimeError(f"CUDA library not built: {lib}")
+    L = ctypes.CDLL(lib)
     vp, i32, i64, sz, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)
     P = ctypes.POINTER(LbmParams)
     sig = {
