@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 1
+#define LBM_ABI_VERSION 2
 
 typedef struct lbm_ctx lbm_ctx;
 typedef struct lbm_batch lbm_batch;
@@ -286,21 +286,33 @@ int32_t lbm_step_kernel(const lbm_ctx* ctx);
  * the paper's time loop, Sec. 2 and Fig. 2, is the same either way).
  *   LBM_LOOP_LAUNCHES: one step-kernel launch per step.
  *   LBM_LOOP_PERSISTENT: one cooperative launch per call advances all nsteps steps (nsteps >= 2;
- *     a single step is one launch); its CTAs draw the tiles of each step from a counter and
- *     meet at a grid-wide barrier between steps.  Every barrier wait is bounded: a CTA that
- *     waits longer than 5 s (or than the poll limit of lbm_set_wait_limit) gives up, the
- *     launch ends, and the next lbm_sync returns LBM_ETIMEOUT; the lattice state is then
- *     undefined until it is initialised again (lbm_set_params, lbm_init_fields,
- *     lbm_set_populations or lbm_load_state), and the CUDA context stays usable.  Only the
- *     one-column step forms (LBM_KERNEL_SCALAR, LBM_KERNEL_INTERIOR) have a persistent form.
+ *     a single step is one launch).  Where the step tiling fits in one wave, each CTA keeps
+ *     its tile and the CTAs meet at a grid-wide barrier between steps.  Where it needs more
+ *     CTAs than are resident, and the geometry is a channel, walls or periodic box, the
+ *     launch overlaps consecutive steps (reported as LBM_LOOP_OVERLAPPED): the CTAs draw
+ *     (step, tile) tickets in order, and a tile starts as soon as the tiles around it (the
+ *     rows and columns its pulls read) have finished the previous step, the step before that
+ *     is complete, and the inlet and outlet tiles of the previous step have posted the mass
+ *     that crossed the open ends; its
+ *     buoyancy mean (Eq. 14) is the mean density two steps back plus that mass over the
+ *     nodes, which is the previous step's mean up to the rounding of one collision.  Otherwise
+ *     (the pool geometry) the CTAs draw each step's tiles from a counter and meet at a
+ *     barrier between steps.  Every wait is bounded: a CTA that waits longer than 5 s (or
+ *     than the poll limit of lbm_set_wait_limit) gives up, the launch ends, and the next
+ *     lbm_sync returns LBM_ETIMEOUT; the lattice state is then undefined until it is
+ *     initialised again (lbm_set_params, lbm_init_fields, lbm_set_populations or
+ *     lbm_load_state), and the CUDA context stays usable.  Only the one-column step forms
+ *     (LBM_KERNEL_SCALAR, LBM_KERNEL_INTERIOR) have a persistent form.
  *   LBM_LOOP_AUTO (default): persistent where the step tiling fits in one wave of the
  *     persistent kernel (small lattices, whose steps are short enough for the launch gap and
- *     the kernel boundary to count), else one launch per step.
- * Results are the same either way up to the rounding of separately compiled kernels.
- * LBM_EINVAL for other values. */
-enum { LBM_LOOP_AUTO = 0, LBM_LOOP_LAUNCHES = 1, LBM_LOOP_PERSISTENT = 2 };
+ *     the kernel boundary to count) or where it takes at least two and a half waves and the
+ *     launch can overlap the steps, else one launch per step.
+ * Results are the same either way up to the rounding of separately compiled kernels (and,
+ * overlapped, of one collision in the buoyancy mean).  LBM_EINVAL for other values. */
+enum { LBM_LOOP_AUTO = 0, LBM_LOOP_LAUNCHES = 1, LBM_LOOP_PERSISTENT = 2, LBM_LOOP_OVERLAPPED = 3 };
 lbm_status lbm_set_step_loop(lbm_ctx* ctx, int32_t loop);
-/* The loop (LBM_LOOP_LAUNCHES or _PERSISTENT) a multi-step call takes now; -1 if ctx is NULL. */
+/* The loop a multi-step call takes now: LBM_LOOP_LAUNCHES, _PERSISTENT (a barrier between
+ * steps) or _OVERLAPPED (a persistent launch that overlaps the steps); -1 if ctx is NULL. */
 int32_t lbm_step_loop(lbm_ctx* ctx);
 /* Poll limit of the step's bounded device waits: the persistent launch's grid-barrier waits
  * (default: 5 s of polling) and the TMA form's waits for its staged rows (default: 2^22

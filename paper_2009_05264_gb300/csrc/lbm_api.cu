@@ -25,19 +25,19 @@ cudaError_t launch_init_builtin_f32(const Inst*, int, int, InitSpec, cudaStream_
 cudaError_t launch_init_builtin_f64(const Inst*, int, int, InitSpec, cudaStream_t);
 
 cudaError_t launch_persistent_f32(int, int, int, bool, const Inst*, const Tile*, int, int, GridBar*, unsigned,
-                                  cudaStream_t, const Inst*);
+                                  cudaStream_t, const Inst*, const FlowPlan&);
 cudaError_t launch_persistent_f64(int, int, int, bool, const Inst*, const Tile*, int, int, GridBar*, unsigned,
-                                  cudaStream_t, const Inst*);
+                                  cudaStream_t, const Inst*, const FlowPlan&);
 int persistent_resident_f32(int, int, int, bool, bool);
 int persistent_resident_f64(int, int, int, bool, bool);
 
 cudaError_t launch_persistent(int fp64, int thermal, int cols, int kernel, bool full, const Inst* d_inst,
                               const Tile* d_tiles, int ntiles, int nsteps, GridBar* bar, unsigned max_polls,
-                              cudaStream_t s, const Inst* h_inst) {
+                              cudaStream_t s, const Inst* h_inst, const FlowPlan& flow) {
   return fp64 ? launch_persistent_f64(thermal, cols, kernel, full, d_inst, d_tiles, ntiles, nsteps, bar, max_polls, s,
-                                      h_inst)
+                                      h_inst, flow)
               : launch_persistent_f32(thermal, cols, kernel, full, d_inst, d_tiles, ntiles, nsteps, bar, max_polls, s,
-                                      h_inst);
+                                      h_inst, flow);
 }
 
 long long persistent_slots(int fp64, int thermal, int cols, int kernel, bool full, bool single) {
@@ -272,7 +272,7 @@ struct Layout {
   long long plane;
   size_t pop_bytes;  // one 9-plane buffer
   int max_tiles;
-  size_t off_f[2], off_g[2], off_rho_prev, off_tmaps, off_inst, off_state, off_sums, off_bar, off_ring,
+  size_t off_f[2], off_g[2], off_rho_prev, off_tmaps, off_inst, off_state, off_sums, off_bar, off_cells, off_ring,
       off_tiles_step, off_tiles_aux, total;
 };
 
@@ -292,8 +292,9 @@ Layout make_layout(int nx, int ny, lbm_precision prec) {
   L.off_tmaps = off; off += align_up(4 * sizeof(CUtensorMap));
   L.off_inst = off; off += align_up(sizeof(Inst));
   L.off_state = off; off += align_up(sizeof(InstState));
-  L.off_sums = off; off += align_up(NPART * sizeof(unsigned long long));
+  L.off_sums = off; off += align_up(2 * NPART * sizeof(unsigned long long));  // two steps' totals
   L.off_bar = off; off += align_up(sizeof(GridBar));
+  L.off_cells = off; off += align_up((size_t)L.max_tiles * sizeof(unsigned long long));  // overlapped loop
   L.off_ring = off; off += align_up((size_t)RING * NDIAG * sizeof(double));
   L.off_tiles_step = off; off += align_up((size_t)L.max_tiles * sizeof(Tile));
   L.off_tiles_aux = off; off += align_up((size_t)L.max_tiles * sizeof(Tile));
@@ -318,18 +319,19 @@ void build_tiles(int nx, int ny, int cols, const BandPlan& plan, std::vector<Til
       t.y0 = y0;
       t.y1 = y1;
       t.interior = tile_is_interior(geometry, nx, cols, t.x0);
+      t.open_end = geometry == GEOM_CHANNEL && (t.x0 == 0 || t.x0 + w >= nx);
       out.push_back(t);
     }
   };
   for (int b = 0; b < plan.tall_count; ++b) band(b * plan.tall_rows, (b + 1) * plan.tall_rows);
-  const size_t ntall = out.size();
   for (int y = plan.tall_count * plan.tall_rows; y < ny; y += plan.short_rows)
     band(y, std::min(ny, y + plan.short_rows));
-  // Longest tiles first: within each band class the tiles that take the general loop (the
-  // strips at the open ends or at a wrap, slower per row than the interior path) go before
-  // the interior ones, so that none of them is among the last tiles the launch dispatches.
-  std::stable_partition(out.begin(), out.begin() + ntall, general_tile);
-  std::stable_partition(out.begin() + ntall, out.end(), general_tile);
+  // The tiles that take the general loop (the strips at the open ends or at a wrap, slower per
+  // row than the interior path) first, tall bands before short ones, then the interior tiles
+  // of the tall and the short bands: none of the slow tiles is among the last a launch
+  // dispatches, and in the overlapped persistent loop the inlet and outlet tiles, whose mass
+  // balance every tile of the next step waits for, finish early in their step.
+  std::stable_partition(out.begin(), out.end(), general_tile);
   for (size_t k = 0; k < out.size(); ++k) {
     out[k].local = (int)k;
     out[k].ntiles = (int)out.size();
@@ -390,6 +392,7 @@ struct lbm_ctx {
   BandPlan plan{0, 0, 16};  // the step tiling's bands
   bool rows_default = true;  // band height chosen by default_band_rows (re-chosen on changes)
   int ntiles_step = 0, ntiles_aux = 0;
+  int nopen_step = 0;  // step tiles with an open end (inlet or outlet columns)
   Tile* d_tiles_step = nullptr;
   Tile* d_tiles_aux = nullptr;
   lbm_params params{};
@@ -397,6 +400,7 @@ struct lbm_ctx {
   int thermal = 0;
   long long launches = 0;
   long long step_host = 0;  // step count as last synchronised
+  long long step_next = 0;  // step of the next step launch (enqueued steps included)
   unsigned long long params_gen = 0;  // bumped whenever the descriptor changes
   int kernel = LBM_KERNEL_AUTO;        // requested step kernel form (resolve_kernel picks the one launched)
   int loop = LBM_LOOP_AUTO;            // requested step loop (one launch per step or persistent)
@@ -439,7 +443,7 @@ size_t elt_size(const lbm_ctx* c) { return c->prec == LBM_FP64 ? 8 : 4; }
 // and zero totals of the partial sums (a launch that gave up waiting may have left some).
 lbm_status upload_state(lbm_ctx* c) {
   LBM_CUDA(c, cudaMemcpyAsync(c->d_state, c->h_state, sizeof(InstState), cudaMemcpyHostToDevice, c->stream));
-  LBM_CUDA(c, cudaMemsetAsync(c->base + c->L.off_sums, 0, NPART * sizeof(unsigned long long), c->stream));
+  LBM_CUDA(c, cudaMemsetAsync(c->base + c->L.off_sums, 0, 2 * NPART * sizeof(unsigned long long), c->stream));
   return LBM_OK;
 }
 
@@ -461,6 +465,7 @@ lbm_status set_tiling(lbm_ctx* c, int cols, const BandPlan& plan) {
   c->rows = plan.short_rows;
   c->plan = plan;
   c->ntiles_step = (int)t.size();
+  c->nopen_step = (int)std::count_if(t.begin(), t.end(), [](const Tile& x) { return x.open_end != 0; });
   return LBM_OK;
 }
 
@@ -478,10 +483,27 @@ lbm_status retile_default(lbm_ctx* c, int cols) {
   return s;
 }
 
+// Whether a persistent launch of this context may overlap consecutive steps (FlowPlan): the
+// channel, walls and periodic geometries (the mass through the pool's open top is not
+// accounted), with distinct inlet and outlet columns.
+bool flow_eligible(const lbm_ctx* c) {
+  return c->have_params && c->params.geometry != LBM_GEOM_POOL && c->nx >= 3;
+}
+
+// Whether a persistent launch of the current tiling overlaps the steps: more tiles than CTAs.
+bool overlapped(lbm_ctx* c) {
+  if (!flow_eligible(c)) return false;
+  const long long slots = persistent_slots(c->prec == LBM_FP64, c->thermal, c->cols, step_kernel(c, c->cols),
+                                           needs_full_step(c->hinst), true);
+  return c->ntiles_step > slots;
+}
+
 // Whether lbm_step_async takes the persistent launch: requested, or (LBM_LOOP_AUTO) when the
 // step tiling is one wave of the persistent kernel, where a step's launch gap and kernel
-// boundary are a large part of it.  Only the one-column kernel (general or interior path)
-// has a persistent form.
+// boundary are a large part of it, or at least two and a half waves that the overlapped form
+// can run (the end of each step then overlaps the start of the next; with fewer tiles per CTA
+// the next step's first tiles mostly wait, and one launch per step measured faster).  Only
+// the one-column kernel (general or interior path) has a persistent form.
 bool use_persistent(lbm_ctx* c) {
   if (c->loop == LBM_LOOP_LAUNCHES) return false;
   const int kernel = step_kernel(c, c->cols);
@@ -489,7 +511,7 @@ bool use_persistent(lbm_ctx* c) {
   if (c->loop == LBM_LOOP_PERSISTENT) return true;
   const long long slots = persistent_slots(c->prec == LBM_FP64, c->thermal, c->cols, kernel,
                                            needs_full_step(c->hinst), true);
-  return c->ntiles_step <= slots;
+  return c->ntiles_step <= slots || (flow_eligible(c) && 2 * (long long)c->ntiles_step >= 5 * slots);
 }
 
 lbm_status launch(lbm_ctx* c, int mode) {
@@ -534,6 +556,7 @@ void reset_state_mirror(lbm_ctx* c, long long step, int local, double rho_avg_pr
   S.local_read = local;
   S.rho_avg[(step - 1) & 1] = rho_avg_prev;
   S.rho_avg[step & 1] = rho_avg_prev;
+  c->step_next = step;
 }
 
 lbm_status create_impl(lbm_ctx** out, int32_t nx, int32_t ny, lbm_precision prec, int32_t device, void* stream,
@@ -601,7 +624,7 @@ lbm_status create_impl(lbm_ctx** out, int32_t nx, int32_t ny, lbm_precision prec
   if (cudaMemcpyAsync(c->d_tiles_aux, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream) !=
           cudaSuccess ||
       cudaMemsetAsync(c->base + c->L.off_state, 0, sizeof(InstState), c->stream) != cudaSuccess ||
-      cudaMemsetAsync(c->base + c->L.off_sums, 0, NPART * sizeof(unsigned long long), c->stream) != cudaSuccess) {
+      cudaMemsetAsync(c->base + c->L.off_sums, 0, 2 * NPART * sizeof(unsigned long long), c->stream) != cudaSuccess) {
     lbm_destroy(c);
     return LBM_ECUDA;
   }
@@ -734,23 +757,44 @@ lbm_status lbm_step_async(lbm_ctx* c, int64_t nsteps) {
   DeviceGuard g(c->device);
   if (nsteps >= 2 && use_persistent(c)) {
     const int kernel = step_kernel(c, c->cols);
+    const bool full = needs_full_step(c->hinst);
     GridBar* bar = reinterpret_cast<GridBar*>(c->base + c->L.off_bar);
+    FlowPlan flow{};
+    if (overlapped(c)) {
+      flow.enabled = 1;
+      flow.strips = (c->nx + tile_cols(c->cols) - 1) / tile_cols(c->cols);
+      flow.nbands = c->ntiles_step / flow.strips;
+      flow.tall_rows = c->plan.tall_rows;
+      flow.tall_count = c->plan.tall_count;
+      flow.short_rows = c->plan.short_rows;
+      flow.n_open = c->nopen_step;
+      flow.pery = c->params.geometry == LBM_GEOM_PERIODIC;
+      flow.tile_w = tile_cols(c->cols);
+      flow.perx = c->params.geometry != LBM_GEOM_CHANNEL;
+      flow.cell_done = reinterpret_cast<unsigned long long*>(c->base + c->L.off_cells);
+    }
     for (int64_t done = 0; done < nsteps;) {
       const int n = (int)std::min<int64_t>(nsteps - done, 1 << 30);
       LBM_CUDA(c, cudaMemsetAsync(bar, 0, sizeof(GridBar), c->stream));
-      cudaError_t e = launch_persistent(c->prec == LBM_FP64, c->thermal, c->cols, kernel, needs_full_step(c->hinst),
-                                        c->d_inst, c->d_tiles_step, c->ntiles_step, n, bar, c->max_polls, c->stream,
-                                        &c->hinst);
+      if (flow.enabled)
+        LBM_CUDA(c, cudaMemsetAsync(flow.cell_done, 0, (size_t)c->ntiles_step * sizeof(unsigned long long),
+                                    c->stream));
+      flow.step0 = c->step_next + done;
+      cudaError_t e = launch_persistent(c->prec == LBM_FP64, c->thermal, c->cols, kernel, full, c->d_inst,
+                                        c->d_tiles_step, c->ntiles_step, n, bar, c->max_polls, c->stream, &c->hinst,
+                                        flow);
       if (e != cudaSuccess) return cuda_fail(c, e, "persistent kernel launch");
       ++c->launches;
       done += n;
     }
+    c->step_next += nsteps;
     return LBM_OK;
   }
   for (int64_t k = 0; k < nsteps; ++k) {
     lbm_status s = launch(c, MODE_STEP);
     if (s != LBM_OK) return s;
   }
+  c->step_next += nsteps;
   return LBM_OK;
 }
 
@@ -924,7 +968,7 @@ lbm_status lbm_save_state(lbm_ctx* c, void* host_buf, size_t bytes) {
   h.abi = LBM_ABI_VERSION;
   h.params = c->params;
   h.state = *c->h_state;
-  h.state.counter = 0;
+  h.state.counter[0] = h.state.counter[1] = 0;
   char* dst = static_cast<char*>(host_buf);
   std::memcpy(dst, &h, sizeof(h));
   dst += sizeof(h);
@@ -957,7 +1001,7 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t bytes) {
   if (s != LBM_OK) return s;
   if ((s = c->rows_default ? retile_default(c, c->cols) : set_tiling(c, c->cols, c->plan)) != LBM_OK) return s;
   *c->h_state = h.state;
-  c->h_state->counter = 0;
+  c->h_state->counter[0] = c->h_state->counter[1] = 0;
   if ((s = upload_state(c)) != LBM_OK) return s;
   const char* src = static_cast<const char*>(host_buf) + sizeof(h);
   const size_t elt = elt_size(c);
@@ -972,6 +1016,7 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t bytes) {
                                 (size_t)c->ny, cudaMemcpyHostToDevice, c->stream));
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
   c->step_host = h.state.step;
+  c->step_next = h.state.step;
   return LBM_OK;
 }
 
@@ -1000,7 +1045,8 @@ int32_t lbm_step_loop(lbm_ctx* c) {
   if (!c) return -1;
   if (!c->have_params) return c->loop == LBM_LOOP_PERSISTENT ? LBM_LOOP_PERSISTENT : LBM_LOOP_LAUNCHES;
   DeviceGuard g(c->device);
-  return use_persistent(c) ? LBM_LOOP_PERSISTENT : LBM_LOOP_LAUNCHES;
+  if (!use_persistent(c)) return LBM_LOOP_LAUNCHES;
+  return overlapped(c) ? LBM_LOOP_OVERLAPPED : LBM_LOOP_PERSISTENT;
 }
 
 lbm_status lbm_set_wait_limit(lbm_ctx* c, int64_t max_polls) {

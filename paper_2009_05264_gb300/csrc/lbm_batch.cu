@@ -134,10 +134,9 @@ lbm_status rebuild(lbm_batch* b) {
     for (int bd = 0; bd < plan.tall_count; ++bd) band(bd * plan.tall_rows, (bd + 1) * plan.tall_rows, tiles);
     for (int y = y_short; y < m.ny; y += plan.short_rows) band(y, std::min(m.ny, y + plan.short_rows), shorts);
   }
-  // longest tiles first within each class: the general-loop tiles before the interior ones
-  std::stable_partition(tiles.begin(), tiles.end(), general_tile);
-  std::stable_partition(shorts.begin(), shorts.end(), general_tile);
+  // the general-loop tiles first (tall bands, then short), then the interior ones
   tiles.insert(tiles.end(), shorts.begin(), shorts.end());
+  std::stable_partition(tiles.begin(), tiles.end(), general_tile);
   if (insts.size() > b->cap_insts) {
     if (b->d_insts) cudaFree(b->d_insts);
     b->d_insts = nullptr;
@@ -198,7 +197,8 @@ lbm_status launch_persistent_steps(lbm_batch* b, int64_t nsteps) {
     const int n = (int)std::min<int64_t>(nsteps - done, 1 << 30);
     LBM_BCUDA(b, cudaMemsetAsync(b->d_bar, 0, sizeof(GridBar), b->stream));
     LBM_BCUDA(b, launch_persistent(b->prec == LBM_FP64, b->thermal, b->cols, b->launch_kernel, b->any_full, b->d_insts,
-                                   b->d_tiles, b->ntiles, n, b->d_bar, b->max_polls, b->stream, nullptr));
+                                   b->d_tiles, b->ntiles, n, b->d_bar, b->max_polls, b->stream, nullptr,
+                                   FlowPlan{}));
     ++b->launches;
     done += n;
   }

@@ -16,10 +16,10 @@ cudaError_t launch_lbm_f32(int thermal, int cols, int mode, int kernel, bool ful
 
 cudaError_t launch_persistent_f32(int thermal, int cols, int kernel, bool full, const Inst* d_inst,
                                   const Tile* d_tiles, int ntiles, int nsteps, GridBar* bar, unsigned max_polls,
-                                  cudaStream_t s, const Inst* h_inst) {
+                                  cudaStream_t s, const Inst* h_inst, const FlowPlan& flow) {
   if (kernel != LBM_KERNEL_SCALAR && kernel != LBM_KERNEL_INTERIOR) return cudaErrorNotSupported;
   return launch_persistent_precision<float>(thermal, cols, full, kernel == LBM_KERNEL_INTERIOR, d_inst, d_tiles,
-                                            ntiles, nsteps, bar, max_polls, s, h_inst);
+                                            ntiles, nsteps, bar, max_polls, s, h_inst, flow);
 }
 
 int persistent_resident_f32(int thermal, int cols, int kernel, bool full, bool single) {

@@ -35,14 +35,20 @@ enum : int { MODE_STEP = 0, MODE_FIELDS = 1, MODE_POPS = 2, MODE_MOMENTS = 3 };
 enum : unsigned { STATUS_UNSTABLE = 1u, STATUS_TIMEOUT = 2u, STATUS_BOUNDS = 4u };
 
 // Device-resident mutable state of one lattice instance.
+// Step n uses the slots n & 1 of counter and p_probe and the slot n % 4 of the open-end mass
+// exchange: the overlapped persistent loop has tiles of two consecutive steps in flight.
 struct InstState {
   long long step;       // steps completed
   int local_read;       // 1: buffer (step & 1) holds post-stream populations (after init/load)
-  unsigned int counter; // tiles of the current launch that have posted their partials
   unsigned int status;  // sticky STATUS_* bits, cleared by the host
+  unsigned int counter[2];   // tiles of step n that have posted their partials, in slot n & 1
   unsigned int bounds_hits;  // accesses a bounds-checked build rejected (STATUS_BOUNDS), else 0
+  unsigned int open_posted[4];  // open-end tiles of step n that posted open_mass, in slot n % 4
+  int pad0;
   double rho_avg[2];    // domain-mean rho of step n in slot n & 1 (buoyancy of step n+1, Eq. 14)
-  double p_probe[2];    // EOS pressure at (1, ny/2) and (nx-2, ny/2) of the current step
+  double p_probe[4];    // EOS pressure at (1, ny/2) and (nx-2, ny/2) of step n in slots 2 (n & 1) + {0, 1}
+  long long open_mass[4];  // fixed-point mass that step n's pull took in and let out through the
+                           // open ends (created minus lost populations), in slot n % 4
 };
 
 // Read-only description of one lattice instance (host-filled, device-resident).
@@ -97,10 +103,28 @@ struct Inst {
 // zeroed by the host before every persistent launch).  count: CTAs arrived at the current
 // barrier; gen: barriers completed; status: 1 once a CTA gave up waiting; next[2]: the
 // dynamic tile counters of even and odd steps.
+//
+// Overlapped form (FlowPlan.enabled, a parameter of the launch; one instance with more tiles than resident CTAs): the CTAs
+// draw (step, tile) tickets in order from `claim`, and a tile of step s waits only for what
+// it reads, instead of a barrier for the whole lattice: the tiles around it to have finished
+// step s - 1 (cell_done), step s - 2 to be complete (its mean density), and the
+// open-end tiles of step s - 1 to have posted the mass that crossed the inlet and outlet; its
+// buoyancy mean is the mean of step s - 2 plus that mass over the nodes (Eq. 14).  Tiles of
+// two consecutive steps run at once, so the end of one step overlaps the start of the next.
+struct FlowPlan {
+  int enabled;
+  int strips, nbands, tile_w;             // tiles per band, bands per step, output columns per tile
+  int tall_rows, tall_count, short_rows;  // band layout (row y -> band)
+  int n_open;                             // tiles per step with an open end
+  int perx, pery;                         // strips wrap in x (walls, periodic), bands in y (periodic)
+  long long step0;                        // step of the launch's first tickets
+  unsigned long long* cell_done;          // per tile position (band * strips + strip): steps of this
+                                          // launch it has finished (zeroed before the launch)
+};
 struct GridBar {
   unsigned int count, gen, status, pad;
   unsigned int next[2];
-  unsigned int pad2[2];
+  unsigned long long claim;  // overlapped form: (step, tile) tickets drawn in this launch
 };
 // Bounded waits of the persistent launch: a CTA stops waiting at a barrier after wait_ns
 // nanoseconds of polling, or after max_polls polls when max_polls > 0 (a test lowers it to
@@ -114,7 +138,7 @@ struct Tile {
   int ntiles;  // tiles of this instance in the launch
   int interior;  // 1: every column the tile pulls, [x0 - 2, x0 + cols - 6), lies in [1, nx - 2] of a
                  // channel or walls lattice (no open end, no wrap): the interior path may take it
-  int pad1;
+  int open_end;  // 1: the tile's output columns include the inlet or the outlet of a channel
 };
 // Whether a tile of a cols-thread step tiling starting at column x0 may take the interior path.
 inline int tile_is_interior(int geometry, int nx, int cols, int x0) {
@@ -136,9 +160,10 @@ cudaError_t launch_lbm(int fp64, int thermal, int cols, int mode, int kernel, bo
 // nsteps steps of the step kernel in one cooperative launch (tiles drawn dynamically from a
 // counter, a bounded grid barrier between steps; MODE_STEP only).  grid <= resident CTAs of
 // the device; bar: zeroed GridBar in device memory.
+// flow.enabled: the overlapped form (one instance; more tiles than resident CTAs).
 cudaError_t launch_persistent(int fp64, int thermal, int cols, int kernel, bool full, const Inst* d_inst,
                               const Tile* d_tiles, int ntiles, int nsteps, GridBar* bar, unsigned max_polls,
-                              cudaStream_t s, const Inst* h_inst);
+                              cudaStream_t s, const Inst* h_inst, const FlowPlan& flow);
 // CTAs one persistent launch may hold on the current device (SMs x resident CTAs per SM).
 long long persistent_slots(int fp64, int thermal, int cols, int kernel, bool full, bool single);
 // Whether an instance needs the step's full form.

@@ -795,7 +795,7 @@ __device__ __forceinline__ void finish_step(const Inst& I, InstState* st, const 
     rec[1] = mass;
     rec[2] = energy;
     rec[3] = mass / n;
-    rec[4] = channel ? __ldcg(&st->p_probe[0]) - __ldcg(&st->p_probe[1]) : 0.0;
+    rec[4] = channel ? __ldcg(&st->p_probe[2 * (step & 1)]) - __ldcg(&st->p_probe[2 * (step & 1) + 1]) : 0.0;
     rec[5] = dtstar;
     rec[6] = channel ? tot[3] : 0.0;
     rec[7] = channel ? tot[4] : 0.0;
@@ -804,12 +804,19 @@ __device__ __forceinline__ void finish_step(const Inst& I, InstState* st, const 
     rec[10] = tot[7];
     rec[11] = tot[8];
     st->rho_avg[step & 1] = mass / n;
-    st->step = step + 1;
     st->local_read = 0;
   } else {
     st->rho_avg[(step - 1) & 1] = mass / n;
   }
-  st->counter = 0u;
+  // every tile of this step has read the open-end mass of the step before (its slot is free
+  // until step + 3 posts there), and has taken its ticket
+  st->counter[step & 1] = 0u;
+  st->open_mass[(step - 1) & 3] = 0;
+  st->open_posted[(step - 1) & 3] = 0u;
+  if (MODE == MODE_STEP) {
+    __threadfence();  // the record, the mean and the resets are visible before the step count
+    atomicExch(reinterpret_cast<unsigned long long*>(&st->step), (unsigned long long)(step + 1));
+  }
 }
 
 // End of a tile of a MODE_STEP / MODE_MOMENTS launch: post its partial sums (acc, per thread).
@@ -818,16 +825,40 @@ __device__ __forceinline__ void finish_step(const Inst& I, InstState* st, const 
 // tile drawing the last ticket takes the totals (and leaves zeros for the next launch) by one
 // atomic exchange each and finishes the step.  A sum outside the totals' range (only a diverged
 // run, or a NaN) marks the instance unstable.  Every tile of a launch must post exactly once.
+// open: the tile also posts open_acc, its share of the mass that this step's pull took in and
+// let out through the channel's open ends (the overlapped persistent loop derives the next
+// step's buoyancy mean from it); the fixed-point grid is the inflow total's.
 template <int BLOCK, bool THERMAL, int MODE>
 __device__ __forceinline__ void post_partials(const Inst& I, InstState* st, const Tile& tile, const double (&acc)[NPART],
-                                              double (*red)[NPART], int* flag, long long step) {
+                                              double (*red)[NPART], int* flag, long long step, bool open = false,
+                                              double open_acc = 0.0) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned long long* const sums = I.sums + (step & 1) * NPART;
 #pragma unroll
   for (int j = 0; j < NPART; ++j) {
     double x = acc[j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     if (lane == 0) red[warp][j] = x;
+  }
+  if (open) {
+    double x = open_acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    __shared__ double s_open[BLOCK / 32];
+    if (lane == 0) s_open[warp] = x;
+    __syncthreads();
+    if (tid == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < BLOCK / 32; ++w) sum += s_open[w];
+      const double q = sum * I.fix_scale[3];
+      long long v = 0;
+      if (fabs(q) < 0x1p62) v = __double2ll_rn(q);
+      else atomicOr(&st->status, STATUS_UNSTABLE);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&st->open_mass[step & 3]), (unsigned long long)v);
+      __threadfence();  // the addition is performed before the count
+      atomicAdd(&st->open_posted[step & 3], 1u);
+    }
   }
   __syncthreads();
   if (tid < NPART) {
@@ -837,18 +868,18 @@ __device__ __forceinline__ void post_partials(const Inst& I, InstState* st, cons
     long long q = 0;
     if (fabs(x) < 0x1p62) q = __double2ll_rn(x);
     else atomicOr(&st->status, STATUS_UNSTABLE);
-    atomicAdd(I.sums + tid, (unsigned long long)q);
+    atomicAdd(sums + tid, (unsigned long long)q);
   }
   __syncthreads();
   if (tid == 0) {
     __threadfence();  // the block's additions are performed before its ticket
-    const unsigned ticket = atomicAdd(&st->counter, 1u);
+    const unsigned ticket = atomicAdd(&st->counter[step & 1], 1u);
     *flag = (ticket == (unsigned)(tile.ntiles - 1));
   }
   __syncthreads();
   if (!*flag) return;
   __threadfence();
-  if (tid < NPART) red[0][tid] = (double)(long long)atomicExch(I.sums + tid, 0ull) * I.fix_unscale[tid];
+  if (tid < NPART) red[0][tid] = (double)(long long)atomicExch(sums + tid, 0ull) * I.fix_unscale[tid];
   __syncthreads();
   if (tid == 0) {
     double tot[NPART];
@@ -1112,6 +1143,17 @@ __device__ __forceinline__ void interior_rows(const Inst& I, const KConst<Real>&
 // Otherwise every CTA copies its instance's descriptor and constants into shared memory.
 // INTERIOR: tiles flagged interior take the interior path (MODE_STEP, lean form only).
 //
+// A tile's step when the launch, not the instance state, fixes it (the overlapped persistent
+// loop): step >= 0 takes step, local and rho_avg_prev (the mean density its buoyancy uses)
+// from here, and post_open makes a tile at a channel's inlet or outlet post the mass its pull
+// took in and let out there.  The default (step < 0) reads them from the instance state.
+struct TileStep {
+  long long step = -1;
+  bool local = false;
+  bool post_open = false;
+  double rho_avg_prev = 0.0;
+};
+
 // Per-CTA shared state of the step kernels besides the dynamic rings.  Launches over several
 // instances also keep the tile's instance descriptor and its converted constants there;
 // single-instance launches (PCONST) read both from the kernel parameter.
@@ -1144,7 +1186,8 @@ __device__ __forceinline__ const KConst<Real>& tile_consts(const KParams<Real>& 
 // One tile of the fused step (the body of lbm_fused_kernel and of the persistent kernel).
 template <typename Real, bool THERMAL, int B, int MODE, bool FULL, bool PCONST, bool INTERIOR>
 __device__ __forceinline__ void fused_tile(const Inst* __restrict__ insts, const Tile tile, const KParams<Real>& kp,
-                                           unsigned char* dyn_smem, StepShared<Real, B, PCONST>& sh) {
+                                           unsigned char* dyn_smem, StepShared<Real, B, PCONST>& sh,
+                                           const TileStep& ts = TileStep{}) {
   constexpr int BLOCK = B;
   constexpr int W = out_cols<B>();
   constexpr int NS = B - 4;
@@ -1166,9 +1209,9 @@ __device__ __forceinline__ void fused_tile(const Inst* __restrict__ insts, const
   }
   const Inst& I = tile_inst<Real, B, PCONST>(kp, sh);
   InstState* st = I.st;
-  const long long step = st->step;
+  const long long step = ts.step >= 0 ? ts.step : st->step;
   if (tid == 0) {
-    const double rho_avg_prev = st->rho_avg[(step - 1) & 1];
+    const double rho_avg_prev = ts.step >= 0 ? ts.rho_avg_prev : st->rho_avg[(step - 1) & 1];
     if constexpr (!PCONST) fill_consts<Real>(sh.sCv, I, rho_avg_prev);
     sRra = Real(I.rho_ref - rho_avg_prev);
   }
@@ -1177,7 +1220,8 @@ __device__ __forceinline__ void fused_tile(const Inst* __restrict__ insts, const
 
   const int nx = I.nx, ny = I.ny, pitch = I.pitch;
   const int plane = (int)I.plane;  // the host guarantees 9 * plane < 2^31
-  const bool local = st->local_read != 0;
+  const bool local = ts.step >= 0 ? ts.local : st->local_read != 0;
+  const bool post_open = MODE == MODE_STEP && ts.post_open && tile.open_end;  // a first step posts 0
   if (INTERIOR && MODE == MODE_STEP && !FULL && tile.interior) {
     Real am = Real(0), ae = Real(0), ah = Real(0);
     bool bad_any = false;
@@ -1238,6 +1282,7 @@ __device__ __forceinline__ void fused_tile(const Inst* __restrict__ insts, const
 
   Real acc_m = Real(0), acc_e = Real(0), acc_h = Real(0), acc_fi = Real(0), acc_fo = Real(0);
   float acc_va = 0.0f, acc_wv = 0.0f, acc_hv = 0.0f, acc_zv = 0.0f;  // vapour node counts (exact in FP32)
+  double acc_open = 0.0;  // mass through the open ends (post_open)
   const bool zone_col = xn >= I.heater_x0 - I.heater_len && xn < I.heater_x0 + 2 * I.heater_len;
   // node scalars carried between iterations: row r-1 (f collision), row r-2 (g collision)
   Real rho_p = Real(1), drho_p = Real(0), ux_p = Real(0), uy_p = Real(0), T_p = T0, dT_p = Real(0), coef_p = Real(0);
@@ -1286,6 +1331,25 @@ __device__ __forceinline__ void fused_tile(const Inst* __restrict__ insts, const
       if (ns.bad) atomicOr(&st->status, STATUS_UNSTABLE);
       sPsi[f_cur * NS + s] = ns.dpsi;
       const bool out_row = r >= tile.y0 && r < tile.y1;
+      if (post_open && !local && (inl || outl) && out_col && out_row) {
+        // mass this node's pull took in minus the mass the pull let out of the lattice: in, the
+        // open-end links that boundary_fill set; out, this node's post-collision populations
+        // that point out of the open end (no node pulls them; at a wall row the diagonal one is
+        // bounced back instead).  Summed over the open ends this is the change of the total
+        // mass from the previous step to this one, up to the rounding of the collision.
+        const bool lo = rn == 0, hi = rn == ny - 1;
+        const int node = rn * pitch + xn;
+        auto fload = [&](int i) {
+          const int k = i * plane + node;
+          return idx_ok(I.st, k, 9LL * plane) ? (double)ld_ro(Fin + k) : 0.0;
+        };
+        if (inl)
+          acc_open += (double)fc[1] + (lo ? 0.0 : (double)fc[5]) + (hi ? 0.0 : (double)fc[8]) -
+                      (fload(3) + (hi ? 0.0 : fload(6)) + (lo ? 0.0 : fload(7)));
+        else
+          acc_open += (double)fc[3] + (lo ? 0.0 : (double)fc[6]) + (hi ? 0.0 : (double)fc[7]) -
+                      (fload(1) + (hi ? 0.0 : fload(5)) + (lo ? 0.0 : fload(8)));
+      }
       const Real hmc = ns.hmc;
       ns.hmc = Real(0);  // becomes the source term of this node (output nodes of the step only)
       if (hazi && out_col && out_row) {
@@ -1313,8 +1377,8 @@ __device__ __forceinline__ void fused_tile(const Inst* __restrict__ insts, const
           }
         }
         if (MODE == MODE_STEP && channel && rn == ny / 2 && (xn == 1 || xn == nx - 2)) {
-          if (xn == 1) st->p_probe[0] = (double)ns.p;
-          if (xn == nx - 2) st->p_probe[1] = (double)ns.p;
+          if (xn == 1) st->p_probe[2 * (step & 1)] = (double)ns.p;
+          if (xn == nx - 2) st->p_probe[2 * (step & 1) + 1] = (double)ns.p;
           __threadfence();
         }
       }
@@ -1429,7 +1493,7 @@ __device__ __forceinline__ void fused_tile(const Inst* __restrict__ insts, const
   // ---------------- per-tile partials into the launch's totals ----------------
   double acc[NPART] = {(double)acc_m,  (double)acc_e,  (double)acc_h,  (double)acc_fi, (double)acc_fo,
                        (double)acc_va, (double)acc_wv, (double)acc_hv, (double)acc_zv};
-  post_partials<BLOCK, THERMAL, MODE>(I, st, tile, acc, sRed, &sLast, step);
+  post_partials<BLOCK, THERMAL, MODE>(I, st, tile, acc, sRed, &sLast, step, post_open, acc_open);
 }
 
 // Resident CTAs per SM the step kernels are compiled for (register budget).  The FP32 kernel
@@ -1499,10 +1563,144 @@ __device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned nblocks, uns
   return *s_ok != 0;
 }
 
+// Band of row y in the overlapped form's tiling (tall bands first, then short ones).
+__device__ __forceinline__ int flow_band(const FlowPlan& f, int y) {
+  const int ytall = f.tall_rows * f.tall_count;
+  return y < ytall ? y / f.tall_rows : f.tall_count + (y - ytall) / f.short_rows;
+}
+
+// Thread 0 polls *p until it reaches `need`, at most max_polls polls (0: no cap) and
+// BARRIER_WAIT_NS from t0, and gives up early once another CTA has given up (bar->status).
+template <typename T>
+__device__ __forceinline__ bool flow_wait(const volatile T* p, T need, const GridBar* bar, unsigned max_polls,
+                                          unsigned& polls, unsigned long long t0) {
+  const volatile unsigned* vstatus = &bar->status;
+  while (*p < need) {
+    ++polls;
+    if ((max_polls != 0 && polls >= max_polls) || *vstatus != 0 || global_ns() - t0 > BARRIER_WAIT_NS)
+      return *p >= need;
+  }
+  return true;
+}
+
+// The overlapped persistent loop (see FlowPlan): nsteps steps of one instance's tiles in
+// (step, tile) ticket order.  A ticket's tile waits, on thread 0 with bounded polls, for
+//  - the tiles holding rows y0 - 3 .. y1 + 2 and columns x0 - 3 .. x1 + 2 (what its pulls read,
+//    wrapped where the lattice is periodic) to have finished the previous step: the tiles it
+//    reads from and those that read what it overwrites;
+//  - the step two back to be complete (its diagnostics record and mean density written);
+//  - the open-end tiles of the previous step to have posted the mass through the open ends;
+// then runs with the buoyancy mean rho_avg(s - 2) + (mass through the open ends in s - 1) / N,
+// which is the previous step's mean up to the rounding of one collision, whatever the timing.
+// Tickets are drawn in order and a tile waits only for tickets drawn before it, all of them
+// held by resident CTAs, so the loop always progresses; a CTA that gives up marks the launch
+// (bar->status), every CTA then stops at its next wait, and the instance reports a timeout.
+template <typename Real, bool THERMAL, int B, bool FULL, bool PCONST, bool INTERIOR>
+__device__ __forceinline__ void overlapped_steps(const Inst* __restrict__ insts, const Tile* __restrict__ tiles,
+                                                 int ntiles, int nsteps, GridBar* bar, unsigned max_polls,
+                                                 const KParams<Real>& kp, const FlowPlan& flow,
+                                                 unsigned char* dyn_smem, StepShared<Real, B, PCONST>& sh) {
+  __shared__ long long s_q;
+  __shared__ int s_ok;
+  __shared__ double s_rho;
+  const Inst& Ig = PCONST ? kp.I : insts[tiles[0].inst];
+  InstState* st = Ig.st;
+  // the state's "own populations" flag is that of the launch's first step until that step
+  // completes, and only tickets of the first step use it
+  const bool local0 = st->local_read != 0;
+  const long long total = (long long)nsteps * ntiles;
+  const double inv_n = 1.0 / ((double)Ig.nx * (double)Ig.ny);
+  for (;;) {
+    if (threadIdx.x == 0) s_q = (long long)atomicAdd(&bar->claim, 1ull);
+    __syncthreads();
+    const long long q = s_q;
+    if (q >= total) return;
+    const int k = (int)(q / ntiles);
+    const Tile tile = tiles[q - (long long)k * ntiles];
+    const long long step = flow.step0 + k;
+    if (threadIdx.x == 0) {
+      bool ok = true;
+      double rho = 0.0;
+      if (k == 0) {
+        rho = st->rho_avg[(step - 1) & 1];
+      } else {
+        unsigned polls = 0;
+        const unsigned long long t0 = global_ns();
+        const unsigned long long need = (unsigned long long)k;  // steps each neighbour has finished
+        const int ny = Ig.ny, nx = Ig.nx;
+        // the rows and columns this tile's pulls read: its own, 3 rows and 3 columns around
+        int ylo = tile.y0 - 3, yhi = tile.y1 + 2;
+        if (!flow.pery) {
+          ylo = ylo < 0 ? 0 : ylo;
+          yhi = yhi > ny - 1 ? ny - 1 : yhi;
+        } else if (yhi - ylo + 1 >= ny) {
+          ylo = 0;
+          yhi = ny - 1;
+        }
+        const int x1 = tile.x0 + flow.tile_w < nx ? tile.x0 + flow.tile_w : nx;
+        int xlo = tile.x0 - 3, xhi = x1 + 2;
+        if (!flow.perx) {
+          xlo = xlo < 0 ? 0 : xlo;
+          xhi = xhi > nx - 1 ? nx - 1 : xhi;
+        } else if (xhi - xlo + 1 >= nx) {
+          xlo = 0;
+          xhi = nx - 1;
+        }
+        const int ytall = flow.tall_rows * flow.tall_count;
+        for (int y = ylo; ok && y <= yhi;) {
+          const int yy = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+          const int b = flow_band(flow, yy);
+          for (int x = xlo; ok && x <= xhi;) {
+            const int xx = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+            const int j = xx / flow.tile_w;
+            ok = flow_wait<unsigned long long>(flow.cell_done + (long long)b * flow.strips + j, need, bar, max_polls,
+                                               polls, t0);
+            const int xend = (j + 1) * flow.tile_w;
+            x += (xend < nx ? xend : nx) - xx;  // first column of the next strip
+          }
+          const int bend = b < flow.tall_count ? (b + 1) * flow.tall_rows
+                                               : ytall + (b - flow.tall_count + 1) * flow.short_rows;
+          y += (bend < ny ? bend : ny) - yy;  // first row of the next band
+        }
+        if (ok) ok = flow_wait<long long>(&st->step, step - 1, bar, max_polls, polls, t0);
+        if (ok && flow.n_open > 0)
+          ok = flow_wait<unsigned>(&st->open_posted[(step - 1) & 3], (unsigned)flow.n_open, bar, max_polls, polls,
+                                   t0);
+        __threadfence();  // what the awaited tiles wrote is visible after their counts
+        if (ok) {
+          const long long m = *reinterpret_cast<const volatile long long*>(&st->open_mass[(step - 1) & 3]);
+          rho = *reinterpret_cast<const volatile double*>(&st->rho_avg[(step - 2) & 1]) +
+                (double)m * Ig.fix_unscale[3] * inv_n;
+        }
+      }
+      if (!ok) {
+        atomicOr(&bar->status, 1u);
+        atomicOr(&st->status, STATUS_TIMEOUT);
+      }
+      s_ok = ok;
+      s_rho = rho;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    TileStep ts;
+    ts.step = step;
+    ts.local = k == 0 && local0;
+    ts.post_open = true;
+    ts.rho_avg_prev = s_rho;
+    fused_tile<Real, THERMAL, B, MODE_STEP, FULL, PCONST, INTERIOR>(insts, tile, kp, dyn_smem, sh, ts);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();  // the tile's populations are written before its count
+      atomicAdd(flow.cell_done + (long long)flow_band(flow, tile.y0) * flow.strips + tile.x0 / flow.tile_w, 1ull);
+    }
+  }
+}
+
 template <typename Real, bool THERMAL, int B, bool FULL, bool PCONST, bool INTERIOR>
 __global__ void __launch_bounds__(B, (step_min_blocks<Real, B, INTERIOR>()))
 lbm_persistent_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, int ntiles, int nsteps,
-                      GridBar* bar, unsigned max_polls, const __grid_constant__ KParams<Real> kp) {
+                      GridBar* bar, unsigned max_polls, const __grid_constant__ KParams<Real> kp,
+                      const __grid_constant__ FlowPlan flow) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   __shared__ StepShared<Real, B, PCONST> sh;
   __shared__ int s_tile, s_ok;
@@ -1510,6 +1708,11 @@ lbm_persistent_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ t
   // With a CTA per tile (one wave) every CTA runs tile blockIdx.x; otherwise the CTAs draw tiles
   // from the step's counter, so that the tall bands dispatched first are shared out as they end.
   const bool one_wave = ntiles <= (int)gridDim.x;
+  if (!one_wave && flow.enabled) {
+    overlapped_steps<Real, THERMAL, B, FULL, PCONST, INTERIOR>(insts, tiles, ntiles, nsteps, bar, max_polls, kp,
+                                                               flow, dyn_smem, sh);
+    return;
+  }
   for (int n = 0; n < nsteps; ++n) {
     if (one_wave) {
       const Tile tile = tiles[blockIdx.x];
@@ -1539,7 +1742,8 @@ lbm_persistent_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ t
 
 template <typename Real, bool THERMAL, int B, bool FULL, bool PCONST, bool INTERIOR>
 cudaError_t launch_persistent_one(const Inst* d_inst, const Tile* d_tiles, int ntiles, int nsteps, GridBar* bar,
-                                  unsigned max_polls, cudaStream_t s, const KParams<Real>& kp) {
+                                  unsigned max_polls, cudaStream_t s, const KParams<Real>& kp,
+                                  const FlowPlan& flow) {
   constexpr size_t smem = step_smem_bytes<Real, THERMAL, B, INTERIOR>();
   auto fn = lbm_persistent_kernel<Real, THERMAL, B, FULL, PCONST, INTERIOR>;
   int dev = 0, sms = 0, per_sm = 0;
@@ -1560,7 +1764,7 @@ cudaError_t launch_persistent_one(const Inst* d_inst, const Tile* d_tiles, int n
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, fn, d_inst, d_tiles, ntiles, nsteps, bar, max_polls, kp);
+  return cudaLaunchKernelEx(&cfg, fn, d_inst, d_tiles, ntiles, nsteps, bar, max_polls, kp, flow);
 }
 
 template <typename Real, bool THERMAL, int B, bool FULL, bool PCONST, bool INTERIOR>
@@ -1578,24 +1782,25 @@ int persistent_resident() {
 // constants as the kernel parameter), or the full form.
 template <typename Real, bool THERMAL, int B>
 cudaError_t launch_persistent_cols(bool full, bool interior, const Inst* d_inst, const Tile* d_tiles, int ntiles,
-                                   int nsteps, GridBar* bar, unsigned max_polls, cudaStream_t s, const Inst* h_inst) {
+                                   int nsteps, GridBar* bar, unsigned max_polls, cudaStream_t s, const Inst* h_inst,
+                                   const FlowPlan& flow) {
   KParams<Real> kp{};
   if (full) return launch_persistent_one<Real, THERMAL, B, true, false, false>(d_inst, d_tiles, ntiles, nsteps, bar,
-                                                                               max_polls, s, kp);
+                                                                               max_polls, s, kp, flow);
   if (h_inst) {
     kp.I = *h_inst;
     fill_consts<Real>(kp.C, *h_inst, h_inst->rho_ref);
     if (interior)
       return launch_persistent_one<Real, THERMAL, B, false, true, true>(d_inst, d_tiles, ntiles, nsteps, bar,
-                                                                        max_polls, s, kp);
+                                                                        max_polls, s, kp, flow);
     return launch_persistent_one<Real, THERMAL, B, false, true, false>(d_inst, d_tiles, ntiles, nsteps, bar,
-                                                                       max_polls, s, kp);
+                                                                       max_polls, s, kp, flow);
   }
   if (interior)
     return launch_persistent_one<Real, THERMAL, B, false, false, true>(d_inst, d_tiles, ntiles, nsteps, bar,
-                                                                       max_polls, s, kp);
+                                                                       max_polls, s, kp, flow);
   return launch_persistent_one<Real, THERMAL, B, false, false, false>(d_inst, d_tiles, ntiles, nsteps, bar, max_polls,
-                                                                      s, kp);
+                                                                      s, kp, flow);
 }
 
 template <typename Real, bool THERMAL, int B>
@@ -1610,10 +1815,10 @@ int persistent_resident_cols(bool full, bool interior, bool single) {
 template <typename Real>
 cudaError_t launch_persistent_precision(int thermal, int cols, bool full, bool interior, const Inst* d_inst,
                                         const Tile* d_tiles, int ntiles, int nsteps, GridBar* bar, unsigned max_polls,
-                                        cudaStream_t s, const Inst* h_inst) {
+                                        cudaStream_t s, const Inst* h_inst, const FlowPlan& flow) {
   if (ntiles <= 0 || nsteps <= 0) return cudaSuccess;
 #define PPLBM_PERSIST(TH, COLS) \
-  launch_persistent_cols<Real, TH, COLS>(full, interior, d_inst, d_tiles, ntiles, nsteps, bar, max_polls, s, h_inst)
+  launch_persistent_cols<Real, TH, COLS>(full, interior, d_inst, d_tiles, ntiles, nsteps, bar, max_polls, s, h_inst, flow)
   if (thermal) {
     switch (cols) {
       case 64: return PPLBM_PERSIST(true, 64);

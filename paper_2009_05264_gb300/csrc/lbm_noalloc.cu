@@ -26,7 +26,7 @@ constexpr size_t kOffInst = 0;
 constexpr size_t kOffState = align256(kOffInst + sizeof(Inst));
 constexpr size_t kOffRing = align256(kOffState + sizeof(InstState));
 constexpr size_t kOffSums = align256(kOffRing + sizeof(double) * RING * NDIAG);
-constexpr size_t kOffTiles = align256(kOffSums + sizeof(unsigned long long) * NPART);
+constexpr size_t kOffTiles = align256(kOffSums + sizeof(unsigned long long) * 2 * NPART);
 constexpr size_t kScratchBytes = align256(kOffTiles + sizeof(Tile) * kNoAllocMaxTiles);
 
 }  // namespace
@@ -117,7 +117,7 @@ extern "C" lbm_status lbm_step_noalloc(const lbm_params* p, int32_t nx, int32_t 
   // both copies read host stack memory, staged by the runtime before the calls return
   if (cudaMemcpyAsync(base + kOffInst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(base + kOffState, &S, sizeof(InstState), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemsetAsync(base + kOffSums, 0, sizeof(unsigned long long) * NPART, s) != cudaSuccess)
+      cudaMemsetAsync(base + kOffSums, 0, sizeof(unsigned long long) * 2 * NPART, s) != cudaSuccess)
     return LBM_ECUDA;
   Tile* tiles = reinterpret_cast<Tile*>(base + kOffTiles);
   fill_tiles_kernel<<<(ntiles + 255) / 256, 256, 0, s>>>(tiles, nx, ny, w, rows, strips, ntiles);

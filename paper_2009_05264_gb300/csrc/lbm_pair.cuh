@@ -438,10 +438,10 @@ lbm_pair_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles) 
           }
         }
         if (channel && rn == ny / 2) {
-          if (xn0 == 1) st->p_probe[0] = (double)ns.p.x;
-          if (out1 && xn1 == 1) st->p_probe[0] = (double)ns.p.y;
-          if (xn0 == nx - 2) st->p_probe[1] = (double)ns.p.x;
-          if (out1 && xn1 == nx - 2) st->p_probe[1] = (double)ns.p.y;
+          if (xn0 == 1) st->p_probe[2 * (step & 1)] = (double)ns.p.x;
+          if (out1 && xn1 == 1) st->p_probe[2 * (step & 1)] = (double)ns.p.y;
+          if (xn0 == nx - 2) st->p_probe[2 * (step & 1) + 1] = (double)ns.p.x;
+          if (out1 && xn1 == nx - 2) st->p_probe[2 * (step & 1) + 1] = (double)ns.p.y;
           __threadfence();
         }
       }

@@ -339,8 +339,8 @@ lbm_tma_kernel(const Inst* __restrict__ insts, const Tile* __restrict__ tiles, u
           if (!pery && rn == 0 && xn >= I.heater_x0 && xn < I.heater_x0 + I.heater_len) acc_h += ns.dT;
         }
         if (channel && rn == ny / 2 && (xn == 1 || xn == nx - 2)) {
-          if (xn == 1) st->p_probe[0] = (double)ns.p;
-          if (xn == nx - 2) st->p_probe[1] = (double)ns.p;
+          if (xn == 1) st->p_probe[2 * (step & 1)] = (double)ns.p;
+          if (xn == nx - 2) st->p_probe[2 * (step & 1) + 1] = (double)ns.p;
           __threadfence();
         }
       }

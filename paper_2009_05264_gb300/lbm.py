@@ -46,7 +46,7 @@ EXPORTS = (
 KERNELS = {"auto": 0, "scalar": 1, "paired": 2, "tma": 3, "interior": 4}
 KERNEL_NAMES = {v: k for k, v in KERNELS.items()}
 LOOPS = {"auto": 0, "launches": 1, "persistent": 2}
-LOOP_NAMES = {v: k for k, v in LOOPS.items()}
+LOOP_NAMES = {0: "auto", 1: "launches", 2: "persistent", 3: "overlapped"}
 
 
 class LbmParams(ctypes.Structure):
@@ -275,7 +275,8 @@ class Lattice:
 
     @property
     def step_loop(self) -> str:
-        """The loop a multi-step call takes now ("launches" or "persistent")."""
+        """The loop a multi-step call takes now: "launches", "persistent" (a barrier between
+        steps) or "overlapped" (a persistent launch that overlaps consecutive steps)."""
         return LOOP_NAMES[int(self._L.lbm_step_loop(self._h))]
 
     def set_wait_limit(self, max_polls: int):

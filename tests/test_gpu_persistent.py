@@ -183,3 +183,83 @@ def test_tma_row_wait_timeout_is_reported_and_the_context_recovers():
     fresh.step(20)
     for a, b in zip(lat.populations(), fresh.populations()):
         assert np.array_equal(a, b)
+
+
+# The overlapped form: tilings with more tiles than the persistent launch's CTAs (608 of the
+# FP32 one-column kernel, 304 in FP64, on 152 SMs), 120-column strips of 4-row bands.
+OVERLAP_CASES = [("channel", 3000, 160), ("walls", 2600, 120), ("periodic", 2500, 124)]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("geometry,nx,ny", OVERLAP_CASES)
+def test_overlapped_loop_agrees_with_one_launch_per_step(precision, geometry, nx, ny):
+    """Tiles of consecutive steps in flight at once agree with one launch per step to rounding
+    (the buoyancy mean differs by the rounding of one collision), records included."""
+    L = lbm()
+    p, fields = channel(nx, ny, geometry=geometry)
+    steps = 120
+    per, n_per = run(L, nx, ny, p, fields, precision, "persistent", steps, (128, 4), calls=3)
+    assert per.step_loop == "overlapped"
+    ref, n_ref = run(L, nx, ny, p, fields, precision, "launches", steps, (128, 4))
+    assert n_per == 3 and n_ref == steps
+    assert per.step_count == ref.step_count == steps
+    tol = ROUNDING[precision]
+    for a, b in zip(per.populations(), ref.populations()):
+        assert np.abs(a - b).max() <= tol * np.abs(b).max()
+    rec_p, rec_r = per.diagnostics_range(0, steps), ref.diagnostics_range(0, steps)
+    assert np.array_equal(rec_p[:, 0], rec_r[:, 0])
+    for j in (1, 2, 3, 4, 5, 6, 7):
+        scale = max(np.abs(rec_r[:, j]).max(), 1e-300)
+        assert np.abs(rec_p[:, j] - rec_r[:, j]).max() <= 100 * tol * scale, j
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_overlapped_loop_matches_oracle(precision):
+    L = lbm()
+    nx, ny, steps = 3000, 100, 400
+    p, fields = channel(nx, ny)
+    lat = L.Lattice(nx, ny, precision)
+    lat.set_params(p)
+    lat.set_step_loop("persistent")
+    lat.set_tiling(128, 4)  # 625 tiles
+    lat.init_fields(*fields)
+    assert lat.step_loop == "overlapped"
+    for _ in range(4):
+        lat.step(steps // 4)
+    orc = oracle.Oracle(nx, ny, p, threads=8)
+    orc.init_fields(*fields)
+    assert orc.step(steps) == 0
+    got, ref = lat.fields(), orc.fields()
+    scale_u = max(np.abs(ref["ux"]).max(), np.abs(ref["uy"]).max())
+    for k in ("rho", "ux", "uy", "T"):
+        scale = scale_u if k in ("ux", "uy") else np.abs(ref[k]).max()
+        assert np.abs(got[k] - ref[k]).max() < TOL[precision] * scale, k
+    d, od = lat.diagnostics(), orc.last_diag()
+    for k in ("mass", "energy", "rho_avg", "dp", "flux_in", "flux_out"):
+        assert d[k] == pytest.approx(od[k], rel=TOL[precision], abs=TOL[precision] * 1e-3), k
+
+
+def test_overlapped_loop_timeout_is_reported_and_the_context_recovers():
+    """With the poll limit at one poll the first tile that has to wait gives up; the launch
+    ends without a fault, the call reports LBM_ETIMEOUT, and the context, initialised again,
+    reproduces a fresh overlapped run bit for bit (the overlapped loop is deterministic)."""
+    L = lbm()
+    nx, ny = 3000, 160
+    p, fields = channel(nx, ny)
+    lat = L.Lattice(nx, ny, "fp32")
+    lat.set_params(p)
+    lat.set_step_loop("persistent")
+    lat.set_tiling(128, 4)
+    lat.init_fields(*fields)
+    assert lat.step_loop == "overlapped"
+    lat.set_wait_limit(1)
+    with pytest.raises(L.LbmError) as err:
+        lat.step(20)
+    assert err.value.status == 4  # LBM_ETIMEOUT
+    lat.set_wait_limit(0)
+    lat.init_fields(*fields)
+    lat.step(30)
+    fresh, _ = run(L, nx, ny, p, fields, "fp32", "persistent", 30, (128, 4))
+    for a, b in zip(lat.populations(), fresh.populations()):
+        assert np.array_equal(a, b)
+    assert lat.diagnostics()["mass"] == fresh.diagnostics()["mass"]
