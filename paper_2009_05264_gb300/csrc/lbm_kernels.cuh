@@ -1653,8 +1653,9 @@ __device__ __forceinline__ void overlapped_steps(const Inst* __restrict__ insts,
           for (int x = xlo; ok && x <= xhi;) {
             const int xx = x < 0 ? x + nx : (x >= nx ? x - nx : x);
             const int j = xx / flow.tile_w;
-            ok = flow_wait<unsigned long long>(flow.cell_done + (long long)b * flow.strips + j, need, bar, max_polls,
-                                               polls, t0);
+            const long long cell = (long long)b * flow.strips + j;
+            if (idx_ok(st, cell, (long long)flow.nbands * flow.strips))
+              ok = flow_wait<unsigned long long>(flow.cell_done + cell, need, bar, max_polls, polls, t0);
             const int xend = (j + 1) * flow.tile_w;
             x += (xend < nx ? xend : nx) - xx;  // first column of the next strip
           }
@@ -1691,7 +1692,8 @@ __device__ __forceinline__ void overlapped_steps(const Inst* __restrict__ insts,
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();  // the tile's populations are written before its count
-      atomicAdd(flow.cell_done + (long long)flow_band(flow, tile.y0) * flow.strips + tile.x0 / flow.tile_w, 1ull);
+      const long long cell = (long long)flow_band(flow, tile.y0) * flow.strips + tile.x0 / flow.tile_w;
+      if (idx_ok(st, cell, (long long)flow.nbands * flow.strips)) atomicAdd(flow.cell_done + cell, 1ull);
     }
   }
 }

@@ -3,14 +3,14 @@
 In that build every global access of the kernels checks its element index against the buffer it
 addresses; an index outside it is skipped, counted and reported as LBM_EBOUNDS (nothing traps).
 A child process that loads the checked library runs each kernel form (interior path, general
-loop, paired columns, TMA staging, persistent loop), each geometry (channel, walls, periodic,
-pool), FP32 and FP64, thermal and isothermal, the Hazi-Markus source and the bubble counters
-(the full form), 64-column tiles, a batch of uneven members and the allocation-free step, on
-lattices whose tiles end raggedly (3 x 2, 6 x 5, 16 x 8, 33 x 17, 150 x 37, 257 x 37), then reads
-fields and populations back.  No access may be rejected, and the populations must equal the
-default build's to rounding (the two builds are compiled separately).  A probe compiled from the
-kernel header with the flag shows that the check itself rejects and counts an index outside its
-buffer without dereferencing it.
+loop, paired columns, TMA staging, the persistent loop with a barrier and overlapped), each
+geometry (channel, walls, periodic, pool), FP32 and FP64, thermal and isothermal, the
+Hazi-Markus source and the bubble counters (the full form), 64-column tiles, a batch of uneven
+members and the allocation-free step, on lattices whose tiles end raggedly (3 x 2 up to
+3000 x 160), then reads fields and populations back.  No access may be rejected, and the
+populations must equal the default build's to rounding (the two builds are compiled
+separately).  A probe compiled from the kernel header with the flag shows that the check itself
+rejects and counts an index outside its buffer without dereferencing it.
 """
 import ctypes
 import os
@@ -46,6 +46,8 @@ CASES = [
     ("channel_paired", "fp32", "channel", 150, 37, {}, "paired", "launches", None),
     ("channel_tma", "fp32", "channel", 257, 37, {}, "tma", "launches", (128, 0)),
     ("channel_persistent", "fp32", "channel", 150, 37, {}, "auto", "persistent", None),
+    ("channel_overlapped", "fp32", "channel", 3000, 160, {}, "auto", "persistent", (128, 4)),
+    ("walls_overlapped_fp64", "fp64", "walls", 2600, 121, {}, "auto", "persistent", (128, 4)),
     ("channel_hazi_markus", "fp32", "channel", 150, 37, {"source_model": 1}, "auto", "launches", None),
     ("channel_bubbles_fp64", "fp64", "channel", 150, 37, {"bubble_stats": 1}, "auto", "launches", None),
 ]
