@@ -240,7 +240,8 @@ def run_c2(steps: int = 2000, nx: int = 1000, ny: int = 100):
 
 def run_batch(steps: int, trial_steps: int = 4, n: int = 64, seed: int = SEED + 4):
     """64 seeded channels (Nx U{400..2000}, Ny U{50..200}, u_in U[0.01,0.05], superheat U[0.03,0.12] Tc,
-    rho_w U[2.2,4.0] i.e. contact angles of about 137 to 46 degrees), FP32: one batch (autotuned tiles, graph replay) against one at a time."""
+    rho_w U[2.2,4.0] i.e. contact angles of about 137 to 46 degrees), FP32: one batch (autotuned tiles, the
+    library's default loop) against one at a time."""
     import torch
 
     from paper_2009_05264_gb300 import inputs as I
@@ -259,6 +260,7 @@ def run_batch(steps: int, trial_steps: int = 4, n: int = 64, seed: int = SEED + 
     cols, rows = b.autotune(trial_steps=trial_steps)
     tune_s = time.perf_counter() - t0
     b.step(3)
+    loop = b.step_loop
     st = b.stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = b.launches
@@ -287,7 +289,7 @@ def run_batch(steps: int, trial_steps: int = 4, n: int = 64, seed: int = SEED + 
             "nodes": nodes, "steps": steps, "value": batched, "unit": "MLUPS", "ms_per_step": ms_b / steps,
             "sequential": {"value": seq, "unit": "MLUPS", "ms_per_step": ms_s / steps,
                            "how": "each lattice alone through lbm_step_async, one after another"},
-            "speedup_vs_sequential": batched / seq, "tiling": f"{cols}x{rows}", "autotune_s": tune_s,
+            "speedup_vs_sequential": batched / seq, "tiling": f"{cols}x{rows}", "loop": loop, "autotune_s": tune_s,
             "gpu_launches": launches, "launches_sequential": n * steps, "finite": bool(ok),
             "members_finite": sum(member_ok), "members": len(member_ok),
             "solves_per_hour_50k_steps": n * 3600.0 / (50000 * ms_b * 1e-3 / steps),

@@ -370,13 +370,18 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps);
  * status and its slot in *unstable_slot (-1 if none; may be NULL). */
 lbm_status lbm_batch_step_async(lbm_batch* b, int64_t nsteps);
 lbm_status lbm_batch_sync(lbm_batch* b, int32_t* unstable_slot);
-/* The step loop of the batch's multi-step calls (LBM_LOOP_* as lbm_set_step_loop: one
- * cooperative launch per call over every member's tiles with bounded grid barriers between
- * steps, or one launch per step replayed from CUDA graphs; LBM_LOOP_AUTO takes the graph-
- * replayed launches, measured faster for batches).  A barrier wait that gives up sets
- * LBM_ETIMEOUT on the members of the CTAs that gave up; lbm_batch_sync reports it. */
+/* The step loop of the batch's multi-step calls (LBM_LOOP_* as lbm_set_step_loop): one
+ * cooperative launch per call over every member's tiles, which overlaps consecutive steps
+ * (each member's tiles wait only for that member's neighbouring tiles, its step two back and
+ * its open-end balance) where every member is a channel, walls or periodic lattice and the
+ * tiling needs more CTAs than are resident, and otherwise meets at bounded grid barriers
+ * between steps; or one launch per step replayed from CUDA graphs.  LBM_LOOP_AUTO takes the
+ * overlapped launch from two and a half waves of tiles up and the graph-replayed launches
+ * below (measured faster for small served mixes).  A wait that gives up sets LBM_ETIMEOUT on
+ * the member whose tile gave up; lbm_batch_sync reports it. */
 lbm_status lbm_batch_set_step_loop(lbm_batch* b, int32_t loop);
-/* The loop a multi-step call takes now (LBM_LOOP_LAUNCHES or _PERSISTENT); -1 on error. */
+/* The loop a multi-step call takes now (LBM_LOOP_LAUNCHES, _PERSISTENT or _OVERLAPPED); -1 on
+ * error. */
 int32_t lbm_batch_step_loop(lbm_batch* b);
 /* As lbm_set_wait_limit, for the batch's persistent and TMA launches. */
 lbm_status lbm_batch_set_wait_limit(lbm_batch* b, int64_t max_polls);

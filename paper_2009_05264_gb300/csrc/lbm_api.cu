@@ -272,7 +272,7 @@ struct Layout {
   long long plane;
   size_t pop_bytes;  // one 9-plane buffer
   int max_tiles;
-  size_t off_f[2], off_g[2], off_rho_prev, off_tmaps, off_inst, off_state, off_sums, off_bar, off_cells, off_ring,
+  size_t off_f[2], off_g[2], off_rho_prev, off_tmaps, off_inst, off_state, off_sums, off_bar, off_cells, off_step0, off_ring,
       off_tiles_step, off_tiles_aux, total;
 };
 
@@ -295,6 +295,7 @@ Layout make_layout(int nx, int ny, lbm_precision prec) {
   L.off_sums = off; off += align_up(2 * NPART * sizeof(unsigned long long));  // two steps' totals
   L.off_bar = off; off += align_up(sizeof(GridBar));
   L.off_cells = off; off += align_up((size_t)L.max_tiles * sizeof(unsigned long long));  // overlapped loop
+  L.off_step0 = off; off += align_up(sizeof(long long));
   L.off_ring = off; off += align_up((size_t)RING * NDIAG * sizeof(double));
   L.off_tiles_step = off; off += align_up((size_t)L.max_tiles * sizeof(Tile));
   L.off_tiles_aux = off; off += align_up((size_t)L.max_tiles * sizeof(Tile));
@@ -400,7 +401,6 @@ struct lbm_ctx {
   int thermal = 0;
   long long launches = 0;
   long long step_host = 0;  // step count as last synchronised
-  long long step_next = 0;  // step of the next step launch (enqueued steps included)
   unsigned long long params_gen = 0;  // bumped whenever the descriptor changes
   int kernel = LBM_KERNEL_AUTO;        // requested step kernel form (resolve_kernel picks the one launched)
   int loop = LBM_LOOP_AUTO;            // requested step loop (one launch per step or persistent)
@@ -556,7 +556,6 @@ void reset_state_mirror(lbm_ctx* c, long long step, int local, double rho_avg_pr
   S.local_read = local;
   S.rho_avg[(step - 1) & 1] = rho_avg_prev;
   S.rho_avg[step & 1] = rho_avg_prev;
-  c->step_next = step;
 }
 
 lbm_status create_impl(lbm_ctx** out, int32_t nx, int32_t ny, lbm_precision prec, int32_t device, void* stream,
@@ -761,16 +760,19 @@ lbm_status lbm_step_async(lbm_ctx* c, int64_t nsteps) {
     GridBar* bar = reinterpret_cast<GridBar*>(c->base + c->L.off_bar);
     FlowPlan flow{};
     if (overlapped(c)) {
+      FlowInst& f = flow.single;
+      f.tile_w = tile_cols(c->cols);
+      f.strips = (c->nx + f.tile_w - 1) / f.tile_w;
+      f.nbands = c->ntiles_step / f.strips;
+      f.tall_rows = c->plan.tall_rows;
+      f.tall_count = c->plan.tall_count;
+      f.short_rows = c->plan.short_rows;
+      f.n_open = c->nopen_step;
+      f.perx = c->params.geometry != LBM_GEOM_CHANNEL;
+      f.pery = c->params.geometry == LBM_GEOM_PERIODIC;
       flow.enabled = 1;
-      flow.strips = (c->nx + tile_cols(c->cols) - 1) / tile_cols(c->cols);
-      flow.nbands = c->ntiles_step / flow.strips;
-      flow.tall_rows = c->plan.tall_rows;
-      flow.tall_count = c->plan.tall_count;
-      flow.short_rows = c->plan.short_rows;
-      flow.n_open = c->nopen_step;
-      flow.pery = c->params.geometry == LBM_GEOM_PERIODIC;
-      flow.tile_w = tile_cols(c->cols);
-      flow.perx = c->params.geometry != LBM_GEOM_CHANNEL;
+      flow.ninst = 1;
+      flow.step0 = reinterpret_cast<long long*>(c->base + c->L.off_step0);
       flow.cell_done = reinterpret_cast<unsigned long long*>(c->base + c->L.off_cells);
     }
     for (int64_t done = 0; done < nsteps;) {
@@ -779,7 +781,6 @@ lbm_status lbm_step_async(lbm_ctx* c, int64_t nsteps) {
       if (flow.enabled)
         LBM_CUDA(c, cudaMemsetAsync(flow.cell_done, 0, (size_t)c->ntiles_step * sizeof(unsigned long long),
                                     c->stream));
-      flow.step0 = c->step_next + done;
       cudaError_t e = launch_persistent(c->prec == LBM_FP64, c->thermal, c->cols, kernel, full, c->d_inst,
                                         c->d_tiles_step, c->ntiles_step, n, bar, c->max_polls, c->stream, &c->hinst,
                                         flow);
@@ -787,14 +788,12 @@ lbm_status lbm_step_async(lbm_ctx* c, int64_t nsteps) {
       ++c->launches;
       done += n;
     }
-    c->step_next += nsteps;
     return LBM_OK;
   }
   for (int64_t k = 0; k < nsteps; ++k) {
     lbm_status s = launch(c, MODE_STEP);
     if (s != LBM_OK) return s;
   }
-  c->step_next += nsteps;
   return LBM_OK;
 }
 
@@ -1016,7 +1015,6 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* host_buf, size_t bytes) {
                                 (size_t)c->ny, cudaMemcpyHostToDevice, c->stream));
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
   c->step_host = h.state.step;
-  c->step_next = h.state.step;
   return LBM_OK;
 }
 

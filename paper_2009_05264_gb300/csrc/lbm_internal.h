@@ -104,22 +104,31 @@ struct Inst {
 // barrier; gen: barriers completed; status: 1 once a CTA gave up waiting; next[2]: the
 // dynamic tile counters of even and odd steps.
 //
-// Overlapped form (FlowPlan.enabled, a parameter of the launch; one instance with more tiles than resident CTAs): the CTAs
-// draw (step, tile) tickets in order from `claim`, and a tile of step s waits only for what
-// it reads, instead of a barrier for the whole lattice: the tiles around it to have finished
-// step s - 1 (cell_done), step s - 2 to be complete (its mean density), and the
-// open-end tiles of step s - 1 to have posted the mass that crossed the inlet and outlet; its
-// buoyancy mean is the mean of step s - 2 plus that mass over the nodes (Eq. 14).  Tiles of
-// two consecutive steps run at once, so the end of one step overlaps the start of the next.
-struct FlowPlan {
-  int enabled;
+// Overlapped form (FlowPlan.enabled, a parameter of the launch; a lattice or a batch whose
+// tiling has more tiles than resident CTAs): the CTAs draw (step, tile) tickets in order from
+// `claim`, and a tile of step s waits only for what it reads, instead of a barrier for all the
+// tiles: the tiles of its instance around it to have finished step s - 1 (cell_done), step
+// s - 2 of its instance to be complete (its mean density), and the instance's open-end tiles
+// of step s - 1 to have posted the mass that crossed the inlet and outlet; its buoyancy mean is
+// the mean of step s - 2 plus that mass over the nodes (Eq. 14).  Tiles of two consecutive
+// steps run at once, so the end of one step overlaps the start of the next.
+struct FlowInst {  // one instance's tiling
   int strips, nbands, tile_w;             // tiles per band, bands per step, output columns per tile
   int tall_rows, tall_count, short_rows;  // band layout (row y -> band)
   int n_open;                             // tiles per step with an open end
   int perx, pery;                         // strips wrap in x (walls, periodic), bands in y (periodic)
-  long long step0;                        // step of the launch's first tickets
-  unsigned long long* cell_done;          // per tile position (band * strips + strip): steps of this
-                                          // launch it has finished (zeroed before the launch)
+  int pad;
+  long long cell_base;                    // the instance's first tile position in cell_done
+};
+struct FlowPlan {
+  int enabled;
+  int ninst;
+  FlowInst single;                 // the instance of a single-lattice launch (inst == nullptr)
+  const FlowInst* inst;            // a batch's table (device memory), indexed by Tile.inst
+  long long* step0;                // per instance: its step when the launch starts (written by the
+                                   // launch's first CTA before the tickets start)
+  unsigned long long* cell_done;   // per tile position (cell_base + band * strips + strip): steps
+                                   // of this launch it has finished (zeroed before the launch)
 };
 struct GridBar {
   unsigned int count, gen, status, pad;

@@ -1563,8 +1563,8 @@ __device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned nblocks, uns
   return *s_ok != 0;
 }
 
-// Band of row y in the overlapped form's tiling (tall bands first, then short ones).
-__device__ __forceinline__ int flow_band(const FlowPlan& f, int y) {
+// Band of row y in an instance's overlapped tiling (tall bands first, then short ones).
+__device__ __forceinline__ int flow_band(const FlowInst& f, int y) {
   const int ytall = f.tall_rows * f.tall_count;
   return y < ytall ? y / f.tall_rows : f.tall_count + (y - ytall) / f.short_rows;
 }
@@ -1583,13 +1583,16 @@ __device__ __forceinline__ bool flow_wait(const volatile T* p, T need, const Gri
   return true;
 }
 
-// The overlapped persistent loop (see FlowPlan): nsteps steps of one instance's tiles in
-// (step, tile) ticket order.  A ticket's tile waits, on thread 0 with bounded polls, for
-//  - the tiles holding rows y0 - 3 .. y1 + 2 and columns x0 - 3 .. x1 + 2 (what its pulls read,
-//    wrapped where the lattice is periodic) to have finished the previous step: the tiles it
-//    reads from and those that read what it overwrites;
-//  - the step two back to be complete (its diagnostics record and mean density written);
-//  - the open-end tiles of the previous step to have posted the mass through the open ends;
+// The overlapped persistent loop (see FlowPlan): nsteps steps of the launch's tiles in
+// (step, tile) ticket order.  The launch's first CTA records every instance's step count
+// before a grid barrier, so that the tickets of step k of the launch run step step0 + k of
+// their instance.  A ticket's tile waits, on thread 0 with bounded polls, for
+//  - the tiles of its instance holding rows y0 - 3 .. y1 + 2 and columns x0 - 3 .. x1 + 2
+//    (what its pulls read, wrapped where the lattice is periodic) to have finished the
+//    previous step: the tiles it reads from and those that read what it overwrites;
+//  - the instance's step two back to be complete (its diagnostics record and mean density);
+//  - the instance's open-end tiles of the previous step to have posted the mass through the
+//    open ends;
 // then runs with the buoyancy mean rho_avg(s - 2) + (mass through the open ends in s - 1) / N,
 // which is the previous step's mean up to the rounding of one collision, whatever the timing.
 // Tickets are drawn in order and a tile waits only for tickets drawn before it, all of them
@@ -1603,13 +1606,14 @@ __device__ __forceinline__ void overlapped_steps(const Inst* __restrict__ insts,
   __shared__ long long s_q;
   __shared__ int s_ok;
   __shared__ double s_rho;
-  const Inst& Ig = PCONST ? kp.I : insts[tiles[0].inst];
-  InstState* st = Ig.st;
-  // the state's "own populations" flag is that of the launch's first step until that step
-  // completes, and only tickets of the first step use it
-  const bool local0 = st->local_read != 0;
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < flow.ninst; i += B) flow.step0[i] = (PCONST ? kp.I.st : insts[i].st)->step;
+  }
+  if (!grid_barrier(bar, gridDim.x, max_polls, &s_ok)) {
+    if (threadIdx.x == 0) atomicOr(&(PCONST ? kp.I.st : insts[tiles[0].inst].st)->status, STATUS_TIMEOUT);
+    return;
+  }
   const long long total = (long long)nsteps * ntiles;
-  const double inv_n = 1.0 / ((double)Ig.nx * (double)Ig.ny);
   for (;;) {
     if (threadIdx.x == 0) s_q = (long long)atomicAdd(&bar->claim, 1ull);
     __syncthreads();
@@ -1617,7 +1621,10 @@ __device__ __forceinline__ void overlapped_steps(const Inst* __restrict__ insts,
     if (q >= total) return;
     const int k = (int)(q / ntiles);
     const Tile tile = tiles[q - (long long)k * ntiles];
-    const long long step = flow.step0 + k;
+    const Inst& Ii = PCONST ? kp.I : insts[tile.inst];
+    const FlowInst& fi = flow.inst ? flow.inst[tile.inst] : flow.single;
+    InstState* st = Ii.st;
+    const long long step = flow.step0[tile.inst] + k;
     if (threadIdx.x == 0) {
       bool ok = true;
       double rho = 0.0;
@@ -1627,51 +1634,52 @@ __device__ __forceinline__ void overlapped_steps(const Inst* __restrict__ insts,
         unsigned polls = 0;
         const unsigned long long t0 = global_ns();
         const unsigned long long need = (unsigned long long)k;  // steps each neighbour has finished
-        const int ny = Ig.ny, nx = Ig.nx;
+        const int ny = Ii.ny, nx = Ii.nx;
+        const long long ncells = (long long)fi.nbands * fi.strips;
         // the rows and columns this tile's pulls read: its own, 3 rows and 3 columns around
         int ylo = tile.y0 - 3, yhi = tile.y1 + 2;
-        if (!flow.pery) {
+        if (!fi.pery) {
           ylo = ylo < 0 ? 0 : ylo;
           yhi = yhi > ny - 1 ? ny - 1 : yhi;
         } else if (yhi - ylo + 1 >= ny) {
           ylo = 0;
           yhi = ny - 1;
         }
-        const int x1 = tile.x0 + flow.tile_w < nx ? tile.x0 + flow.tile_w : nx;
+        const int x1 = tile.x0 + fi.tile_w < nx ? tile.x0 + fi.tile_w : nx;
         int xlo = tile.x0 - 3, xhi = x1 + 2;
-        if (!flow.perx) {
+        if (!fi.perx) {
           xlo = xlo < 0 ? 0 : xlo;
           xhi = xhi > nx - 1 ? nx - 1 : xhi;
         } else if (xhi - xlo + 1 >= nx) {
           xlo = 0;
           xhi = nx - 1;
         }
-        const int ytall = flow.tall_rows * flow.tall_count;
+        const int ytall = fi.tall_rows * fi.tall_count;
         for (int y = ylo; ok && y <= yhi;) {
           const int yy = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-          const int b = flow_band(flow, yy);
+          const int b = flow_band(fi, yy);
           for (int x = xlo; ok && x <= xhi;) {
             const int xx = x < 0 ? x + nx : (x >= nx ? x - nx : x);
-            const int j = xx / flow.tile_w;
-            const long long cell = (long long)b * flow.strips + j;
-            if (idx_ok(st, cell, (long long)flow.nbands * flow.strips))
-              ok = flow_wait<unsigned long long>(flow.cell_done + cell, need, bar, max_polls, polls, t0);
-            const int xend = (j + 1) * flow.tile_w;
+            const int j = xx / fi.tile_w;
+            const long long cell = (long long)b * fi.strips + j;
+            if (idx_ok(st, cell, ncells))
+              ok = flow_wait<unsigned long long>(flow.cell_done + fi.cell_base + cell, need, bar, max_polls, polls,
+                                                 t0);
+            const int xend = (j + 1) * fi.tile_w;
             x += (xend < nx ? xend : nx) - xx;  // first column of the next strip
           }
-          const int bend = b < flow.tall_count ? (b + 1) * flow.tall_rows
-                                               : ytall + (b - flow.tall_count + 1) * flow.short_rows;
+          const int bend = b < fi.tall_count ? (b + 1) * fi.tall_rows
+                                             : ytall + (b - fi.tall_count + 1) * fi.short_rows;
           y += (bend < ny ? bend : ny) - yy;  // first row of the next band
         }
         if (ok) ok = flow_wait<long long>(&st->step, step - 1, bar, max_polls, polls, t0);
-        if (ok && flow.n_open > 0)
-          ok = flow_wait<unsigned>(&st->open_posted[(step - 1) & 3], (unsigned)flow.n_open, bar, max_polls, polls,
-                                   t0);
+        if (ok && fi.n_open > 0)
+          ok = flow_wait<unsigned>(&st->open_posted[(step - 1) & 3], (unsigned)fi.n_open, bar, max_polls, polls, t0);
         __threadfence();  // what the awaited tiles wrote is visible after their counts
         if (ok) {
           const long long m = *reinterpret_cast<const volatile long long*>(&st->open_mass[(step - 1) & 3]);
           rho = *reinterpret_cast<const volatile double*>(&st->rho_avg[(step - 2) & 1]) +
-                (double)m * Ig.fix_unscale[3] * inv_n;
+                (double)m * Ii.fix_unscale[3] / ((double)Ii.nx * (double)Ii.ny);
         }
       }
       if (!ok) {
@@ -1685,15 +1693,17 @@ __device__ __forceinline__ void overlapped_steps(const Inst* __restrict__ insts,
     if (!s_ok) return;
     TileStep ts;
     ts.step = step;
-    ts.local = k == 0 && local0;
+    // a first step reads the populations in place; the flag stays set until that step of the
+    // instance completes, which needs this tile
+    ts.local = k == 0 && st->local_read != 0;
     ts.post_open = true;
     ts.rho_avg_prev = s_rho;
     fused_tile<Real, THERMAL, B, MODE_STEP, FULL, PCONST, INTERIOR>(insts, tile, kp, dyn_smem, sh, ts);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();  // the tile's populations are written before its count
-      const long long cell = (long long)flow_band(flow, tile.y0) * flow.strips + tile.x0 / flow.tile_w;
-      if (idx_ok(st, cell, (long long)flow.nbands * flow.strips)) atomicAdd(flow.cell_done + cell, 1ull);
+      const long long cell = (long long)flow_band(fi, tile.y0) * fi.strips + tile.x0 / fi.tile_w;
+      if (idx_ok(st, cell, (long long)fi.nbands * fi.strips)) atomicAdd(flow.cell_done + fi.cell_base + cell, 1ull);
     }
   }
 }

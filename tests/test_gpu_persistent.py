@@ -263,3 +263,51 @@ def test_overlapped_loop_timeout_is_reported_and_the_context_recovers():
     for a, b in zip(lat.populations(), fresh.populations()):
         assert np.array_equal(a, b)
     assert lat.diagnostics()["mass"] == fresh.diagnostics()["mass"]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_overlapped_batch_agrees_with_launches_and_the_oracle(precision):
+    """A batch whose tiling needs several waves of CTAs (three channels and a walls lattice of
+    uneven size, 120-column strips of 4-row bands) advanced by overlapped persistent launches
+    agrees member by member with graph-replayed launches to rounding, and its first member with
+    the oracle at the parity tolerance; members keep their own step counts."""
+    L = lbm()
+    sizes = [(2000, 160, "channel"), (1500, 120, "channel"), (1800, 90, "walls"), (1300, 140, "channel")]
+    steps = 90
+    runs = {}
+    for loop in ("persistent", "launches"):
+        b = L.Batch(precision, thermal=True)
+        b.set_step_loop(loop)
+        b.set_tiling(128, 4)
+        members, cases = [], []
+        for k, (nx, ny, geo) in enumerate(sizes):
+            p, fields = channel(nx, ny, geometry=geo, u_in=0.01 + 0.005 * k)
+            m = b.add(nx, ny, p)
+            m.init_fields(*fields)
+            members.append(m)
+            cases.append((p, fields))
+        if loop == "persistent":
+            assert b.step_loop == "overlapped"
+        for _ in range(3):
+            b.step(steps // 3)
+        runs[loop] = [(m.populations(), m.diagnostics_range(0, steps)) for m in members]
+        assert all(m.step_count == steps for m in members)
+        if loop == "persistent":
+            nx, ny, _ = sizes[0]
+            orc = oracle.Oracle(nx, ny, cases[0][0], threads=8)
+            orc.init_fields(*cases[0][1])
+            assert orc.step(steps) == 0
+            got, ref = members[0].fields(), orc.fields()
+            scale_u = max(np.abs(ref["ux"]).max(), np.abs(ref["uy"]).max())
+            for key in ("rho", "ux", "uy", "T"):
+                scale = scale_u if key in ("ux", "uy") else np.abs(ref[key]).max()
+                assert np.abs(got[key] - ref[key]).max() < TOL[precision] * scale, key
+        b.close()
+    tol = ROUNDING[precision]
+    for ((fp, gp), rp), ((fr, gr), rr) in zip(runs["persistent"], runs["launches"]):
+        assert np.abs(fp - fr).max() <= tol * np.abs(fr).max()
+        assert np.abs(gp - gr).max() <= tol * np.abs(gr).max()
+        assert np.array_equal(rp[:, 0], rr[:, 0])
+        for j in (1, 2, 3, 6, 7):
+            scale = max(np.abs(rr[:, j]).max(), 1e-300)
+            assert np.abs(rp[:, j] - rr[:, j]).max() <= 100 * tol * scale, j
