@@ -827,15 +827,17 @@ __device__ __forceinline__ void finish_step(const Inst& I, InstState* st, const 
 // run, or a NaN) marks the instance unstable.  Every tile of a launch must post exactly once.
 // open: the tile also posts open_acc, its share of the mass that this step's pull took in and
 // let out through the channel's open ends (the overlapped persistent loop derives the next
-// step's buoyancy mean from it); the fixed-point grid is the inflow total's.
-template <int BLOCK, bool THERMAL, int MODE>
+// step's buoyancy mean from it); the fixed-point grid is the inflow total's.  NA: the partials
+// the tile can have nonzero (the first NA of acc; an interior tile has mass, energy and the
+// heater row only); a total that a tile leaves at zero takes no atomic.
+template <int BLOCK, bool THERMAL, int MODE, int NA = NPART>
 __device__ __forceinline__ void post_partials(const Inst& I, InstState* st, const Tile& tile, const double (&acc)[NPART],
                                               double (*red)[NPART], int* flag, long long step, bool open = false,
                                               double open_acc = 0.0) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned long long* const sums = I.sums + (step & 1) * NPART;
 #pragma unroll
-  for (int j = 0; j < NPART; ++j) {
+  for (int j = 0; j < NA; ++j) {
     double x = acc[j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
@@ -861,14 +863,14 @@ __device__ __forceinline__ void post_partials(const Inst& I, InstState* st, cons
     }
   }
   __syncthreads();
-  if (tid < NPART) {
+  if (tid < NA) {
     double sum = 0.0;
     for (int w = 0; w < BLOCK / 32; ++w) sum += red[w][tid];
     const double x = sum * I.fix_scale[tid];  // a power of two: exact
     long long q = 0;
     if (fabs(x) < 0x1p62) q = __double2ll_rn(x);
     else atomicOr(&st->status, STATUS_UNSTABLE);
-    atomicAdd(sums + tid, (unsigned long long)q);
+    if (q != 0) atomicAdd(sums + tid, (unsigned long long)q);
   }
   __syncthreads();
   if (tid == 0) {
@@ -1228,7 +1230,7 @@ __device__ __forceinline__ void fused_tile(const Inst* __restrict__ insts, const
     interior_rows<Real, THERMAL, B>(I, sC, sRra, tile, step, local, dyn_smem, am, ae, ah, bad_any);
     if (bad_any) atomicOr(&st->status, STATUS_UNSTABLE);
     const double acc[NPART] = {(double)am, (double)ae, (double)ah, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    post_partials<BLOCK, THERMAL, MODE>(I, st, tile, acc, sRed, &sLast, step);
+    post_partials<BLOCK, THERMAL, MODE, 3>(I, st, tile, acc, sRed, &sLast, step);
     return;
   }
   const bool perx = I.geometry != GEOM_CHANNEL;
