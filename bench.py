@@ -200,6 +200,33 @@ def fp64_peak_tflops():
         return FP64_NOMINAL_TFLOPS, f"nominal GB300 FP64 (non-tensor) rate; probe failed: {exc!r}"
 
 
+def fp32_alu_roofline(kernel: str, nodes: int, step_s: float) -> dict | None:
+    """FP32 arithmetic of the FP32 step against the FP32 rate this GPU sustains: the step's FP32
+    thread-instructions per node (ncu, committed summary) per second over the probed FFMA rate
+    (independent FFMA chains, one instruction per issue slot); None without a current figure."""
+    import re
+
+    if kernel not in PROFILES:
+        return None
+    path = os.path.join(ROOT, PROFILES[kernel])
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"fp32-inst-per-node:\s*([0-9.]+)\s*\(source digest ([0-9a-f]+)", open(path).read())
+    if not m or m.group(2) != step_source_digest(kernel):
+        return None
+    try:
+        from paper_2009_05264_gb300 import lbm
+
+        ffma = max(lbm.probe_fma_rate("fp32", 1 << 16) for _ in range(3)) / 2.0  # FFMA per second
+    except Exception as exc:  # reporting only
+        return {"unavailable": repr(exc)}
+    ipn = float(m.group(1))
+    achieved = ipn * nodes / step_s
+    return {"achieved": achieved / 1e12, "peak": ffma / 1e12, "unit": "T FP32 thread-instructions/s",
+            "frac": achieved / ffma, "inst_per_node": ipn,
+            "peak_source": "measured: FP32 FMA probe (independent FFMA chains, best of 3, CUDA events)"}
+
+
 def run_c2(steps: int = 2000, nx: int = 1000, ny: int = 100):
     """The 1000 x 100 channel (heater of 40 nodes at nx/5, u_in = 0.03, superheat 0.08 Tc, as the
     large channel) in FP32 and FP64: MLUPS of each.  Its state (14-29 MB) stays in L2, so no HBM
@@ -653,6 +680,10 @@ def run_ours(args):
             "gpu_launches": gpu_launches,
             "clocks": clocks,
         }
+        if prec == "fp32":  # FP32 arithmetic is far from its rate: reported to show it is not the bound
+            alu = fp32_alu_roofline(step_kernel, nodes, step_ms * 1e-3)
+            if alu:
+                line["roofline"]["alu"] = alu
         ipn = profiled_inst_per_node(step_kernel) if prec == "fp32" else None
         if ipn and clocks and clocks.get("sm_mhz"):  # the step is issue-bound: its fraction of the issue peak
             try:
