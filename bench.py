@@ -667,6 +667,7 @@ def run_ours(args):
                        "parallelism": f"{world} independent channel replicas"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": tpn * nodes if tpn else None,
+                         "traffic_per": "step (the timed launch runs all timed steps; achieved is per step too)",
                          "traffic_source": tsrc,
                          "peak_source": f"{peak_kind} HBM copy bandwidth",
                          "algorithmic_bytes_per_node": bpn,
